@@ -1,0 +1,160 @@
+/*
+ * igamg — multigrid-preconditioned CG for multi-patch isogeometric Poisson problems on
+ * one GB300 (sm_103a).  C ABI.
+ *
+ * Method (Hofer & Takacs, "A parallel multigrid solver for multi-patch Isogeometric
+ * Analysis"): the Poisson model problem of Sec. 2 (-Laplace u = f, u = 0 on Gamma_D,
+ * du/dn = 0 on Gamma_N) discretised by a fully matching multi-patch spline space V_l
+ * (Eq. vh), grid levels l = 0..L by uniform refinement (Sec. 3), the cycle of
+ * Algorithm 1 with the additive Schwarz smoother of Eq. additive, an exact coarsest solve,
+ * used as the preconditioner of PCG (Sec. 4, Sec. 5).
+ *
+ * Conventions shared by every entry point
+ *  - All calls return an igamg_status and never abort or throw.  After an error the
+ *    context stays valid for igamg_free() and igamg_last_error().
+ *  - Device vectors are FP64, length N_l (igamg_num_dofs), in the library's global dof
+ *    numbering of level l (igamg_dof_map).  They are caller-owned device memory; every
+ *    call runs on the stream given to igamg_setup and returns without synchronising it
+ *    unless stated.  Level index l: 0 = coarsest, L = num_levels-1 = finest; -1 = finest.
+ *  - Host arrays passed to igamg_setup are read during the call only.
+ *  - The context owns the grid hierarchy (band coefficients, smoother bases, transfer
+ *    tables, coarse factor) and its device workspaces; only igamg_free releases them.
+ */
+#ifndef IGAMG_H
+#define IGAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IGAMG_OK = 0,
+  IGAMG_ERR_ARG = 1,          /* NULL pointer, bad size, bad level, bad enum          */
+  IGAMG_ERR_GEOMETRY = 2,     /* non-matching patches, tagged interface, bad vertices */
+  IGAMG_ERR_UNSUPPORTED = 3,  /* non-uniform knots, geometry degree != 1, ...         */
+  IGAMG_ERR_OOM = 4,          /* device allocation failed                              */
+  IGAMG_ERR_CUDA = 5,         /* a CUDA runtime call failed                           */
+  IGAMG_ERR_NUMERIC = 6,      /* NaN/Inf in PCG scalars, Cholesky/eigen breakdown      */
+  IGAMG_ERR_NOT_CONVERGED = 7,/* max_iter reached; x and res->relres are filled        */
+  IGAMG_ERR_TIMEOUT = 8
+} igamg_status;
+
+/* Side tags (Sec. 2: Gamma_D / Gamma_N).  Side s of a patch is parameter direction s/2 at
+ * end s%2, order -x,+x,-y,+y,-z,+z.  AUTO: interface when another patch has the same side
+ * (same corner vertices), otherwise Dirichlet.  An interface side must be tagged AUTO. */
+enum { IGAMG_SIDE_AUTO = 0, IGAMG_SIDE_DIRICHLET = 1, IGAMG_SIDE_NEUMANN = 2 };
+
+enum { IGAMG_FP64 = 0, IGAMG_FP32 = 1, IGAMG_BF16 = 2 };
+
+/* Multi-patch problem (Sec. 2, Eq. matching).  Patch k has, per direction j, a spline
+ * degree degree[k*dim+j] and an open uniform knot vector at the finest level (num_knots
+ * entries, concatenated over k and j in that order in `knots`).  The geometry map G_k is
+ * multilinear: geo_degree = 1 and geo_num_ctrl = 2 in every direction, and geo_ctrl holds,
+ * per patch, its 2^dim corner points (dim coordinates each), corner c = sum_j c_j 2^j with
+ * c_j the end of direction j.  Patches must be fully matching (common sides have the same
+ * corners and the same knot vectors).  Level 0 has m_L / 2^L intervals per direction. */
+typedef struct {
+  int dim;                 /* 2 or 3                                          */
+  int num_patches;         /* K >= 1                                          */
+  const int* degree;       /* [K*dim]   p >= 1                                 */
+  const int* num_knots;    /* [K*dim]                                          */
+  const double* knots;     /* sum(num_knots) values                            */
+  const int* geo_degree;   /* [K*dim]   must be 1                              */
+  const int* geo_num_ctrl; /* [K*dim]   must be 2                              */
+  const double* geo_ctrl;  /* [K * 2^dim * dim]                                */
+  const int* side_bc;      /* [K*2*dim] IGAMG_SIDE_*                           */
+  int num_levels;          /* L+1 >= 1                                         */
+} igamg_problem;
+
+/* Solver parameters; defaults are the paper's (Sec. 5): tau = 0.25, sigma = h^{-2}/0.2,
+ * one pre- and one post-smoothing step, V-cycle. */
+typedef struct {
+  double tau;          /* smoother damping (Eq. sm)                                 */
+  double sigma_scale;  /* sigma = sigma_scale * h_l^{-2} in the interior smoother      */
+  int nu;              /* smoothing steps before and after the coarse correction       */
+  int mu;              /* 1 = V-cycle, 2 = W-cycle (Algorithm 1)                      */
+  int max_iter;        /* PCG iteration limit                                        */
+  int precision;       /* IGAMG_FP64 (only FP64 is accepted by this version)          */
+} igamg_options;
+
+typedef struct {
+  int iters;           /* PCG iterations performed                                    */
+  double relres;       /* ||b - A x||_2 / ||b - A x_0||_2 at exit                      */
+  double t_setup_ms;   /* igamg_setup wall time (host + device, synchronised)          */
+  double t_assemble_ms;/* part of setup spent assembling the level matrices           */
+  double t_solve_ms;   /* this solve, device-synchronised wall time                    */
+} igamg_result;
+
+typedef struct igamg_ctx igamg_ctx;
+
+/* Fills *opt with the defaults above (max_iter = 500, precision FP64). */
+igamg_status igamg_default_options(igamg_options* opt);
+
+/* Sec. 5 setup phase (dof mappers, refinement and transfers, piece-local smoothers,
+ * coarse solver) plus the assembly of every level's patch matrices (Eq. model:bil) on
+ * the device.  `opt` may be NULL (defaults).  `cuda_stream` is a cudaStream_t or NULL
+ * for the legacy default stream; the context issues all its work there.  Uses the
+ * current CUDA device.  On success *out owns a new context; on failure *out is NULL. */
+igamg_status igamg_setup(const igamg_problem* problem, const igamg_options* opt,
+                         void* cuda_stream, igamg_ctx** out);
+
+/* Number of active (non-Dirichlet) dofs N_l of level l (-1 = finest). */
+igamg_status igamg_num_dofs(const igamg_ctx* ctx, int level, int64_t* n);
+
+/* Total number of patch-local basis functions sum_k prod_j n_kj at level l. */
+igamg_status igamg_num_local(const igamg_ctx* ctx, int level, int64_t* n);
+
+/* Host array local_to_global[sum_k prod_j n_kj]: for patch k (in order) and its local
+ * tensor index (C order, last direction fastest) the global dof id, -1 if eliminated by a
+ * Dirichlet side (Sec. 2 dof mapper). */
+igamg_status igamg_dof_map(const igamg_ctx* ctx, int level, int64_t* local_to_global);
+
+/* Load vector b_i = (f_h, phi_i)_{L2(Omega)} of the source f_h = sum_j c_j phi_j given by
+ * its spline coefficients c on the active dofs of the finest level (Sec. 2 right-hand side
+ * (f, v)), by Gauss quadrature with the geometry.  Both device vectors of length N_L. */
+igamg_status igamg_rhs_from_coefs(igamg_ctx* ctx, const double* coef_dev, double* rhs_dev);
+
+/* PCG with one multigrid cycle (Algorithm 1) per iteration as preconditioner (Sec. 4),
+ * started from x_dev (in: x_0, out: x), stopped when ||b - A x||_2 <= tol ||b - A x_0||_2
+ * or after max_iter iterations (tol = 0 runs exactly max_iter).  Synchronises the stream.
+ * `res` may be NULL. */
+igamg_status igamg_solve(igamg_ctx* ctx, const double* rhs_dev, double* x_dev, double tol,
+                         igamg_result* res);
+
+/* igamg_solve with HOST vectors: copies rhs and x_0 to the device, solves, copies x back
+ * (the end-to-end call).  Synchronises. */
+igamg_status igamg_solve_host(igamg_ctx* ctx, const double* rhs_host, double* x_host,
+                              double tol, igamg_result* res);
+
+/* Single steps of the cycle, for per-step checks and measurement.  Device vectors in the
+ * global numbering of the level named.
+ *   igamg_apply:        y = A_l x                                  (Eq. linear:system)
+ *   igamg_smooth:       z = L_l^{-1} r, l >= 1                      (Eq. additive)
+ *   igamg_restrict:     rc = P_l^T r,  r on level l, rc on l-1, l >= 1  (Sec. 3)
+ *   igamg_prolong:      u = P_l uc,    uc on level l-1, u on l, l >= 1  (Sec. 3)
+ *   igamg_coarse_solve: x = A_0^{-1} r                             (Sec. 4, exact solve)
+ *   igamg_precondition: z = Multigrid(L, 0, r)                      (Algorithm 1) */
+igamg_status igamg_apply(igamg_ctx* ctx, int level, const double* x_dev, double* y_dev);
+igamg_status igamg_smooth(igamg_ctx* ctx, int level, const double* r_dev, double* z_dev);
+igamg_status igamg_restrict(igamg_ctx* ctx, int level, const double* r_dev, double* rc_dev);
+igamg_status igamg_prolong(igamg_ctx* ctx, int level, const double* uc_dev, double* u_dev);
+igamg_status igamg_coarse_solve(igamg_ctx* ctx, const double* r_dev, double* x_dev);
+igamg_status igamg_precondition(igamg_ctx* ctx, const double* r_dev, double* z_dev);
+
+/* Synchronises the context's stream. */
+igamg_status igamg_sync(igamg_ctx* ctx);
+
+/* Releases everything the context owns.  NULL-safe. */
+igamg_status igamg_free(igamg_ctx* ctx);
+
+/* Message of the last error on this context (or of the last failed setup when ctx is
+ * NULL).  Never NULL; valid until the next call on the same context. */
+const char* igamg_last_error(const igamg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGAMG_H */

@@ -1,0 +1,203 @@
+"""ctypes binding of libigamg (include/igamg.h): same entry-point names, argument
+marshalling only.  Device vectors are torch CUDA tensors (FP64, contiguous); the
+library runs everything on the stream passed to igamg_setup.  There is no fallback: if
+the shared library is missing the import of this module raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libigamg.so")
+
+IGAMG_OK, IGAMG_ERR_NOT_CONVERGED = 0, 7
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_GEOMETRY", 3: "ERR_UNSUPPORTED", 4: "ERR_OOM",
+          5: "ERR_CUDA", 6: "ERR_NUMERIC", 7: "ERR_NOT_CONVERGED", 8: "ERR_TIMEOUT"}
+
+
+class igamg_problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("num_patches", C.c_int),
+                ("degree", C.POINTER(C.c_int)), ("num_knots", C.POINTER(C.c_int)),
+                ("knots", C.POINTER(C.c_double)), ("geo_degree", C.POINTER(C.c_int)),
+                ("geo_num_ctrl", C.POINTER(C.c_int)), ("geo_ctrl", C.POINTER(C.c_double)),
+                ("side_bc", C.POINTER(C.c_int)), ("num_levels", C.c_int)]
+
+
+class igamg_options(C.Structure):
+    _fields_ = [("tau", C.c_double), ("sigma_scale", C.c_double), ("nu", C.c_int),
+                ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int)]
+
+
+class igamg_result(C.Structure):
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("t_setup_ms", C.c_double),
+                ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double)]
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libigamg.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "igamg_default_options": ([C.POINTER(igamg_options)], C.c_int),
+        "igamg_setup": ([C.POINTER(igamg_problem), C.POINTER(igamg_options), P, C.POINTER(P)], C.c_int),
+        "igamg_num_dofs": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+        "igamg_num_local": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+        "igamg_dof_map": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+        "igamg_rhs_from_coefs": ([P, P, P], C.c_int),
+        "igamg_solve": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
+        "igamg_solve_host": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
+        "igamg_apply": ([P, C.c_int, P, P], C.c_int),
+        "igamg_smooth": ([P, C.c_int, P, P], C.c_int),
+        "igamg_restrict": ([P, C.c_int, P, P], C.c_int),
+        "igamg_prolong": ([P, C.c_int, P, P], C.c_int),
+        "igamg_coarse_solve": ([P, P, P], C.c_int),
+        "igamg_precondition": ([P, P, P], C.c_int),
+        "igamg_sync": ([P], C.c_int),
+        "igamg_free": ([P], C.c_int),
+        "igamg_last_error": ([P], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class IgamgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous(), "need a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Problem:
+    """igamg_problem built from any object with dim, degree (K,d), knots[k][j],
+    corners (K, 2^d, d), side_bc (K, 2d) and num_levels; keeps the arrays alive."""
+
+    def __init__(self, pr):
+        K, d = np.asarray(pr.degree).shape
+        self._deg = np.ascontiguousarray(np.asarray(pr.degree).ravel(), dtype=np.int32)
+        kn = [np.asarray(pr.knots[k][j], dtype=np.float64) for k in range(K) for j in range(d)]
+        self._nk = np.array([len(t) for t in kn], dtype=np.int32)
+        self._kn = np.ascontiguousarray(np.concatenate(kn))
+        self._gd = np.ones(K * d, dtype=np.int32)
+        self._gn = np.full(K * d, 2, dtype=np.int32)
+        self._ctrl = np.ascontiguousarray(np.asarray(pr.corners, dtype=np.float64).ravel())
+        self._bc = np.ascontiguousarray(np.asarray(pr.side_bc).ravel(), dtype=np.int32)
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        self.struct = igamg_problem(d, K, ip(self._deg), ip(self._nk), dp(self._kn), ip(self._gd),
+                                    ip(self._gn), dp(self._ctrl), ip(self._bc), int(pr.num_levels))
+
+
+def igamg_default_options() -> igamg_options:
+    o = igamg_options()
+    lib().igamg_default_options(C.byref(o))
+    return o
+
+
+class Context:
+    """Owns one igamg_ctx.  Methods are the ABI entry points without the igamg_ prefix."""
+
+    def __init__(self, problem, options: igamg_options | None = None, stream=None):
+        import torch
+        self.problem = Problem(problem)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().igamg_setup(C.byref(self.problem.struct), C.byref(options) if options else None,
+                               C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != IGAMG_OK:
+            raise IgamgError(st, lib().igamg_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st, allow_nc=False):
+        if st == IGAMG_OK or (allow_nc and st == IGAMG_ERR_NOT_CONVERGED):
+            return st
+        raise IgamgError(st, lib().igamg_last_error(self.h).decode())
+
+    def num_dofs(self, level=-1) -> int:
+        n = C.c_int64()
+        self._check(lib().igamg_num_dofs(self.h, level, C.byref(n)))
+        return n.value
+
+    def num_local(self, level=-1) -> int:
+        n = C.c_int64()
+        self._check(lib().igamg_num_local(self.h, level, C.byref(n)))
+        return n.value
+
+    def dof_map(self, level=-1) -> np.ndarray:
+        out = np.empty(self.num_local(level), dtype=np.int64)
+        self._check(lib().igamg_dof_map(self.h, level, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def rhs_from_coefs(self, coef, rhs):
+        self._check(lib().igamg_rhs_from_coefs(self.h, _ptr(coef), _ptr(rhs)))
+
+    def solve(self, rhs, x, tol=1e-8):
+        res = igamg_result()
+        st = self._check(lib().igamg_solve(self.h, _ptr(rhs), _ptr(x), tol, C.byref(res)), allow_nc=True)
+        return res, st
+
+    def solve_host(self, rhs: np.ndarray, x: np.ndarray, tol=1e-8):
+        res = igamg_result()
+        st = self._check(lib().igamg_solve_host(self.h, _host_ptr(rhs), _host_ptr(x), tol, C.byref(res)),
+                         allow_nc=True)
+        return res, st
+
+    def apply(self, level, x, y):
+        self._check(lib().igamg_apply(self.h, level, _ptr(x), _ptr(y)))
+
+    def smooth(self, level, r, z):
+        self._check(lib().igamg_smooth(self.h, level, _ptr(r), _ptr(z)))
+
+    def restrict(self, level, r, rc):
+        self._check(lib().igamg_restrict(self.h, level, _ptr(r), _ptr(rc)))
+
+    def prolong(self, level, uc, u):
+        self._check(lib().igamg_prolong(self.h, level, _ptr(uc), _ptr(u)))
+
+    def coarse_solve(self, r, x):
+        self._check(lib().igamg_coarse_solve(self.h, _ptr(r), _ptr(x)))
+
+    def precondition(self, r, z):
+        self._check(lib().igamg_precondition(self.h, _ptr(r), _ptr(z)))
+
+    def sync(self):
+        self._check(lib().igamg_sync(self.h))
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().igamg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

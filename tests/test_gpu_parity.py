@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step:
+stiffness apply, smoother, restriction, prolongation, coarse solve, one multigrid cycle,
+and PCG (same iterates after k iterations, iteration counts within +-1, tight solves).
+
+Tolerances (FP64, different summation orders): apply 1e-13, smoother and transfers 1e-12,
+one cycle 1e-11, PCG iterates 1e-10 (relative, 2-norm)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import multipatch, solver
+from tests.helpers import permutation, rel, to_lib, from_lib
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def cases():
+    return {
+        "square_p2_m8": lambda: workloads.unit_square_quadrants(8, 2, 4),
+        "grid3x3_p3_m16": lambda: workloads.perturbed_grid_2d(3, 3, 16, 5, 31),
+        "grid4x4_p4_m16": lambda: workloads.perturbed_grid_2d(4, 4, 16, 5, 2),
+        "grid2x2_p5_m32_ragged": lambda: workloads.perturbed_grid_2d(2, 5, 32, 4, 7),
+        "single_patch_p2_m64": lambda: workloads.perturbed_grid_2d(1, 2, 64, 7, 3),
+        "grid2x2_p1_m8": lambda: workloads.perturbed_grid_2d(2, 1, 8, 4, 5),
+    }
+
+
+_CACHE = {}
+
+
+def setup_case(name):
+    if name not in _CACHE:
+        from paper_1804_02539_gb300 import igamg
+        pr = cases()[name]()
+        H = solver.build_hierarchy(pr)
+        ctx = igamg.Context(pr)
+        perms = [permutation(H.levels[l].space, ctx.dof_map(l)) for l in range(pr.num_levels)]
+        _CACHE[name] = (pr, H, ctx, perms)
+    return _CACHE[name]
+
+
+def dev(v):
+    return torch.tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+NAMES = list(cases())
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_dof_counts(name):
+    pr, H, ctx, perms = setup_case(name)
+    for l in range(pr.num_levels):
+        assert ctx.num_dofs(l) == H.levels[l].space.N
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_apply_every_level(name):
+    pr, H, ctx, perms = setup_case(name)
+    rng = np.random.default_rng(0)
+    for l in range(pr.num_levels):
+        A = H.levels[l].A
+        x = rng.normal(size=A.shape[0])
+        y = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        ctx.apply(l, dev(to_lib(perms[l], x)), y)
+        assert rel(from_lib(perms[l], host(y)), A @ x) < 1e-13
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_smoother_every_level(name):
+    from oracle import smoother
+    pr, H, ctx, perms = setup_case(name)
+    rng = np.random.default_rng(1)
+    for l in range(1, pr.num_levels):
+        r = rng.normal(size=H.levels[l].space.N)
+        z = torch.empty_like(dev(r))
+        ctx.smooth(l, dev(to_lib(perms[l], r)), z)
+        ref = smoother.apply_smoother(H.levels[l].smooth, r)
+        assert rel(from_lib(perms[l], host(z)), ref) < 1e-12
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_transfers_every_level(name):
+    pr, H, ctx, perms = setup_case(name)
+    rng = np.random.default_rng(2)
+    for l in range(1, pr.num_levels):
+        P = H.levels[l].P
+        r = rng.normal(size=P.shape[0])
+        rc = torch.empty(P.shape[1], dtype=torch.float64, device="cuda")
+        ctx.restrict(l, dev(to_lib(perms[l], r)), rc)
+        assert rel(from_lib(perms[l - 1], host(rc)), P.T @ r) < 1e-12
+        uc = rng.normal(size=P.shape[1])
+        u = torch.empty(P.shape[0], dtype=torch.float64, device="cuda")
+        ctx.prolong(l, dev(to_lib(perms[l - 1], uc)), u)
+        assert rel(from_lib(perms[l], host(u)), P @ uc) < 1e-12
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_coarse_solve(name):
+    import scipy.linalg as sla
+    pr, H, ctx, perms = setup_case(name)
+    r = np.random.default_rng(3).normal(size=H.levels[0].space.N)
+    x = torch.empty_like(dev(r))
+    ctx.coarse_solve(dev(to_lib(perms[0], r)), x)
+    assert rel(from_lib(perms[0], host(x)), sla.cho_solve(H.coarse_chol, r)) < 1e-11
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_one_cycle(name):
+    pr, H, ctx, perms = setup_case(name)
+    r = np.random.default_rng(4).normal(size=H.levels[-1].space.N)
+    z = torch.empty_like(dev(r))
+    ctx.precondition(dev(to_lib(perms[-1], r)), z)
+    assert rel(from_lib(perms[-1], host(z)), solver.precondition(H, r)) < 1e-11
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_pcg_parity(name):
+    from paper_1804_02539_gb300 import igamg
+    pr, H, ctx, perms = setup_case(name)
+    N = H.levels[-1].space.N
+    b = workloads.rhs_coefficients(N, 5)
+    ref = solver.pcg(H, b, tol=1e-8)
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    res, st = ctx.solve(dev(to_lib(perms[-1], b)), x, 1e-8)
+    assert st == igamg.IGAMG_OK
+    assert abs(res.iters - ref.iters) <= 1, (res.iters, ref.iters)
+    # same iterates: exactly k iterations on both sides
+    k = ref.iters
+    fixed = solver.pcg(H, b, fixed_iters=k)
+    opts = igamg.igamg_default_options()
+    opts.max_iter = k
+    ctx_k = igamg.Context(pr, opts)
+    xk = torch.zeros_like(x)
+    res_k, _ = ctx_k.solve(dev(to_lib(perms[-1], b)), xk, 0.0)
+    assert res_k.iters == k
+    assert rel(from_lib(perms[-1], host(xk)), fixed.x) < 1e-10
+    ctx_k.free()
+    # tight solve equals the oracle's tight solve
+    tight = solver.pcg(H, b, tol=1e-13, max_iter=300)
+    xt = torch.zeros_like(x)
+    ctx.solve(dev(to_lib(perms[-1], b)), xt, 1e-13)
+    assert rel(from_lib(perms[-1], host(xt)), tight.x) < 1e-10
+
+
+def test_nonzero_initial_guess_and_zero_rhs():
+    pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
+    N = H.levels[-1].space.N
+    b = np.zeros(N)
+    x = dev(np.zeros(N))
+    res, st = ctx.solve(dev(b), x, 1e-8)
+    assert res.iters == 0 and np.all(host(x) == 0)
+    b = workloads.rhs_coefficients(N, 9)
+    x0 = np.random.default_rng(9).normal(size=N)
+    ref = solver.pcg(H, b, x0=x0, tol=1e-8)
+    x = dev(to_lib(perms[-1], x0))
+    res, st = ctx.solve(dev(to_lib(perms[-1], b)), x, 1e-8)
+    assert abs(res.iters - ref.iters) <= 1
+    assert rel(from_lib(perms[-1], host(x)), solver.direct_solve(H.levels[-1].A, b)) < 1e-6
+
+
+def test_solve_host_matches_device():
+    pr, H, ctx, perms = setup_case("grid4x4_p4_m16")
+    N = H.levels[-1].space.N
+    b = workloads.rhs_coefficients(N, 11)
+    xd = dev(np.zeros(N))
+    r1, _ = ctx.solve(dev(b), xd, 1e-8)
+    xh = np.zeros(N)
+    r2, _ = ctx.solve_host(b.copy(), xh, 1e-8)
+    assert r1.iters == r2.iters
+    assert np.array_equal(host(xd), xh)      # deterministic: bit-identical reruns
+
+
+def test_errors_are_reported():
+    from paper_1804_02539_gb300 import igamg
+    pr = workloads.unit_square_quadrants(8, 2, 4)
+    pr.knots[0][0] = pr.knots[0][0] ** 1.5     # non-uniform knots
+    with pytest.raises(igamg.IgamgError) as e:
+        igamg.Context(pr)
+    assert e.value.status == 3
+    pr = workloads.unit_square_quadrants(8, 2, 4)
+    pr.side_bc[0, 1] = 1                       # interface tagged Dirichlet
+    with pytest.raises(igamg.IgamgError) as e:
+        igamg.Context(pr)
+    assert e.value.status == 2
+    pr = workloads.unit_square_quadrants(6, 2, 4)   # 6 not divisible by 2^3
+    with pytest.raises(igamg.IgamgError) as e:
+        igamg.Context(pr)
+    assert e.value.status == 1
+    ctx = setup_case("square_p2_m8")[2]
+    with pytest.raises(igamg.IgamgError):
+        ctx.smooth(0, dev(np.zeros(9)), dev(np.zeros(9)))
