@@ -1,0 +1,288 @@
+"""Benchmark: FP64 multigrid-preconditioned CG (one V(1,1)-cycle per iteration, tau=0.25,
+sigma=5h^-2) on the 2D multi-patch workload, solved from x0 = 0 to relative residual
+1e-8 through the C ABI.  One step = one complete solve.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64 NumPy/SciPy restatement of the method) on
+the host cores, one thread, on a bounded sample of the same workload family."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MDOF/s to rel. residual 1e-8 (FP64 vs mixed), V-cycle HBM frac; p50/p99 lat"
+WORKLOAD = "grid2d_K16_p4_m256"
+WORKLOAD_DESC = ("2D Poisson, K=16 bilinear patches of a 5x5 vertex grid on [0,4]^2 with interior "
+                 "vertices perturbed by U(-0.1,0.1) (seed 2), p=4, 256 intervals per patch direction, "
+                 "9 levels (coarsest 1 interval/patch), Dirichlet x=0,y=0, Neumann x=4,y=4, "
+                 "rhs = mass matrix times U(-1,1) spline coefficients (seed 2), FP64 PCG + V(1,1), tol 1e-8")
+ORACLE_SAMPLE = dict(nper=4, p=4, m=64, levels=7, seed=2)
+TOL = 1e-8
+# FP64 FMA pipe of one GB300: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample_json():
+    """Runs in a subprocess with one BLAS/OpenMP thread: oracle setup (untimed), then one
+    full PCG solve to 1e-8 of the sample problem (timed)."""
+    import numpy as np  # noqa: F401
+    import workloads
+    from oracle import multipatch, solver
+    s = ORACLE_SAMPLE
+    pr = workloads.perturbed_grid_2d(s["nper"], s["p"], s["m"], s["levels"], s["seed"])
+    t0 = time.perf_counter()
+    H = solver.build_hierarchy(pr)
+    sp = H.levels[-1].space
+    _, Mg = multipatch.stiffness(pr, sp, want_mass=True)
+    b = Mg @ workloads.rhs_coefficients(sp.N, 2)
+    t_setup = time.perf_counter() - t0
+    steps = int(os.environ.get("IGAMG_ORACLE_STEPS", "1"))
+    warm = int(os.environ.get("IGAMG_ORACLE_WARMUP", "0"))
+    for _ in range(warm):
+        solver.pcg(H, b, tol=TOL)
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(steps):
+        its.append(solver.pcg(H, b, tol=TOL).iters)
+    t = (time.perf_counter() - t0) / steps
+    return {"N": sp.N, "t_solve_s": t, "iters": its[-1], "t_setup_s": t_setup, "steps": steps}
+
+
+def run_oracle(steps=1, warmup=0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               IGAMG_ORACLE_STEPS=str(steps), IGAMG_ORACLE_WARMUP=str(warmup))
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle"], env=env,
+                         stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_desc():
+    s = ORACLE_SAMPLE
+    return (f"same workload family at {s['m']} intervals per patch direction ({s['levels']} levels): "
+            f"one full PCG+V(1,1) solve to 1e-8, setup excluded, 1 thread")
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1804_02539_gb300 import igamg
+
+    dist = world > 1
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    stream = torch.cuda.Stream(device=dev)
+    pr = workloads.CONFIGS[args.workload]()
+    with torch.cuda.stream(stream):
+        ctx = igamg.Context(pr, stream=stream)
+        N = ctx.num_dofs()
+        coef = torch.tensor(workloads.rhs_coefficients(N, 2), device=dev)
+        b = torch.empty(N, dtype=torch.float64, device=dev)
+        ctx.rhs_from_coefs(coef, b)
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            x.zero_()
+            res, st = ctx.solve(b, x, TOL)
+        iters = res.iters if args.warmup else None
+        sampler = ClockSampler(local_rank)
+        ctx.profile_enable(True)
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()
+            res, st = ctx.solve(b, x, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        ms_total = e0.elapsed_time(e1)
+        clocks = sampler.stop()
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        iters = res.iters
+        relres = res.relres
+        if dist:
+            t = torch.tensor([ms_total], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        # end to end: host vectors, H2D + D2H inside the timed region
+        e2e_s = float("nan")
+        if not args.no_e2e:
+            bh = b.cpu().numpy().copy()
+            xh = np.zeros(N)
+            ctx.solve_host(bh, xh, TOL)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                xh[:] = 0.0
+                r2, _ = ctx.solve_host(bh, xh, TOL)
+            e2e_s = (time.perf_counter() - t0) / args.steps
+        setup_ms = res.t_setup_ms
+        assemble_ms = res.t_assemble_ms
+    ms_step = ms_total / args.steps
+    value = N * world / (ms_step * 1e-3) / 1e6
+    # dominant kernel class and its roofline
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    pk, src = peaks()
+    if dom in ("interior_fd", "interface", "coarse"):
+        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "kernel": dom, "traffic": None}
+    else:
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": src, "kernel": dom, "traffic": None}
+    roof["avg_launch_ms"] = round(d["ms"] / max(d["launches"], 1), 5)
+    breakdown = {k: {"ms_per_step": round(v["ms"] / args.steps, 3),
+                     "launches_per_step": v["launches"] // args.steps,
+                     "gflop_per_step": round(v["flops"] / args.steps / 1e9, 4),
+                     "gbyte_per_step": round(v["bytes"] / args.steps / 1e9, 4)} for k, v in prof.items()}
+    launches = sum(v["launches"] for v in prof.values())
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_DESC if args.workload == WORKLOAD
+                   else args.workload, "dofs": N, "iters": iters,
+                   "relres": relres, "tol": TOL, "l2": "inputs larger than L2 (operator bands 0.94 GB)",
+                   "parallelism": f"replicas x{world}", "setup_ms": round(setup_ms, 1),
+                   "assemble_ms": round(assemble_ms, 1)},
+        "e2e": {"value": None if e2e_s != e2e_s else round(N * world / e2e_s / 1e6, 4), "unit": "MDOF/s",
+                "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clocks,
+        "kernel_breakdown": breakdown,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = run_oracle(1, 0)
+        out["cpu_baseline"] = {"value": round(o["N"] / o["t_solve_s"] / 1e6, 6), "unit": "MDOF/s",
+                               "cores": 1, "kind": "oracle", "sample": sample_desc(),
+                               "sample_dofs": o["N"], "sample_iters": o["iters"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.free()
+    if dist:
+        tdist.destroy_process_group()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    o = run_oracle(max(args.steps, 1), args.warmup)
+    value = o["N"] / o["t_solve_s"] / 1e6
+    out = {"metric": METRIC, "value": round(value, 6), "unit": "MDOF/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(o["t_solve_s"] * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "sample": sample_desc(),
+                      "sample_dofs": o["N"], "iters": o["iters"]},
+           "cpu_baseline": {"value": round(value, 6), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                            "sample": sample_desc()},
+           "e2e": {"value": round(value, 6), "unit": "MDOF/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    if "--_oracle" in sys.argv:
+        print(json.dumps(oracle_sample_json()))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -143,6 +143,18 @@ igamg_status igamg_prolong(igamg_ctx* ctx, int level, const double* uc_dev, doub
 igamg_status igamg_coarse_solve(igamg_ctx* ctx, const double* r_dev, double* x_dev);
 igamg_status igamg_precondition(igamg_ctx* ctx, const double* r_dev, double* z_dev);
 
+/* Per-kernel-class accounting for measurement.  While enabled, every kernel the context
+ * launches is bracketed by CUDA events on its stream and counted; igamg_profile_read
+ * returns, for class `cls`, the launches, the summed device time in ms, and the
+ * algorithmic FLOPs and bytes of those launches (the operands the method itself must
+ * read and write once: band coefficients, vectors, smoother bases).  Classes: 0 stiffness apply/residual, 1 patch-interior smoother contractions,
+ * 2 interface smoothers (gather, edge contractions, scatter), 3 transfers, 4 coarse solve,
+ * 5 vector operations (reductions, PCG updates, conversions).  Enabling resets the
+ * counters.  Reading synchronises the stream. */
+igamg_status igamg_profile_enable(igamg_ctx* ctx, int enable);
+igamg_status igamg_profile_read(igamg_ctx* ctx, int cls, int64_t* launches, double* ms,
+                                double* flops, double* bytes);
+
 /* Synchronises the context's stream. */
 igamg_status igamg_sync(igamg_ctx* ctx);
 

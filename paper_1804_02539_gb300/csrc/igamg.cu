@@ -70,6 +70,7 @@ struct Smoother1D {  // subspace-corrected mass smoother data of one direction s
 struct GemmSet {
   GemmDesc* d = nullptr;
   int batch = 0, maxM = 0, maxN = 0;
+  double flops = 0, bytes = 0;  // algorithmic work of one launch
 };
 
 struct Level {
@@ -93,6 +94,7 @@ struct Level {
   TransferDev* td = nullptr;
   double* ttmp = nullptr;
   int max_nf = 0, max_nc = 0;
+  double apply_flops = 0, band_bytes = 0, xfer_flops = 0, xfer_bytes = 0;
 };
 
 }  // namespace
@@ -110,11 +112,71 @@ struct igamg_ctx {
   double* h_scal = nullptr;  // pinned
   std::string err;
   double t_setup_ms = 0, t_assemble_ms = 0;
+  // per-class launch accounting (igamg_profile_*)
+  bool prof = false;
+  int64_t prof_launch[8] = {0};
+  double prof_ms[8] = {0}, prof_flops[8] = {0}, prof_bytes[8] = {0};
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_open;
+  int cur_cls = -1;
+  cudaEvent_t cur_start = nullptr;
 };
 
 static std::string g_setup_error = "no error";
 
 namespace {
+
+enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5 };
+
+cudaEvent_t prof_event(igamg_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+// Brackets one launch of class `cls` with algorithmic work (flops, bytes).
+struct ProfScope {
+  igamg_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  ProfScope(igamg_ctx* c_, int cls_, double flops, double bytes, int launches = 1) : c(c_), cls(cls_) {
+    if (!c->prof) return;
+    c->prof_launch[cls] += launches;
+    c->prof_flops[cls] += flops;
+    c->prof_bytes[cls] += bytes;
+    a = prof_event(c);
+    CK(cudaEventRecord(a, c->stream));
+  }
+  ~ProfScope() noexcept(false) {
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    CK(cudaEventRecord(b, c->stream));
+    c->ev_open.emplace_back(cls, a, b);
+  }
+};
+
+// Folds completed event pairs into the per-class totals (stream must be synchronised).
+void prof_collect(igamg_ctx* c) {
+  for (auto& t : c->ev_open) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
+    c->prof_ms[std::get<0>(t)] += ms;
+    c->ev_free.push_back(std::get<1>(t));
+    c->ev_free.push_back(std::get<2>(t));
+  }
+  c->ev_open.clear();
+}
+
+double gemm_flops(const std::vector<GemmDesc>& v) {
+  double f = 0;
+  for (auto& d : v) f += 2.0 * d.M * double(d.N) * d.K;
+  return f;
+}
 
 void set_gemm(igamg_ctx* c, GemmSet& gs, const std::vector<GemmDesc>& v) {
   gs.batch = int(v.size());
@@ -124,18 +186,25 @@ void set_gemm(igamg_ctx* c, GemmSet& gs, const std::vector<GemmDesc>& v) {
     gs.maxN = std::max(gs.maxN, d.N);
   }
   gs.d = v.empty() ? nullptr : c->mem.upload(v, c->stream);
+  gs.flops = gemm_flops(v);
+  gs.bytes = 0;
+  for (auto& d : v) gs.bytes += 8.0 * (double(d.M) * d.K + double(d.K) * d.N + 2.0 * d.M * d.N);
 }
 
-void run_gemm(igamg_ctx* c, const GemmSet& gs, bool ta, bool tb, int epi, double alpha) {
-  if (gs.batch) CK(launch_gemm(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, alpha));
+void run_gemm(igamg_ctx* c, const GemmSet& gs, bool ta, bool tb, int epi, double alpha, int cls) {
+  if (!gs.batch) return;
+  ProfScope ps(c, cls, gs.flops, gs.bytes);
+  CK(launch_gemm(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, alpha));
 }
 
 // ---------------------------------------------------------------- setup helpers
 
-// Subspace-corrected mass smoother on one direction (reading stated in the header of
-// oracle/smoother.py and in the design doc): S~ = splines of the index set with odd
-// derivatives < p vanishing at kept ends and even derivatives 2..<p vanishing at dropped
-// ends; S^G its M-orthogonal complement; mu = sigma on S~, lambda + sigma on S^G.
+// Subspace-corrected mass smoother on one direction (Sec. 3 names it for the patch
+// interiors; this library reads it as follows): S~ = splines of the index set with odd
+// derivatives < p vanishing at kept (Neumann) ends and even derivatives 2..<p vanishing at
+// dropped (interface / Dirichlet) ends; S^G its M-orthogonal complement; the FD basis is an
+// M-orthonormal basis of S~ followed by the (K, M) eigenvectors on S^G, with
+// mu = sigma on S~ and lambda + sigma on S^G.
 Smoother1D build_scms(int m, int p, bool drop_lo, bool drop_hi, double sigma) {
   Mat M, K;
   mass_stiffness_1d(m, p, M, K);
@@ -306,6 +375,8 @@ void build_levels(igamg_ctx* c) {
       }
       P.band_off = band_total;
       band_total += nn * nb;
+      L.apply_flops += 2.0 * double(nn) * nb;
+      L.band_bytes += 8.0 * double(nn) * nb;
     }
     L.pd = c->mem.upload(L.pd_h, s);
     L.l2g = c->mem.upload(T.l2g, s);
@@ -357,6 +428,7 @@ void build_levels(igamg_ctx* c) {
       std::map<std::tuple<int, int, int, int, int, int>, double*> dinv_cache;
       for (const Interior& in : T.interiors) {
         const PatchDev& P = L.pd_h[in.k];
+        if (in.len[0] == 0 || in.len[1] == 0) continue;  // empty piece (p = 1, one element)
         Smoother1D* S[2];
         for (int j = 0; j < 2; ++j) {
           double sigma = c->opt.sigma_scale * double(P.m[j]) * double(P.m[j]);
@@ -527,6 +599,8 @@ void build_levels(igamg_ctx* c) {
           td.wp[j] = int((intptr_t)v[5]);
         }
         ttot += int64_t(td.nc[0]) * td.nf[1];
+        L.xfer_flops += 2.0 * (double(td.nc[0]) * td.nf[1] * td.wr[0] + double(td.nc[0]) * td.nc[1] * td.wr[1]);
+        L.xfer_bytes += 8.0 * (double(td.nf[0]) * td.nf[1] + double(td.nc[0]) * td.nc[1]);
         L.max_nf = std::max(L.max_nf, std::max(td.nf[0], td.nf[1]));
         L.max_nc = std::max(L.max_nc, std::max(td.nc[0], td.nc[1]));
       }
@@ -592,6 +666,7 @@ void build_levels(igamg_ctx* c) {
 
 void residual(igamg_ctx* c, int l, const double* f, const double* u, double* r) {
   Level& L = c->lv[l];
+  ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes + 8.0 * L.topo.T * (f ? 3 : 2));
   CK(launch_band_apply_2d(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, L.band, u, f, r));
 }
 
@@ -603,19 +678,24 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   const double* v = from_F ? L.F : L.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
-  run_gemm(c, from_F ? L.st0F : L.st0R, true, false, EPI_STORE, 1.0);
-  run_gemm(c, L.st1, false, false, EPI_MUL, 1.0);
-  run_gemm(c, L.st2, false, false, EPI_STORE, 1.0);
-  run_gemm(c, L.st3, false, true, epi, tau);
+  run_gemm(c, from_F ? L.st0F : L.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
+  run_gemm(c, L.st1, false, false, EPI_MUL, 1.0, CLS_FD);
+  run_gemm(c, L.st2, false, false, EPI_STORE, 1.0, CLS_FD);
+  run_gemm(c, L.st3, false, true, epi, tau, CLS_FD);
   if (L.n_if == 0) return;
-  CK(launch_iface_gather(c->stream, L.n_if, L.if_ptr, L.if_idx, v, L.G));
-  run_gemm(c, L.edgeA, false, false, EPI_COLSCALE, 1.0);
-  run_gemm(c, L.edgeB, false, true, EPI_STORE, 1.0);
+  {
+    ProfScope ps(c, CLS_IFACE, 0.0, 16.0 * L.n_if);
+    CK(launch_iface_gather(c->stream, L.n_if, L.if_ptr, L.if_idx, v, L.G));
+  }
+  run_gemm(c, L.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
+  run_gemm(c, L.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 24.0 * L.n_if);
   CK(launch_iface_scatter(c->stream, L.n_if, L.if_ptr, L.if_idx, L.Z, L.G, L.vscale, tau, add ? 1 : 0, L.U));
 }
 
 void coarse_solve(igamg_ctx* c) {
   Level& L0 = c->lv[0];
+  ProfScope ps(c, CLS_COARSE, 2.0 * double(c->N0) * c->N0, 8.0 * double(c->N0) * c->N0);
   CK(launch_coarse_solve(c->stream, c->N0, L0.g2t_ptr, L0.g2t, c->A0inv, L0.F, L0.U));
 }
 
@@ -633,13 +713,17 @@ void multigrid(igamg_ctx* c, int l, bool zero_init) {
   }
   residual(c, l, L.F, L.U, L.R);
   Level& C = c->lv[l - 1];
+  ProfScope pr(c, CLS_TRANSFER, L.xfer_flops, L.xfer_bytes, 2);
   CK(launch_restrict_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, L.R, L.ttmp, C.F, C.l2g, C.topo.T));
   if (l == 1) {
     coarse_solve(c);
   } else {
     for (int j = 0; j < mu; ++j) multigrid(c, l - 1, j == 0);
   }
-  CK(launch_prolong_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, C.U, L.ttmp, L.U));
+  {
+    ProfScope pp(c, CLS_TRANSFER, 2.0 * L.xfer_flops, 2.0 * L.xfer_bytes, 2);
+    CK(launch_prolong_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, C.U, L.ttmp, L.U));
+  }
   for (int i = 0; i < nu; ++i) {
     residual(c, l, L.F, L.U, L.R);
     smooth(c, l, false, true);
@@ -662,27 +746,43 @@ int level_index(const igamg_ctx* c, int level) {
 
 void to_dist(igamg_ctx* c, int l, const double* xg, double* xt) {
   Level& L = c->lv[l];
+  ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(cudaMemsetAsync(xt, 0, L.topo.T * sizeof(double), c->stream));
   CK(launch_global_to_tile(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 1));
 }
 void to_acc(igamg_ctx* c, int l, const double* xg, double* xt) {
   Level& L = c->lv[l];
+  ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(cudaMemsetAsync(xt, 0, L.topo.T * sizeof(double), c->stream));
   CK(launch_global_to_tile(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 0));
 }
 void from_acc(igamg_ctx* c, int l, const double* xt, double* xg) {
   Level& L = c->lv[l];
+  ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(launch_tile_to_global(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 0));
 }
 void from_dist(igamg_ctx* c, int l, const double* xt, double* xg) {
   Level& L = c->lv[l];
+  ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(launch_tile_to_global(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 1));
 }
 
 double read_scalar(igamg_ctx* c, int i) {
   CK(cudaMemcpyAsync(c->h_scal + i, c->scal + i, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (c->prof) prof_collect(c);
   return c->h_scal[i];
+}
+
+void vdot(igamg_ctx* c, const double* a, const double* b, int64_t T, double* out) {
+  ProfScope ps(c, CLS_VECTOR, 2.0 * T, 16.0 * T, 2);
+  CK(launch_dot(c->stream, a, b, T, c->partials, out));
+}
+
+void vnorm_dist(igamg_ctx* c, int l, const double* v, double* out) {
+  Level& L = c->lv[l];
+  ProfScope ps(c, CLS_VECTOR, 2.0 * L.topo.N, 8.0 * L.topo.T, 2);
+  CK(launch_norm2_dist(c->stream, L.topo.N, L.g2t_ptr, L.g2t, v, c->partials, out));
 }
 
 // PCG (Sec. 4): r, w distributed; x, z, p accumulated.  scal: 0 rz, 1 pw, 2 rz_new, 3 rr.
@@ -695,7 +795,7 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
   to_dist(c, Lf, b, c->Bt);
   to_acc(c, Lf, x, c->X);
   residual(c, Lf, c->Bt, c->X, L.F);
-  CK(launch_norm2_dist(s, L.topo.N, L.g2t_ptr, L.g2t, L.F, c->partials, c->scal + 3));
+  vnorm_dist(c, Lf, L.F, c->scal + 3);
   double rr0 = read_scalar(c, 3);
   if (!std::isfinite(rr0)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite initial residual"};
   int it = 0;
@@ -704,28 +804,33 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
   if (rr0 > 0.0) {
     precondition(c);
     CK(cudaMemcpyAsync(c->Pv, L.U, T * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(launch_dot(s, L.F, L.U, T, c->partials, c->scal + 0));
+    vdot(c, L.F, L.U, T, c->scal + 0);
     rel = 1.0;
     while (true) {
       if (tol > 0 && rel <= tol) break;
       if (it >= c->opt.max_iter) { st = tol > 0 ? IGAMG_ERR_NOT_CONVERGED : IGAMG_OK; break; }
       residual(c, Lf, nullptr, c->Pv, c->W);
-      CK(launch_dot(s, c->Pv, c->W, T, c->partials, c->scal + 1));
-      CK(launch_pcg_xr(s, T, c->scal, c->X, L.F, c->Pv, c->W));
+      vdot(c, c->Pv, c->W, T, c->scal + 1);
+      {
+        ProfScope ps(c, CLS_VECTOR, 4.0 * T, 48.0 * T);
+        CK(launch_pcg_xr(s, T, c->scal, c->X, L.F, c->Pv, c->W));
+      }
       ++it;
-      CK(launch_norm2_dist(s, L.topo.N, L.g2t_ptr, L.g2t, L.F, c->partials, c->scal + 3));
+      vnorm_dist(c, Lf, L.F, c->scal + 3);
       double rr = read_scalar(c, 3);
       if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in PCG"};
       rel = std::sqrt(rr / rr0);
       if (tol > 0 && rel <= tol) break;
       if (it >= c->opt.max_iter) continue;
       precondition(c);
-      CK(launch_dot(s, L.F, L.U, T, c->partials, c->scal + 2));
+      vdot(c, L.F, L.U, T, c->scal + 2);
+      ProfScope ps(c, CLS_VECTOR, 2.0 * T, 24.0 * T, 2);
       CK(launch_pcg_p(s, T, c->scal, c->Pv, L.U));
     }
   }
   from_acc(c, Lf, c->X, x);
   CK(cudaStreamSynchronize(s));
+  if (c->prof) prof_collect(c);
   if (res) {
     res->iters = it;
     res->relres = rel;
@@ -907,7 +1012,82 @@ igamg_status igamg_precondition(igamg_ctx* c, const double* r, double* z) {
 igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs) {
   return guarded(c, [&]() -> igamg_status {
     if (!coef || !rhs) throw Fail{IGAMG_ERR_ARG, "NULL vector"};
-    throw Fail{IGAMG_ERR_UNSUPPORTED, "rhs_from_coefs not built yet"};
+    // b = M_geo c: assemble the geometry mass bands of the finest level into a temporary
+    // band array (same layout as the stiffness), apply them patch-locally, sum the copies.
+    int Lf = int(c->lv.size()) - 1;
+    Level& L = c->lv[Lf];
+    cudaStream_t s = c->stream;
+    double* mband = nullptr;
+    size_t bytes = size_t(L.band_bytes);
+    CK(cudaMallocAsync(&mband, bytes, s));
+    int64_t gmax = 0;
+    for (auto& P : L.pd_h) gmax = std::max(gmax, int64_t(P.m[0]) * (P.p[0] + 1) * P.m[1] * (P.p[1] + 1) * 4);
+    double *G = nullptr, *dcorn = nullptr;
+    CK(cudaMallocAsync(&G, gmax * sizeof(double), s));
+    CK(cudaMallocAsync(&dcorn, c->pd.corners.size() * sizeof(double), s));
+    CK(cudaMemcpyAsync(dcorn, c->pd.corners.data(), c->pd.corners.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    std::map<std::tuple<int, int>, std::vector<double*>> dt;
+    std::vector<double*> tmp_tabs;
+    for (int k = 0; k < c->pd.K; ++k) {
+      const PatchDev& P = L.pd_h[k];
+      double* tp[2][4];
+      for (int j = 0; j < 2; ++j) {
+        auto key = std::make_tuple(P.m[j], P.p[j]);
+        if (!dt.count(key)) {
+          Tables1D tb = tables_1d(P.m[j], P.p[j]);
+          std::vector<double*> v;
+          for (auto* src : {&tb.xq, &tb.wq, &tb.B, &tb.dB}) {
+            double* d = nullptr;
+            CK(cudaMallocAsync(&d, src->size() * sizeof(double), s));
+            CK(cudaMemcpyAsync(d, src->data(), src->size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            v.push_back(d);
+            tmp_tabs.push_back(d);
+          }
+          CK(cudaStreamSynchronize(s));  // host tables go out of scope
+          dt[key] = v;
+        }
+        for (int q = 0; q < 4; ++q) tp[j][q] = dt[key][q];
+      }
+      CK(launch_geom_factors_2d(s, dcorn + size_t(k) * 8, P.m[0], P.m[1], P.p[0] + 1, tp[0][0], tp[0][1],
+                                tp[1][0], tp[1][1], G));
+      CK(launch_assemble_2d(s, P, G, tp[0][2], tp[0][3], tp[1][2], tp[1][3], L.l2g, 1, mband));
+    }
+    to_acc(c, Lf, coef, L.U);
+    CK(launch_band_apply_2d(s, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, mband, L.U, nullptr, L.R));
+    from_dist(c, Lf, L.R, rhs);
+    for (double* d : tmp_tabs) CK(cudaFreeAsync(d, s));
+    CK(cudaFreeAsync(G, s));
+    CK(cudaFreeAsync(dcorn, s));
+    CK(cudaFreeAsync(mband, s));
+    CK(cudaStreamSynchronize(s));
+    return IGAMG_OK;
+  });
+}
+
+igamg_status igamg_profile_enable(igamg_ctx* c, int enable) {
+  return guarded(c, [&]() {
+    CK(cudaStreamSynchronize(c->stream));
+    prof_collect(c);
+    c->prof = enable != 0;
+    for (int i = 0; i < 8; ++i) {
+      c->prof_launch[i] = 0;
+      c->prof_ms[i] = c->prof_flops[i] = c->prof_bytes[i] = 0.0;
+    }
+    return IGAMG_OK;
+  });
+}
+
+igamg_status igamg_profile_read(igamg_ctx* c, int cls, int64_t* launches, double* ms, double* flops,
+                                double* bytes) {
+  return guarded(c, [&]() {
+    if (cls < 0 || cls >= 8 || !launches || !ms || !flops || !bytes) throw Fail{IGAMG_ERR_ARG, "bad arguments"};
+    CK(cudaStreamSynchronize(c->stream));
+    prof_collect(c);
+    *launches = c->prof_launch[cls];
+    *ms = c->prof_ms[cls];
+    *flops = c->prof_flops[cls];
+    *bytes = c->prof_bytes[cls];
+    return IGAMG_OK;
   });
 }
 
@@ -949,6 +1129,11 @@ igamg_status igamg_free(igamg_ctx* c) {
   if (!c) return IGAMG_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (auto& t : c->ev_open) {
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   c->mem.release();
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;

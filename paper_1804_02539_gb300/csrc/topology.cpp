@@ -238,7 +238,7 @@ std::string build_level(const ProblemDesc& pd, int level, LevelTopo& L, int* cod
       in.drop_hi[j] = pd.side[k * 2 * d + 2 * j + 1] != SIDE_NEUMANN;
       in.lo[j] = in.drop_lo[j] ? 1 : 0;
       in.len[j] = nk[j] - in.lo[j] - (in.drop_hi[j] ? 1 : 0);
-      if (in.len[j] < 1) return fail(code, ERR_UNSUPPORTED, "patch interior is empty");
+      if (in.len[j] < 0) return fail(code, ERR_UNSUPPORTED, "patch interior is ill-formed");
       box *= in.len[j];
     }
     for (int64_t b = 0; b < box; ++b) {

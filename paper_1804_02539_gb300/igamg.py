@@ -56,6 +56,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_coarse_solve": ([P, P, P], C.c_int),
         "igamg_precondition": ([P, P, P], C.c_int),
         "igamg_sync": ([P], C.c_int),
+        "igamg_profile_enable": ([P, C.c_int], C.c_int),
+        "igamg_profile_read": ([P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
         "igamg_free": ([P], C.c_int),
         "igamg_last_error": ([P], C.c_char_p),
     }
@@ -187,6 +190,19 @@ class Context:
 
     def precondition(self, r, z):
         self._check(lib().igamg_precondition(self.h, _ptr(r), _ptr(z)))
+
+    PROFILE_CLASSES = ("apply", "interior_fd", "interface", "transfer", "coarse", "vector")
+
+    def profile_enable(self, on=True):
+        self._check(lib().igamg_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        out = {}
+        for i, name in enumerate(self.PROFILE_CLASSES):
+            n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+            self._check(lib().igamg_profile_read(self.h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+            out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+        return out
 
     def sync(self):
         self._check(lib().igamg_sync(self.h))
