@@ -689,8 +689,10 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   }
   run_gemm(c, L.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
   run_gemm(c, L.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
-  ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 24.0 * L.n_if);
-  CK(launch_iface_scatter(c->stream, L.n_if, L.if_ptr, L.if_idx, L.Z, L.G, L.vscale, tau, add ? 1 : 0, L.U));
+  {
+    ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 24.0 * L.n_if);
+    CK(launch_iface_scatter(c->stream, L.n_if, L.if_ptr, L.if_idx, L.Z, L.G, L.vscale, tau, add ? 1 : 0, L.U));
+  }
 }
 
 void coarse_solve(igamg_ctx* c) {
@@ -713,8 +715,10 @@ void multigrid(igamg_ctx* c, int l, bool zero_init) {
   }
   residual(c, l, L.F, L.U, L.R);
   Level& C = c->lv[l - 1];
-  ProfScope pr(c, CLS_TRANSFER, L.xfer_flops, L.xfer_bytes, 2);
-  CK(launch_restrict_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, L.R, L.ttmp, C.F, C.l2g, C.topo.T));
+  {
+    ProfScope pr(c, CLS_TRANSFER, L.xfer_flops, L.xfer_bytes, 2);
+    CK(launch_restrict_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, L.R, L.ttmp, C.F, C.l2g, C.topo.T));
+  }
   if (l == 1) {
     coarse_solve(c);
   } else {
@@ -824,8 +828,10 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
       if (it >= c->opt.max_iter) continue;
       precondition(c);
       vdot(c, L.F, L.U, T, c->scal + 2);
-      ProfScope ps(c, CLS_VECTOR, 2.0 * T, 24.0 * T, 2);
-      CK(launch_pcg_p(s, T, c->scal, c->Pv, L.U));
+      {
+        ProfScope ps(c, CLS_VECTOR, 2.0 * T, 24.0 * T, 2);
+        CK(launch_pcg_p(s, T, c->scal, c->Pv, L.U));
+      }
     }
   }
   from_acc(c, Lf, c->X, x);
