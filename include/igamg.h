@@ -143,6 +143,23 @@ igamg_status igamg_prolong(igamg_ctx* ctx, int level, const double* uc_dev, doub
 igamg_status igamg_coarse_solve(igamg_ctx* ctx, const double* r_dev, double* x_dev);
 igamg_status igamg_precondition(igamg_ctx* ctx, const double* r_dev, double* z_dev);
 
+/* Fast-diagonalisation apply of one tensor-product local smoother (Sec. 3: the
+ * patch-interior subspace-corrected mass smoother in diagonalised form, L_T^{-1} =
+ * (U0 x U1) diag(Dinv) (U0 x U1)^T), the core contraction of every smoothing step:
+ *     Z = tau * U0 ((U0^T R U1) .* Dinv) U1^T.
+ * No context needed.  Device pointers, FP64, row-major:
+ *   U0 n0 x n0 and U1 n1 x n1 (columns = basis vectors), Dinv n0 x n1 (row stride n1),
+ *   R n0 x n1 with row stride ldr >= n1, Z n0 x n1 with row stride ldz >= n1 (Z may be R
+ *   itself when ldz == ldr: R is read completely before Z is written),
+ *   scratch: caller-provided device buffer of 2*n0*n1 doubles, overwritten; it must not
+ *   overlap any other argument.
+ * Runs on `cuda_stream` (NULL = legacy default stream) and returns without synchronising.
+ * Errors: IGAMG_ERR_ARG for n0, n1 < 1, ld < n1 or a NULL pointer (nothing is launched);
+ * IGAMG_ERR_CUDA if a launch fails.  The message is available from igamg_last_error(NULL). */
+igamg_status igamg_fd_apply(int n0, int n1, const double* U0, const double* U1, const double* Dinv,
+                            const double* R, int ldr, double tau, double* Z, int ldz,
+                            double* scratch, void* cuda_stream);
+
 /* Per-kernel-class accounting for measurement.  While enabled, every kernel the context
  * launches is bracketed by CUDA events on its stream and counted; igamg_profile_read
  * returns, for class `cls`, the launches, the summed device time in ms, and the
@@ -161,8 +178,8 @@ igamg_status igamg_sync(igamg_ctx* ctx);
 /* Releases everything the context owns.  NULL-safe. */
 igamg_status igamg_free(igamg_ctx* ctx);
 
-/* Message of the last error on this context (or of the last failed setup when ctx is
- * NULL).  Never NULL; valid until the next call on the same context. */
+/* Message of the last error on this context; with ctx == NULL, of the last failed setup
+ * or context-free call on the calling thread.  Never NULL; valid until the next call. */
 const char* igamg_last_error(const igamg_ctx* ctx);
 
 #ifdef __cplusplus

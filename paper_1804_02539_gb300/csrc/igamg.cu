@@ -122,7 +122,7 @@ struct igamg_ctx {
   cudaEvent_t cur_start = nullptr;
 };
 
-static std::string g_setup_error = "no error";
+static thread_local std::string g_setup_error = "no error";
 
 namespace {
 
@@ -1068,6 +1068,28 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs)
     CK(cudaStreamSynchronize(s));
     return IGAMG_OK;
   });
+}
+
+igamg_status igamg_fd_apply(int n0, int n1, const double* U0, const double* U1, const double* Dinv,
+                            const double* R, int ldr, double tau, double* Z, int ldz, double* scratch,
+                            void* cuda_stream) {
+  if (n0 < 1 || n1 < 1 || ldr < n1 || ldz < n1 || !U0 || !U1 || !Dinv || !R || !Z || !scratch) {
+    g_setup_error = "igamg_fd_apply: sizes must be >= 1, strides >= n1, pointers non-NULL";
+    return IGAMG_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* T = scratch;
+  double* Y = scratch + int64_t(n0) * n1;
+  try {
+    CK(launch_gemm_one(s, GemmDesc{U0, R, T, nullptr, n0, ldr, n1, 0, n0, n1, n0}, true, false, EPI_STORE, 1.0));
+    CK(launch_gemm_one(s, GemmDesc{T, U1, Y, Dinv, n1, n1, n1, n1, n0, n1, n1}, false, false, EPI_MUL, 1.0));
+    CK(launch_gemm_one(s, GemmDesc{U0, Y, T, nullptr, n0, n1, n1, 0, n0, n1, n0}, false, false, EPI_STORE, 1.0));
+    CK(launch_gemm_one(s, GemmDesc{T, U1, Z, nullptr, n1, n1, ldz, 0, n0, n1, n1}, false, true, EPI_ASSIGN, tau));
+  } catch (const Fail& e) {
+    g_setup_error = e.msg;
+    return e.code;
+  }
+  return IGAMG_OK;
 }
 
 igamg_status igamg_profile_enable(igamg_ctx* c, int enable) {

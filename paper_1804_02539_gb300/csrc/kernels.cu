@@ -177,33 +177,43 @@ cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, 
 
 // ---------------------------------------------------------------- batched FP64 GEMM
 
+// C = op(A) op(B) with an epilogue, one output tile of 8R x 8R per block of 64 threads;
+// thread (tx, ty) owns rows ty + 8r and columns tx + 8c (r, c < R).  Rows/columns of the
+// tile beyond M/N and the k-slab beyond K are skipped warp-uniformly, so ragged sizes
+// (e.g. 258 = 8*32 + 2) waste FP64 work only at 8-granularity.
 namespace {
-constexpr int GB = 32, GK = 16;  // 32 x 32 output tile, 16-deep k slab, 64 threads (4x4 each)
-}
+constexpr int GK = 16;
 
-__global__ void __launch_bounds__(64) k_gemm_f64(const GemmDesc* __restrict__ descs, int ta, int tb,
-                                                 int epi, double alpha) {
-  const GemmDesc d = descs[blockIdx.z];
-  const int i0 = blockIdx.y * GB, j0 = blockIdx.x * GB;
+template <int R>
+__device__ __forceinline__ void gemm_tile(const GemmDesc& d, int ta, int tb, int epi, double alpha,
+                                          int bx, int by) {
+  constexpr int BT = 8 * R;
+  const int i0 = by * BT, j0 = bx * BT;
   if (i0 >= d.M || j0 >= d.N) return;
-  __shared__ double As[GK][GB + 1];
-  __shared__ double Bs[GK][GB + 1];
+  __shared__ double As[GK][BT + 1];
+  __shared__ double Bs[GK][BT + 1];
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-  double acc[4][4];
+  const int wty = (tid >> 5) * 4;  // smallest ty of this warp
+  int rv = 0, cv = 0;              // warp-uniform counts of live micro-rows / micro-columns
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < R; ++r) rv += (i0 + wty + 8 * r < d.M) ? 1 : 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int c = 0; c < R; ++c) cv += (j0 + 8 * c < d.N) ? 1 : 0;
+  double acc[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[r][c] = 0.0;
   for (int k0 = 0; k0 < d.K; k0 += GK) {
-    for (int idx = tid; idx < GB * GK; idx += 64) {
+    for (int idx = tid; idx < BT * GK; idx += 64) {
       int i, kk;
-      if (ta) { i = idx % GB; kk = idx / GB; } else { kk = idx % GK; i = idx / GK; }
+      if (ta) { i = idx % BT; kk = idx / BT; } else { kk = idx % GK; i = idx / GK; }
       int gi = i0 + i, gk = k0 + kk;
       double v = 0.0;
       if (gi < d.M && gk < d.K) v = ta ? d.A[int64_t(gk) * d.lda + gi] : d.A[int64_t(gi) * d.lda + gk];
       As[kk][i] = v;
       int j;
-      if (tb) { kk = idx % GK; j = idx / GK; } else { j = idx % GB; kk = idx / GB; }
+      if (tb) { kk = idx % GK; j = idx / GK; } else { j = idx % BT; kk = idx / BT; }
       int gj = j0 + j;
       gk = k0 + kk;
       v = 0.0;
@@ -211,27 +221,31 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmDesc* __restrict__ de
       Bs[kk][j] = v;
     }
     __syncthreads();
+    const int kmax = min(GK, d.K - k0);
+    for (int kk = 0; kk < kmax; ++kk) {
+      double a[R], b[R];
 #pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
+      for (int r = 0; r < R; ++r) a[r] = As[kk][ty + 8 * r];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+      for (int c = 0; c < R; ++c) b[c] = Bs[kk][tx + 8 * c];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+      for (int r = 0; r < R; ++r) {
+        if (r < rv) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+          for (int c = 0; c < R; ++c)
+            if (c < cv) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    int gi = i0 + ty * 4 + r;
+  for (int r = 0; r < R; ++r) {
+    int gi = i0 + ty + 8 * r;
     if (gi >= d.M) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      int gj = j0 + tx * 4 + c;
+    for (int c = 0; c < R; ++c) {
+      int gj = j0 + tx + 8 * c;
       if (gj >= d.N) continue;
       double v = acc[r][c];
       double* cp = d.C + int64_t(gi) * d.ldc + gj;
@@ -246,12 +260,45 @@ __global__ void __launch_bounds__(64) k_gemm_f64(const GemmDesc* __restrict__ de
     }
   }
 }
+}  // namespace
+
+template <int R>
+__global__ void __launch_bounds__(64) k_gemm_f64(const GemmDesc* __restrict__ descs, int ta, int tb, int epi,
+                                                 double alpha) {
+  gemm_tile<R>(descs[blockIdx.z], ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
+}
+
+template <int R>
+__global__ void __launch_bounds__(64) k_gemm_f64_one(GemmDesc d, int ta, int tb, int epi, double alpha) {
+  gemm_tile<R>(d, ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
+}
+
+// Tile edge 8R: 32 when the 32-wide grid already fills the GPU twice, else 16, else 8.
+static int pick_r(int maxM, int maxN, int batch) {
+  auto tiles = [&](int bt) { return int64_t((maxM + bt - 1) / bt) * ((maxN + bt - 1) / bt) * batch; };
+  if (tiles(32) >= 2 * 152) return 4;
+  if (tiles(16) >= 152) return 2;
+  return 1;
+}
 
 cudaError_t launch_gemm(cudaStream_t s, const GemmDesc* d_desc, int batch, int maxM, int maxN,
                         bool transA, bool transB, int epi, double alpha) {
   if (batch <= 0) return cudaSuccess;
-  dim3 grid((maxN + GB - 1) / GB, (maxM + GB - 1) / GB, batch);
-  k_gemm_f64<<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  int R = pick_r(maxM, maxN, batch), bt = 8 * R;
+  dim3 grid((maxN + bt - 1) / bt, (maxM + bt - 1) / bt, batch);
+  if (R == 4) k_gemm_f64<4><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  else if (R == 2) k_gemm_f64<2><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  else k_gemm_f64<1><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
+                            double alpha) {
+  int R = pick_r(d.M, d.N, 1), bt = 8 * R;
+  dim3 grid((d.N + bt - 1) / bt, (d.M + bt - 1) / bt, 1);
+  if (R == 4) k_gemm_f64_one<4><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
+  else if (R == 2) k_gemm_f64_one<2><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
+  else k_gemm_f64_one<1><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,9 @@ cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, 
 
 cudaError_t launch_gemm(cudaStream_t s, const GemmDesc* d_desc, int batch, int maxM, int maxN,
                         bool transA, bool transB, int epi, double alpha);
+// One GEMM with the descriptor passed by value (no device-side descriptor array).
+cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
+                            double alpha);
 
 // Interface pieces: gather sums of the copies of every interface node from a
 // distributed vector; scatter tau * value to every copy of an accumulated vector.

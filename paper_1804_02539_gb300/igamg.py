@@ -59,6 +59,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_profile_enable": ([P, C.c_int], C.c_int),
         "igamg_profile_read": ([P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+        "igamg_fd_apply": ([C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_double, P, C.c_int, P, P], C.c_int),
         "igamg_free": ([P], C.c_int),
         "igamg_last_error": ([P], C.c_char_p),
     }
@@ -115,6 +116,22 @@ class Problem:
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         self.struct = igamg_problem(d, K, ip(self._deg), ip(self._nk), dp(self._kn), ip(self._gd),
                                     ip(self._gn), dp(self._ctrl), ip(self._bc), int(pr.num_levels))
+
+
+def _stream_handle(stream):
+    return C.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
+def igamg_fd_apply(U0, U1, Dinv, R, tau, Z, scratch, stream=None):
+    """Z = tau U0 ((U0^T R U1) .* Dinv) U1^T (2D row-major CUDA tensors, Z/R may be
+    row-strided views); scratch holds >= 2 n0 n1 doubles."""
+    n0, n1 = U0.shape[0], U1.shape[0]
+    assert R.stride(1) == 1 and Z.stride(1) == 1
+    st = lib().igamg_fd_apply(n0, n1, _ptr(U0), _ptr(U1), _ptr(Dinv), C.c_void_p(R.data_ptr()),
+                              R.stride(0), tau, C.c_void_p(Z.data_ptr()), Z.stride(0), _ptr(scratch),
+                              _stream_handle(stream))
+    if st != IGAMG_OK:
+        raise IgamgError(st, lib().igamg_last_error(None).decode())
 
 
 def igamg_default_options() -> igamg_options:

@@ -148,6 +148,28 @@ def test_pcg_parity(name):
     assert rel(from_lib(perms[-1], host(xt)), tight.x) < 1e-10
 
 
+@pytest.mark.parametrize("n0,n1", [(1, 1), (7, 13), (33, 65), (258, 259)])
+def test_fd_apply_entry_point(n0, n1):
+    """Context-free fast-diagonalisation apply against the oracle's FD (Kronecker identity)."""
+    from oracle import smoother
+    from paper_1804_02539_gb300 import igamg
+    rng = np.random.default_rng(n0 * 1000 + n1)
+    U0, U1 = rng.normal(size=(n0, n0)), rng.normal(size=(n1, n1))
+    Dinv = rng.uniform(0.1, 1.0, size=(n0, n1))
+    big = rng.normal(size=(n0, n1 + 5))          # row stride n1 + 5
+    R = big[:, :n1]
+    ref = 0.3 * smoother.fd_apply([U0, U1], Dinv, R)
+    Rd = dev(big)[:, :n1]
+    Zbig = torch.zeros((n0, n1 + 3), dtype=torch.float64, device="cuda")
+    Z = Zbig[:, :n1]
+    scratch = torch.empty(2 * n0 * n1, dtype=torch.float64, device="cuda")
+    igamg.igamg_fd_apply(dev(U0), dev(U1), dev(Dinv), Rd, 0.3, Z, scratch)
+    assert rel(host(Z), ref) < 1e-13
+    assert torch.all(Zbig[:, n1:] == 0)          # nothing outside the n0 x n1 window
+    assert igamg.lib().igamg_fd_apply(0, n1, None, None, None, None, n1, 1.0, None, n1, None, None) == 1
+    assert b"igamg_fd_apply" in igamg.lib().igamg_last_error(None)
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
