@@ -160,6 +160,29 @@ igamg_status igamg_fd_apply(int n0, int n1, const double* U0, const double* U1, 
                             const double* R, int ldr, double tau, double* Z, int ldz,
                             double* scratch, void* cuda_stream);
 
+/* The same apply as igamg_fd_apply for callers that cannot allocate device memory: a
+ * plugin or host framework that owns the device allocator and forbids allocations outside
+ * it, a fixed-budget or real-time caller that may not allocate after start-up, or a
+ * caller with no place to keep a scratch buffer between calls.  This entry point
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine); its scratch
+ * is a fixed device array of 2 * 262144 doubles (4 MiB) built into the library, which
+ * every GPU that loads the library holds until the process exits.  The paper has no
+ * counterpart: this is a memory-management variant, not a step of the method.
+ *   - Arguments and results are those of igamg_fd_apply without `scratch`.
+ *   - n0 * n1 must not exceed 262144 (512 x 512); larger tiles are rejected with
+ *     IGAMG_ERR_ARG and a message naming the limit, and nothing is launched.
+ *   - The first call on a device looks up that device's address of the array (once per
+ *     device, with that device current); make that first call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the last call's contents;
+ *     every element is written before it is read, so nothing has to be cleared.  Calls
+ *     whose kernels overlap on the GPU (different streams, or threads) race on the array:
+ *     serialise them, e.g. on one stream.
+ *   - Errors: IGAMG_ERR_ARG as above, IGAMG_ERR_CUDA if the lookup or a launch fails;
+ *     message from igamg_last_error(NULL). */
+igamg_status igamg_fd_apply_noalloc(int n0, int n1, const double* U0, const double* U1,
+                                    const double* Dinv, const double* R, int ldr, double tau,
+                                    double* Z, int ldz, void* cuda_stream);
+
 /* Per-kernel-class accounting for measurement.  While enabled, every kernel the context
  * launches is bracketed by CUDA events on its stream and counted; igamg_profile_read
  * returns, for class `cls`, the launches, the summed device time in ms, and the

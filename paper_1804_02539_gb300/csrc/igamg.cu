@@ -124,6 +124,11 @@ struct igamg_ctx {
 
 static thread_local std::string g_setup_error = "no error";
 
+namespace igamg {
+// Message returned by igamg_last_error(NULL) on this thread.
+void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
+}  // namespace igamg
+
 namespace {
 
 enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5 };

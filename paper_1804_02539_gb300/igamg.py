@@ -60,6 +60,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_profile_read": ([P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
         "igamg_fd_apply": ([C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_double, P, C.c_int, P, P], C.c_int),
+        "igamg_fd_apply_noalloc": ([C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_double, P, C.c_int, P],
+                                   C.c_int),
         "igamg_free": ([P], C.c_int),
         "igamg_last_error": ([P], C.c_char_p),
     }
