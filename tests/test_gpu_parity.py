@@ -170,6 +170,18 @@ def test_fd_apply_entry_point(n0, n1):
     assert b"igamg_fd_apply" in igamg.lib().igamg_last_error(None)
 
 
+@pytest.mark.parametrize("name", ["square_p2_m8", "grid3x3_p3_m16", "grid2x2_p5_m32_ragged"])
+def test_rhs_from_coefs(name):
+    """b = M_geo c (load vector of the spline source with coefficients c)."""
+    pr, H, ctx, perms = setup_case(name)
+    sp_ = H.levels[-1].space
+    _, Mg = multipatch.stiffness(pr, sp_, want_mass=True)
+    c = workloads.rhs_coefficients(sp_.N, 3)
+    b = torch.empty(sp_.N, dtype=torch.float64, device="cuda")
+    ctx.rhs_from_coefs(dev(to_lib(perms[-1], c)), b)
+    assert rel(from_lib(perms[-1], host(b)), Mg @ c) < 1e-13
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
