@@ -82,18 +82,27 @@ struct Level {
   int64_t *g2t_ptr = nullptr, *g2t = nullptr;
   double* band = nullptr;
   double *F = nullptr, *U = nullptr, *R = nullptr;
-  // interior smoother: stage GEMMs; stage 0 reads F or R
+  // 2D interior smoother: stage GEMMs; stage 0 reads F or R
   GemmSet st0F, st0R, st1, st2, st3;
   double *fdT = nullptr, *fdY = nullptr;
+  // 3D interior smoother: compact boxes and six mode products
+  BoxDev* boxes = nullptr;
+  int nbox = 0;
+  int64_t max_box = 0;
+  double *cX = nullptr, *cB1 = nullptr, *cB2 = nullptr;
+  GemmSet m0f, m1f, m2f, m0b, m1b, m2b;
   // interface pieces
   int64_t n_if = 0;
   int64_t *if_ptr = nullptr, *if_idx = nullptr;
   double *G = nullptr, *Z = nullptr, *Yif = nullptr, *vscale = nullptr;
-  GemmSet edgeA, edgeB;  // 1D FD of edge groups
-  // transfer from level-1 (valid for level >= 1)
-  TransferDev* td = nullptr;
-  double* ttmp = nullptr;
-  int max_nf = 0, max_nc = 0;
+  GemmSet edgeA, edgeB;          // 1D FD of edge groups
+  GemmSet face0, face1, face2, face3;  // 2D FD of 3D faces
+  double *fT = nullptr, *fY = nullptr;
+  // transfer from level l-1 (valid for level >= 1): one descriptor array per pass
+  Xfer1D* rpass[3] = {nullptr, nullptr, nullptr};
+  Xfer1D* ppass[3] = {nullptr, nullptr, nullptr};
+  int64_t rmax[3] = {0, 0, 0}, pmax[3] = {0, 0, 0};
+  double *tA = nullptr, *tB = nullptr;
   double apply_flops = 0, band_bytes = 0, xfer_flops = 0, xfer_bytes = 0;
 };
 
@@ -349,21 +358,94 @@ Tables1D tables_1d(int m, int p) {
   return t;
 }
 
+struct DevTables {  // device copies of one Tables1D
+  double *xq, *wq, *B, *dB;
+};
+
+// Edge (1D) smoother of an interface piece: (h/p)^{d-1} K + (h/p)^{d-3} M on the interior
+// indices of the edge's knot vector, applied by its generalised eigenvectors.
+void edge_fd(int d, int m, int p, Mat& U, std::vector<double>& dinv) {
+  Mat Mm, Km;
+  mass_stiffness_1d(m, p, Mm, Km);
+  std::vector<int> I;
+  for (int i = 1; i < m + p - 1; ++i) I.push_back(i);
+  int len = int(I.size());
+  Mat MI = submatrix(Mm, m + p, I), KI = submatrix(Km, m + p, I);
+  std::vector<double> lam;
+  if (!generalized_eigen(len, KI, MI, lam, U)) throw Fail{IGAMG_ERR_NUMERIC, "edge eigen failed"};
+  double h = 1.0 / m, a = std::pow(h / p, d - 1), b = std::pow(h / p, d - 3);
+  dinv.resize(len);
+  for (int q = 0; q < len; ++q) dinv[q] = 1.0 / (a * lam[q] + b);
+}
+
+void assemble_level(igamg_ctx* c, Level& L, std::map<std::tuple<int, int>, DevTables>& dtabs,
+                    std::map<std::tuple<int, int>, Tables1D>& tabs, double* dcorn, bool mass, double* band) {
+  const int d = c->pd.dim, K = c->pd.K;
+  for (int k = 0; k < K; ++k) {
+    const PatchDev& P = L.pd_h[k];
+    ElemAsm ea{};
+    ea.dim = d;
+    ea.p = P.p[0];
+    ea.mass = mass ? 1 : 0;
+    int64_t nn = 1;
+    for (int j = 0; j < 3; ++j) {
+      ea.n[j] = P.n[j];
+      ea.m[j] = P.m[j];
+      ea.color[j] = 0;
+    }
+    for (int j = 0; j < d; ++j) {
+      nn *= P.n[j];
+      if (P.p[j] != P.p[0]) throw Fail{IGAMG_ERR_UNSUPPORTED, "direction-dependent degree"};
+      auto key = std::make_tuple(P.m[j], P.p[j]);
+      if (!tabs.count(key)) tabs[key] = tables_1d(P.m[j], P.p[j]);
+      if (!dtabs.count(key)) {
+        const Tables1D& tb = tabs[key];
+        dtabs[key] = DevTables{c->mem.upload(tb.xq, c->stream), c->mem.upload(tb.wq, c->stream),
+                               c->mem.upload(tb.B, c->stream), c->mem.upload(tb.dB, c->stream)};
+      }
+      const DevTables& t = dtabs[key];
+      ea.xq[j] = t.xq;
+      ea.wq[j] = t.wq;
+      ea.B[j] = t.B;
+      ea.dB[j] = t.dB;
+    }
+    ea.off = P.off;
+    ea.band_off = P.band_off;
+    ea.nn = nn;
+    ea.corners = dcorn + size_t(k) * (1 << d) * d;
+    ea.l2g = L.l2g;
+    ea.band = band;
+    CK(launch_assemble_elem(c->stream, ea));
+  }
+}
+
 void build_levels(igamg_ctx* c) {
   cudaStream_t s = c->stream;
   const int d = c->pd.dim, K = c->pd.K;
-  if (d != 2) throw Fail{IGAMG_ERR_UNSUPPORTED, "this build solves 2D problems only"};
   const int NL = c->pd.levels;
+  for (int k = 0; k < K; ++k) {
+    int lim = d == 2 ? 10 : 4;
+    if (c->pd.p[k * d] > lim)
+      throw Fail{IGAMG_ERR_UNSUPPORTED, "degree above " + std::to_string(lim) + " in " + std::to_string(d) + "D"};
+  }
   c->lv.resize(NL);
   std::map<std::tuple<int, int, int, int, double>, Smoother1D> scms;  // (m,p,lo,hi,sigma)
   std::map<std::tuple<int, int>, Tables1D> tabs;
+  std::map<std::tuple<int, int>, DevTables> dtabs;
+  double* dcorn = c->mem.upload(c->pd.corners, s);
+  auto get_scms = [&](int m, int p, bool lo, bool hi, double sigma) -> Smoother1D* {
+    auto key = std::make_tuple(m, p, int(lo), int(hi), sigma);
+    if (!scms.count(key)) scms[key] = build_scms(m, p, lo, hi, sigma);
+    Smoother1D* S = &scms[key];
+    if (!S->dU) S->dU = c->mem.upload(S->U, s);
+    return S;
+  };
   for (int l = 0; l < NL; ++l) {
     Level& L = c->lv[l];
     int code = 0;
     std::string e = build_level(c->pd, l, L.topo, &code);
     if (!e.empty()) throw Fail{igamg_status(code), e};
     const LevelTopo& T = L.topo;
-    // patch descriptors and bands
     int64_t band_total = 0;
     L.pd_h.resize(K);
     for (int k = 0; k < K; ++k) {
@@ -394,58 +476,28 @@ void build_levels(igamg_ctx* c) {
     CK(cudaMemsetAsync(L.F, 0, T.T * sizeof(double), s));
     CK(cudaMemsetAsync(L.U, 0, T.T * sizeof(double), s));
     CK(cudaMemsetAsync(L.R, 0, T.T * sizeof(double), s));
-    // assembly (Eq. model:bil) patch by patch
+    CK(cudaMemsetAsync(L.band, 0, band_total * sizeof(double), s));
     double ta0 = now_ms();
-    {
-      int64_t gmax = 0;
-      for (auto& P : L.pd_h) gmax = std::max(gmax, int64_t(P.m[0]) * (P.p[0] + 1) * P.m[1] * (P.p[1] + 1) * 4);
-      double* G = c->mem.alloc<double>(gmax);
-      double* dcorn = c->mem.alloc<double>(c->pd.corners.size());
-      CK(cudaMemcpyAsync(dcorn, c->pd.corners.data(), c->pd.corners.size() * sizeof(double),
-                         cudaMemcpyHostToDevice, s));
-      std::map<std::tuple<int, int>, std::vector<double*>> dtabs;
-      for (int k = 0; k < K; ++k) {
-        const PatchDev& P = L.pd_h[k];
-        double* tp[2][4];
-        for (int j = 0; j < 2; ++j) {
-          auto key = std::make_tuple(P.m[j], P.p[j]);
-          if (!tabs.count(key)) tabs[key] = tables_1d(P.m[j], P.p[j]);
-          if (!dtabs.count(key)) {
-            const Tables1D& tb = tabs[key];
-            dtabs[key] = {c->mem.upload(tb.xq, s), c->mem.upload(tb.wq, s), c->mem.upload(tb.B, s),
-                          c->mem.upload(tb.dB, s)};
-          }
-          for (int q = 0; q < 4; ++q) tp[j][q] = dtabs[key][q];
-        }
-        if (P.p[0] != P.p[1]) throw Fail{IGAMG_ERR_UNSUPPORTED, "direction-dependent degree"};
-        CK(launch_geom_factors_2d(s, dcorn + size_t(k) * 4 * 2, P.m[0], P.m[1], P.p[0] + 1, tp[0][0],
-                                  tp[0][1], tp[1][0], tp[1][1], G));
-        CK(launch_assemble_2d(s, P, G, tp[0][2], tp[0][3], tp[1][2], tp[1][3], L.l2g, 0, L.band));
-      }
-      CK(cudaStreamSynchronize(s));
-    }
+    assemble_level(c, L, dtabs, tabs, dcorn, false, L.band);
+    CK(cudaStreamSynchronize(s));
     c->t_assemble_ms += now_ms() - ta0;
-    // smoother (levels >= 1)
-    if (l >= 1) {
-      // interiors
+    if (l == 0) continue;
+
+    // ---------------- patch-interior smoother
+    std::map<std::string, double*> dinv_cache;
+    if (d == 2) {
       int64_t fd_total = 0;
       std::vector<GemmDesc> s0F, s0R, s1, s2, s3;
-      std::map<std::tuple<int, int, int, int, int, int>, double*> dinv_cache;
       for (const Interior& in : T.interiors) {
         const PatchDev& P = L.pd_h[in.k];
         if (in.len[0] == 0 || in.len[1] == 0) continue;  // empty piece (p = 1, one element)
         Smoother1D* S[2];
         for (int j = 0; j < 2; ++j) {
-          double sigma = c->opt.sigma_scale * double(P.m[j]) * double(P.m[j]);
-          auto key = std::make_tuple(P.m[j], P.p[j], int(in.drop_lo[j]), int(in.drop_hi[j]), sigma);
-          if (!scms.count(key)) scms[key] = build_scms(P.m[j], P.p[j], in.drop_lo[j], in.drop_hi[j], sigma);
-          S[j] = &scms[key];
-          if (!S[j]->dU) S[j]->dU = c->mem.upload(S[j]->U, s);
+          S[j] = get_scms(P.m[j], P.p[j], in.drop_lo[j], in.drop_hi[j], c->opt.sigma_scale * double(P.m[j]) * P.m[j]);
           if (S[j]->len != in.len[j]) throw Fail{IGAMG_ERR_NUMERIC, "smoother size mismatch"};
         }
         int n0 = in.len[0], n1 = in.len[1];
-        auto dk = std::make_tuple(P.m[0], P.p[0], int(in.drop_lo[0]) + 2 * int(in.drop_hi[0]), P.m[1], P.p[1],
-                                  int(in.drop_lo[1]) + 2 * int(in.drop_hi[1]));
+        std::string dk = std::to_string(intptr_t(S[0])) + "/" + std::to_string(intptr_t(S[1]));
         if (!dinv_cache.count(dk)) {
           std::vector<double> Dv(size_t(n0) * n1);
           for (int a = 0; a < n0; ++a)
@@ -456,19 +508,15 @@ void build_levels(igamg_ctx* c) {
         int64_t base = fd_total;
         fd_total += int64_t(n0) * n1;
         int64_t xoff = P.off + int64_t(in.lo[0]) * P.n[1] + in.lo[1];
-        // stage descriptors: pointers to T/Y scratch are patched after allocation
         GemmDesc g0{S[0]->dU, nullptr, (double*)(intptr_t)base, nullptr, n0, P.n[1], n1, 0, n0, n1, n0};
         GemmDesc gF = g0, gR = g0;
         gF.B = L.F + xoff;
         gR.B = L.R + xoff;
         s0F.push_back(gF);
         s0R.push_back(gR);
-        s1.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, (double*)(intptr_t)base, Dinv, n1, n1, n1, n1,
-                              n0, n1, n1});
-        s2.push_back(GemmDesc{S[0]->dU, (double*)(intptr_t)base, (double*)(intptr_t)base, nullptr, n0, n1, n1, 0,
-                              n0, n1, n0});
-        s3.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, L.U + xoff, nullptr, n1, n1, P.n[1], 0, n0, n1,
-                              n1});
+        s1.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, (double*)(intptr_t)base, Dinv, n1, n1, n1, n1, n0, n1, n1});
+        s2.push_back(GemmDesc{S[0]->dU, (double*)(intptr_t)base, (double*)(intptr_t)base, nullptr, n0, n1, n1, 0, n0, n1, n0});
+        s3.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, L.U + xoff, nullptr, n1, n1, P.n[1], 0, n0, n1, n1});
       }
       L.fdT = c->mem.alloc<double>(fd_total);
       L.fdY = c->mem.alloc<double>(fd_total);
@@ -482,135 +530,272 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.st1, s1);
       set_gemm(c, L.st2, s2);
       set_gemm(c, L.st3, s3);
-      // interface pieces, grouped: vertices, then edges by (m, p, len)
-      std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;  // (kind, m, p, len)
-      for (int i = 0; i < int(T.ifaces.size()); ++i) {
-        const IfacePiece& pc = T.ifaces[i];
-        if (pc.kind == PIECE_VERTEX) groups[std::make_tuple(0, 0, 0, 1)].push_back(i);
-        else {
-          const PatchDev& P = L.pd_h[pc.k];
-          int j = pc.dirs[0];
-          groups[std::make_tuple(1, P.m[j], P.p[j], pc.len[0])].push_back(i);
-        }
-      }
-      std::vector<int64_t> ptr{0}, idx;
-      std::vector<double> vsc;
-      std::vector<GemmDesc> eA, eB;
-      for (auto& kv : groups) {
-        int kind = std::get<0>(kv.first);
-        int64_t gbase = int64_t(vsc.size());
-        for (int i : kv.second) {
-          const IfacePiece& pc = T.ifaces[i];
-          int64_t cnt = int64_t(pc.len[0]) * pc.len[1];
-          for (int64_t q = 0; q < cnt; ++q) {
-            int64_t g = T.iface_gid[pc.first + q];
-            for (int64_t cc = T.g2t_ptr[g]; cc < T.g2t_ptr[g + 1]; ++cc) idx.push_back(T.g2t[cc]);
-            ptr.push_back(int64_t(idx.size()));
-            double vs = 0.0;
-            if (kind == 0) {
-              const PatchDev& P = L.pd_h[pc.k];
-              double h = 1.0 / P.m[0], p = P.p[0];
-              vs = 1.0 / std::pow(h / p, d - 2);
-            }
-            vsc.push_back(vs);
-          }
-        }
-        if (kind == 1) {
-          int m = std::get<1>(kv.first), p = std::get<2>(kv.first), len = std::get<3>(kv.first);
-          Mat Mm, Km;
-          mass_stiffness_1d(m, p, Mm, Km);
-          std::vector<int> I;
-          for (int i = 1; i < m + p - 1; ++i) I.push_back(i);
-          Mat MI = submatrix(Mm, m + p, I), KI = submatrix(Km, m + p, I);
-          std::vector<double> lam;
-          Mat U;
-          if (!generalized_eigen(len, KI, MI, lam, U)) throw Fail{IGAMG_ERR_NUMERIC, "edge eigen failed"};
-          double h = 1.0 / m, a = std::pow(h / p, d - 1), b = std::pow(h / p, d - 3);
-          std::vector<double> dv(len);
-          for (int q = 0; q < len; ++q) dv[q] = 1.0 / (a * lam[q] + b);
-          double* dU = c->mem.upload(U, s);
-          double* ddv = c->mem.upload(dv, s);
-          int np = int(kv.second.size());
-          // Y = (R U) colscale dinv ; Z = Y U^T   (R: np x len, row per piece)
-          eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len, len, len, 0, np,
-                                len, len});
-          eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len, len, len, 0,
-                                np, len, len});
-        }
-      }
-      L.n_if = int64_t(vsc.size());
-      L.if_ptr = c->mem.upload(ptr, s);
-      L.if_idx = c->mem.upload(idx, s);
-      L.vscale = c->mem.upload(vsc, s);
-      L.G = c->mem.alloc<double>(L.n_if);
-      L.Z = c->mem.alloc<double>(L.n_if);
-      L.Yif = c->mem.alloc<double>(L.n_if);
-      CK(cudaMemsetAsync(L.Z, 0, std::max<int64_t>(L.n_if, 1) * sizeof(double), s));
-      for (auto& g : eA) { g.A = L.G + (intptr_t)g.A; g.C = L.Yif + (intptr_t)g.C; }
-      for (auto& g : eB) { g.A = L.Yif + (intptr_t)g.A; g.C = L.Z + (intptr_t)g.C; }
-      set_gemm(c, L.edgeA, eA);
-      set_gemm(c, L.edgeB, eB);
-      // transfers from level l-1
-      const Level& C = c->lv[l - 1];
-      std::map<std::tuple<int, int>, std::vector<void*>> ptabs;
-      std::vector<TransferDev> tds(K);
-      int64_t ttot = 0;
-      for (int k = 0; k < K; ++k) {
-        TransferDev& td = tds[k];
-        td.off_f = L.pd_h[k].off;
-        td.off_c = C.pd_h[k].off;
-        td.off_t = ttot;
+    } else {
+      // 3D: compact boxes, three mode products forward, Dinv, three backward
+      std::vector<BoxDev> boxes;
+      std::vector<GemmDesc> f0, f1, f2, b0, b1, b2;
+      int64_t tot = 0;
+      struct Pend { int64_t base; int n0, n1, n2; Smoother1D* S[3]; double* Dinv; };
+      std::vector<Pend> pend;
+      for (const Interior& in : T.interiors) {
+        const PatchDev& P = L.pd_h[in.k];
+        if (in.len[0] == 0 || in.len[1] == 0 || in.len[2] == 0) continue;
+        Pend pe;
         for (int j = 0; j < 3; ++j) {
-          td.nf[j] = L.pd_h[k].n[j];
-          td.nc[j] = C.pd_h[k].n[j];
-          td.rw[j] = td.pw[j] = nullptr;
-          td.rs[j] = td.ps[j] = nullptr;
-          td.wr[j] = td.wp[j] = 0;
-          if (j >= d) continue;
-          int mc = C.pd_h[k].m[j], p = C.pd_h[k].p[j];
-          auto key = std::make_tuple(mc, p);
-          if (!ptabs.count(key)) {
-            Mat P = prolongation_1d(mc, p);
-            int nf = 2 * mc + p, nc = mc + p, wp = 0, wr = 0;
-            std::vector<int> ps(nf), rs(nc);
-            for (int i = 0; i < nf; ++i) {
-              int lo = nc, hi = -1;
-              for (int jj = 0; jj < nc; ++jj)
-                if (P[size_t(i) * nc + jj] != 0.0) { lo = std::min(lo, jj); hi = std::max(hi, jj); }
-              ps[i] = hi < 0 ? 0 : lo;
-              wp = std::max(wp, hi - lo + 1);
-            }
-            for (int jj = 0; jj < nc; ++jj) {
-              int lo = nf, hi = -1;
-              for (int i = 0; i < nf; ++i)
-                if (P[size_t(i) * nc + jj] != 0.0) { lo = std::min(lo, i); hi = std::max(hi, i); }
-              rs[jj] = hi < 0 ? 0 : lo;
-              wr = std::max(wr, hi - lo + 1);
-            }
-            std::vector<double> pw(size_t(nf) * wp, 0.0), rw(size_t(nc) * wr, 0.0);
-            for (int i = 0; i < nf; ++i)
-              for (int a = 0; a < wp && ps[i] + a < nc; ++a) pw[size_t(i) * wp + a] = P[size_t(i) * nc + ps[i] + a];
-            for (int jj = 0; jj < nc; ++jj)
-              for (int a = 0; a < wr && rs[jj] + a < nf; ++a) rw[size_t(jj) * wr + a] = P[size_t(rs[jj] + a) * nc + jj];
-            ptabs[key] = {c->mem.upload(rw, s), c->mem.upload(rs, s), c->mem.upload(pw, s), c->mem.upload(ps, s),
-                          (void*)(intptr_t)wr, (void*)(intptr_t)wp};
-          }
-          auto& v = ptabs[key];
-          td.rw[j] = (const double*)v[0];
-          td.rs[j] = (const int*)v[1];
-          td.pw[j] = (const double*)v[2];
-          td.ps[j] = (const int*)v[3];
-          td.wr[j] = int((intptr_t)v[4]);
-          td.wp[j] = int((intptr_t)v[5]);
+          pe.S[j] = get_scms(P.m[j], P.p[j], in.drop_lo[j], in.drop_hi[j], c->opt.sigma_scale * double(P.m[j]) * P.m[j]);
+          if (pe.S[j]->len != in.len[j]) throw Fail{IGAMG_ERR_NUMERIC, "smoother size mismatch"};
         }
-        ttot += int64_t(td.nc[0]) * td.nf[1];
-        L.xfer_flops += 2.0 * (double(td.nc[0]) * td.nf[1] * td.wr[0] + double(td.nc[0]) * td.nc[1] * td.wr[1]);
-        L.xfer_bytes += 8.0 * (double(td.nf[0]) * td.nf[1] + double(td.nc[0]) * td.nc[1]);
-        L.max_nf = std::max(L.max_nf, std::max(td.nf[0], td.nf[1]));
-        L.max_nc = std::max(L.max_nc, std::max(td.nc[0], td.nc[1]));
+        pe.n0 = in.len[0];
+        pe.n1 = in.len[1];
+        pe.n2 = in.len[2];
+        std::string dk = std::to_string(intptr_t(pe.S[0])) + "/" + std::to_string(intptr_t(pe.S[1])) + "/" +
+                         std::to_string(intptr_t(pe.S[2]));
+        if (!dinv_cache.count(dk)) {
+          std::vector<double> Dv(size_t(pe.n0) * pe.n1 * pe.n2);
+          for (int a = 0; a < pe.n0; ++a)
+            for (int b = 0; b < pe.n1; ++b)
+              for (int q = 0; q < pe.n2; ++q)
+                Dv[(size_t(a) * pe.n1 + b) * pe.n2 + q] = 1.0 / (pe.S[0]->mu[a] + pe.S[1]->mu[b] + pe.S[2]->mu[q]);
+          dinv_cache[dk] = c->mem.upload(Dv, s);
+        }
+        pe.Dinv = dinv_cache[dk];
+        pe.base = tot;
+        BoxDev bx;
+        bx.tile_off = P.off;
+        bx.compact_off = tot;
+        for (int j = 0; j < 3; ++j) {
+          bx.n[j] = P.n[j];
+          bx.lo[j] = in.lo[j];
+          bx.len[j] = in.len[j];
+        }
+        boxes.push_back(bx);
+        int64_t vol = int64_t(pe.n0) * pe.n1 * pe.n2;
+        L.max_box = std::max(L.max_box, vol);
+        tot += vol;
+        pend.push_back(pe);
       }
-      L.td = c->mem.upload(tds, s);
-      L.ttmp = c->mem.alloc<double>(ttot);
+      L.nbox = int(boxes.size());
+      L.boxes = c->mem.upload(boxes, s);
+      L.cX = c->mem.alloc<double>(tot);
+      L.cB1 = c->mem.alloc<double>(tot);
+      L.cB2 = c->mem.alloc<double>(tot);
+      for (const Pend& pe : pend) {
+        int n0 = pe.n0, n1 = pe.n1, n2 = pe.n2, n12 = n1 * n2;
+        double *X = L.cX + pe.base, *B1 = L.cB1 + pe.base, *B2 = L.cB2 + pe.base;
+        const double *U0 = pe.S[0]->dU, *U1 = pe.S[1]->dU, *U2 = pe.S[2]->dU;
+        f0.push_back(GemmDesc{U0, X, B1, nullptr, n0, n12, n12, 0, n0, n12, n0});
+        for (int a = 0; a < n0; ++a)
+          f1.push_back(GemmDesc{U1, B1 + int64_t(a) * n12, B2 + int64_t(a) * n12, nullptr, n1, n2, n2, 0, n1, n2, n1});
+        f2.push_back(GemmDesc{B2, U2, B1, pe.Dinv, n2, n2, n2, n2, n0 * n1, n2, n2});
+        b0.push_back(GemmDesc{U0, B1, B2, nullptr, n0, n12, n12, 0, n0, n12, n0});
+        for (int a = 0; a < n0; ++a)
+          b1.push_back(GemmDesc{U1, B2 + int64_t(a) * n12, B1 + int64_t(a) * n12, nullptr, n1, n2, n2, 0, n1, n2, n1});
+        b2.push_back(GemmDesc{B1, U2, X, nullptr, n2, n2, n2, 0, n0 * n1, n2, n2});
+      }
+      set_gemm(c, L.m0f, f0);
+      set_gemm(c, L.m1f, f1);
+      set_gemm(c, L.m2f, f2);
+      set_gemm(c, L.m0b, b0);
+      set_gemm(c, L.m1b, b1);
+      set_gemm(c, L.m2b, b2);
+    }
+
+    // ---------------- interface pieces: vertices; edges and faces grouped by signature
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;  // (kind, m, p, len0, len1)
+    for (int i = 0; i < int(T.ifaces.size()); ++i) {
+      const IfacePiece& pc = T.ifaces[i];
+      const PatchDev& P = L.pd_h[pc.k];
+      if (pc.kind == PIECE_VERTEX) groups[std::make_tuple(0, 0, 0, 1, 1)].push_back(i);
+      else {
+        int j = pc.dirs[0];
+        groups[std::make_tuple(pc.kind, P.m[j], P.p[j], pc.len[0], pc.len[1])].push_back(i);
+      }
+    }
+    std::vector<int64_t> ptr{0}, idx;
+    std::vector<double> vsc;
+    std::vector<GemmDesc> eA, eB, q0, q1, q2, q3;
+    int64_t face_tot = 0;
+    for (auto& kv : groups) {
+      int kind = std::get<0>(kv.first);
+      int64_t gbase = int64_t(vsc.size());
+      for (int i : kv.second) {
+        const IfacePiece& pc = T.ifaces[i];
+        int64_t cnt = int64_t(pc.len[0]) * pc.len[1];
+        for (int64_t q = 0; q < cnt; ++q) {
+          int64_t g = T.iface_gid[pc.first + q];
+          for (int64_t cc = T.g2t_ptr[g]; cc < T.g2t_ptr[g + 1]; ++cc) idx.push_back(T.g2t[cc]);
+          ptr.push_back(int64_t(idx.size()));
+          double vs = 0.0;
+          if (kind == PIECE_VERTEX) {
+            const PatchDev& P = L.pd_h[pc.k];
+            double h = 1.0 / P.m[0], p = P.p[0];
+            vs = 1.0 / std::pow(h / p, d - 2);
+          }
+          vsc.push_back(vs);
+        }
+      }
+      int m = std::get<1>(kv.first), p = std::get<2>(kv.first);
+      int len0 = std::get<3>(kv.first), len1 = std::get<4>(kv.first);
+      int np = int(kv.second.size());
+      if (kind == PIECE_EDGE && len0 > 0) {
+        Mat U;
+        std::vector<double> dv;
+        edge_fd(d, m, p, U, dv);
+        double* dU = c->mem.upload(U, s);
+        double* ddv = c->mem.upload(dv, s);
+        eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len0, len0, len0, 0, np, len0, len0});
+        eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len0, len0, len0, 0, np, len0, len0});
+      } else if (kind == PIECE_FACE && len0 > 0 && len1 > 0) {
+        // 2D subspace-corrected mass smoother of the face, D = (h/p)(mu0 + mu1 + p^2/h^2)
+        double h = 1.0 / m, sigma = c->opt.sigma_scale * double(m) * m;
+        Smoother1D* S0 = get_scms(m, p, true, true, sigma);
+        Smoother1D* S1 = get_scms(m, p, true, true, sigma);
+        std::vector<double> Dv(size_t(len0) * len1);
+        for (int a = 0; a < len0; ++a)
+          for (int b = 0; b < len1; ++b)
+            Dv[size_t(a) * len1 + b] = 1.0 / ((h / p) * (S0->mu[a] + S1->mu[b] + double(p) * p / (h * h)));
+        double* Dinv = c->mem.upload(Dv, s);
+        for (int f = 0; f < np; ++f) {
+          int64_t off = gbase + int64_t(f) * len0 * len1, tb = face_tot + int64_t(f) * len0 * len1;
+          q0.push_back(GemmDesc{S0->dU, (double*)(intptr_t)off, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
+          q1.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)tb, Dinv, len1, len1, len1, len1, len0, len1, len1});
+          q2.push_back(GemmDesc{S0->dU, (double*)(intptr_t)tb, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
+          q3.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)off, nullptr, len1, len1, len1, 0, len0, len1, len1});
+        }
+        face_tot += int64_t(np) * len0 * len1;
+      }
+    }
+    L.n_if = int64_t(vsc.size());
+    L.if_ptr = c->mem.upload(ptr, s);
+    L.if_idx = c->mem.upload(idx, s);
+    L.vscale = c->mem.upload(vsc, s);
+    L.G = c->mem.alloc<double>(L.n_if);
+    L.Z = c->mem.alloc<double>(L.n_if);
+    L.Yif = c->mem.alloc<double>(L.n_if);
+    L.fT = c->mem.alloc<double>(face_tot);
+    L.fY = c->mem.alloc<double>(face_tot);
+    CK(cudaMemsetAsync(L.Z, 0, std::max<int64_t>(L.n_if, 1) * sizeof(double), s));
+    for (auto& g : eA) { g.A = L.G + (intptr_t)g.A; g.C = L.Yif + (intptr_t)g.C; }
+    for (auto& g : eB) { g.A = L.Yif + (intptr_t)g.A; g.C = L.Z + (intptr_t)g.C; }
+    for (auto& g : q0) { g.B = L.G + (intptr_t)g.B; g.C = L.fT + (intptr_t)g.C; }
+    for (auto& g : q1) { g.A = L.fT + (intptr_t)g.A; g.C = L.fY + (intptr_t)g.C; }
+    for (auto& g : q2) { g.B = L.fY + (intptr_t)g.B; g.C = L.fT + (intptr_t)g.C; }
+    for (auto& g : q3) { g.A = L.fT + (intptr_t)g.A; g.C = L.Z + (intptr_t)g.C; }
+    set_gemm(c, L.edgeA, eA);
+    set_gemm(c, L.edgeB, eB);
+    set_gemm(c, L.face0, q0);
+    set_gemm(c, L.face1, q1);
+    set_gemm(c, L.face2, q2);
+    set_gemm(c, L.face3, q3);
+
+    // ---------------- transfers from level l-1 (one 1D pass per direction)
+    const Level& C = c->lv[l - 1];
+    std::map<std::tuple<int, int>, std::vector<void*>> ptabs;
+    auto tables = [&](int mc, int p) -> std::vector<void*>& {
+      auto key = std::make_tuple(mc, p);
+      if (!ptabs.count(key)) {
+        Mat P = prolongation_1d(mc, p);
+        int nf = 2 * mc + p, nc = mc + p, wp = 0, wr = 0;
+        std::vector<int> ps(nf), rs(nc);
+        for (int i = 0; i < nf; ++i) {
+          int lo = nc, hi = -1;
+          for (int jj = 0; jj < nc; ++jj)
+            if (P[size_t(i) * nc + jj] != 0.0) { lo = std::min(lo, jj); hi = std::max(hi, jj); }
+          ps[i] = hi < 0 ? 0 : lo;
+          wp = std::max(wp, hi - lo + 1);
+        }
+        for (int jj = 0; jj < nc; ++jj) {
+          int lo = nf, hi = -1;
+          for (int i = 0; i < nf; ++i)
+            if (P[size_t(i) * nc + jj] != 0.0) { lo = std::min(lo, i); hi = std::max(hi, i); }
+          rs[jj] = hi < 0 ? 0 : lo;
+          wr = std::max(wr, hi - lo + 1);
+        }
+        std::vector<double> pw(size_t(nf) * wp, 0.0), rw(size_t(nc) * wr, 0.0);
+        for (int i = 0; i < nf; ++i)
+          for (int a = 0; a < wp && ps[i] + a < nc; ++a) pw[size_t(i) * wp + a] = P[size_t(i) * nc + ps[i] + a];
+        for (int jj = 0; jj < nc; ++jj)
+          for (int a = 0; a < wr && rs[jj] + a < nf; ++a) rw[size_t(jj) * wr + a] = P[size_t(rs[jj] + a) * nc + jj];
+        ptabs[key] = {c->mem.upload(rw, s), c->mem.upload(rs, s), c->mem.upload(pw, s), c->mem.upload(ps, s),
+                      (void*)(intptr_t)wr, (void*)(intptr_t)wp};
+      }
+      return ptabs[key];
+    };
+    std::vector<Xfer1D> rp[3], pp[3];
+    int64_t tAsz = 0, tBsz = 0;
+    for (int k = 0; k < K; ++k) {
+      const PatchDev &Pf = L.pd_h[k], &Pc = C.pd_h[k];
+      // restriction: dims go fine -> coarse one at a time: shape after pass j has coarse
+      // sizes in directions <= j
+      int shp[3];
+      for (int j = 0; j < 3; ++j) shp[j] = Pf.n[j];
+      int64_t in_off = Pf.off;
+      double* bufs[2] = {nullptr, nullptr};
+      (void)bufs;
+      for (int j = 0; j < d; ++j) {
+        auto& tb = tables(Pc.m[j], Pc.p[j]);
+        Xfer1D x{};
+        x.outer = 1;
+        for (int i = 0; i < j; ++i) x.outer *= shp[i];
+        x.inner = 1;
+        for (int i = j + 1; i < d; ++i) x.inner *= shp[i];
+        x.nin = Pf.n[j];
+        x.nout = Pc.n[j];
+        x.width = int((intptr_t)tb[4]);
+        x.wt = (const double*)tb[0];
+        x.st = (const int*)tb[1];
+        x.in_off = in_off;
+        int64_t outsz = int64_t(x.outer) * x.nout * x.inner;
+        if (j == d - 1) x.out_off = Pc.off;
+        else if (j % 2 == 0) { x.out_off = tAsz; }
+        else { x.out_off = tBsz; }
+        rp[j].push_back(x);
+        L.rmax[j] = std::max(L.rmax[j], outsz);
+        shp[j] = Pc.n[j];
+        in_off = x.out_off;
+        L.xfer_flops += 2.0 * double(outsz) * x.width;
+        L.xfer_bytes += 8.0 * double(outsz);
+        if (j < d - 1) { if (j % 2 == 0) tAsz += outsz; else tBsz += outsz; }
+      }
+    }
+    int64_t rA = tAsz, rB = tBsz;
+    tAsz = tBsz = 0;
+    for (int k = 0; k < K; ++k) {
+      const PatchDev &Pf = L.pd_h[k], &Pc = C.pd_h[k];
+      int shp[3];
+      for (int j = 0; j < 3; ++j) shp[j] = Pc.n[j];
+      int64_t in_off = Pc.off;
+      for (int j = 0; j < d; ++j) {
+        auto& tb = tables(Pc.m[j], Pc.p[j]);
+        Xfer1D x{};
+        x.outer = 1;
+        for (int i = 0; i < j; ++i) x.outer *= shp[i];
+        x.inner = 1;
+        for (int i = j + 1; i < d; ++i) x.inner *= shp[i];
+        x.nin = Pc.n[j];
+        x.nout = Pf.n[j];
+        x.width = int((intptr_t)tb[5]);
+        x.wt = (const double*)tb[2];
+        x.st = (const int*)tb[3];
+        x.in_off = in_off;
+        int64_t outsz = int64_t(x.outer) * x.nout * x.inner;
+        if (j == d - 1) x.out_off = Pf.off;
+        else if (j % 2 == 0) x.out_off = tAsz;
+        else x.out_off = tBsz;
+        pp[j].push_back(x);
+        L.pmax[j] = std::max(L.pmax[j], outsz);
+        shp[j] = Pf.n[j];
+        in_off = x.out_off;
+        L.xfer_flops += 2.0 * double(outsz) * x.width;
+        L.xfer_bytes += 8.0 * double(outsz);
+        if (j < d - 1) { if (j % 2 == 0) tAsz += outsz; else tBsz += outsz; }
+      }
+    }
+    L.tA = c->mem.alloc<double>(std::max(rA, tAsz));
+    L.tB = c->mem.alloc<double>(std::max(rB, tBsz));
+    for (int j = 0; j < d; ++j) {
+      L.rpass[j] = c->mem.upload(rp[j], s);
+      L.ppass[j] = c->mem.upload(pp[j], s);
     }
   }
   // coarse solver: dense A_0 from the level-0 bands, Cholesky, explicit inverse
@@ -619,29 +804,42 @@ void build_levels(igamg_ctx* c) {
   int64_t N0 = T0.N;
   if (N0 > 20000) throw Fail{IGAMG_ERR_UNSUPPORTED, "coarse problem too large for the dense solver"};
   int64_t bsz = 0;
-  for (int k = 0; k < K; ++k) bsz = std::max(bsz, L0.pd_h[k].band_off + (T0.off[k + 1] - T0.off[k]) *
-                                                   int64_t(2 * L0.pd_h[k].p[0] + 1) * (2 * L0.pd_h[k].p[1] + 1));
+  for (int k = 0; k < K; ++k) {
+    int64_t nb = 1;
+    for (int j = 0; j < d; ++j) nb *= 2 * L0.pd_h[k].p[j] + 1;
+    bsz = std::max(bsz, L0.pd_h[k].band_off + (T0.off[k + 1] - T0.off[k]) * nb);
+  }
   std::vector<double> hb(bsz);
   CK(cudaMemcpyAsync(hb.data(), L0.band, bsz * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   Mat A0(size_t(N0) * N0, 0.0);
   for (int k = 0; k < K; ++k) {
     const PatchDev& P = L0.pd_h[k];
-    int64_t nn = int64_t(P.n[0]) * P.n[1];
-    int w1 = 2 * P.p[1] + 1;
-    for (int i0 = 0; i0 < P.n[0]; ++i0)
-      for (int i1 = 0; i1 < P.n[1]; ++i1) {
-        int64_t gi = T0.l2g[P.off + int64_t(i0) * P.n[1] + i1];
-        if (gi < 0) continue;
-        for (int t0 = 0; t0 <= 2 * P.p[0]; ++t0)
-          for (int t1 = 0; t1 < w1; ++t1) {
-            int j0 = i0 + t0 - P.p[0], j1 = i1 + t1 - P.p[1];
-            if (j0 < 0 || j0 >= P.n[0] || j1 < 0 || j1 >= P.n[1]) continue;
-            int64_t gj = T0.l2g[P.off + int64_t(j0) * P.n[1] + j1];
-            if (gj < 0) continue;
-            A0[size_t(gi) * N0 + gj] += hb[P.band_off + int64_t(t0 * w1 + t1) * nn + int64_t(i0) * P.n[1] + i1];
-          }
+    int64_t nn = T0.off[k + 1] - T0.off[k];
+    int W[3] = {1, 1, 1}, nt = 1;
+    for (int j = 0; j < d; ++j) { W[j] = 2 * P.p[j] + 1; nt *= W[j]; }
+    for (int64_t li = 0; li < nn; ++li) {
+      int64_t gi = T0.l2g[P.off + li];
+      if (gi < 0) continue;
+      int ii[3] = {0, 0, 0};
+      int64_t r = li;
+      for (int j = d - 1; j >= 0; --j) { ii[j] = int(r % P.n[j]); r /= P.n[j]; }
+      for (int t = 0; t < nt; ++t) {
+        int tt[3] = {0, 0, 0}, rr = t;
+        for (int j = d - 1; j >= 0; --j) { tt[j] = rr % W[j]; rr /= W[j]; }
+        int64_t lj = 0;
+        bool ok = true;
+        for (int j = 0; j < d; ++j) {
+          int jj = ii[j] + tt[j] - P.p[j];
+          ok = ok && jj >= 0 && jj < P.n[j];
+          lj = lj * P.n[j] + jj;
+        }
+        if (!ok) continue;
+        int64_t gj = T0.l2g[P.off + lj];
+        if (gj < 0) continue;
+        A0[size_t(gi) * N0 + gj] += hb[P.band_off + int64_t(t) * nn + li];
       }
+    }
   }
   Mat Lc = A0;
   if (!cholesky(int(N0), Lc)) throw Fail{IGAMG_ERR_NUMERIC, "coarse Cholesky failed (A_0 not SPD)"};
@@ -672,21 +870,40 @@ void build_levels(igamg_ctx* c) {
 void residual(igamg_ctx* c, int l, const double* f, const double* u, double* r) {
   Level& L = c->lv[l];
   ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes + 8.0 * L.topo.T * (f ? 3 : 2));
-  CK(launch_band_apply_2d(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, L.band, u, f, r));
+  if (c->pd.dim == 2)
+    CK(launch_band_apply_2d(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, L.band, u, f, r));
+  else
+    CK(launch_band_apply_3d(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, L.band, u, f, r));
 }
 
 // u (=|+=) tau L^{-1} v for a distributed v (F or R of the level): patch interiors by
-// fast diagonalisation, edges by their 1D fast diagonalisation, vertices by scaling
-// (Eq. additive; the pieces are disjoint, so the sum is a set of independent blocks).
+// fast diagonalisation, faces by their 2D and edges by their 1D fast diagonalisation,
+// vertices by scaling (Eq. additive; the pieces are disjoint, so the sum is a set of
+// independent blocks).
 void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   Level& L = c->lv[l];
   const double* v = from_F ? L.F : L.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
-  run_gemm(c, from_F ? L.st0F : L.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
-  run_gemm(c, L.st1, false, false, EPI_MUL, 1.0, CLS_FD);
-  run_gemm(c, L.st2, false, false, EPI_STORE, 1.0, CLS_FD);
-  run_gemm(c, L.st3, false, true, epi, tau, CLS_FD);
+  if (c->pd.dim == 2) {
+    run_gemm(c, from_F ? L.st0F : L.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.st1, false, false, EPI_MUL, 1.0, CLS_FD);
+    run_gemm(c, L.st2, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.st3, false, true, epi, tau, CLS_FD);
+  } else if (L.nbox) {
+    {
+      ProfScope ps(c, CLS_FD, 0.0, 16.0 * L.max_box * L.nbox);
+      CK(launch_box_copy(c->stream, L.boxes, L.nbox, L.max_box, v, L.cX, 1, 1.0, 0));
+    }
+    run_gemm(c, L.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.m2f, false, false, EPI_MUL, 1.0, CLS_FD);
+    run_gemm(c, L.m0b, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.m1b, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, L.m2b, false, true, EPI_STORE, 1.0, CLS_FD);
+    ProfScope ps(c, CLS_FD, 0.0, 16.0 * L.max_box * L.nbox);
+    CK(launch_box_copy(c->stream, L.boxes, L.nbox, L.max_box, L.cX, L.U, 0, tau, add ? 1 : 0));
+  }
   if (L.n_if == 0) return;
   {
     ProfScope ps(c, CLS_IFACE, 0.0, 16.0 * L.n_if);
@@ -694,9 +911,41 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   }
   run_gemm(c, L.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
   run_gemm(c, L.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, L.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, L.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
+  run_gemm(c, L.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, L.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
   {
     ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 24.0 * L.n_if);
     CK(launch_iface_scatter(c->stream, L.n_if, L.if_ptr, L.if_idx, L.Z, L.G, L.vscale, tau, add ? 1 : 0, L.U));
+  }
+}
+
+// r_{l-1} = P_l^T r_l (distributed -> distributed), one direction at a time.
+void restrict_to_coarse(igamg_ctx* c, int l, const double* rf) {
+  Level& L = c->lv[l];
+  Level& C = c->lv[l - 1];
+  const int d = c->pd.dim, K = c->pd.K;
+  ProfScope pr(c, CLS_TRANSFER, L.xfer_flops / 3, L.xfer_bytes / 3, d);
+  const double* in = rf;
+  for (int j = 0; j < d; ++j) {
+    double* out = j == d - 1 ? C.F : (j % 2 == 0 ? L.tA : L.tB);
+    CK(launch_transfer_1d(c->stream, L.rpass[j], K, L.rmax[j], in, out, 0, j == d - 1 ? C.l2g : nullptr));
+    in = out;
+  }
+}
+
+// u_l += P_l u_{l-1} (accumulated -> accumulated).
+void prolong_add(igamg_ctx* c, int l) {
+  Level& L = c->lv[l];
+  Level& C = c->lv[l - 1];
+  const int d = c->pd.dim, K = c->pd.K;
+  ProfScope pp(c, CLS_TRANSFER, 2 * L.xfer_flops / 3, 2 * L.xfer_bytes / 3, d);
+  const double* in = C.U;
+  for (int j = 0; j < d; ++j) {
+    double* out = j == d - 1 ? L.U : (j % 2 == 0 ? L.tA : L.tB);
+    CK(launch_transfer_1d(c->stream, L.ppass[j], K, L.pmax[j], in, out, j == d - 1 ? 1 : 0, nullptr));
+    in = out;
   }
 }
 
@@ -719,20 +968,13 @@ void multigrid(igamg_ctx* c, int l, bool zero_init) {
     }
   }
   residual(c, l, L.F, L.U, L.R);
-  Level& C = c->lv[l - 1];
-  {
-    ProfScope pr(c, CLS_TRANSFER, L.xfer_flops, L.xfer_bytes, 2);
-    CK(launch_restrict_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, L.R, L.ttmp, C.F, C.l2g, C.topo.T));
-  }
+  restrict_to_coarse(c, l, L.R);
   if (l == 1) {
     coarse_solve(c);
   } else {
     for (int j = 0; j < mu; ++j) multigrid(c, l - 1, j == 0);
   }
-  {
-    ProfScope pp(c, CLS_TRANSFER, 2.0 * L.xfer_flops, 2.0 * L.xfer_bytes, 2);
-    CK(launch_prolong_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, C.U, L.ttmp, L.U));
-  }
+  prolong_add(c, l);
   for (int i = 0; i < nu; ++i) {
     residual(c, l, L.F, L.U, L.R);
     smooth(c, l, false, true);
@@ -978,7 +1220,7 @@ igamg_status igamg_restrict(igamg_ctx* c, int level, const double* r, double* rc
     Level& L = c->lv[l];
     Level& C = c->lv[l - 1];
     to_dist(c, l, r, L.R);
-    CK(launch_restrict_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, L.R, L.ttmp, C.F, C.l2g, C.topo.T));
+    restrict_to_coarse(c, l, L.R);
     from_dist(c, l - 1, C.F, rc);
     return IGAMG_OK;
   });
@@ -993,7 +1235,7 @@ igamg_status igamg_prolong(igamg_ctx* c, int level, const double* uc, double* u)
     Level& C = c->lv[l - 1];
     to_acc(c, l - 1, uc, C.U);
     CK(cudaMemsetAsync(L.U, 0, L.topo.T * sizeof(double), c->stream));
-    CK(launch_prolong_2d(c->stream, L.td, c->pd.K, L.max_nf, L.max_nc, C.U, L.ttmp, L.U));
+    prolong_add(c, l);
     from_acc(c, l, L.U, u);
     return IGAMG_OK;
   });
@@ -1029,48 +1271,23 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs)
     Level& L = c->lv[Lf];
     cudaStream_t s = c->stream;
     double* mband = nullptr;
-    size_t bytes = size_t(L.band_bytes);
-    CK(cudaMallocAsync(&mband, bytes, s));
-    int64_t gmax = 0;
-    for (auto& P : L.pd_h) gmax = std::max(gmax, int64_t(P.m[0]) * (P.p[0] + 1) * P.m[1] * (P.p[1] + 1) * 4);
-    double *G = nullptr, *dcorn = nullptr;
-    CK(cudaMallocAsync(&G, gmax * sizeof(double), s));
-    CK(cudaMallocAsync(&dcorn, c->pd.corners.size() * sizeof(double), s));
-    CK(cudaMemcpyAsync(dcorn, c->pd.corners.data(), c->pd.corners.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    std::map<std::tuple<int, int>, std::vector<double*>> dt;
-    std::vector<double*> tmp_tabs;
-    for (int k = 0; k < c->pd.K; ++k) {
-      const PatchDev& P = L.pd_h[k];
-      double* tp[2][4];
-      for (int j = 0; j < 2; ++j) {
-        auto key = std::make_tuple(P.m[j], P.p[j]);
-        if (!dt.count(key)) {
-          Tables1D tb = tables_1d(P.m[j], P.p[j]);
-          std::vector<double*> v;
-          for (auto* src : {&tb.xq, &tb.wq, &tb.B, &tb.dB}) {
-            double* d = nullptr;
-            CK(cudaMallocAsync(&d, src->size() * sizeof(double), s));
-            CK(cudaMemcpyAsync(d, src->data(), src->size() * sizeof(double), cudaMemcpyHostToDevice, s));
-            v.push_back(d);
-            tmp_tabs.push_back(d);
-          }
-          CK(cudaStreamSynchronize(s));  // host tables go out of scope
-          dt[key] = v;
-        }
-        for (int q = 0; q < 4; ++q) tp[j][q] = dt[key][q];
-      }
-      CK(launch_geom_factors_2d(s, dcorn + size_t(k) * 8, P.m[0], P.m[1], P.p[0] + 1, tp[0][0], tp[0][1],
-                                tp[1][0], tp[1][1], G));
-      CK(launch_assemble_2d(s, P, G, tp[0][2], tp[0][3], tp[1][2], tp[1][3], L.l2g, 1, mband));
-    }
+    CK(cudaMallocAsync(&mband, size_t(L.band_bytes), s));
+    CK(cudaMemsetAsync(mband, 0, size_t(L.band_bytes), s));
+    size_t mark = c->mem.ptrs.size();
+    std::map<std::tuple<int, int>, Tables1D> tabs;
+    std::map<std::tuple<int, int>, DevTables> dtabs;
+    double* dcorn = c->mem.upload(c->pd.corners, s);
+    assemble_level(c, L, dtabs, tabs, dcorn, true, mband);
     to_acc(c, Lf, coef, L.U);
-    CK(launch_band_apply_2d(s, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, mband, L.U, nullptr, L.R));
+    if (c->pd.dim == 2)
+      CK(launch_band_apply_2d(s, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, mband, L.U, nullptr, L.R));
+    else
+      CK(launch_band_apply_3d(s, L.pd, c->pd.K, L.max_n, L.max_p, mband, L.U, nullptr, L.R));
     from_dist(c, Lf, L.R, rhs);
-    for (double* d : tmp_tabs) CK(cudaFreeAsync(d, s));
-    CK(cudaFreeAsync(G, s));
-    CK(cudaFreeAsync(dcorn, s));
     CK(cudaFreeAsync(mband, s));
     CK(cudaStreamSynchronize(s));
+    for (size_t i = mark; i < c->mem.ptrs.size(); ++i) cudaFree(c->mem.ptrs[i]);  // temporary tables
+    c->mem.ptrs.resize(mark);
     return IGAMG_OK;
   });
 }

@@ -32,104 +32,6 @@ __device__ double block_sum_256(double v, double* sh) {
 }
 }  // namespace
 
-// ---------------------------------------------------------------- setup: assembly
-
-__global__ void k_geom_factors_2d(const double* __restrict__ cr, int m0, int m1, int nq0, int nq1,
-                                  const double* __restrict__ xq0, const double* __restrict__ wq0,
-                                  const double* __restrict__ xq1, const double* __restrict__ wq1,
-                                  double* __restrict__ G) {
-  int Q1 = m1 * nq1;
-  int64_t total = int64_t(m0) * nq0 * Q1;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
-       q += int64_t(gridDim.x) * blockDim.x) {
-    int a = int(q / Q1), b = int(q % Q1);
-    double s = xq0[a], t = xq1[b], w = wq0[a] * wq1[b];
-    // bilinear map: corners c = c0 + 2 c1, phi_0 = 1 - x, phi_1 = x
-    double J00 = 0, J01 = 0, J10 = 0, J11 = 0;
-    for (int c = 0; c < 4; ++c) {
-      int c0 = c & 1, c1 = c >> 1;
-      double ds = c0 ? 1.0 : -1.0, dt = c1 ? 1.0 : -1.0;
-      double ps = c0 ? s : 1.0 - s, pt = c1 ? t : 1.0 - t;
-      J00 += cr[2 * c] * ds * pt;
-      J10 += cr[2 * c + 1] * ds * pt;
-      J01 += cr[2 * c] * ps * dt;
-      J11 += cr[2 * c + 1] * ps * dt;
-    }
-    double det = J00 * J11 - J01 * J10;
-    double ad = fabs(det);
-    double* g = G + 4 * q;
-    g[0] = w * (J11 * J11 + J01 * J01) / ad;
-    g[1] = -w * (J11 * J10 + J01 * J00) / ad;
-    g[2] = w * (J10 * J10 + J00 * J00) / ad;
-    g[3] = w * ad;
-  }
-}
-
-cudaError_t launch_geom_factors_2d(cudaStream_t s, const double* corners, int m0, int m1, int nq,
-                                   const double* xq0, const double* wq0, const double* xq1,
-                                   const double* wq1, double* G) {
-  k_geom_factors_2d<<<1216, 256, 0, s>>>(corners, m0, m1, nq, nq, xq0, wq0, xq1, wq1, G);
-  return cudaGetLastError();
-}
-
-// One thread per row (i0, i1) of one patch; loops over the (2p+1)^2 taps and the Gauss
-// points of the elements shared by the two supports.
-__global__ void k_assemble_2d(PatchDev pd, const double* __restrict__ G,
-                              const double* __restrict__ B0, const double* __restrict__ dB0,
-                              const double* __restrict__ B1, const double* __restrict__ dB1,
-                              const int64_t* __restrict__ l2g, int mass, double* __restrict__ band) {
-  int i1 = blockIdx.x * blockDim.x + threadIdx.x;
-  int i0 = blockIdx.y;
-  const int n0 = pd.n[0], n1 = pd.n[1], p0 = pd.p[0], p1 = pd.p[1];
-  const int m0 = pd.m[0], m1 = pd.m[1], nq0 = p0 + 1, nq1 = p1 + 1, w1 = 2 * p1 + 1;
-  if (i1 >= n1) return;
-  const int64_t nn = int64_t(n0) * n1, node = int64_t(i0) * n1 + i1;
-  const bool active = l2g[pd.off + node] >= 0;
-  const int64_t Q1 = int64_t(m1) * nq1;
-  for (int t0 = 0; t0 <= 2 * p0; ++t0)
-    for (int t1 = 0; t1 < w1; ++t1) {
-      int j0 = i0 + t0 - p0, j1 = i1 + t1 - p1;
-      double acc = 0.0;
-      if (active && j0 >= 0 && j0 < n0 && j1 >= 0 && j1 < n1) {
-        int e0lo = max(max(i0, j0) - p0, 0), e0hi = min(min(i0, j0), m0 - 1);
-        int e1lo = max(max(i1, j1) - p1, 0), e1hi = min(min(i1, j1), m1 - 1);
-        for (int e0 = e0lo; e0 <= e0hi; ++e0) {
-          int a0 = i0 - e0, b0 = j0 - e0;
-          for (int q0 = 0; q0 < nq0; ++q0) {
-            int64_t Q0 = int64_t(e0) * nq0 + q0;
-            double vi0 = B0[Q0 * (p0 + 1) + a0], di0 = dB0[Q0 * (p0 + 1) + a0];
-            double vj0 = B0[Q0 * (p0 + 1) + b0], dj0 = dB0[Q0 * (p0 + 1) + b0];
-            double f00 = di0 * dj0, f01 = di0 * vj0, f10 = vi0 * dj0, f11 = vi0 * vj0;
-            for (int e1 = e1lo; e1 <= e1hi; ++e1) {
-              int a1 = i1 - e1, b1 = j1 - e1;
-              for (int q1 = 0; q1 < nq1; ++q1) {
-                int64_t Qb = int64_t(e1) * nq1 + q1;
-                double vi1 = B1[Qb * (p1 + 1) + a1], di1 = dB1[Qb * (p1 + 1) + a1];
-                double vj1 = B1[Qb * (p1 + 1) + b1], dj1 = dB1[Qb * (p1 + 1) + b1];
-                const double* g = G + 4 * (Q0 * Q1 + Qb);
-                if (mass)
-                  acc += g[3] * f11 * vi1 * vj1;
-                else
-                  acc += g[0] * f00 * vi1 * vj1 + g[1] * (f01 * vi1 * dj1 + f10 * di1 * vj1) +
-                         g[2] * f11 * di1 * dj1;
-              }
-            }
-          }
-        }
-      }
-      band[pd.band_off + int64_t(t0 * w1 + t1) * nn + node] = acc;
-    }
-}
-
-cudaError_t launch_assemble_2d(cudaStream_t s, const PatchDev& pd, const double* G,
-                               const double* B0, const double* dB0, const double* B1,
-                               const double* dB1, const int64_t* l2g_tile, int mass,
-                               double* band) {
-  dim3 grid((pd.n[1] + 63) / 64, pd.n[0]);
-  k_assemble_2d<<<grid, 64, 0, s>>>(pd, G, B0, dB0, B1, dB1, l2g_tile, mass, band);
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- stiffness apply
 
 // y = f - A u (f != NULL) or y = A u, per patch tile; u staged in shared memory with a
@@ -346,95 +248,6 @@ cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t*
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- transfers (Sec. 3)
-
-// Restriction P^T (distributed -> distributed), direction 0 then direction 1:
-// tmp[i0c][j1] = sum_w rw0[i0c][w] rf[rs0[i0c]+w][j1];  rc[i0c][i1c] = sum_w rw1[i1c][w] tmp[i0c][rs1[i1c]+w]
-__global__ void k_restrict_a(const TransferDev* __restrict__ tds, const double* __restrict__ rf,
-                             double* __restrict__ tmp) {
-  const TransferDev td = tds[blockIdx.z];
-  int j1 = blockIdx.x * blockDim.x + threadIdx.x, i0c = blockIdx.y;
-  if (i0c >= td.nc[0] || j1 >= td.nf[1]) return;
-  const int W = td.wr[0];
-  const double* w = td.rw[0] + int64_t(i0c) * W;
-  int r0 = td.rs[0][i0c];
-  double acc = 0.0;
-  for (int a = 0; a < W; ++a) {
-    int j0 = r0 + a;
-    if (j0 < td.nf[0]) acc = fma(w[a], rf[td.off_f + int64_t(j0) * td.nf[1] + j1], acc);
-  }
-  tmp[td.off_t + int64_t(i0c) * td.nf[1] + j1] = acc;
-}
-
-__global__ void k_restrict_b(const TransferDev* __restrict__ tds, const double* __restrict__ tmp,
-                             double* __restrict__ rc, const int64_t* __restrict__ l2g_c) {
-  const TransferDev td = tds[blockIdx.z];
-  int i1c = blockIdx.x * blockDim.x + threadIdx.x, i0c = blockIdx.y;
-  if (i0c >= td.nc[0] || i1c >= td.nc[1]) return;
-  const int W = td.wr[1];
-  const double* w = td.rw[1] + int64_t(i1c) * W;
-  int r1 = td.rs[1][i1c];
-  const double* row = tmp + td.off_t + int64_t(i0c) * td.nf[1];
-  double acc = 0.0;
-  for (int a = 0; a < W; ++a) {
-    int j1 = r1 + a;
-    if (j1 < td.nf[1]) acc = fma(w[a], row[j1], acc);
-  }
-  int64_t t = td.off_c + int64_t(i0c) * td.nc[1] + i1c;
-  rc[t] = l2g_c[t] >= 0 ? acc : 0.0;
-}
-
-// Prolongation P (accumulated -> accumulated, added into uf), direction 1 then 0:
-// tmp[i0c][j1] = sum_w pw1[j1][w] uc[i0c][ps1[j1]+w];  uf[j0][j1] += sum_w pw0[j0][w] tmp[ps0[j0]+w][j1]
-__global__ void k_prolong_a(const TransferDev* __restrict__ tds, const double* __restrict__ uc,
-                            double* __restrict__ tmp) {
-  const TransferDev td = tds[blockIdx.z];
-  int j1 = blockIdx.x * blockDim.x + threadIdx.x, i0c = blockIdx.y;
-  if (i0c >= td.nc[0] || j1 >= td.nf[1]) return;
-  const int W = td.wp[1];
-  const double* w = td.pw[1] + int64_t(j1) * W;
-  int c1 = td.ps[1][j1];
-  const double* row = uc + td.off_c + int64_t(i0c) * td.nc[1];
-  double acc = 0.0;
-  for (int a = 0; a < W; ++a) {
-    int i1c = c1 + a;
-    if (i1c < td.nc[1]) acc = fma(w[a], row[i1c], acc);
-  }
-  tmp[td.off_t + int64_t(i0c) * td.nf[1] + j1] = acc;
-}
-
-__global__ void k_prolong_b(const TransferDev* __restrict__ tds, const double* __restrict__ tmp,
-                            double* __restrict__ uf) {
-  const TransferDev td = tds[blockIdx.z];
-  int j1 = blockIdx.x * blockDim.x + threadIdx.x, j0 = blockIdx.y;
-  if (j0 >= td.nf[0] || j1 >= td.nf[1]) return;
-  const int W = td.wp[0];
-  const double* w = td.pw[0] + int64_t(j0) * W;
-  int c0 = td.ps[0][j0];
-  double acc = 0.0;
-  for (int a = 0; a < W; ++a) {
-    int i0c = c0 + a;
-    if (i0c < td.nc[0]) acc = fma(w[a], tmp[td.off_t + int64_t(i0c) * td.nf[1] + j1], acc);
-  }
-  uf[td.off_f + int64_t(j0) * td.nf[1] + j1] += acc;
-}
-
-cudaError_t launch_restrict_2d(cudaStream_t s, const TransferDev* td, int K, int max_nf,
-                               int max_nc, const double* rf, double* tmp, double* rc,
-                               const int64_t* l2g_c, int64_t Tc) {
-  (void)Tc;
-  k_restrict_a<<<dim3((max_nf + 127) / 128, max_nc, K), 128, 0, s>>>(td, rf, tmp);
-  k_restrict_b<<<dim3((max_nc + 127) / 128, max_nc, K), 128, 0, s>>>(td, tmp, rc, l2g_c);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_prolong_2d(cudaStream_t s, const TransferDev* td, int K, int max_nf,
-                              int max_nc, const double* uc, double* tmp, double* uf) {
-  k_prolong_a<<<dim3((max_nf + 127) / 128, max_nc, K), 128, 0, s>>>(td, uc, tmp);
-  k_prolong_b<<<dim3((max_nf + 127) / 128, max_nf, K), 128, 0, s>>>(td, tmp, uf);
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- coarse solve (Sec. 4)
 
 __global__ void k_coarse_solve(int64_t N0, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
@@ -588,6 +401,335 @@ cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, double* p, con
 
 cudaError_t launch_axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y) {
   k_axpby<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
+}  // namespace igamg
+
+// ================================================================ dimension-generic kernels
+
+namespace igamg {
+
+// ---------------------------------------------------------------- element assembly
+
+// Element matrices of the patch form a_k (Eq. model:bil) by sum factorisation over the
+// Gauss points of one element, added into the band storage.  Elements of one colour
+// (e_j mod (p+1) fixed in every direction) share no row, so a colour is assembled without
+// atomics and the summation order is fixed.  One block (128 threads) per element.
+// Geometry factors are evaluated on the fly from the multilinear map.
+template <int D>
+__global__ void __launch_bounds__(128) k_assemble_elem(ElemAsm ea) {
+  constexpr int NC = 1 << D;
+  extern __shared__ double sm[];
+  const int P = ea.p + 1, Q = ea.p + 1;
+  int PD = 1, QD = 1;
+  for (int j = 0; j < D; ++j) { PD *= P; QD *= Q; }
+  // element index of this block within the colour
+  int e[3] = {0, 0, 0};
+  {
+    int64_t r = blockIdx.x;
+    for (int j = D - 1; j >= 0; --j) {
+      int cnt = (ea.m[j] - ea.color[j] + P - 1) / P;
+      e[j] = ea.color[j] + P * int(r % cnt);
+      r /= cnt;
+    }
+  }
+  // shared layout
+  double* Fv = sm;                      // [D][Q][P]
+  double* Fd = Fv + D * Q * P;          // [D][Q][P]
+  double* Cq = Fd + D * Q * P;          // [D*D or 1][QD]
+  const int nterm = ea.mass ? 1 : D * D;
+  double* A = Cq + nterm * QD;          // [PD][PD]
+  double* S1 = A + PD * PD;             // [Q][P^2]^(D-1) ... sized by host
+  double* S2 = S1 + Q * (D == 3 ? P * P * P * P : P * P);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < D * Q * P; i += blockDim.x) {
+    int j = i / (Q * P), qa = i % (Q * P);
+    const double* Bt = ea.B[j] + int64_t(e[j]) * Q * P;
+    const double* dBt = ea.dB[j] + int64_t(e[j]) * Q * P;
+    Fv[i] = Bt[qa];
+    Fd[i] = dBt[qa];
+  }
+  for (int i = tid; i < PD * PD; i += blockDim.x) A[i] = 0.0;
+  // geometry factors at the element's Gauss points
+  for (int q = tid; q < QD; q += blockDim.x) {
+    int qi[3] = {0, 0, 0};
+    int r = q;
+    for (int j = D - 1; j >= 0; --j) { qi[j] = r % Q; r /= Q; }
+    double xi[3], w = 1.0;
+    for (int j = 0; j < D; ++j) {
+      xi[j] = ea.xq[j][e[j] * Q + qi[j]];
+      w *= ea.wq[j][e[j] * Q + qi[j]];
+    }
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int c = 0; c < NC; ++c)
+      for (int j = 0; j < D; ++j) {
+        double f = ((c >> j) & 1) ? 1.0 : -1.0;
+        for (int i = 0; i < D; ++i)
+          if (i != j) f *= ((c >> i) & 1) ? xi[i] : 1.0 - xi[i];
+        for (int a = 0; a < D; ++a) J[a][j] += f * ea.corners[c * D + a];
+      }
+    double det, Ji[3][3];
+    if (D == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+      Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+    } else {
+      double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      Ji[0][0] = c00 / det;
+      Ji[1][0] = c01 / det;
+      Ji[2][0] = c02 / det;
+      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    }
+    double ad = fabs(det);
+    if (ea.mass) {
+      Cq[q] = w * ad;
+    } else {
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+          double s = 0.0;
+          for (int i = 0; i < D; ++i) s += Ji[a][i] * Ji[b][i];  // (J^{-1} J^{-T})_ab
+          Cq[(a * D + b) * QD + q] = w * ad * s;
+        }
+    }
+  }
+  __syncthreads();
+  // sum factorisation, term by term: F_j[q][a][b] = X_j(a, q) Y_j(b, q) with X/Y the value
+  // or the derivative table depending on whether j is the derivative direction of the
+  // test / trial function.
+  for (int term = 0; term < nterm; ++term) {
+    const int al = ea.mass ? -1 : term / D, be = ea.mass ? -1 : term % D;
+    const double* C = Cq + term * QD;
+    const double* X[3];
+    const double* Y[3];
+    for (int j = 0; j < D; ++j) {
+      X[j] = (j == al ? Fd : Fv) + j * Q * P;
+      Y[j] = (j == be ? Fd : Fv) + j * Q * P;
+    }
+    const int P2 = P * P;
+    if (D == 2) {
+      // S1[q0][a1 b1] = sum_q1 C[q0 q1] X1[q1 a1] Y1[q1 b1]
+      for (int i = tid; i < Q * P2; i += blockDim.x) {
+        int q0 = i / P2, ab = i % P2, a1 = ab / P, b1 = ab % P;
+        double s = 0.0;
+        for (int q1 = 0; q1 < Q; ++q1) s += C[q0 * Q + q1] * X[1][q1 * P + a1] * Y[1][q1 * P + b1];
+        S1[i] = s;
+      }
+      __syncthreads();
+      // A[(a0 a1),(b0 b1)] += sum_q0 S1[q0][a1 b1] X0[q0 a0] Y0[q0 b0]
+      for (int i = tid; i < PD * PD; i += blockDim.x) {
+        int row = i / PD, col = i % PD;
+        int a0 = row / P, a1 = row % P, b0 = col / P, b1 = col % P;
+        double s = 0.0;
+        for (int q0 = 0; q0 < Q; ++q0) s += S1[q0 * P2 + a1 * P + b1] * X[0][q0 * P + a0] * Y[0][q0 * P + b0];
+        A[i] += s;
+      }
+      __syncthreads();
+    } else {
+      const int P4 = P2 * P2;
+      // S2[q0 q1][a2 b2] = sum_q2 C[q0 q1 q2] X2[q2 a2] Y2[q2 b2]
+      for (int i = tid; i < Q * Q * P2; i += blockDim.x) {
+        int qq = i / P2, ab = i % P2, a2 = ab / P, b2 = ab % P;
+        double s = 0.0;
+        for (int q2 = 0; q2 < Q; ++q2) s += C[qq * Q + q2] * X[2][q2 * P + a2] * Y[2][q2 * P + b2];
+        S2[i] = s;
+      }
+      __syncthreads();
+      // S1[q0][a1 b1 a2 b2] = sum_q1 S2[q0 q1][a2 b2] X1[q1 a1] Y1[q1 b1]
+      for (int i = tid; i < Q * P4; i += blockDim.x) {
+        int q0 = i / P4, rem = i % P4, ab1 = rem / P2, ab2 = rem % P2, a1 = ab1 / P, b1 = ab1 % P;
+        double s = 0.0;
+        for (int q1 = 0; q1 < Q; ++q1) s += S2[(q0 * Q + q1) * P2 + ab2] * X[1][q1 * P + a1] * Y[1][q1 * P + b1];
+        S1[i] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < PD * PD; i += blockDim.x) {
+        int row = i / PD, col = i % PD;
+        int a0 = row / P2, a1 = (row / P) % P, a2 = row % P;
+        int b0 = col / P2, b1 = (col / P) % P, b2 = col % P;
+        int rem = ((a1 * P + b1) * P + a2) * P + b2;
+        double s = 0.0;
+        for (int q0 = 0; q0 < Q; ++q0) s += S1[q0 * P4 + rem] * X[0][q0 * P + a0] * Y[0][q0 * P + b0];
+        A[i] += s;
+      }
+      __syncthreads();
+    }
+  }
+  // add the element matrix into the band rows (Dirichlet rows stay zero)
+  const int W = 2 * ea.p + 1;
+  for (int i = tid; i < PD * PD; i += blockDim.x) {
+    int row = i / PD, col = i % PD;
+    int a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    int r = row, c = col;
+    for (int j = D - 1; j >= 0; --j) { a[j] = r % P; r /= P; b[j] = c % P; c /= P; }
+    int64_t node = 0;
+    int t = 0;
+    for (int j = 0; j < D; ++j) {
+      node = node * ea.n[j] + (e[j] + a[j]);
+      t = t * W + (b[j] - a[j] + ea.p);
+    }
+    if (ea.l2g[ea.off + node] < 0) continue;
+    ea.band[ea.band_off + int64_t(t) * ea.nn + node] += A[i];
+  }
+}
+
+size_t elem_asm_smem(int D, int p, bool mass) {
+  int P = p + 1, PD = 1, QD = 1;
+  for (int j = 0; j < D; ++j) { PD *= P; QD *= P; }
+  size_t n = 2 * D * P * P + (mass ? 1 : D * D) * QD + PD * PD;
+  n += (D == 3) ? (P * P * P * P * P + P * P * P * P) : P * P * P;
+  return n * sizeof(double);
+}
+
+cudaError_t launch_assemble_elem(cudaStream_t s, const ElemAsm& base) {
+  const int D = base.dim, P = base.p + 1;
+  size_t smem = elem_asm_smem(D, base.p, base.mass);
+  cudaError_t e;
+  if (D == 2) e = cudaFuncSetAttribute(k_assemble_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  else e = cudaFuncSetAttribute(k_assemble_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int ncol = 1;
+  for (int j = 0; j < D; ++j) ncol *= P;
+  for (int col = 0; col < ncol; ++col) {
+    ElemAsm ea = base;
+    int r = col;
+    int64_t cnt = 1;
+    for (int j = D - 1; j >= 0; --j) {
+      ea.color[j] = r % P;
+      r /= P;
+      int c = (ea.m[j] - ea.color[j] + P - 1) / P;
+      cnt *= c > 0 ? c : 0;
+    }
+    if (cnt == 0) continue;
+    if (D == 2) k_assemble_elem<2><<<unsigned(cnt), 128, smem, s>>>(ea);
+    else k_assemble_elem<3><<<unsigned(cnt), 128, smem, s>>>(ea);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- 3D stiffness apply
+
+namespace {
+constexpr int BX3 = 32, BY3 = 4, BZ3 = 2;
+}
+
+__global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDev* __restrict__ pds,
+                                                                   const double* __restrict__ band,
+                                                                   const double* __restrict__ u,
+                                                                   const double* __restrict__ f,
+                                                                   double* __restrict__ y, int tiles1) {
+  extern __shared__ double su[];
+  const PatchDev pd = pds[blockIdx.z];
+  const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2], p0 = pd.p[0], p1 = pd.p[1], p2 = pd.p[2];
+  const int i0b = (blockIdx.y / tiles1) * BZ3, i1b = (blockIdx.y % tiles1) * BY3, i2b = blockIdx.x * BX3;
+  if (i0b >= n0 || i1b >= n1 || i2b >= n2) return;
+  const int H0 = BZ3 + 2 * p0, H1 = BY3 + 2 * p1, H2 = BX3 + 2 * p2;
+  const double* ut = u + pd.off;
+  const int tid = (threadIdx.z * BY3 + threadIdx.y) * BX3 + threadIdx.x;
+  for (int idx = tid; idx < H0 * H1 * H2; idx += BX3 * BY3 * BZ3) {
+    int a = idx / (H1 * H2), rem = idx % (H1 * H2), b = rem / H2, c = rem % H2;
+    int g0 = i0b - p0 + a, g1 = i1b - p1 + b, g2 = i2b - p2 + c;
+    su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1 && g2 >= 0 && g2 < n2)
+                  ? ut[(int64_t(g0) * n1 + g1) * n2 + g2] : 0.0;
+  }
+  __syncthreads();
+  const int i0 = i0b + threadIdx.z, i1 = i1b + threadIdx.y, i2 = i2b + threadIdx.x;
+  if (i0 >= n0 || i1 >= n1 || i2 >= n2) return;
+  const int64_t nn = int64_t(n0) * n1 * n2, node = (int64_t(i0) * n1 + i1) * n2 + i2;
+  const double* bp = band + pd.band_off + node;
+  const int w1 = 2 * p1 + 1, w2 = 2 * p2 + 1;
+  double acc = 0.0;
+  int t = 0;
+  for (int t0 = 0; t0 <= 2 * p0; ++t0)
+    for (int t1 = 0; t1 < w1; ++t1) {
+      const double* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
+      for (int t2 = 0; t2 < w2; ++t2, ++t) acc = fma(__ldg(bp + int64_t(t) * nn), srow[t2], acc);
+    }
+  y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
+}
+
+cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
+                                 const double* band, const double* u, const double* f, double* y) {
+  int t1 = (max_n[1] + BY3 - 1) / BY3, t0 = (max_n[0] + BZ3 - 1) / BZ3;
+  dim3 grid((max_n[2] + BX3 - 1) / BX3, t0 * t1, K);
+  size_t sm = sizeof(double) * (BZ3 + 2 * max_p) * (BY3 + 2 * max_p) * (BX3 + 2 * max_p);
+  cudaError_t e = cudaFuncSetAttribute(k_band_apply_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  if (e != cudaSuccess) return e;
+  k_band_apply_3d<<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- 1D transfer along one direction
+
+// out[i_<j, o, i_>j] (=|+=) sum_w wt[o][w] in[i_<j, st[o] + w, i_>j] for one patch per
+// blockIdx.y; shapes/offsets from Xfer1D.  Restriction uses the column band of P_l,
+// prolongation its row band.  mask: zero outputs whose node is eliminated (coarse
+// Dirichlet after restriction).
+__global__ void k_transfer_1d(const Xfer1D* __restrict__ xs, const double* __restrict__ in,
+                              double* __restrict__ out, int add, const int64_t* __restrict__ mask) {
+  const Xfer1D x = xs[blockIdx.y];
+  const int64_t total = int64_t(x.outer) * x.nout * x.inner;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t oi = i / (int64_t(x.nout) * x.inner), rem = i % (int64_t(x.nout) * x.inner);
+    int o = int(rem / x.inner), ii = int(rem % x.inner);
+    const double* w = x.wt + int64_t(o) * x.width;
+    int s0 = x.st[o];
+    const double* src = in + x.in_off + (oi * x.nin) * x.inner + ii;
+    double acc = 0.0;
+    for (int a = 0; a < x.width; ++a) {
+      int k = s0 + a;
+      if (k < x.nin) acc = fma(w[a], src[int64_t(k) * x.inner], acc);
+    }
+    int64_t t = x.out_off + i;
+    if (mask && mask[t] < 0) acc = 0.0;
+    out[t] = add ? out[t] + acc : acc;
+  }
+}
+
+cudaError_t launch_transfer_1d(cudaStream_t s, const Xfer1D* xs, int npatch, int64_t max_out,
+                               const double* in, double* out, int add, const int64_t* mask) {
+  int64_t g = (max_out + 255) / 256;
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  k_transfer_1d<<<dim3(unsigned(g), npatch), 256, 0, s>>>(xs, in, out, add, mask);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- interior box gather/scatter
+
+// Compact copy of every patch-interior box (3D FD works on compact tensors) and the
+// scatter of tau * Z back into the boxes.
+__global__ void k_box_copy(const BoxDev* __restrict__ boxes, const double* __restrict__ src, double* __restrict__ dst,
+                           int to_compact, double tau, int add) {
+  const BoxDev b = boxes[blockIdx.y];
+  const int64_t total = int64_t(b.len[0]) * b.len[1] * b.len[2];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t i0 = i / (int64_t(b.len[1]) * b.len[2]), rem = i % (int64_t(b.len[1]) * b.len[2]);
+    int i1 = int(rem / b.len[2]), i2 = int(rem % b.len[2]);
+    int64_t t = b.tile_off + ((i0 + b.lo[0]) * b.n[1] + (i1 + b.lo[1])) * int64_t(b.n[2]) + (i2 + b.lo[2]);
+    int64_t c = b.compact_off + i;
+    if (to_compact) dst[c] = src[t];
+    else dst[t] = add ? fma(tau, src[c], dst[t]) : tau * src[c];
+  }
+}
+
+cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const double* src,
+                            double* dst, int to_compact, double tau, int add) {
+  if (nbox <= 0) return cudaSuccess;
+  int64_t g = (max_box + 255) / 256;
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  k_box_copy<<<dim3(unsigned(g), nbox), 256, 0, s>>>(boxes, src, dst, to_compact, tau, add);
   return cudaGetLastError();
 }
 

@@ -15,17 +15,6 @@ struct PatchDev {
   int m[3];          // intervals per direction
 };
 
-// Transfer descriptor (fine level l, coarse level l-1) of one patch; 1D tables per direction.
-struct TransferDev {
-  int64_t off_f, off_c, off_t;  // fine/coarse tile offsets, temp offset
-  int nf[3], nc[3];
-  const double* rw[3];  // restriction weights [nc * wr] (column j of P: fine rows rs[j]..)
-  const int* rs[3];     // [nc] first fine row of column j
-  const double* pw[3];  // prolongation weights [nf * wp] (row i of P: coarse cols ps[i]..)
-  const int* ps[3];     // [nf]
-  int wr[3], wp[3];
-};
-
 // Batched GEMM descriptor: C = op(A) op(B), M x N with inner dimension K (row-major).
 struct GemmDesc {
   const double* A;
@@ -38,19 +27,46 @@ struct GemmDesc {
 
 enum GemmEpilogue { EPI_STORE = 0, EPI_MUL = 1, EPI_ROWSCALE = 2, EPI_ASSIGN = 3, EPI_ADD = 4, EPI_COLSCALE = 5 };
 
-// Geometry factors at all Gauss points of a patch: 4 values per point,
-// w|detJ|(J^{-1}J^{-T})_{00,01,11} and w|detJ| (2D).
-cudaError_t launch_geom_factors_2d(cudaStream_t s, const double* corners, int m0, int m1, int nq,
-                                   const double* xq0, const double* wq0, const double* xq1,
-                                   const double* wq1, double* G);
-// Band coefficients of the patch stiffness (mass=0) or geometry mass (mass=1) matrix.
-cudaError_t launch_assemble_2d(cudaStream_t s, const PatchDev& pd, const double* G,
-                               const double* B0, const double* dB0, const double* B1,
-                               const double* dB1, const int64_t* l2g_tile, int mass,
-                               double* band);
+// Element-by-element assembly of one patch (any colour loop inside the launcher).
+struct ElemAsm {
+  int dim, p, mass;
+  int n[3], m[3], color[3];
+  int64_t off, band_off, nn;
+  const double* corners;       // [2^d * d] of this patch
+  const double* xq[3];         // [m * (p+1)] Gauss points per element
+  const double* wq[3];
+  const double* B[3];          // [m][p+1 q][p+1 a]
+  const double* dB[3];
+  const int64_t* l2g;          // level l2g (tile indexed)
+  double* band;
+};
+cudaError_t launch_assemble_elem(cudaStream_t s, const ElemAsm& ea);
+size_t elem_asm_smem(int D, int p, bool mass);
 
-// y = beta*f - A u per tile (f may be NULL, then y = -A u if beta... see launcher), i.e.
-// residual (f != NULL) or apply (f == NULL, y = A u).
+// 3D band apply (same contract as the 2D one).
+cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
+                                 const double* band, const double* u, const double* f, double* y);
+
+// One direction of a tensor transfer: out has `nout` entries along the direction, in has
+// `nin`; outer/inner are the products of the sizes before/after it.
+struct Xfer1D {
+  int64_t in_off, out_off;
+  int outer, inner, nin, nout, width;
+  const double* wt;  // [nout][width]
+  const int* st;     // [nout]
+};
+cudaError_t launch_transfer_1d(cudaStream_t s, const Xfer1D* xs, int npatch, int64_t max_out,
+                               const double* in, double* out, int add, const int64_t* mask);
+
+// Interior box of a tile <-> compact tensor.
+struct BoxDev {
+  int64_t tile_off, compact_off;
+  int n[3], lo[3], len[3];
+};
+cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const double* src,
+                            double* dst, int to_compact, double tau, int add);
+
+// y = f - A u per tile (residual) or y = A u when f == NULL (apply).
 cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0,
                                  int max_n1, int max_p, const double* band, const double* u,
                                  const double* f, double* y);
@@ -68,12 +84,6 @@ cudaError_t launch_iface_gather(cudaStream_t s, int64_t n_nodes, const int64_t* 
 cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t* ptr,
                                  const int64_t* idx, const double* Z, const double* G,
                                  const double* vscale, double tau, int add, double* u);
-
-cudaError_t launch_restrict_2d(cudaStream_t s, const TransferDev* td, int K, int max_nf,
-                               int max_nc, const double* rf, double* tmp, double* rc,
-                               const int64_t* l2g_c, int64_t Tc);
-cudaError_t launch_prolong_2d(cudaStream_t s, const TransferDev* td, int K, int max_nf,
-                              int max_nc, const double* uc, double* tmp, double* uf);
 
 // Coarse solve: x_copies = A0inv * (sum of copies of f) for the N0 level-0 dofs.
 cudaError_t launch_coarse_solve(cudaStream_t s, int64_t N0, const int64_t* ptr,

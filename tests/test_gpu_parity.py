@@ -23,6 +23,10 @@ def cases():
         "grid2x2_p5_m32_ragged": lambda: workloads.perturbed_grid_2d(2, 5, 32, 4, 7),
         "single_patch_p2_m64": lambda: workloads.perturbed_grid_2d(1, 2, 64, 7, 3),
         "grid2x2_p1_m8": lambda: workloads.perturbed_grid_2d(2, 1, 8, 4, 5),
+        "cube_p2_m4": lambda: workloads.perturbed_cube_3d(2, 2, 4, 3, 3),
+        "cube_p3_m8": lambda: workloads.perturbed_cube_3d(2, 3, 8, 4, 3),
+        "fichera_p2_m4": lambda: workloads.fichera_corner(1, 2, 4, 3),
+        "cube_p4_m4_single": lambda: workloads.perturbed_cube_3d(1, 4, 4, 3, 5),
     }
 
 
