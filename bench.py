@@ -144,8 +144,11 @@ def run_ours(args, rank, world, local_rank):
         tdist.init_process_group("nccl")
     stream = torch.cuda.Stream(device=dev)
     pr = workloads.CONFIGS[args.workload]()
+    prec = {"fp64": igamg.IGAMG_FP64, "fp32": igamg.IGAMG_FP32, "bf16": igamg.IGAMG_BF16}[args.precision]
+    opts = igamg.igamg_default_options()
+    opts.precision = prec
     with torch.cuda.stream(stream):
-        ctx = igamg.Context(pr, stream=stream)
+        ctx = igamg.Context(pr, opts, stream=stream)
         N = ctx.num_dofs()
         coef = torch.tensor(workloads.rhs_coefficients(N, 2), device=dev)
         b = torch.empty(N, dtype=torch.float64, device=dev)
@@ -175,7 +178,17 @@ def run_ours(args, rank, world, local_rank):
         prof = ctx.profile_read()
         ctx.profile_enable(False)
         iters = res.iters
+        outer = res.outer_iters
         relres = res.relres
+        err_vs_fp64 = None
+        if prec != igamg.IGAMG_FP64:
+            # error of the mixed-precision solution against the FP64 GPU solution (the FP64
+            # path is the one parity-tested against the FP64 oracle)
+            ref = igamg.Context(pr, stream=stream)
+            xr = torch.zeros_like(x)
+            ref.solve(b, xr, 1e-12)
+            err_vs_fp64 = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
+            ref.free()
         if dist:
             t = torch.tensor([ms_total], device=dev)
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
@@ -218,10 +231,12 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 (f64 refinement)", "bf16": "bf16 bands, f32 (f64 refinement)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_DESC if args.workload == WORKLOAD
-                   else args.workload, "dofs": N, "iters": iters,
+                   else args.workload, "dofs": N, "iters": iters, "outer_iters": outer,
+                   "precision": args.precision, "rel_err_vs_fp64_solution": err_vs_fp64,
                    "relres": relres, "tol": TOL, "l2": "inputs larger than L2 (operator bands 0.94 GB)",
                    "parallelism": f"replicas x{world}", "setup_ms": round(setup_ms, 1),
                    "assemble_ms": round(assemble_ms, 1)},
@@ -251,7 +266,8 @@ def run_reference(args, rank):
     value = o["N"] / o["t_solve_s"] / 1e6
     out = {"metric": METRIC, "value": round(value, 6), "unit": "MDOF/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(o["t_solve_s"] * 1e3, 1),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 (f64 refinement)", "bf16": "bf16 bands, f32 (f64 refinement)"}[args.precision],
            "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "sample": sample_desc(),
                       "sample_dofs": o["N"], "iters": o["iters"]},
@@ -274,6 +290,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="key of workloads.CONFIGS")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -75,12 +75,19 @@ typedef struct {
   double sigma_scale;  /* sigma = sigma_scale * h_l^{-2} in the interior smoother      */
   int nu;              /* smoothing steps before and after the coarse correction       */
   int mu;              /* 1 = V-cycle, 2 = W-cycle (Algorithm 1)                      */
-  int max_iter;        /* PCG iteration limit                                        */
-  int precision;       /* IGAMG_FP64 (only FP64 is accepted by this version)          */
+  int max_iter;        /* PCG iteration limit (inner iterations in total for mixed)   */
+  int precision;       /* IGAMG_FP64: PCG in FP64.  IGAMG_FP32 / IGAMG_BF16: FP64
+                          iterative refinement around a PCG whose vectors, smoother
+                          contractions and transfers are FP32 and whose band
+                          coefficients are FP32 / BF16 (FP32 accumulation); the
+                          eigendecompositions, the refinement residual and the coarse
+                          solve stay FP64                                            */
+  double inner_tol;    /* mixed precision: relative reduction of each inner PCG (1e-4) */
 } igamg_options;
 
 typedef struct {
-  int iters;           /* PCG iterations performed                                    */
+  int iters;           /* PCG iterations performed (inner iterations for mixed)       */
+  int outer_iters;     /* FP64 refinement steps (1 for FP64)                          */
   double relres;       /* ||b - A x||_2 / ||b - A x_0||_2 at exit                      */
   double t_setup_ms;   /* igamg_setup wall time (host + device, synchronised)          */
   double t_assemble_ms;/* part of setup spent assembling the level matrices           */

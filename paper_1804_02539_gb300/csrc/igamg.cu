@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -67,10 +68,30 @@ struct Smoother1D {  // subspace-corrected mass smoother data of one direction s
   double* dU = nullptr;
 };
 
-struct GemmSet {
-  GemmDesc* d = nullptr;
+template <class T>
+struct GemmSetT {
+  GemmDescT<T>* d = nullptr;
+  std::vector<GemmDescT<T>> h;  // host copy (FP64 sets are translated into lower precision)
   int batch = 0, maxM = 0, maxN = 0;
   double flops = 0, bytes = 0;  // algorithmic work of one launch
+};
+using GemmSet = GemmSetT<double>;
+
+// Numeric data of one level in one precision: the vectors and the descriptor sets the
+// cycle launches.  FP64 data are built by the setup; lower-precision data are twins of them.
+template <class T>
+struct Num {
+  const void* band = nullptr;  // band coefficients: T, or __nv_bfloat16 when bf16 is set
+  bool bf16 = false;
+  T *F = nullptr, *U = nullptr, *R = nullptr;
+  GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
+  GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
+  T* cX = nullptr;                                  // compact 3D interior tensor
+  T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
+  GemmSetT<T> edgeA, edgeB, face0, face1, face2, face3;
+  XferT<T>* rpass[3] = {nullptr, nullptr, nullptr};
+  XferT<T>* ppass[3] = {nullptr, nullptr, nullptr};
+  T *tA = nullptr, *tB = nullptr;
 };
 
 struct Level {
@@ -80,31 +101,25 @@ struct Level {
   int max_n[3] = {1, 1, 1}, max_p = 1;
   int64_t* l2g = nullptr;
   int64_t *g2t_ptr = nullptr, *g2t = nullptr;
-  double* band = nullptr;
-  double *F = nullptr, *U = nullptr, *R = nullptr;
-  // 2D interior smoother: stage GEMMs; stage 0 reads F or R
-  GemmSet st0F, st0R, st1, st2, st3;
-  double *fdT = nullptr, *fdY = nullptr;
-  // 3D interior smoother: compact boxes and six mode products
+  double* band = nullptr;  // FP64 band coefficients
+  Num<double> n64;
+  Num<float> n32;
+  // 3D interior boxes (shared by all precisions)
   BoxDev* boxes = nullptr;
   int nbox = 0;
   int64_t max_box = 0;
-  double *cX = nullptr, *cB1 = nullptr, *cB2 = nullptr;
-  GemmSet m0f, m1f, m2f, m0b, m1b, m2b;
-  // interface pieces
+  // interface nodes (shared)
   int64_t n_if = 0;
   int64_t *if_ptr = nullptr, *if_idx = nullptr;
-  double *G = nullptr, *Z = nullptr, *Yif = nullptr, *vscale = nullptr;
-  GemmSet edgeA, edgeB;          // 1D FD of edge groups
-  GemmSet face0, face1, face2, face3;  // 2D FD of 3D faces
-  double *fT = nullptr, *fY = nullptr;
-  // transfer from level l-1 (valid for level >= 1): one descriptor array per pass
-  Xfer1D* rpass[3] = {nullptr, nullptr, nullptr};
-  Xfer1D* ppass[3] = {nullptr, nullptr, nullptr};
+  // transfer from level l-1 (valid for level >= 1): host descriptors per pass
+  std::vector<XferT<double>> rp_h[3], pp_h[3];
   int64_t rmax[3] = {0, 0, 0}, pmax[3] = {0, 0, 0};
-  double *tA = nullptr, *tB = nullptr;
   double apply_flops = 0, band_bytes = 0, xfer_flops = 0, xfer_bytes = 0;
 };
+
+template <class T> Num<T>& num(Level& L);
+template <> Num<double>& num<double>(Level& L) { return L.n64; }
+template <> Num<float>& num<float>(Level& L) { return L.n32; }
 
 }  // namespace
 
@@ -117,6 +132,13 @@ struct igamg_ctx {
   double* A0inv = nullptr;
   int64_t N0 = 0;
   double *X = nullptr, *Pv = nullptr, *W = nullptr, *Bt = nullptr, *gtmp = nullptr;
+  float *X32 = nullptr, *P32 = nullptr, *W32 = nullptr;  // inner (low-precision) PCG vectors
+  double* Rr = nullptr;                                    // FP64 residual of the refinement
+  bool low = false;                                        // low-precision numerics built
+  bool low_bf16 = false;                                   // bands stored in BF16
+  // FP64 device arrays referenced by the cycle: (base, count, constant?) for the twins
+  std::vector<std::tuple<double*, int64_t, bool>> reg;
+  std::vector<int64_t> band_count;                         // band doubles per level
   double *partials = nullptr, *scal = nullptr;
   double* h_scal = nullptr;  // pinned
   std::string err;
@@ -139,6 +161,15 @@ void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
 }  // namespace igamg
 
 namespace {
+
+double* reg_const(igamg_ctx* c, double* p, size_t n) {
+  c->reg.emplace_back(p, int64_t(n), true);
+  return p;
+}
+double* reg_work(igamg_ctx* c, double* p, int64_t n) {
+  c->reg.emplace_back(p, n, false);
+  return p;
+}
 
 enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5 };
 
@@ -186,13 +217,16 @@ void prof_collect(igamg_ctx* c) {
   c->ev_open.clear();
 }
 
-double gemm_flops(const std::vector<GemmDesc>& v) {
+template <class T>
+double gemm_flops(const std::vector<GemmDescT<T>>& v) {
   double f = 0;
   for (auto& d : v) f += 2.0 * d.M * double(d.N) * d.K;
   return f;
 }
 
-void set_gemm(igamg_ctx* c, GemmSet& gs, const std::vector<GemmDesc>& v) {
+template <class T>
+void set_gemm(igamg_ctx* c, GemmSetT<T>& gs, const std::vector<GemmDescT<T>>& v) {
+  gs.h = v;
   gs.batch = int(v.size());
   gs.maxM = gs.maxN = 0;
   for (auto& d : v) {
@@ -205,10 +239,11 @@ void set_gemm(igamg_ctx* c, GemmSet& gs, const std::vector<GemmDesc>& v) {
   for (auto& d : v) gs.bytes += 8.0 * (double(d.M) * d.K + double(d.K) * d.N + 2.0 * d.M * d.N);
 }
 
-void run_gemm(igamg_ctx* c, const GemmSet& gs, bool ta, bool tb, int epi, double alpha, int cls) {
+template <class T>
+void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, double alpha, int cls) {
   if (!gs.batch) return;
-  ProfScope ps(c, cls, gs.flops, gs.bytes);
-  CK(launch_gemm(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, alpha));
+  ProfScope ps(c, cls, gs.flops, gs.bytes * sizeof(T) / 8.0);
+  CK(launch_gemm<T>(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, T(alpha)));
 }
 
 // ---------------------------------------------------------------- setup helpers
@@ -437,7 +472,7 @@ void build_levels(igamg_ctx* c) {
     auto key = std::make_tuple(m, p, int(lo), int(hi), sigma);
     if (!scms.count(key)) scms[key] = build_scms(m, p, lo, hi, sigma);
     Smoother1D* S = &scms[key];
-    if (!S->dU) S->dU = c->mem.upload(S->U, s);
+    if (!S->dU) S->dU = reg_const(c, c->mem.upload(S->U, s), S->U.size());
     return S;
   };
   for (int l = 0; l < NL; ++l) {
@@ -470,12 +505,14 @@ void build_levels(igamg_ctx* c) {
     L.g2t_ptr = c->mem.upload(T.g2t_ptr, s);
     L.g2t = c->mem.upload(T.g2t, s);
     L.band = c->mem.alloc<double>(band_total);
-    L.F = c->mem.alloc<double>(T.T);
-    L.U = c->mem.alloc<double>(T.T);
-    L.R = c->mem.alloc<double>(T.T);
-    CK(cudaMemsetAsync(L.F, 0, T.T * sizeof(double), s));
-    CK(cudaMemsetAsync(L.U, 0, T.T * sizeof(double), s));
-    CK(cudaMemsetAsync(L.R, 0, T.T * sizeof(double), s));
+    L.n64.F = reg_work(c, c->mem.alloc<double>(T.T), T.T);
+    L.n64.U = reg_work(c, c->mem.alloc<double>(T.T), T.T);
+    L.n64.R = reg_work(c, c->mem.alloc<double>(T.T), T.T);
+    CK(cudaMemsetAsync(L.n64.F, 0, T.T * sizeof(double), s));
+    CK(cudaMemsetAsync(L.n64.U, 0, T.T * sizeof(double), s));
+    CK(cudaMemsetAsync(L.n64.R, 0, T.T * sizeof(double), s));
+    L.n64.band = L.band;
+    c->band_count.push_back(band_total);
     CK(cudaMemsetAsync(L.band, 0, band_total * sizeof(double), s));
     double ta0 = now_ms();
     assemble_level(c, L, dtabs, tabs, dcorn, false, L.band);
@@ -502,7 +539,7 @@ void build_levels(igamg_ctx* c) {
           std::vector<double> Dv(size_t(n0) * n1);
           for (int a = 0; a < n0; ++a)
             for (int b = 0; b < n1; ++b) Dv[size_t(a) * n1 + b] = 1.0 / (S[0]->mu[a] + S[1]->mu[b]);
-          dinv_cache[dk] = c->mem.upload(Dv, s);
+          dinv_cache[dk] = reg_const(c, c->mem.upload(Dv, s), Dv.size());
         }
         double* Dinv = dinv_cache[dk];
         int64_t base = fd_total;
@@ -510,26 +547,26 @@ void build_levels(igamg_ctx* c) {
         int64_t xoff = P.off + int64_t(in.lo[0]) * P.n[1] + in.lo[1];
         GemmDesc g0{S[0]->dU, nullptr, (double*)(intptr_t)base, nullptr, n0, P.n[1], n1, 0, n0, n1, n0};
         GemmDesc gF = g0, gR = g0;
-        gF.B = L.F + xoff;
-        gR.B = L.R + xoff;
+        gF.B = L.n64.F + xoff;
+        gR.B = L.n64.R + xoff;
         s0F.push_back(gF);
         s0R.push_back(gR);
         s1.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, (double*)(intptr_t)base, Dinv, n1, n1, n1, n1, n0, n1, n1});
         s2.push_back(GemmDesc{S[0]->dU, (double*)(intptr_t)base, (double*)(intptr_t)base, nullptr, n0, n1, n1, 0, n0, n1, n0});
-        s3.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, L.U + xoff, nullptr, n1, n1, P.n[1], 0, n0, n1, n1});
+        s3.push_back(GemmDesc{(double*)(intptr_t)base, S[1]->dU, L.n64.U + xoff, nullptr, n1, n1, P.n[1], 0, n0, n1, n1});
       }
-      L.fdT = c->mem.alloc<double>(fd_total);
-      L.fdY = c->mem.alloc<double>(fd_total);
-      for (auto& g : s0F) g.C = L.fdT + (intptr_t)g.C;
-      for (auto& g : s0R) g.C = L.fdT + (intptr_t)g.C;
-      for (auto& g : s1) { g.A = L.fdT + (intptr_t)g.A; g.C = L.fdY + (intptr_t)g.C; }
-      for (auto& g : s2) { g.B = L.fdY + (intptr_t)g.B; g.C = L.fdT + (intptr_t)g.C; }
-      for (auto& g : s3) g.A = L.fdT + (intptr_t)g.A;
-      set_gemm(c, L.st0F, s0F);
-      set_gemm(c, L.st0R, s0R);
-      set_gemm(c, L.st1, s1);
-      set_gemm(c, L.st2, s2);
-      set_gemm(c, L.st3, s3);
+      double* fdT = reg_work(c, c->mem.alloc<double>(fd_total), fd_total);
+      double* fdY = reg_work(c, c->mem.alloc<double>(fd_total), fd_total);
+      for (auto& g : s0F) g.C = fdT + (intptr_t)g.C;
+      for (auto& g : s0R) g.C = fdT + (intptr_t)g.C;
+      for (auto& g : s1) { g.A = fdT + (intptr_t)g.A; g.C = fdY + (intptr_t)g.C; }
+      for (auto& g : s2) { g.B = fdY + (intptr_t)g.B; g.C = fdT + (intptr_t)g.C; }
+      for (auto& g : s3) g.A = fdT + (intptr_t)g.A;
+      set_gemm(c, L.n64.st0F, s0F);
+      set_gemm(c, L.n64.st0R, s0R);
+      set_gemm(c, L.n64.st1, s1);
+      set_gemm(c, L.n64.st2, s2);
+      set_gemm(c, L.n64.st3, s3);
     } else {
       // 3D: compact boxes, three mode products forward, Dinv, three backward
       std::vector<BoxDev> boxes;
@@ -556,7 +593,7 @@ void build_levels(igamg_ctx* c) {
             for (int b = 0; b < pe.n1; ++b)
               for (int q = 0; q < pe.n2; ++q)
                 Dv[(size_t(a) * pe.n1 + b) * pe.n2 + q] = 1.0 / (pe.S[0]->mu[a] + pe.S[1]->mu[b] + pe.S[2]->mu[q]);
-          dinv_cache[dk] = c->mem.upload(Dv, s);
+          dinv_cache[dk] = reg_const(c, c->mem.upload(Dv, s), Dv.size());
         }
         pe.Dinv = dinv_cache[dk];
         pe.base = tot;
@@ -576,12 +613,12 @@ void build_levels(igamg_ctx* c) {
       }
       L.nbox = int(boxes.size());
       L.boxes = c->mem.upload(boxes, s);
-      L.cX = c->mem.alloc<double>(tot);
-      L.cB1 = c->mem.alloc<double>(tot);
-      L.cB2 = c->mem.alloc<double>(tot);
+      L.n64.cX = reg_work(c, c->mem.alloc<double>(tot), tot);
+      double* cB1 = reg_work(c, c->mem.alloc<double>(tot), tot);
+      double* cB2 = reg_work(c, c->mem.alloc<double>(tot), tot);
       for (const Pend& pe : pend) {
         int n0 = pe.n0, n1 = pe.n1, n2 = pe.n2, n12 = n1 * n2;
-        double *X = L.cX + pe.base, *B1 = L.cB1 + pe.base, *B2 = L.cB2 + pe.base;
+        double *X = L.n64.cX + pe.base, *B1 = cB1 + pe.base, *B2 = cB2 + pe.base;
         const double *U0 = pe.S[0]->dU, *U1 = pe.S[1]->dU, *U2 = pe.S[2]->dU;
         f0.push_back(GemmDesc{U0, X, B1, nullptr, n0, n12, n12, 0, n0, n12, n0});
         for (int a = 0; a < n0; ++a)
@@ -592,12 +629,12 @@ void build_levels(igamg_ctx* c) {
           b1.push_back(GemmDesc{U1, B2 + int64_t(a) * n12, B1 + int64_t(a) * n12, nullptr, n1, n2, n2, 0, n1, n2, n1});
         b2.push_back(GemmDesc{B1, U2, X, nullptr, n2, n2, n2, 0, n0 * n1, n2, n2});
       }
-      set_gemm(c, L.m0f, f0);
-      set_gemm(c, L.m1f, f1);
-      set_gemm(c, L.m2f, f2);
-      set_gemm(c, L.m0b, b0);
-      set_gemm(c, L.m1b, b1);
-      set_gemm(c, L.m2b, b2);
+      set_gemm(c, L.n64.m0f, f0);
+      set_gemm(c, L.n64.m1f, f1);
+      set_gemm(c, L.n64.m2f, f2);
+      set_gemm(c, L.n64.m0b, b0);
+      set_gemm(c, L.n64.m1b, b1);
+      set_gemm(c, L.n64.m2b, b2);
     }
 
     // ---------------- interface pieces: vertices; edges and faces grouped by signature
@@ -641,8 +678,8 @@ void build_levels(igamg_ctx* c) {
         Mat U;
         std::vector<double> dv;
         edge_fd(d, m, p, U, dv);
-        double* dU = c->mem.upload(U, s);
-        double* ddv = c->mem.upload(dv, s);
+        double* dU = reg_const(c, c->mem.upload(U, s), U.size());
+        double* ddv = reg_const(c, c->mem.upload(dv, s), dv.size());
         eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len0, len0, len0, 0, np, len0, len0});
         eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len0, len0, len0, 0, np, len0, len0});
       } else if (kind == PIECE_FACE && len0 > 0 && len1 > 0) {
@@ -654,7 +691,7 @@ void build_levels(igamg_ctx* c) {
         for (int a = 0; a < len0; ++a)
           for (int b = 0; b < len1; ++b)
             Dv[size_t(a) * len1 + b] = 1.0 / ((h / p) * (S0->mu[a] + S1->mu[b] + double(p) * p / (h * h)));
-        double* Dinv = c->mem.upload(Dv, s);
+        double* Dinv = reg_const(c, c->mem.upload(Dv, s), Dv.size());
         for (int f = 0; f < np; ++f) {
           int64_t off = gbase + int64_t(f) * len0 * len1, tb = face_tot + int64_t(f) * len0 * len1;
           q0.push_back(GemmDesc{S0->dU, (double*)(intptr_t)off, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
@@ -668,25 +705,25 @@ void build_levels(igamg_ctx* c) {
     L.n_if = int64_t(vsc.size());
     L.if_ptr = c->mem.upload(ptr, s);
     L.if_idx = c->mem.upload(idx, s);
-    L.vscale = c->mem.upload(vsc, s);
-    L.G = c->mem.alloc<double>(L.n_if);
-    L.Z = c->mem.alloc<double>(L.n_if);
-    L.Yif = c->mem.alloc<double>(L.n_if);
-    L.fT = c->mem.alloc<double>(face_tot);
-    L.fY = c->mem.alloc<double>(face_tot);
-    CK(cudaMemsetAsync(L.Z, 0, std::max<int64_t>(L.n_if, 1) * sizeof(double), s));
-    for (auto& g : eA) { g.A = L.G + (intptr_t)g.A; g.C = L.Yif + (intptr_t)g.C; }
-    for (auto& g : eB) { g.A = L.Yif + (intptr_t)g.A; g.C = L.Z + (intptr_t)g.C; }
-    for (auto& g : q0) { g.B = L.G + (intptr_t)g.B; g.C = L.fT + (intptr_t)g.C; }
-    for (auto& g : q1) { g.A = L.fT + (intptr_t)g.A; g.C = L.fY + (intptr_t)g.C; }
-    for (auto& g : q2) { g.B = L.fY + (intptr_t)g.B; g.C = L.fT + (intptr_t)g.C; }
-    for (auto& g : q3) { g.A = L.fT + (intptr_t)g.A; g.C = L.Z + (intptr_t)g.C; }
-    set_gemm(c, L.edgeA, eA);
-    set_gemm(c, L.edgeB, eB);
-    set_gemm(c, L.face0, q0);
-    set_gemm(c, L.face1, q1);
-    set_gemm(c, L.face2, q2);
-    set_gemm(c, L.face3, q3);
+    L.n64.vscale = reg_const(c, c->mem.upload(vsc, s), vsc.size());
+    L.n64.G = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
+    L.n64.Z = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
+    double* Yif = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
+    double* fT = reg_work(c, c->mem.alloc<double>(face_tot), face_tot);
+    double* fY = reg_work(c, c->mem.alloc<double>(face_tot), face_tot);
+    CK(cudaMemsetAsync(L.n64.Z, 0, std::max<int64_t>(L.n_if, 1) * sizeof(double), s));
+    for (auto& g : eA) { g.A = L.n64.G + (intptr_t)g.A; g.C = Yif + (intptr_t)g.C; }
+    for (auto& g : eB) { g.A = Yif + (intptr_t)g.A; g.C = L.n64.Z + (intptr_t)g.C; }
+    for (auto& g : q0) { g.B = L.n64.G + (intptr_t)g.B; g.C = fT + (intptr_t)g.C; }
+    for (auto& g : q1) { g.A = fT + (intptr_t)g.A; g.C = fY + (intptr_t)g.C; }
+    for (auto& g : q2) { g.B = fY + (intptr_t)g.B; g.C = fT + (intptr_t)g.C; }
+    for (auto& g : q3) { g.A = fT + (intptr_t)g.A; g.C = L.n64.Z + (intptr_t)g.C; }
+    set_gemm(c, L.n64.edgeA, eA);
+    set_gemm(c, L.n64.edgeB, eB);
+    set_gemm(c, L.n64.face0, q0);
+    set_gemm(c, L.n64.face1, q1);
+    set_gemm(c, L.n64.face2, q2);
+    set_gemm(c, L.n64.face3, q3);
 
     // ---------------- transfers from level l-1 (one 1D pass per direction)
     const Level& C = c->lv[l - 1];
@@ -716,12 +753,13 @@ void build_levels(igamg_ctx* c) {
           for (int a = 0; a < wp && ps[i] + a < nc; ++a) pw[size_t(i) * wp + a] = P[size_t(i) * nc + ps[i] + a];
         for (int jj = 0; jj < nc; ++jj)
           for (int a = 0; a < wr && rs[jj] + a < nf; ++a) rw[size_t(jj) * wr + a] = P[size_t(rs[jj] + a) * nc + jj];
-        ptabs[key] = {c->mem.upload(rw, s), c->mem.upload(rs, s), c->mem.upload(pw, s), c->mem.upload(ps, s),
+        ptabs[key] = {reg_const(c, c->mem.upload(rw, s), rw.size()), c->mem.upload(rs, s),
+                      reg_const(c, c->mem.upload(pw, s), pw.size()), c->mem.upload(ps, s),
                       (void*)(intptr_t)wr, (void*)(intptr_t)wp};
       }
       return ptabs[key];
     };
-    std::vector<Xfer1D> rp[3], pp[3];
+    std::vector<XferT<double>> rp[3], pp[3];
     int64_t tAsz = 0, tBsz = 0;
     for (int k = 0; k < K; ++k) {
       const PatchDev &Pf = L.pd_h[k], &Pc = C.pd_h[k];
@@ -734,7 +772,7 @@ void build_levels(igamg_ctx* c) {
       (void)bufs;
       for (int j = 0; j < d; ++j) {
         auto& tb = tables(Pc.m[j], Pc.p[j]);
-        Xfer1D x{};
+        XferT<double> x{};
         x.outer = 1;
         for (int i = 0; i < j; ++i) x.outer *= shp[i];
         x.inner = 1;
@@ -767,7 +805,7 @@ void build_levels(igamg_ctx* c) {
       int64_t in_off = Pc.off;
       for (int j = 0; j < d; ++j) {
         auto& tb = tables(Pc.m[j], Pc.p[j]);
-        Xfer1D x{};
+        XferT<double> x{};
         x.outer = 1;
         for (int i = 0; i < j; ++i) x.outer *= shp[i];
         x.inner = 1;
@@ -791,11 +829,14 @@ void build_levels(igamg_ctx* c) {
         if (j < d - 1) { if (j % 2 == 0) tAsz += outsz; else tBsz += outsz; }
       }
     }
-    L.tA = c->mem.alloc<double>(std::max(rA, tAsz));
-    L.tB = c->mem.alloc<double>(std::max(rB, tBsz));
+    int64_t na = std::max(rA, tAsz), nb2 = std::max(rB, tBsz);
+    L.n64.tA = reg_work(c, c->mem.alloc<double>(na), na);
+    L.n64.tB = reg_work(c, c->mem.alloc<double>(nb2), nb2);
     for (int j = 0; j < d; ++j) {
-      L.rpass[j] = c->mem.upload(rp[j], s);
-      L.ppass[j] = c->mem.upload(pp[j], s);
+      L.rp_h[j] = rp[j];
+      L.pp_h[j] = pp[j];
+      L.n64.rpass[j] = c->mem.upload(rp[j], s);
+      L.n64.ppass[j] = c->mem.upload(pp[j], s);
     }
   }
   // coarse solver: dense A_0 from the level-0 bands, Cholesky, explicit inverse
@@ -855,6 +896,7 @@ void build_levels(igamg_ctx* c) {
   c->Pv = c->mem.alloc<double>(Tf);
   c->W = c->mem.alloc<double>(Tf);
   c->Bt = c->mem.alloc<double>(Tf);
+  c->Rr = c->mem.alloc<double>(Tf);
   int64_t gmaxN = 0;
   for (auto& L : c->lv) gmaxN = std::max(gmaxN, L.topo.N);
   c->gtmp = c->mem.alloc<double>(gmaxN);
@@ -867,125 +909,152 @@ void build_levels(igamg_ctx* c) {
 
 // ---------------------------------------------------------------- cycle
 
-void residual(igamg_ctx* c, int l, const double* f, const double* u, double* r) {
+template <class T>
+void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r) {
   Level& L = c->lv[l];
-  ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes + 8.0 * L.topo.T * (f ? 3 : 2));
+  Num<T>& N = num<T>(L);
+  double bb = N.bf16 ? 0.25 : double(sizeof(T)) / 8.0;  // band bytes relative to FP64
+  ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes * bb + double(sizeof(T)) * L.topo.T * (f ? 3 : 2));
+  if (N.bf16) {
+    if constexpr (std::is_same<T, float>::value) {
+      const __nv_bfloat16* band = static_cast<const __nv_bfloat16*>(N.band);
+      if (c->pd.dim == 2)
+        CK((launch_band_apply_2d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p,
+                                                         band, u, f, r)));
+      else
+        CK((launch_band_apply_3d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r)));
+    }
+    return;
+  }
+  const T* band = static_cast<const T*>(N.band);
   if (c->pd.dim == 2)
-    CK(launch_band_apply_2d(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, L.band, u, f, r));
+    CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r)));
   else
-    CK(launch_band_apply_3d(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, L.band, u, f, r));
+    CK((launch_band_apply_3d<T, T>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r)));
 }
 
 // u (=|+=) tau L^{-1} v for a distributed v (F or R of the level): patch interiors by
 // fast diagonalisation, faces by their 2D and edges by their 1D fast diagonalisation,
 // vertices by scaling (Eq. additive; the pieces are disjoint, so the sum is a set of
 // independent blocks).
+template <class T>
 void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   Level& L = c->lv[l];
-  const double* v = from_F ? L.F : L.R;
+  Num<T>& N = num<T>(L);
+  const T* v = from_F ? N.F : N.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
   if (c->pd.dim == 2) {
-    run_gemm(c, from_F ? L.st0F : L.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.st1, false, false, EPI_MUL, 1.0, CLS_FD);
-    run_gemm(c, L.st2, false, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.st3, false, true, epi, tau, CLS_FD);
+    run_gemm(c, from_F ? N.st0F : N.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.st1, false, false, EPI_MUL, 1.0, CLS_FD);
+    run_gemm(c, N.st2, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.st3, false, true, epi, tau, CLS_FD);
   } else if (L.nbox) {
     {
-      ProfScope ps(c, CLS_FD, 0.0, 16.0 * L.max_box * L.nbox);
-      CK(launch_box_copy(c->stream, L.boxes, L.nbox, L.max_box, v, L.cX, 1, 1.0, 0));
+      ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
+      CK(launch_box_copy<T>(c->stream, L.boxes, L.nbox, L.max_box, v, N.cX, 1, T(1), 0));
     }
-    run_gemm(c, L.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.m2f, false, false, EPI_MUL, 1.0, CLS_FD);
-    run_gemm(c, L.m0b, false, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.m1b, false, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, L.m2b, false, true, EPI_STORE, 1.0, CLS_FD);
-    ProfScope ps(c, CLS_FD, 0.0, 16.0 * L.max_box * L.nbox);
-    CK(launch_box_copy(c->stream, L.boxes, L.nbox, L.max_box, L.cX, L.U, 0, tau, add ? 1 : 0));
+    run_gemm(c, N.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.m2f, false, false, EPI_MUL, 1.0, CLS_FD);
+    run_gemm(c, N.m0b, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.m1b, false, false, EPI_STORE, 1.0, CLS_FD);
+    run_gemm(c, N.m2b, false, true, EPI_STORE, 1.0, CLS_FD);
+    ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
+    CK(launch_box_copy<T>(c->stream, L.boxes, L.nbox, L.max_box, N.cX, N.U, 0, T(tau), add ? 1 : 0));
   }
   if (L.n_if == 0) return;
   {
-    ProfScope ps(c, CLS_IFACE, 0.0, 16.0 * L.n_if);
-    CK(launch_iface_gather(c->stream, L.n_if, L.if_ptr, L.if_idx, v, L.G));
+    ProfScope ps(c, CLS_IFACE, 0.0, 2.0 * sizeof(T) * L.n_if);
+    CK(launch_iface_gather<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, v, N.G));
   }
-  run_gemm(c, L.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
-  run_gemm(c, L.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, L.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, L.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
-  run_gemm(c, L.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, L.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, N.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
+  run_gemm(c, N.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
+  run_gemm(c, N.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
+  run_gemm(c, N.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
   {
-    ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 24.0 * L.n_if);
-    CK(launch_iface_scatter(c->stream, L.n_if, L.if_ptr, L.if_idx, L.Z, L.G, L.vscale, tau, add ? 1 : 0, L.U));
+    ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 3.0 * sizeof(T) * L.n_if);
+    CK(launch_iface_scatter<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, N.Z, N.G, N.vscale, T(tau), add ? 1 : 0, N.U));
   }
 }
 
 // r_{l-1} = P_l^T r_l (distributed -> distributed), one direction at a time.
-void restrict_to_coarse(igamg_ctx* c, int l, const double* rf) {
+template <class T>
+void restrict_to_coarse(igamg_ctx* c, int l, const T* rf) {
   Level& L = c->lv[l];
   Level& C = c->lv[l - 1];
+  Num<T>& N = num<T>(L);
   const int d = c->pd.dim, K = c->pd.K;
-  ProfScope pr(c, CLS_TRANSFER, L.xfer_flops / 3, L.xfer_bytes / 3, d);
-  const double* in = rf;
+  ProfScope pr(c, CLS_TRANSFER, L.xfer_flops / 3, L.xfer_bytes / 3 * sizeof(T) / 8.0, d);
+  const T* in = rf;
   for (int j = 0; j < d; ++j) {
-    double* out = j == d - 1 ? C.F : (j % 2 == 0 ? L.tA : L.tB);
-    CK(launch_transfer_1d(c->stream, L.rpass[j], K, L.rmax[j], in, out, 0, j == d - 1 ? C.l2g : nullptr));
+    T* out = j == d - 1 ? num<T>(C).F : (j % 2 == 0 ? N.tA : N.tB);
+    CK(launch_transfer_1d<T>(c->stream, N.rpass[j], K, L.rmax[j], in, out, 0, j == d - 1 ? C.l2g : nullptr));
     in = out;
   }
 }
 
 // u_l += P_l u_{l-1} (accumulated -> accumulated).
+template <class T>
 void prolong_add(igamg_ctx* c, int l) {
   Level& L = c->lv[l];
   Level& C = c->lv[l - 1];
+  Num<T>& N = num<T>(L);
   const int d = c->pd.dim, K = c->pd.K;
-  ProfScope pp(c, CLS_TRANSFER, 2 * L.xfer_flops / 3, 2 * L.xfer_bytes / 3, d);
-  const double* in = C.U;
+  ProfScope pp(c, CLS_TRANSFER, 2 * L.xfer_flops / 3, 2 * L.xfer_bytes / 3 * sizeof(T) / 8.0, d);
+  const T* in = num<T>(C).U;
   for (int j = 0; j < d; ++j) {
-    double* out = j == d - 1 ? L.U : (j % 2 == 0 ? L.tA : L.tB);
-    CK(launch_transfer_1d(c->stream, L.ppass[j], K, L.pmax[j], in, out, j == d - 1 ? 1 : 0, nullptr));
+    T* out = j == d - 1 ? N.U : (j % 2 == 0 ? N.tA : N.tB);
+    CK(launch_transfer_1d<T>(c->stream, N.ppass[j], K, L.pmax[j], in, out, j == d - 1 ? 1 : 0, nullptr));
     in = out;
   }
 }
 
+// Exact coarsest solve, always in FP64 (the inverse is applied in FP64 to the gathered
+// coarse residual whatever the vector precision).
+template <class T>
 void coarse_solve(igamg_ctx* c) {
   Level& L0 = c->lv[0];
   ProfScope ps(c, CLS_COARSE, 2.0 * double(c->N0) * c->N0, 8.0 * double(c->N0) * c->N0);
-  CK(launch_coarse_solve(c->stream, c->N0, L0.g2t_ptr, L0.g2t, c->A0inv, L0.F, L0.U));
+  CK(launch_coarse_solve<T>(c->stream, c->N0, L0.g2t_ptr, L0.g2t, c->A0inv, num<T>(L0).F, num<T>(L0).U));
 }
 
 // Algorithm 1 on level l >= 1: f = F_l (distributed), u = U_l (accumulated).
+template <class T>
 void multigrid(igamg_ctx* c, int l, bool zero_init) {
   Level& L = c->lv[l];
+  Num<T>& N = num<T>(L);
   const int nu = c->opt.nu, mu = c->opt.mu;
   for (int i = 0; i < nu; ++i) {
     if (zero_init && i == 0) {
-      smooth(c, l, true, false);  // u = 0: the residual is f itself
+      smooth<T>(c, l, true, false);  // u = 0: the residual is f itself
     } else {
-      residual(c, l, L.F, L.U, L.R);
-      smooth(c, l, false, true);
+      residual<T>(c, l, N.F, N.U, N.R);
+      smooth<T>(c, l, false, true);
     }
   }
-  residual(c, l, L.F, L.U, L.R);
-  restrict_to_coarse(c, l, L.R);
+  residual<T>(c, l, N.F, N.U, N.R);
+  restrict_to_coarse<T>(c, l, N.R);
   if (l == 1) {
-    coarse_solve(c);
+    coarse_solve<T>(c);
   } else {
-    for (int j = 0; j < mu; ++j) multigrid(c, l - 1, j == 0);
+    for (int j = 0; j < mu; ++j) multigrid<T>(c, l - 1, j == 0);
   }
-  prolong_add(c, l);
+  prolong_add<T>(c, l);
   for (int i = 0; i < nu; ++i) {
-    residual(c, l, L.F, L.U, L.R);
-    smooth(c, l, false, true);
+    residual<T>(c, l, N.F, N.U, N.R);
+    smooth<T>(c, l, false, true);
   }
 }
 
 // z = U_L = Multigrid(L, 0, F_L)
+template <class T>
 void precondition(igamg_ctx* c) {
   int Lf = int(c->lv.size()) - 1;
-  if (Lf == 0) coarse_solve(c);
-  else multigrid(c, Lf, true);
+  if (Lf == 0) coarse_solve<T>(c);
+  else multigrid<T>(c, Lf, true);
 }
 
 int level_index(const igamg_ctx* c, int level) {
@@ -999,23 +1068,23 @@ void to_dist(igamg_ctx* c, int l, const double* xg, double* xt) {
   Level& L = c->lv[l];
   ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(cudaMemsetAsync(xt, 0, L.topo.T * sizeof(double), c->stream));
-  CK(launch_global_to_tile(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 1));
+  CK(launch_global_to_tile<double>(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 1));
 }
 void to_acc(igamg_ctx* c, int l, const double* xg, double* xt) {
   Level& L = c->lv[l];
   ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
   CK(cudaMemsetAsync(xt, 0, L.topo.T * sizeof(double), c->stream));
-  CK(launch_global_to_tile(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 0));
+  CK(launch_global_to_tile<double>(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xg, xt, 0));
 }
 void from_acc(igamg_ctx* c, int l, const double* xt, double* xg) {
   Level& L = c->lv[l];
   ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
-  CK(launch_tile_to_global(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 0));
+  CK(launch_tile_to_global<double>(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 0));
 }
 void from_dist(igamg_ctx* c, int l, const double* xt, double* xg) {
   Level& L = c->lv[l];
   ProfScope ps(c, CLS_VECTOR, 0.0, 16.0 * L.topo.N);
-  CK(launch_tile_to_global(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 1));
+  CK(launch_tile_to_global<double>(c->stream, L.topo.N, L.g2t_ptr, L.g2t, xt, xg, 1));
 }
 
 double read_scalar(igamg_ctx* c, int i) {
@@ -1025,18 +1094,73 @@ double read_scalar(igamg_ctx* c, int i) {
   return c->h_scal[i];
 }
 
-void vdot(igamg_ctx* c, const double* a, const double* b, int64_t T, double* out) {
-  ProfScope ps(c, CLS_VECTOR, 2.0 * T, 16.0 * T, 2);
-  CK(launch_dot(c->stream, a, b, T, c->partials, out));
+template <class T>
+void vdot(igamg_ctx* c, const T* a, const T* b, int64_t n, double* out) {
+  ProfScope ps(c, CLS_VECTOR, 2.0 * n, 2.0 * sizeof(T) * n, 2);
+  CK(launch_dot<T>(c->stream, a, b, n, c->partials, out));
 }
 
-void vnorm_dist(igamg_ctx* c, int l, const double* v, double* out) {
+template <class T>
+void vnorm_dist(igamg_ctx* c, int l, const T* v, double* out) {
   Level& L = c->lv[l];
-  ProfScope ps(c, CLS_VECTOR, 2.0 * L.topo.N, 8.0 * L.topo.T, 2);
-  CK(launch_norm2_dist(c->stream, L.topo.N, L.g2t_ptr, L.g2t, v, c->partials, out));
+  ProfScope ps(c, CLS_VECTOR, 2.0 * L.topo.N, double(sizeof(T)) * L.topo.T, 2);
+  CK(launch_norm2_dist<T>(c->stream, L.topo.N, L.g2t_ptr, L.g2t, v, c->partials, out));
 }
 
-// PCG (Sec. 4): r, w distributed; x, z, p accumulated.  scal: 0 rz, 1 pw, 2 rz_new, 3 rr.
+// PCG (Sec. 4) in precision T on the tile layout of the finest level: r = F_L and w
+// distributed; x, z = U_L, p accumulated.  The residual r must be set on entry, x is
+// zeroed.  Stops when ||r|| <= tol * ||r_0|| (tol > 0) or after max_iter iterations.
+// scal: 0 rz, 1 pw, 2 rz_new, 3 rr.  Returns the iterations and the final ratio.
+template <class T>
+int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* rel_out, bool* stalled) {
+  const int Lf = int(c->lv.size()) - 1;
+  Level& L = c->lv[Lf];
+  Num<T>& N = num<T>(L);
+  const int64_t T_ = L.topo.T;
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(x, 0, T_ * sizeof(T), s));
+  vnorm_dist<T>(c, Lf, N.F, c->scal + 3);
+  double rr0 = read_scalar(c, 3);
+  if (!std::isfinite(rr0)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite initial residual"};
+  *rel_out = 0.0;
+  *stalled = false;
+  if (rr0 == 0.0) return 0;
+  int it = 0;
+  double rel = 1.0;
+  precondition<T>(c);
+  CK(cudaMemcpyAsync(p, N.U, T_ * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  vdot<T>(c, N.F, N.U, T_, c->scal + 0);
+  while (!(tol > 0 && rel <= tol) && it < max_iter) {
+    residual<T>(c, Lf, nullptr, p, w);
+    vdot<T>(c, p, w, T_, c->scal + 1);
+    {
+      ProfScope ps(c, CLS_VECTOR, 4.0 * T_, 6.0 * sizeof(T) * T_);
+      CK(launch_pcg_xr<T>(s, T_, c->scal, x, N.F, p, w));
+    }
+    ++it;
+    vnorm_dist<T>(c, Lf, N.F, c->scal + 3);
+    double rr = read_scalar(c, 3);
+    if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in PCG"};
+    double rel_new = std::sqrt(rr / rr0);
+    if (sizeof(T) < 8 && it > 4 && rel_new > 0.9 * rel && rel_new < 1e-4) {
+      *stalled = true;  // low precision: no more progress to be had
+      rel = rel_new;
+      break;
+    }
+    rel = rel_new;
+    if ((tol > 0 && rel <= tol) || it >= max_iter) break;
+    precondition<T>(c);
+    vdot<T>(c, N.F, N.U, T_, c->scal + 2);
+    {
+      ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 3.0 * sizeof(T) * T_, 2);
+      CK(launch_pcg_p<T>(s, T_, c->scal, p, N.U));
+    }
+  }
+  *rel_out = rel;
+  return it;
+}
+
+// FP64 PCG from x (global) with rhs b (global).
 igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_result* res) {
   double t0 = now_ms();
   const int Lf = int(c->lv.size()) - 1;
@@ -1045,53 +1169,152 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
   cudaStream_t s = c->stream;
   to_dist(c, Lf, b, c->Bt);
   to_acc(c, Lf, x, c->X);
-  residual(c, Lf, c->Bt, c->X, L.F);
-  vnorm_dist(c, Lf, L.F, c->scal + 3);
-  double rr0 = read_scalar(c, 3);
-  if (!std::isfinite(rr0)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite initial residual"};
-  int it = 0;
+  // solve A d = b - A x0 from d = 0, then x = x0 + d (Rr holds x0)
+  residual<double>(c, Lf, c->Bt, c->X, L.n64.F);
+  CK(cudaMemcpyAsync(c->Rr, c->X, T * sizeof(double), cudaMemcpyDeviceToDevice, s));
   double rel = 0.0;
-  igamg_status st = IGAMG_OK;
-  if (rr0 > 0.0) {
-    precondition(c);
-    CK(cudaMemcpyAsync(c->Pv, L.U, T * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    vdot(c, L.F, L.U, T, c->scal + 0);
-    rel = 1.0;
-    while (true) {
-      if (tol > 0 && rel <= tol) break;
-      if (it >= c->opt.max_iter) { st = tol > 0 ? IGAMG_ERR_NOT_CONVERGED : IGAMG_OK; break; }
-      residual(c, Lf, nullptr, c->Pv, c->W);
-      vdot(c, c->Pv, c->W, T, c->scal + 1);
-      {
-        ProfScope ps(c, CLS_VECTOR, 4.0 * T, 48.0 * T);
-        CK(launch_pcg_xr(s, T, c->scal, c->X, L.F, c->Pv, c->W));
-      }
-      ++it;
-      vnorm_dist(c, Lf, L.F, c->scal + 3);
-      double rr = read_scalar(c, 3);
-      if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in PCG"};
-      rel = std::sqrt(rr / rr0);
-      if (tol > 0 && rel <= tol) break;
-      if (it >= c->opt.max_iter) continue;
-      precondition(c);
-      vdot(c, L.F, L.U, T, c->scal + 2);
-      {
-        ProfScope ps(c, CLS_VECTOR, 2.0 * T, 24.0 * T, 2);
-        CK(launch_pcg_p(s, T, c->scal, c->Pv, L.U));
-      }
-    }
-  }
+  bool stalled = false;
+  int it = pcg_core<double>(c, c->X, c->Pv, c->W, tol, c->opt.max_iter, &rel, &stalled);
+  CK(launch_axpby(s, T, 1.0, c->Rr, 1.0, c->X));
   from_acc(c, Lf, c->X, x);
   CK(cudaStreamSynchronize(s));
   if (c->prof) prof_collect(c);
   if (res) {
     res->iters = it;
+    res->outer_iters = 1;
+    res->relres = rel;
+    res->t_setup_ms = c->t_setup_ms;
+    res->t_assemble_ms = c->t_assemble_ms;
+    res->t_solve_ms = now_ms() - t0;
+  }
+  return (tol > 0 && rel > tol) ? IGAMG_ERR_NOT_CONVERGED : IGAMG_OK;
+}
+
+// FP64 iterative refinement around a low-precision PCG (the precision variant):
+// r = b - A x in FP64; the inner PCG (FP32 vectors, FP32 or BF16 bands, FP32 smoother
+// contractions, FP64 coarse solve) reduces the scaled residual by inner_tol; x += d.
+igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, igamg_result* res) {
+  double t0 = now_ms();
+  const int Lf = int(c->lv.size()) - 1;
+  Level& L = c->lv[Lf];
+  const int64_t T = L.topo.T;
+  cudaStream_t s = c->stream;
+  to_dist(c, Lf, b, c->Bt);
+  to_acc(c, Lf, x, c->X);
+  int total = 0, outer = 0;
+  double rel = 1.0, rr0 = -1.0;
+  igamg_status st = IGAMG_OK;
+  while (true) {
+    residual<double>(c, Lf, c->Bt, c->X, c->Rr);
+    vnorm_dist<double>(c, Lf, c->Rr, c->scal + 3);
+    double rr = read_scalar(c, 3);
+    if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in refinement"};
+    if (rr0 < 0) rr0 = rr;
+    rel = rr0 > 0 ? std::sqrt(rr / rr0) : 0.0;
+    if (rr0 == 0.0 || (tol > 0 && rel <= tol)) break;
+    if (total >= c->opt.max_iter || outer >= 60) { st = tol > 0 ? IGAMG_ERR_NOT_CONVERGED : IGAMG_OK; break; }
+    // scaled FP32 residual (norm 1) so FP32 range never matters
+    double scale = 1.0 / std::sqrt(rr);
+    CK(launch_convert_f64_f32(s, T, c->Rr, scale, L.n32.F));
+    double irel = 0.0;
+    bool stalled = false;
+    int it = pcg_core<float>(c, c->X32, c->P32, c->W32, c->opt.inner_tol, c->opt.max_iter - total, &irel, &stalled);
+    total += it;
+    ++outer;
+    CK(launch_add_scaled_f32(s, T, c->X32, 1.0 / scale, c->X));
+    if (it == 0) { st = IGAMG_ERR_NUMERIC; break; }
+  }
+  from_acc(c, Lf, c->X, x);
+  CK(cudaStreamSynchronize(s));
+  if (c->prof) prof_collect(c);
+  if (res) {
+    res->iters = total;
+    res->outer_iters = outer;
     res->relres = rel;
     res->t_setup_ms = c->t_setup_ms;
     res->t_assemble_ms = c->t_assemble_ms;
     res->t_solve_ms = now_ms() - t0;
   }
   return st;
+}
+
+// Twins of the FP64 numerics in FP32 (bands in FP32 or BF16): every registered FP64 array
+// gets an FP32 copy (constants converted, work buffers allocated) and every FP64
+// descriptor is translated pointer by pointer.
+void build_low(igamg_ctx* c, bool bf16_bands) {
+  cudaStream_t s = c->stream;
+  std::vector<std::tuple<double*, int64_t, float*>> tw;
+  for (auto& r : c->reg) {
+    double* base = std::get<0>(r);
+    int64_t n = std::get<1>(r);
+    float* f = c->mem.alloc<float>(std::max<int64_t>(n, 1));
+    if (std::get<2>(r)) CK(launch_convert_f64_f32(s, n, base, 1.0, f));
+    else CK(cudaMemsetAsync(f, 0, std::max<int64_t>(n, 1) * sizeof(float), s));
+    tw.emplace_back(base, n, f);
+  }
+  std::sort(tw.begin(), tw.end(), [](const auto& a, const auto& b) { return std::get<0>(a) < std::get<0>(b); });
+  auto tr = [&](const double* p) -> float* {
+    if (!p) return nullptr;
+    auto it = std::upper_bound(tw.begin(), tw.end(), p,
+                               [](const double* q, const auto& e) { return q < std::get<0>(e); });
+    if (it == tw.begin()) throw Fail{IGAMG_ERR_NUMERIC, "untracked array in a descriptor"};
+    --it;
+    int64_t off = p - std::get<0>(*it);
+    if (off < 0 || off > std::get<1>(*it)) throw Fail{IGAMG_ERR_NUMERIC, "untracked array in a descriptor"};
+    return std::get<2>(*it) + off;
+  };
+  auto tr_set = [&](const GemmSet& g, GemmSetT<float>& out) {
+    std::vector<GemmDescT<float>> v;
+    for (const GemmDesc& d : g.h)
+      v.push_back(GemmDescT<float>{tr(d.A), tr(d.B), tr(d.C), tr(d.E), d.lda, d.ldb, d.ldc, d.lde, d.M, d.N, d.K});
+    set_gemm(c, out, v);
+  };
+  for (size_t l = 0; l < c->lv.size(); ++l) {
+    Level& L = c->lv[l];
+    Num<double>& A = L.n64;
+    Num<float>& B = L.n32;
+    B.F = tr(A.F);
+    B.U = tr(A.U);
+    B.R = tr(A.R);
+    B.cX = tr(A.cX);
+    B.G = tr(A.G);
+    B.Z = tr(A.Z);
+    B.vscale = tr(A.vscale);
+    B.tA = tr(A.tA);
+    B.tB = tr(A.tB);
+    int64_t nb = c->band_count[l];
+    if (bf16_bands) {
+      __nv_bfloat16* bb = c->mem.alloc<__nv_bfloat16>(nb);
+      CK(launch_convert_f64_bf16(s, nb, L.band, bb));
+      B.band = bb;
+      B.bf16 = true;
+    } else {
+      float* bb = c->mem.alloc<float>(nb);
+      CK(launch_convert_f64_f32(s, nb, L.band, 1.0, bb));
+      B.band = bb;
+    }
+    tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
+    tr_set(A.st3, B.st3);
+    tr_set(A.m0f, B.m0f); tr_set(A.m1f, B.m1f); tr_set(A.m2f, B.m2f);
+    tr_set(A.m0b, B.m0b); tr_set(A.m1b, B.m1b); tr_set(A.m2b, B.m2b);
+    tr_set(A.edgeA, B.edgeA); tr_set(A.edgeB, B.edgeB);
+    tr_set(A.face0, B.face0); tr_set(A.face1, B.face1); tr_set(A.face2, B.face2); tr_set(A.face3, B.face3);
+    for (int j = 0; j < 3; ++j) {
+      if (L.rp_h[j].empty()) continue;
+      std::vector<XferT<float>> rp, pp;
+      for (auto& x : L.rp_h[j]) rp.push_back(XferT<float>{x.in_off, x.out_off, x.outer, x.inner, x.nin, x.nout, x.width, tr(x.wt), x.st});
+      for (auto& x : L.pp_h[j]) pp.push_back(XferT<float>{x.in_off, x.out_off, x.outer, x.inner, x.nin, x.nout, x.width, tr(x.wt), x.st});
+      B.rpass[j] = c->mem.upload(rp, s);
+      B.ppass[j] = c->mem.upload(pp, s);
+    }
+  }
+  int64_t Tf = c->lv.back().topo.T;
+  c->X32 = c->mem.alloc<float>(Tf);
+  c->P32 = c->mem.alloc<float>(Tf);
+  c->W32 = c->mem.alloc<float>(Tf);
+  c->low = true;
+  c->low_bf16 = bf16_bands;
+  CK(cudaStreamSynchronize(s));
 }
 
 template <class F>
@@ -1123,6 +1346,7 @@ igamg_status igamg_default_options(igamg_options* opt) {
   opt->mu = 1;
   opt->max_iter = 500;
   opt->precision = IGAMG_FP64;
+  opt->inner_tol = 1e-4;
   return IGAMG_OK;
 }
 
@@ -1137,7 +1361,9 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
   if (opt) c->opt = *opt;
   double t0 = now_ms();
   try {
-    if (c->opt.precision != IGAMG_FP64) throw Fail{IGAMG_ERR_UNSUPPORTED, "only FP64 is accepted"};
+    if (c->opt.precision < IGAMG_FP64 || c->opt.precision > IGAMG_BF16) throw Fail{IGAMG_ERR_ARG, "bad precision"};
+    if (c->opt.precision != IGAMG_FP64 && !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1))
+      throw Fail{IGAMG_ERR_ARG, "inner_tol must be in (0, 1)"};
     if (c->opt.nu < 1 || c->opt.mu < 1 || c->opt.mu > 2 || c->opt.max_iter < 0 || !(c->opt.tau > 0))
       throw Fail{IGAMG_ERR_ARG, "bad options"};
     int code = 0;
@@ -1146,6 +1372,7 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
                                   prob->num_levels, c->pd, &code);
     if (!e.empty()) throw Fail{igamg_status(code), e};
     build_levels(c);
+    if (c->opt.precision != IGAMG_FP64) build_low(c, c->opt.precision == IGAMG_BF16);
   } catch (const Fail& e) {
     g_setup_error = e.msg;
     c->mem.release();
@@ -1190,9 +1417,9 @@ igamg_status igamg_apply(igamg_ctx* c, int level, const double* x, double* y) {
     if (!x || !y) throw Fail{IGAMG_ERR_ARG, "NULL vector"};
     int l = level_index(c, level);
     Level& L = c->lv[l];
-    to_acc(c, l, x, L.U);
-    residual(c, l, nullptr, L.U, L.R);
-    from_dist(c, l, L.R, y);
+    to_acc(c, l, x, L.n64.U);
+    residual<double>(c, l, nullptr, L.n64.U, L.n64.R);
+    from_dist(c, l, L.n64.R, y);
     return IGAMG_OK;
   });
 }
@@ -1203,11 +1430,11 @@ igamg_status igamg_smooth(igamg_ctx* c, int level, const double* r, double* z) {
     int l = level_index(c, level);
     if (l < 1) throw Fail{IGAMG_ERR_ARG, "the smoother exists on levels >= 1"};
     Level& L = c->lv[l];
-    to_dist(c, l, r, L.R);
-    CK(cudaMemsetAsync(L.U, 0, L.topo.T * sizeof(double), c->stream));
-    smooth(c, l, false, false);
-    CK(launch_axpby(c->stream, L.topo.T, 0.0, L.U, 1.0 / c->opt.tau, L.U));
-    from_acc(c, l, L.U, z);
+    to_dist(c, l, r, L.n64.R);
+    CK(cudaMemsetAsync(L.n64.U, 0, L.topo.T * sizeof(double), c->stream));
+    smooth<double>(c, l, false, false);
+    CK(launch_axpby(c->stream, L.topo.T, 0.0, L.n64.U, 1.0 / c->opt.tau, L.n64.U));
+    from_acc(c, l, L.n64.U, z);
     return IGAMG_OK;
   });
 }
@@ -1219,9 +1446,9 @@ igamg_status igamg_restrict(igamg_ctx* c, int level, const double* r, double* rc
     if (l < 1) throw Fail{IGAMG_ERR_ARG, "restriction needs level >= 1"};
     Level& L = c->lv[l];
     Level& C = c->lv[l - 1];
-    to_dist(c, l, r, L.R);
-    restrict_to_coarse(c, l, L.R);
-    from_dist(c, l - 1, C.F, rc);
+    to_dist(c, l, r, L.n64.R);
+    restrict_to_coarse<double>(c, l, L.n64.R);
+    from_dist(c, l - 1, C.n64.F, rc);
     return IGAMG_OK;
   });
 }
@@ -1233,10 +1460,10 @@ igamg_status igamg_prolong(igamg_ctx* c, int level, const double* uc, double* u)
     if (l < 1) throw Fail{IGAMG_ERR_ARG, "prolongation needs level >= 1"};
     Level& L = c->lv[l];
     Level& C = c->lv[l - 1];
-    to_acc(c, l - 1, uc, C.U);
-    CK(cudaMemsetAsync(L.U, 0, L.topo.T * sizeof(double), c->stream));
-    prolong_add(c, l);
-    from_acc(c, l, L.U, u);
+    to_acc(c, l - 1, uc, C.n64.U);
+    CK(cudaMemsetAsync(L.n64.U, 0, L.topo.T * sizeof(double), c->stream));
+    prolong_add<double>(c, l);
+    from_acc(c, l, L.n64.U, u);
     return IGAMG_OK;
   });
 }
@@ -1244,9 +1471,9 @@ igamg_status igamg_prolong(igamg_ctx* c, int level, const double* uc, double* u)
 igamg_status igamg_coarse_solve(igamg_ctx* c, const double* r, double* x) {
   return guarded(c, [&]() {
     if (!r || !x) throw Fail{IGAMG_ERR_ARG, "NULL vector"};
-    to_dist(c, 0, r, c->lv[0].F);
-    coarse_solve(c);
-    from_acc(c, 0, c->lv[0].U, x);
+    to_dist(c, 0, r, c->lv[0].n64.F);
+    coarse_solve<double>(c);
+    from_acc(c, 0, c->lv[0].n64.U, x);
     return IGAMG_OK;
   });
 }
@@ -1255,9 +1482,9 @@ igamg_status igamg_precondition(igamg_ctx* c, const double* r, double* z) {
   return guarded(c, [&]() {
     if (!r || !z) throw Fail{IGAMG_ERR_ARG, "NULL vector"};
     int Lf = int(c->lv.size()) - 1;
-    to_dist(c, Lf, r, c->lv[Lf].F);
-    precondition(c);
-    from_acc(c, Lf, c->lv[Lf].U, z);
+    to_dist(c, Lf, r, c->lv[Lf].n64.F);
+    precondition<double>(c);
+    from_acc(c, Lf, c->lv[Lf].n64.U, z);
     return IGAMG_OK;
   });
 }
@@ -1278,12 +1505,14 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs)
     std::map<std::tuple<int, int>, DevTables> dtabs;
     double* dcorn = c->mem.upload(c->pd.corners, s);
     assemble_level(c, L, dtabs, tabs, dcorn, true, mband);
-    to_acc(c, Lf, coef, L.U);
+    to_acc(c, Lf, coef, L.n64.U);
     if (c->pd.dim == 2)
-      CK(launch_band_apply_2d(s, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, mband, L.U, nullptr, L.R));
+      CK((launch_band_apply_2d<double, double>(s, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, mband, L.n64.U,
+                                                nullptr, L.n64.R)));
     else
-      CK(launch_band_apply_3d(s, L.pd, c->pd.K, L.max_n, L.max_p, mband, L.U, nullptr, L.R));
-    from_dist(c, Lf, L.R, rhs);
+      CK((launch_band_apply_3d<double, double>(s, L.pd, c->pd.K, L.max_n, L.max_p, mband, L.n64.U, nullptr,
+                                                L.n64.R)));
+    from_dist(c, Lf, L.n64.R, rhs);
     CK(cudaFreeAsync(mband, s));
     CK(cudaStreamSynchronize(s));
     for (size_t i = mark; i < c->mem.ptrs.size(); ++i) cudaFree(c->mem.ptrs[i]);  // temporary tables
@@ -1344,7 +1573,7 @@ igamg_status igamg_profile_read(igamg_ctx* c, int cls, int64_t* launches, double
 igamg_status igamg_solve(igamg_ctx* c, const double* b, double* x, double tol, igamg_result* res) {
   return guarded(c, [&]() {
     if (!b || !x || !(tol >= 0)) throw Fail{IGAMG_ERR_ARG, "bad arguments"};
-    return pcg(c, b, x, tol, res);
+    return c->low ? pcg_refined(c, b, x, tol, res) : pcg(c, b, x, tol, res);
   });
 }
 
@@ -1358,7 +1587,7 @@ igamg_status igamg_solve_host(igamg_ctx* c, const double* bh, double* xh, double
     CK(cudaMallocAsync(&dx, N * sizeof(double), c->stream));
     CK(cudaMemcpyAsync(db, bh, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(dx, xh, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    igamg_status st = pcg(c, db, dx, tol, res);
+    igamg_status st = c->low ? pcg_refined(c, db, dx, tol, res) : pcg(c, db, dx, tol, res);
     CK(cudaMemcpyAsync(xh, dx, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaFreeAsync(db, c->stream));
     CK(cudaFreeAsync(dx, c->stream));

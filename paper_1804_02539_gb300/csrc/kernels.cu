@@ -35,65 +35,87 @@ __device__ double block_sum_256(double v, double* sh) {
 // ---------------------------------------------------------------- stiffness apply
 
 // y = f - A u (f != NULL) or y = A u, per patch tile; u staged in shared memory with a
-// halo of p in every direction (zero outside the tile).
+// halo of p in every direction (zero outside the tile).  TV: vector/accumulator type,
+// TB: band storage type (FP64, FP32 or BF16 bands; BF16 and FP32 accumulate in FP32).
+template <class T> __device__ __forceinline__ float to_acc(T v);
+template <> __device__ __forceinline__ float to_acc<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_acc<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class TV, class TB>
+__device__ __forceinline__ TV band_val(const TB* p) {
+  if constexpr (sizeof(TV) == sizeof(TB) && std::is_same<TV, TB>::value) return __ldg(p);
+  else return TV(to_acc<TB>(*p));
+}
+
+template <class TV, class TB>
 __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __restrict__ pds,
-                                                           const double* __restrict__ band,
-                                                           const double* __restrict__ u,
-                                                           const double* __restrict__ f,
-                                                           double* __restrict__ y) {
-  extern __shared__ double su[];
+                                                           const TB* __restrict__ band,
+                                                           const TV* __restrict__ u,
+                                                           const TV* __restrict__ f,
+                                                           TV* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TV* su = reinterpret_cast<TV*>(smraw);
   const PatchDev pd = pds[blockIdx.z];
   const int n0 = pd.n[0], n1 = pd.n[1], p0 = pd.p[0], p1 = pd.p[1];
   const int i0b = blockIdx.y * AY, i1b = blockIdx.x * AX;
   if (i0b >= n0 || i1b >= n1) return;
   const int H0 = AY + 2 * p0, H1 = AX + 2 * p1;
-  const double* ut = u + pd.off;
+  const TV* ut = u + pd.off;
   for (int idx = threadIdx.y * AX + threadIdx.x; idx < H0 * H1; idx += AX * AY) {
     int r = idx / H1, c = idx % H1;
     int g0 = i0b - p0 + r, g1 = i1b - p1 + c;
-    su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1) ? ut[int64_t(g0) * n1 + g1] : 0.0;
+    su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1) ? ut[int64_t(g0) * n1 + g1] : TV(0);
   }
   __syncthreads();
   const int i0 = i0b + threadIdx.y, i1 = i1b + threadIdx.x;
   if (i0 >= n0 || i1 >= n1) return;
   const int64_t nn = int64_t(n0) * n1, node = int64_t(i0) * n1 + i1;
-  const double* bp = band + pd.band_off + node;
+  const TB* bp = band + pd.band_off + node;
   const int w1 = 2 * p1 + 1;
-  double acc = 0.0;
+  TV acc = 0;
   for (int t0 = 0; t0 <= 2 * p0; ++t0) {
-    const double* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
-    const double* brow = bp + int64_t(t0 * w1) * nn;
-    for (int t1 = 0; t1 < w1; ++t1) acc = fma(__ldg(brow + int64_t(t1) * nn), srow[t1], acc);
+    const TV* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
+    const TB* brow = bp + int64_t(t0 * w1) * nn;
+    for (int t1 = 0; t1 < w1; ++t1) acc = fma(band_val<TV, TB>(brow + int64_t(t1) * nn), srow[t1], acc);
   }
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
 }
 
+template <class TV, class TB>
 cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0,
-                                 int max_n1, int max_p, const double* band, const double* u,
-                                 const double* f, double* y) {
+                                 int max_n1, int max_p, const TB* band, const TV* u,
+                                 const TV* f, TV* y) {
   dim3 grid((max_n1 + AX - 1) / AX, (max_n0 + AY - 1) / AY, K);
-  size_t sm = sizeof(double) * (AY + 2 * max_p) * (AX + 2 * max_p);
-  k_band_apply_2d<<<grid, dim3(AX, AY), sm, s>>>(pd_dev, band, u, f, y);
+  size_t sm = sizeof(TV) * (AY + 2 * max_p) * (AX + 2 * max_p);
+  k_band_apply_2d<TV, TB><<<grid, dim3(AX, AY), sm, s>>>(pd_dev, band, u, f, y);
   return cudaGetLastError();
 }
+template cudaError_t launch_band_apply_2d<double, double>(cudaStream_t, const PatchDev*, int, int, int, int,
+                                                          const double*, const double*, const double*, double*);
+template cudaError_t launch_band_apply_2d<float, float>(cudaStream_t, const PatchDev*, int, int, int, int,
+                                                        const float*, const float*, const float*, float*);
+template cudaError_t launch_band_apply_2d<float, __nv_bfloat16>(cudaStream_t, const PatchDev*, int, int, int, int,
+                                                                const __nv_bfloat16*, const float*, const float*,
+                                                                float*);
 
-// ---------------------------------------------------------------- batched FP64 GEMM
+// ---------------------------------------------------------------- batched GEMM
 
 // C = op(A) op(B) with an epilogue, one output tile of 8R x 8R per block of 64 threads;
 // thread (tx, ty) owns rows ty + 8r and columns tx + 8c (r, c < R).  Rows/columns of the
 // tile beyond M/N and the k-slab beyond K are skipped warp-uniformly, so ragged sizes
-// (e.g. 258 = 8*32 + 2) waste FP64 work only at 8-granularity.
+// (e.g. 258 = 8*32 + 2) waste FMA work only at 8-granularity.  T = double (FP64 path) or
+// float (FP32 inner solves).
 namespace {
 constexpr int GK = 16;
 
-template <int R>
-__device__ __forceinline__ void gemm_tile(const GemmDesc& d, int ta, int tb, int epi, double alpha,
+template <int R, class T>
+__device__ __forceinline__ void gemm_tile(const GemmDescT<T>& d, int ta, int tb, int epi, T alpha,
                                           int bx, int by) {
   constexpr int BT = 8 * R;
   const int i0 = by * BT, j0 = bx * BT;
   if (i0 >= d.M || j0 >= d.N) return;
-  __shared__ double As[GK][BT + 1];
-  __shared__ double Bs[GK][BT + 1];
+  __shared__ T As[GK][BT + 1];
+  __shared__ T Bs[GK][BT + 1];
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const int wty = (tid >> 5) * 4;  // smallest ty of this warp
   int rv = 0, cv = 0;              // warp-uniform counts of live micro-rows / micro-columns
@@ -101,31 +123,31 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& d, int ta, int tb, int
   for (int r = 0; r < R; ++r) rv += (i0 + wty + 8 * r < d.M) ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < R; ++c) cv += (j0 + 8 * c < d.N) ? 1 : 0;
-  double acc[R][R];
+  T acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < R; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < R; ++c) acc[r][c] = T(0);
   for (int k0 = 0; k0 < d.K; k0 += GK) {
     for (int idx = tid; idx < BT * GK; idx += 64) {
       int i, kk;
       if (ta) { i = idx % BT; kk = idx / BT; } else { kk = idx % GK; i = idx / GK; }
       int gi = i0 + i, gk = k0 + kk;
-      double v = 0.0;
+      T v = T(0);
       if (gi < d.M && gk < d.K) v = ta ? d.A[int64_t(gk) * d.lda + gi] : d.A[int64_t(gi) * d.lda + gk];
       As[kk][i] = v;
       int j;
       if (tb) { kk = idx % GK; j = idx / GK; } else { j = idx % BT; kk = idx / BT; }
       int gj = j0 + j;
       gk = k0 + kk;
-      v = 0.0;
+      v = T(0);
       if (gj < d.N && gk < d.K) v = tb ? d.B[int64_t(gj) * d.ldb + gk] : d.B[int64_t(gk) * d.ldb + gj];
       Bs[kk][j] = v;
     }
     __syncthreads();
     const int kmax = min(GK, d.K - k0);
     for (int kk = 0; kk < kmax; ++kk) {
-      double a[R], b[R];
+      T a[R], b[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) a[r] = As[kk][ty + 8 * r];
 #pragma unroll
@@ -149,8 +171,8 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& d, int ta, int tb, int
     for (int c = 0; c < R; ++c) {
       int gj = j0 + tx + 8 * c;
       if (gj >= d.N) continue;
-      double v = acc[r][c];
-      double* cp = d.C + int64_t(gi) * d.ldc + gj;
+      T v = acc[r][c];
+      T* cp = d.C + int64_t(gi) * d.ldc + gj;
       switch (epi) {
         case EPI_MUL: *cp = v * d.E[int64_t(gi) * d.lde + gj]; break;
         case EPI_ROWSCALE: *cp = v * d.E[gi]; break;
@@ -164,15 +186,15 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& d, int ta, int tb, int
 }
 }  // namespace
 
-template <int R>
-__global__ void __launch_bounds__(64) k_gemm_f64(const GemmDesc* __restrict__ descs, int ta, int tb, int epi,
-                                                 double alpha) {
-  gemm_tile<R>(descs[blockIdx.z], ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
+template <int R, class T>
+__global__ void __launch_bounds__(64) k_gemm(const GemmDescT<T>* __restrict__ descs, int ta, int tb, int epi,
+                                             T alpha) {
+  gemm_tile<R, T>(descs[blockIdx.z], ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
 }
 
-template <int R>
-__global__ void __launch_bounds__(64) k_gemm_f64_one(GemmDesc d, int ta, int tb, int epi, double alpha) {
-  gemm_tile<R>(d, ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
+template <int R, class T>
+__global__ void __launch_bounds__(64) k_gemm_one(GemmDescT<T> d, int ta, int tb, int epi, T alpha) {
+  gemm_tile<R, T>(d, ta, tb, epi, alpha, blockIdx.x, blockIdx.y);
 }
 
 // Tile edge 8R: 32 when the 32-wide grid already fills the GPU twice, else 16, else 8.
@@ -183,43 +205,48 @@ static int pick_r(int maxM, int maxN, int batch) {
   return 1;
 }
 
-cudaError_t launch_gemm(cudaStream_t s, const GemmDesc* d_desc, int batch, int maxM, int maxN,
-                        bool transA, bool transB, int epi, double alpha) {
+template <class T>
+cudaError_t launch_gemm(cudaStream_t s, const GemmDescT<T>* d_desc, int batch, int maxM, int maxN,
+                        bool transA, bool transB, int epi, T alpha) {
   if (batch <= 0) return cudaSuccess;
   int R = pick_r(maxM, maxN, batch), bt = 8 * R;
   dim3 grid((maxN + bt - 1) / bt, (maxM + bt - 1) / bt, batch);
-  if (R == 4) k_gemm_f64<4><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
-  else if (R == 2) k_gemm_f64<2><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
-  else k_gemm_f64<1><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  if (R == 4) k_gemm<4, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  else if (R == 2) k_gemm<2, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
+  else k_gemm<1, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
   return cudaGetLastError();
 }
+template cudaError_t launch_gemm<double>(cudaStream_t, const GemmDescT<double>*, int, int, int, bool, bool, int, double);
+template cudaError_t launch_gemm<float>(cudaStream_t, const GemmDescT<float>*, int, int, int, bool, bool, int, float);
 
 cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
                             double alpha) {
   int R = pick_r(d.M, d.N, 1), bt = 8 * R;
   dim3 grid((d.N + bt - 1) / bt, (d.M + bt - 1) / bt, 1);
-  if (R == 4) k_gemm_f64_one<4><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
-  else if (R == 2) k_gemm_f64_one<2><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
-  else k_gemm_f64_one<1><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
+  if (R == 4) k_gemm_one<4, double><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
+  else if (R == 2) k_gemm_one<2, double><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
+  else k_gemm_one<1, double><<<grid, 64, 0, s>>>(d, transA, transB, epi, alpha);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- interface pieces
 
+template <class T>
 __global__ void k_iface_gather(int64_t n, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
-                               const double* __restrict__ v, double* __restrict__ G) {
+                               const T* __restrict__ v, T* __restrict__ G) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     for (int64_t c = ptr[i]; c < ptr[i + 1]; ++c) s += v[idx[c]];
     G[i] = s;
   }
 }
 
+template <class T>
 __global__ void k_iface_scatter(int64_t n, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
-                                const double* __restrict__ Z, const double* __restrict__ G,
-                                const double* __restrict__ vs, double tau, int add, double* __restrict__ u) {
+                                const T* __restrict__ Z, const T* __restrict__ G,
+                                const T* __restrict__ vs, T tau, int add, T* __restrict__ u) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    double val = tau * fma(vs[i], G[i], Z[i]);
+    T val = tau * fma(vs[i], G[i], Z[i]);
     for (int64_t c = ptr[i]; c < ptr[i + 1]; ++c) {
       int64_t t = idx[c];
       u[t] = add ? u[t] + val : val;
@@ -233,30 +260,39 @@ static int grid_for(int64_t n, int threads, int cap = 4 * 152 * 8) {
   return int(g < cap ? g : cap);
 }
 
+template <class T>
 cudaError_t launch_iface_gather(cudaStream_t s, int64_t n_nodes, const int64_t* ptr,
-                                const int64_t* idx, const double* v, double* G) {
+                                const int64_t* idx, const T* v, T* G) {
   if (n_nodes <= 0) return cudaSuccess;
-  k_iface_gather<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, v, G);
+  k_iface_gather<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, v, G);
   return cudaGetLastError();
 }
 
+template <class T>
 cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t* ptr,
-                                 const int64_t* idx, const double* Z, const double* G,
-                                 const double* vscale, double tau, int add, double* u) {
+                                 const int64_t* idx, const T* Z, const T* G,
+                                 const T* vscale, T tau, int add, T* u) {
   if (n_nodes <= 0) return cudaSuccess;
-  k_iface_scatter<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, Z, G, vscale, tau, add, u);
+  k_iface_scatter<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, Z, G, vscale, tau, add, u);
   return cudaGetLastError();
 }
+#define INST_IF(T)                                                                                          \
+  template cudaError_t launch_iface_gather<T>(cudaStream_t, int64_t, const int64_t*, const int64_t*, const T*, T*); \
+  template cudaError_t launch_iface_scatter<T>(cudaStream_t, int64_t, const int64_t*, const int64_t*, const T*,     \
+                                               const T*, const T*, T, int, T*);
+INST_IF(double)
+INST_IF(float)
 
 // ---------------------------------------------------------------- coarse solve (Sec. 4)
 
+// x_copies = A0^{-1} (sum of copies of f), in FP64 whatever the vector type T.
+template <class T>
 __global__ void k_coarse_solve(int64_t N0, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
-                               const double* __restrict__ Ainv, const double* __restrict__ f,
-                               double* __restrict__ x) {
+                               const double* __restrict__ Ainv, const T* __restrict__ f, T* __restrict__ x) {
   extern __shared__ double g[];
   for (int64_t i = threadIdx.x; i < N0; i += blockDim.x) {
     double s = 0.0;
-    for (int64_t c = ptr[i]; c < ptr[i + 1]; ++c) s += f[idx[c]];
+    for (int64_t c = ptr[i]; c < ptr[i + 1]; ++c) s += double(f[idx[c]]);
     g[i] = s;
   }
   __syncthreads();
@@ -266,75 +302,90 @@ __global__ void k_coarse_solve(int64_t N0, const int64_t* __restrict__ ptr, cons
     for (int64_t c = lane; c < N0; c += 32) acc = fma(Ainv[r * N0 + c], g[c], acc);
     acc = warp_sum(acc);
     acc = __shfl_sync(0xffffffffu, acc, 0);
-    for (int64_t c = ptr[r] + lane; c < ptr[r + 1]; c += 32) x[idx[c]] = acc;
+    for (int64_t c = ptr[r] + lane; c < ptr[r + 1]; c += 32) x[idx[c]] = T(acc);
   }
 }
 
+template <class T>
 cudaError_t launch_coarse_solve(cudaStream_t s, int64_t N0, const int64_t* ptr,
-                                const int64_t* idx, const double* A0inv, const double* f,
-                                double* x) {
+                                const int64_t* idx, const double* A0inv, const T* f, T* x) {
   if (N0 <= 0) return cudaSuccess;
   int blocks = int((N0 + 7) / 8);
   if (blocks > 152) blocks = 152;
-  k_coarse_solve<<<blocks, 256, sizeof(double) * N0, s>>>(N0, ptr, idx, A0inv, f, x);
+  k_coarse_solve<T><<<blocks, 256, sizeof(double) * N0, s>>>(N0, ptr, idx, A0inv, f, x);
   return cudaGetLastError();
 }
+template cudaError_t launch_coarse_solve<double>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                                 const double*, const double*, double*);
+template cudaError_t launch_coarse_solve<float>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                                const double*, const float*, float*);
 
 // ---------------------------------------------------------------- global <-> tiles
 
+template <class T>
 __global__ void k_global_to_tile(int64_t N, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
-                                 const double* __restrict__ xg, double* __restrict__ xt, int first_only) {
+                                 const T* __restrict__ xg, T* __restrict__ xt, int first_only) {
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < N; g += int64_t(gridDim.x) * blockDim.x) {
-    double v = xg[g];
-    for (int64_t c = ptr[g]; c < ptr[g + 1]; ++c) xt[idx[c]] = (first_only && c > ptr[g]) ? 0.0 : v;
+    T v = xg[g];
+    for (int64_t c = ptr[g]; c < ptr[g + 1]; ++c) xt[idx[c]] = (first_only && c > ptr[g]) ? T(0) : v;
   }
 }
 
+template <class T>
 __global__ void k_tile_to_global(int64_t N, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
-                                 const double* __restrict__ xt, double* __restrict__ xg, int sum_copies) {
+                                 const T* __restrict__ xt, T* __restrict__ xg, int sum_copies) {
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < N; g += int64_t(gridDim.x) * blockDim.x) {
-    double v = xt[idx[ptr[g]]];
+    T v = xt[idx[ptr[g]]];
     if (sum_copies)
       for (int64_t c = ptr[g] + 1; c < ptr[g + 1]; ++c) v += xt[idx[c]];
     xg[g] = v;
   }
 }
 
+template <class T>
 cudaError_t launch_global_to_tile(cudaStream_t s, int64_t N, const int64_t* ptr,
-                                  const int64_t* idx, const double* xg, double* xt, int first_only) {
+                                  const int64_t* idx, const T* xg, T* xt, int first_only) {
   if (N <= 0) return cudaSuccess;
-  k_global_to_tile<<<grid_for(N, 256), 256, 0, s>>>(N, ptr, idx, xg, xt, first_only);
+  k_global_to_tile<T><<<grid_for(N, 256), 256, 0, s>>>(N, ptr, idx, xg, xt, first_only);
   return cudaGetLastError();
 }
 
+template <class T>
 cudaError_t launch_tile_to_global(cudaStream_t s, int64_t N, const int64_t* ptr,
-                                  const int64_t* idx, const double* xt, double* xg, int sum_copies) {
+                                  const int64_t* idx, const T* xt, T* xg, int sum_copies) {
   if (N <= 0) return cudaSuccess;
-  k_tile_to_global<<<grid_for(N, 256), 256, 0, s>>>(N, ptr, idx, xt, xg, sum_copies);
+  k_tile_to_global<T><<<grid_for(N, 256), 256, 0, s>>>(N, ptr, idx, xt, xg, sum_copies);
   return cudaGetLastError();
 }
+template cudaError_t launch_global_to_tile<double>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                                   const double*, double*, int);
+template cudaError_t launch_tile_to_global<double>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                                   const double*, double*, int);
 
 // ---------------------------------------------------------------- reductions, PCG
 
-__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
+// Partial sums in FP64 whatever the vector type (deterministic fixed grid).
+template <class T>
+__global__ void __launch_bounds__(256) k_dot_partial(const T* __restrict__ a, const T* __restrict__ b,
                                                      int64_t n, double* __restrict__ partials) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256)
-    s = fma(a[i], b[i], s);
+    s = fma(double(a[i]), double(b[i]), s);
   s = block_sum_256(s, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) k_norm2_dist_partial(int64_t N, const int64_t* __restrict__ ptr,
                                                             const int64_t* __restrict__ idx,
-                                                            const double* __restrict__ v,
+                                                            const T* __restrict__ v,
                                                             double* __restrict__ partials) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t g = blockIdx.x * int64_t(256) + threadIdx.x; g < N; g += int64_t(gridDim.x) * 256) {
     double c = 0.0;
-    for (int64_t k = ptr[g]; k < ptr[g + 1]; ++k) c += v[idx[k]];
+    for (int64_t k = ptr[g]; k < ptr[g + 1]; ++k) c += double(v[idx[k]]);
     s = fma(c, c, s);
   }
   s = block_sum_256(s, sh);
@@ -350,57 +401,98 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__
   if (threadIdx.x == 0) *out = s;
 }
 
-cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t n,
-                       double* partials, double* out) {
-  k_dot_partial<<<RED_BLOCKS, 256, 0, s>>>(a, b, n, partials);
+template <class T>
+cudaError_t launch_dot(cudaStream_t s, const T* a, const T* b, int64_t n, double* partials, double* out) {
+  k_dot_partial<T><<<RED_BLOCKS, 256, 0, s>>>(a, b, n, partials);
   k_reduce_final<<<1, 256, 0, s>>>(partials, RED_BLOCKS, out);
   return cudaGetLastError();
 }
 
+template <class T>
 cudaError_t launch_norm2_dist(cudaStream_t s, int64_t N, const int64_t* ptr, const int64_t* idx,
-                              const double* v, double* partials, double* out) {
-  k_norm2_dist_partial<<<RED_BLOCKS, 256, 0, s>>>(N, ptr, idx, v, partials);
+                              const T* v, double* partials, double* out) {
+  k_norm2_dist_partial<T><<<RED_BLOCKS, 256, 0, s>>>(N, ptr, idx, v, partials);
   k_reduce_final<<<1, 256, 0, s>>>(partials, RED_BLOCKS, out);
   return cudaGetLastError();
 }
+template cudaError_t launch_dot<double>(cudaStream_t, const double*, const double*, int64_t, double*, double*);
+template cudaError_t launch_dot<float>(cudaStream_t, const float*, const float*, int64_t, double*, double*);
+template cudaError_t launch_norm2_dist<double>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                               const double*, double*, double*);
+template cudaError_t launch_norm2_dist<float>(cudaStream_t, int64_t, const int64_t*, const int64_t*,
+                                              const float*, double*, double*);
 
-__global__ void k_pcg_xr(int64_t n, const double* __restrict__ scal, double* __restrict__ x,
-                         double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ w) {
-  const double alpha = scal[0] / scal[1];
+template <class T>
+__global__ void k_pcg_xr(int64_t n, const double* __restrict__ scal, T* __restrict__ x,
+                         T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ w) {
+  const T alpha = T(scal[0] / scal[1]);
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     r[i] = fma(-alpha, w[i], r[i]);
   }
 }
 
-__global__ void k_pcg_p(int64_t n, const double* __restrict__ scal, double* __restrict__ p,
-                        const double* __restrict__ z) {
-  const double beta = scal[2] / scal[0];
+template <class T>
+__global__ void k_pcg_p(int64_t n, const double* __restrict__ scal, T* __restrict__ p,
+                        const T* __restrict__ z) {
+  const T beta = T(scal[2] / scal[0]);
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     p[i] = fma(beta, p[i], z[i]);
 }
 
 __global__ void k_scalar_shift(double* scal) { scal[0] = scal[2]; }
 
+template <class T>
+cudaError_t launch_pcg_xr(cudaStream_t s, int64_t n, const double* scal, T* x, T* r, const T* p, const T* w) {
+  k_pcg_xr<T><<<grid_for(n, 256), 256, 0, s>>>(n, scal, x, r, p, w);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, T* p, const T* z) {
+  k_pcg_p<T><<<grid_for(n, 256), 256, 0, s>>>(n, scal, p, z);
+  k_scalar_shift<<<1, 1, 0, s>>>(scal);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pcg_xr<double>(cudaStream_t, int64_t, const double*, double*, double*, const double*,
+                                           const double*);
+template cudaError_t launch_pcg_xr<float>(cudaStream_t, int64_t, const double*, float*, float*, const float*,
+                                          const float*);
+template cudaError_t launch_pcg_p<double>(cudaStream_t, int64_t, double*, double*, const double*);
+template cudaError_t launch_pcg_p<float>(cudaStream_t, int64_t, double*, float*, const float*);
+
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 
-cudaError_t launch_pcg_xr(cudaStream_t s, int64_t n, const double* scal, double* x, double* r,
-                          const double* p, const double* w) {
-  k_pcg_xr<<<grid_for(n, 256), 256, 0, s>>>(n, scal, x, r, p, w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, double* p, const double* z) {
-  k_pcg_p<<<grid_for(n, 256), 256, 0, s>>>(n, scal, p, z);
-  k_scalar_shift<<<1, 1, 0, s>>>(scal);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y) {
   k_axpby<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
+// Precision conversions of whole vectors: dst = scale * src.
+template <class TD, class TS>
+__global__ void k_convert(int64_t n, const TS* __restrict__ src, double scale, TD* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = TD(double(src[i]) * scale);
+}
+// x64 += scale * d32 (iterative refinement update)
+__global__ void k_add_scaled_f32(int64_t n, const float* __restrict__ d, double scale, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = fma(scale, double(d[i]), x[i]);
+}
+
+cudaError_t launch_convert_f64_f32(cudaStream_t s, int64_t n, const double* src, double scale, float* dst) {
+  k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>(n, src, scale, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_f64_bf16(cudaStream_t s, int64_t n, const double* src, __nv_bfloat16* dst) {
+  k_convert<__nv_bfloat16, double><<<grid_for(n, 256), 256, 0, s>>>(n, src, 1.0, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_scaled_f32(cudaStream_t s, int64_t n, const float* d, double scale, double* x) {
+  k_add_scaled_f32<<<grid_for(n, 256), 256, 0, s>>>(n, d, scale, x);
   return cudaGetLastError();
 }
 
@@ -623,94 +715,111 @@ namespace {
 constexpr int BX3 = 32, BY3 = 4, BZ3 = 2;
 }
 
+template <class TV, class TB>
 __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDev* __restrict__ pds,
-                                                                   const double* __restrict__ band,
-                                                                   const double* __restrict__ u,
-                                                                   const double* __restrict__ f,
-                                                                   double* __restrict__ y, int tiles1) {
-  extern __shared__ double su[];
+                                                                   const TB* __restrict__ band,
+                                                                   const TV* __restrict__ u,
+                                                                   const TV* __restrict__ f,
+                                                                   TV* __restrict__ y, int tiles1) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TV* su = reinterpret_cast<TV*>(smraw);
   const PatchDev pd = pds[blockIdx.z];
   const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2], p0 = pd.p[0], p1 = pd.p[1], p2 = pd.p[2];
   const int i0b = (blockIdx.y / tiles1) * BZ3, i1b = (blockIdx.y % tiles1) * BY3, i2b = blockIdx.x * BX3;
   if (i0b >= n0 || i1b >= n1 || i2b >= n2) return;
   const int H0 = BZ3 + 2 * p0, H1 = BY3 + 2 * p1, H2 = BX3 + 2 * p2;
-  const double* ut = u + pd.off;
+  const TV* ut = u + pd.off;
   const int tid = (threadIdx.z * BY3 + threadIdx.y) * BX3 + threadIdx.x;
   for (int idx = tid; idx < H0 * H1 * H2; idx += BX3 * BY3 * BZ3) {
     int a = idx / (H1 * H2), rem = idx % (H1 * H2), b = rem / H2, c = rem % H2;
     int g0 = i0b - p0 + a, g1 = i1b - p1 + b, g2 = i2b - p2 + c;
     su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1 && g2 >= 0 && g2 < n2)
-                  ? ut[(int64_t(g0) * n1 + g1) * n2 + g2] : 0.0;
+                  ? ut[(int64_t(g0) * n1 + g1) * n2 + g2] : TV(0);
   }
   __syncthreads();
   const int i0 = i0b + threadIdx.z, i1 = i1b + threadIdx.y, i2 = i2b + threadIdx.x;
   if (i0 >= n0 || i1 >= n1 || i2 >= n2) return;
   const int64_t nn = int64_t(n0) * n1 * n2, node = (int64_t(i0) * n1 + i1) * n2 + i2;
-  const double* bp = band + pd.band_off + node;
+  const TB* bp = band + pd.band_off + node;
   const int w1 = 2 * p1 + 1, w2 = 2 * p2 + 1;
-  double acc = 0.0;
+  TV acc = 0;
   int t = 0;
   for (int t0 = 0; t0 <= 2 * p0; ++t0)
     for (int t1 = 0; t1 < w1; ++t1) {
-      const double* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
-      for (int t2 = 0; t2 < w2; ++t2, ++t) acc = fma(__ldg(bp + int64_t(t) * nn), srow[t2], acc);
+      const TV* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
+      for (int t2 = 0; t2 < w2; ++t2, ++t) acc = fma(band_val<TV, TB>(bp + int64_t(t) * nn), srow[t2], acc);
     }
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
 }
 
+template <class TV, class TB>
 cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
-                                 const double* band, const double* u, const double* f, double* y) {
+                                 const TB* band, const TV* u, const TV* f, TV* y) {
   int t1 = (max_n[1] + BY3 - 1) / BY3, t0 = (max_n[0] + BZ3 - 1) / BZ3;
   dim3 grid((max_n[2] + BX3 - 1) / BX3, t0 * t1, K);
-  size_t sm = sizeof(double) * (BZ3 + 2 * max_p) * (BY3 + 2 * max_p) * (BX3 + 2 * max_p);
-  cudaError_t e = cudaFuncSetAttribute(k_band_apply_3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  size_t sm = sizeof(TV) * (BZ3 + 2 * max_p) * (BY3 + 2 * max_p) * (BX3 + 2 * max_p);
+  cudaError_t e = cudaFuncSetAttribute(k_band_apply_3d<TV, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   if (e != cudaSuccess) return e;
-  k_band_apply_3d<<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
+  k_band_apply_3d<TV, TB><<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
   return cudaGetLastError();
 }
+template cudaError_t launch_band_apply_3d<double, double>(cudaStream_t, const PatchDev*, int, const int*, int,
+                                                          const double*, const double*, const double*, double*);
+template cudaError_t launch_band_apply_3d<float, float>(cudaStream_t, const PatchDev*, int, const int*, int,
+                                                        const float*, const float*, const float*, float*);
+template cudaError_t launch_band_apply_3d<float, __nv_bfloat16>(cudaStream_t, const PatchDev*, int, const int*, int,
+                                                                const __nv_bfloat16*, const float*, const float*,
+                                                                float*);
 
 // ---------------------------------------------------------------- 1D transfer along one direction
 
 // out[i_<j, o, i_>j] (=|+=) sum_w wt[o][w] in[i_<j, st[o] + w, i_>j] for one patch per
-// blockIdx.y; shapes/offsets from Xfer1D.  Restriction uses the column band of P_l,
+// blockIdx.y; shapes/offsets from XferT.  Restriction uses the column band of P_l,
 // prolongation its row band.  mask: zero outputs whose node is eliminated (coarse
 // Dirichlet after restriction).
-__global__ void k_transfer_1d(const Xfer1D* __restrict__ xs, const double* __restrict__ in,
-                              double* __restrict__ out, int add, const int64_t* __restrict__ mask) {
-  const Xfer1D x = xs[blockIdx.y];
+template <class T>
+__global__ void k_transfer_1d(const XferT<T>* __restrict__ xs, const T* __restrict__ in,
+                              T* __restrict__ out, int add, const int64_t* __restrict__ mask) {
+  const XferT<T> x = xs[blockIdx.y];
   const int64_t total = int64_t(x.outer) * x.nout * x.inner;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     int64_t oi = i / (int64_t(x.nout) * x.inner), rem = i % (int64_t(x.nout) * x.inner);
     int o = int(rem / x.inner), ii = int(rem % x.inner);
-    const double* w = x.wt + int64_t(o) * x.width;
+    const T* w = x.wt + int64_t(o) * x.width;
     int s0 = x.st[o];
-    const double* src = in + x.in_off + (oi * x.nin) * x.inner + ii;
-    double acc = 0.0;
+    const T* src = in + x.in_off + (oi * x.nin) * x.inner + ii;
+    T acc = 0;
     for (int a = 0; a < x.width; ++a) {
       int k = s0 + a;
       if (k < x.nin) acc = fma(w[a], src[int64_t(k) * x.inner], acc);
     }
     int64_t t = x.out_off + i;
-    if (mask && mask[t] < 0) acc = 0.0;
+    if (mask && mask[t] < 0) acc = 0;
     out[t] = add ? out[t] + acc : acc;
   }
 }
 
-cudaError_t launch_transfer_1d(cudaStream_t s, const Xfer1D* xs, int npatch, int64_t max_out,
-                               const double* in, double* out, int add, const int64_t* mask) {
+template <class T>
+cudaError_t launch_transfer_1d(cudaStream_t s, const XferT<T>* xs, int npatch, int64_t max_out,
+                               const T* in, T* out, int add, const int64_t* mask) {
   int64_t g = (max_out + 255) / 256;
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
-  k_transfer_1d<<<dim3(unsigned(g), npatch), 256, 0, s>>>(xs, in, out, add, mask);
+  k_transfer_1d<T><<<dim3(unsigned(g), npatch), 256, 0, s>>>(xs, in, out, add, mask);
   return cudaGetLastError();
 }
+template cudaError_t launch_transfer_1d<double>(cudaStream_t, const XferT<double>*, int, int64_t, const double*,
+                                                double*, int, const int64_t*);
+template cudaError_t launch_transfer_1d<float>(cudaStream_t, const XferT<float>*, int, int64_t, const float*, float*,
+                                               int, const int64_t*);
 
 // ---------------------------------------------------------------- interior box gather/scatter
 
 // Compact copy of every patch-interior box (3D FD works on compact tensors) and the
 // scatter of tau * Z back into the boxes.
-__global__ void k_box_copy(const BoxDev* __restrict__ boxes, const double* __restrict__ src, double* __restrict__ dst,
-                           int to_compact, double tau, int add) {
+template <class T>
+__global__ void k_box_copy(const BoxDev* __restrict__ boxes, const T* __restrict__ src, T* __restrict__ dst,
+                           int to_compact, T tau, int add) {
   const BoxDev b = boxes[blockIdx.y];
   const int64_t total = int64_t(b.len[0]) * b.len[1] * b.len[2];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
@@ -723,14 +832,19 @@ __global__ void k_box_copy(const BoxDev* __restrict__ boxes, const double* __res
   }
 }
 
-cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const double* src,
-                            double* dst, int to_compact, double tau, int add) {
+template <class T>
+cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const T* src,
+                            T* dst, int to_compact, T tau, int add) {
   if (nbox <= 0) return cudaSuccess;
   int64_t g = (max_box + 255) / 256;
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
-  k_box_copy<<<dim3(unsigned(g), nbox), 256, 0, s>>>(boxes, src, dst, to_compact, tau, add);
+  k_box_copy<T><<<dim3(unsigned(g), nbox), 256, 0, s>>>(boxes, src, dst, to_compact, tau, add);
   return cudaGetLastError();
 }
+template cudaError_t launch_box_copy<double>(cudaStream_t, const BoxDev*, int, int64_t, const double*, double*, int,
+                                             double, int);
+template cudaError_t launch_box_copy<float>(cudaStream_t, const BoxDev*, int, int64_t, const float*, float*, int,
+                                            float, int);
 
 }  // namespace igamg

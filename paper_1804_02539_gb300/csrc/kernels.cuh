@@ -1,8 +1,11 @@
 // Device kernels of the multigrid-preconditioned CG (FP64 path) and their launchers.
 // Every launcher takes the stream explicitly and returns the launch status.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
 #include <cstdint>
+#include <type_traits>
 
 namespace igamg {
 
@@ -16,18 +19,20 @@ struct PatchDev {
 };
 
 // Batched GEMM descriptor: C = op(A) op(B), M x N with inner dimension K (row-major).
-struct GemmDesc {
-  const double* A;
-  const double* B;
-  double* C;
-  const double* E;  // epilogue operand (matrix M x N with lde, or vector of length M)
+template <class T>
+struct GemmDescT {
+  const T* A;
+  const T* B;
+  T* C;
+  const T* E;  // epilogue operand (matrix M x N with lde, or vector of length M / N)
   int lda, ldb, ldc, lde;
   int M, N, K;
 };
+using GemmDesc = GemmDescT<double>;
 
 enum GemmEpilogue { EPI_STORE = 0, EPI_MUL = 1, EPI_ROWSCALE = 2, EPI_ASSIGN = 3, EPI_ADD = 4, EPI_COLSCALE = 5 };
 
-// Element-by-element assembly of one patch (any colour loop inside the launcher).
+// Element-by-element assembly of one patch (the colour loop is inside the launcher).
 struct ElemAsm {
   int dim, p, mass;
   int n[3], m[3], color[3];
@@ -43,71 +48,85 @@ struct ElemAsm {
 cudaError_t launch_assemble_elem(cudaStream_t s, const ElemAsm& ea);
 size_t elem_asm_smem(int D, int p, bool mass);
 
-// 3D band apply (same contract as the 2D one).
+// y = f - A u per tile (residual) or y = A u when f == NULL (apply).  TV vector type,
+// TB band storage type: (double, double), (float, float), (float, __nv_bfloat16).
+template <class TV, class TB>
+cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0, int max_n1, int max_p,
+                                 const TB* band, const TV* u, const TV* f, TV* y);
+template <class TV, class TB>
 cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
-                                 const double* band, const double* u, const double* f, double* y);
+                                 const TB* band, const TV* u, const TV* f, TV* y);
+
+template <class T>
+cudaError_t launch_gemm(cudaStream_t s, const GemmDescT<T>* d_desc, int batch, int maxM, int maxN,
+                        bool transA, bool transB, int epi, T alpha);
+// One FP64 GEMM with the descriptor passed by value (no device-side descriptor array).
+cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
+                            double alpha);
+
+// Interface pieces: gather sums of the copies of every interface node from a
+// distributed vector; scatter tau * (Z + vscale * G) to every copy of an accumulated vector.
+template <class T>
+cudaError_t launch_iface_gather(cudaStream_t s, int64_t n_nodes, const int64_t* ptr, const int64_t* idx,
+                                const T* v, T* G);
+template <class T>
+cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t* ptr, const int64_t* idx,
+                                 const T* Z, const T* G, const T* vscale, T tau, int add, T* u);
 
 // One direction of a tensor transfer: out has `nout` entries along the direction, in has
 // `nin`; outer/inner are the products of the sizes before/after it.
-struct Xfer1D {
+template <class T>
+struct XferT {
   int64_t in_off, out_off;
   int outer, inner, nin, nout, width;
-  const double* wt;  // [nout][width]
-  const int* st;     // [nout]
+  const T* wt;   // [nout][width]
+  const int* st; // [nout]
 };
-cudaError_t launch_transfer_1d(cudaStream_t s, const Xfer1D* xs, int npatch, int64_t max_out,
-                               const double* in, double* out, int add, const int64_t* mask);
+template <class T>
+cudaError_t launch_transfer_1d(cudaStream_t s, const XferT<T>* xs, int npatch, int64_t max_out, const T* in, T* out,
+                               int add, const int64_t* mask);
 
 // Interior box of a tile <-> compact tensor.
 struct BoxDev {
   int64_t tile_off, compact_off;
   int n[3], lo[3], len[3];
 };
-cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const double* src,
-                            double* dst, int to_compact, double tau, int add);
+template <class T>
+cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const T* src, T* dst,
+                            int to_compact, T tau, int add);
 
-// y = f - A u per tile (residual) or y = A u when f == NULL (apply).
-cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0,
-                                 int max_n1, int max_p, const double* band, const double* u,
-                                 const double* f, double* y);
-
-cudaError_t launch_gemm(cudaStream_t s, const GemmDesc* d_desc, int batch, int maxM, int maxN,
-                        bool transA, bool transB, int epi, double alpha);
-// One GEMM with the descriptor passed by value (no device-side descriptor array).
-cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
-                            double alpha);
-
-// Interface pieces: gather sums of the copies of every interface node from a
-// distributed vector; scatter tau * value to every copy of an accumulated vector.
-cudaError_t launch_iface_gather(cudaStream_t s, int64_t n_nodes, const int64_t* ptr,
-                                const int64_t* idx, const double* v, double* G);
-cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t* ptr,
-                                 const int64_t* idx, const double* Z, const double* G,
-                                 const double* vscale, double tau, int add, double* u);
-
-// Coarse solve: x_copies = A0inv * (sum of copies of f) for the N0 level-0 dofs.
-cudaError_t launch_coarse_solve(cudaStream_t s, int64_t N0, const int64_t* ptr,
-                                const int64_t* idx, const double* A0inv, const double* f,
-                                double* x);
+// Coarse solve in FP64: x_copies = A0inv * (sum of copies of f) for the N0 level-0 dofs.
+template <class T>
+cudaError_t launch_coarse_solve(cudaStream_t s, int64_t N0, const int64_t* ptr, const int64_t* idx,
+                                const double* A0inv, const T* f, T* x);
 
 // Global <-> tile conversions (g2t CSR of copies per global dof).
-cudaError_t launch_global_to_tile(cudaStream_t s, int64_t N, const int64_t* ptr,
-                                  const int64_t* idx, const double* xg, double* xt, int first_only);
-cudaError_t launch_tile_to_global(cudaStream_t s, int64_t N, const int64_t* ptr,
-                                  const int64_t* idx, const double* xt, double* xg, int sum_copies);
+template <class T>
+cudaError_t launch_global_to_tile(cudaStream_t s, int64_t N, const int64_t* ptr, const int64_t* idx, const T* xg,
+                                  T* xt, int first_only);
+template <class T>
+cudaError_t launch_tile_to_global(cudaStream_t s, int64_t N, const int64_t* ptr, const int64_t* idx, const T* xt,
+                                  T* xg, int sum_copies);
 
-// Deterministic reductions: fixed grid of `nblocks` partial sums, then one block.
+// Deterministic reductions (FP64 partials): fixed grid of RED_BLOCKS partial sums, then one block.
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
-cudaError_t launch_dot(cudaStream_t s, const double* a, const double* b, int64_t n,
-                       double* partials, double* out);
+template <class T>
+cudaError_t launch_dot(cudaStream_t s, const T* a, const T* b, int64_t n, double* partials, double* out);
 // sum over active dofs of (sum of copies of v)^2 for a distributed vector v
-cudaError_t launch_norm2_dist(cudaStream_t s, int64_t N, const int64_t* ptr, const int64_t* idx,
-                              const double* v, double* partials, double* out);
+template <class T>
+cudaError_t launch_norm2_dist(cudaStream_t s, int64_t N, const int64_t* ptr, const int64_t* idx, const T* v,
+                              double* partials, double* out);
 
 // PCG updates with scalars kept on the device: scal[0]=rz, scal[1]=pw, scal[2]=rz_new.
-cudaError_t launch_pcg_xr(cudaStream_t s, int64_t n, const double* scal, double* x, double* r,
-                          const double* p, const double* w);
-cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, double* p, const double* z);
+template <class T>
+cudaError_t launch_pcg_xr(cudaStream_t s, int64_t n, const double* scal, T* x, T* r, const T* p, const T* w);
+template <class T>
+cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, T* p, const T* z);
 cudaError_t launch_axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y);
+
+// Precision conversions for iterative refinement.
+cudaError_t launch_convert_f64_f32(cudaStream_t s, int64_t n, const double* src, double scale, float* dst);
+cudaError_t launch_convert_f64_bf16(cudaStream_t s, int64_t n, const double* src, __nv_bfloat16* dst);
+cudaError_t launch_add_scaled_f32(cudaStream_t s, int64_t n, const float* d, double scale, double* x);
 
 }  // namespace igamg

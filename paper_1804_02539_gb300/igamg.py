@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libigamg.so")
 
 IGAMG_OK, IGAMG_ERR_NOT_CONVERGED = 0, 7
+IGAMG_FP64, IGAMG_FP32, IGAMG_BF16 = 0, 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_GEOMETRY", 3: "ERR_UNSUPPORTED", 4: "ERR_OOM",
           5: "ERR_CUDA", 6: "ERR_NUMERIC", 7: "ERR_NOT_CONVERGED", 8: "ERR_TIMEOUT"}
 
@@ -27,11 +28,11 @@ class igamg_problem(C.Structure):
 
 class igamg_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("sigma_scale", C.c_double), ("nu", C.c_int),
-                ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int)]
+                ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double)]
 
 
 class igamg_result(C.Structure):
-    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("t_setup_ms", C.c_double),
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("relres", C.c_double), ("t_setup_ms", C.c_double),
                 ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double)]
 
 

@@ -186,6 +186,34 @@ def test_rhs_from_coefs(name):
     assert rel(from_lib(perms[-1], host(b)), Mg @ c) < 1e-13
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "cube_p3_m8", "fichera_p2_m4"])
+def test_mixed_precision_refinement(name, prec):
+    """Precision variant: FP64 iterative refinement around a PCG with FP32 vectors and
+    smoother contractions and FP32 (prec=1) or BF16 (prec=2) bands.  The FP64 residual
+    reaches 1e-8 and the solution agrees with the oracle's FP64 solution to what that
+    residual allows (relative error <= cond-scaled 1e-8, checked as 1e-6)."""
+    from paper_1804_02539_gb300 import igamg
+    pr, H, ctx, perms = setup_case(name)
+    N = H.levels[-1].space.N
+    b = workloads.rhs_coefficients(N, 13)
+    opts = igamg.igamg_default_options()
+    opts.precision = prec
+    cm = igamg.Context(pr, opts)
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    res, st = cm.solve(dev(to_lib(perms[-1], b)), x, 1e-8)
+    assert st == igamg.IGAMG_OK
+    assert res.relres <= 1e-8
+    assert res.outer_iters >= 2
+    ref = solver.pcg(H, b, tol=1e-12, max_iter=400).x
+    assert rel(from_lib(perms[-1], host(x)), ref) < 1e-6
+    # the FP64 residual reported by the library is the true residual
+    A = H.levels[-1].A
+    xo = from_lib(perms[-1], host(x))
+    assert np.linalg.norm(b - A @ xo) <= 1.05e-8 * np.linalg.norm(b)
+    cm.free()
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
