@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <type_traits>
@@ -81,8 +82,9 @@ using GemmSet = GemmSetT<double>;
 // cycle launches.  FP64 data are built by the setup; lower-precision data are twins of them.
 template <class T>
 struct Num {
-  const void* band = nullptr;  // band coefficients: T, or __nv_bfloat16 when bf16 is set
+  const void* band = nullptr;  // band coefficients of the cycle: T, or __nv_bfloat16 when bf16
   bool bf16 = false;
+  const T* band_op = nullptr;  // band coefficients of the Krylov operator (always type T)
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
@@ -132,10 +134,11 @@ struct igamg_ctx {
   double* A0inv = nullptr;
   int64_t N0 = 0;
   double *X = nullptr, *Pv = nullptr, *W = nullptr, *Bt = nullptr, *gtmp = nullptr;
-  float *X32 = nullptr, *P32 = nullptr, *W32 = nullptr;  // inner (low-precision) PCG vectors
+  float *X32 = nullptr, *P32 = nullptr, *W32 = nullptr, *Zold32 = nullptr;  // inner (low-precision) PCG vectors
   double* Rr = nullptr;                                    // FP64 residual of the refinement
   bool low = false;                                        // low-precision numerics built
   bool low_bf16 = false;                                   // bands stored in BF16
+  bool verbose = false;                                    // IGAMG_VERBOSE set: log refinement steps
   // FP64 device arrays referenced by the cycle: (base, count, constant?) for the twins
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
@@ -512,6 +515,7 @@ void build_levels(igamg_ctx* c) {
     CK(cudaMemsetAsync(L.n64.U, 0, T.T * sizeof(double), s));
     CK(cudaMemsetAsync(L.n64.R, 0, T.T * sizeof(double), s));
     L.n64.band = L.band;
+    L.n64.band_op = L.band;
     c->band_count.push_back(band_total);
     CK(cudaMemsetAsync(L.band, 0, band_total * sizeof(double), s));
     double ta0 = now_ms();
@@ -910,12 +914,13 @@ void build_levels(igamg_ctx* c) {
 // ---------------------------------------------------------------- cycle
 
 template <class T>
-void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r) {
+void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = false) {
   Level& L = c->lv[l];
   Num<T>& N = num<T>(L);
-  double bb = N.bf16 ? 0.25 : double(sizeof(T)) / 8.0;  // band bytes relative to FP64
+  const bool bf = N.bf16 && !krylov;
+  double bb = bf ? 0.25 : double(sizeof(T)) / 8.0;  // band bytes relative to FP64
   ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes * bb + double(sizeof(T)) * L.topo.T * (f ? 3 : 2));
-  if (N.bf16) {
+  if (bf) {
     if constexpr (std::is_same<T, float>::value) {
       const __nv_bfloat16* band = static_cast<const __nv_bfloat16*>(N.band);
       if (c->pd.dim == 2)
@@ -926,7 +931,7 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r) {
     }
     return;
   }
-  const T* band = static_cast<const T*>(N.band);
+  const T* band = krylov ? N.band_op : static_cast<const T*>(N.band);
   if (c->pd.dim == 2)
     CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r)));
   else
@@ -1117,6 +1122,7 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
   Level& L = c->lv[Lf];
   Num<T>& N = num<T>(L);
   const int64_t T_ = L.topo.T;
+  const bool flexible = sizeof(T) < 8;  // low-precision cycle: Polak-Ribiere beta
   cudaStream_t s = c->stream;
   CK(cudaMemsetAsync(x, 0, T_ * sizeof(T), s));
   vnorm_dist<T>(c, Lf, N.F, c->scal + 3);
@@ -1127,11 +1133,17 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
   if (rr0 == 0.0) return 0;
   int it = 0;
   double rel = 1.0;
+  std::vector<double> hist{1.0};
   precondition<T>(c);
   CK(cudaMemcpyAsync(p, N.U, T_ * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  if (flexible) CK(cudaMemcpyAsync(c->Zold32, N.U, T_ * sizeof(T), cudaMemcpyDeviceToDevice, s));
   vdot<T>(c, N.F, N.U, T_, c->scal + 0);
   while (!(tol > 0 && rel <= tol) && it < max_iter) {
-    residual<T>(c, Lf, nullptr, p, w);
+    residual<T>(c, Lf, nullptr, p, w, true);
+    if (flexible) {  // keep the low-precision residual free of cancellation between copies
+      ProfScope ps(c, CLS_VECTOR, 0.0, 3.0 * sizeof(T) * L.n_if);
+      CK(launch_canonicalize<T>(s, L.n_if, L.if_ptr, L.if_idx, w));
+    }
     vdot<T>(c, p, w, T_, c->scal + 1);
     {
       ProfScope ps(c, CLS_VECTOR, 4.0 * T_, 6.0 * sizeof(T) * T_);
@@ -1141,17 +1153,23 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
     vnorm_dist<T>(c, Lf, N.F, c->scal + 3);
     double rr = read_scalar(c, 3);
     if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in PCG"};
-    double rel_new = std::sqrt(rr / rr0);
-    if (sizeof(T) < 8 && it > 4 && rel_new > 0.9 * rel && rel_new < 1e-4) {
-      *stalled = true;  // low precision: no more progress to be had
-      rel = rel_new;
+    rel = std::sqrt(rr / rr0);
+    hist.push_back(rel);
+    // low precision: stop once the last 8 iterations gained less than a factor 2
+    if (flexible && it >= 8 && rel > 0.5 * hist[it - 8]) {
+      *stalled = true;
       break;
     }
-    rel = rel_new;
     if ((tol > 0 && rel <= tol) || it >= max_iter) break;
     precondition<T>(c);
     vdot<T>(c, N.F, N.U, T_, c->scal + 2);
-    {
+    if (flexible) {
+      if constexpr (std::is_same<T, float>::value) {
+        vdot<T>(c, N.F, c->Zold32, T_, c->scal + 4);
+        ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 4.0 * sizeof(T) * T_, 2);
+        CK(launch_fcg_p(s, T_, c->scal, p, N.U, c->Zold32));
+      }
+    } else {
       ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 3.0 * sizeof(T) * T_, 2);
       CK(launch_pcg_p<T>(s, T_, c->scal, p, N.U));
     }
@@ -1170,7 +1188,7 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
   to_dist(c, Lf, b, c->Bt);
   to_acc(c, Lf, x, c->X);
   // solve A d = b - A x0 from d = 0, then x = x0 + d (Rr holds x0)
-  residual<double>(c, Lf, c->Bt, c->X, L.n64.F);
+  residual<double>(c, Lf, c->Bt, c->X, L.n64.F, true);
   CK(cudaMemcpyAsync(c->Rr, c->X, T * sizeof(double), cudaMemcpyDeviceToDevice, s));
   double rel = 0.0;
   bool stalled = false;
@@ -1205,7 +1223,7 @@ igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, i
   double rel = 1.0, rr0 = -1.0;
   igamg_status st = IGAMG_OK;
   while (true) {
-    residual<double>(c, Lf, c->Bt, c->X, c->Rr);
+    residual<double>(c, Lf, c->Bt, c->X, c->Rr, true);
     vnorm_dist<double>(c, Lf, c->Rr, c->scal + 3);
     double rr = read_scalar(c, 3);
     if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in refinement"};
@@ -1213,7 +1231,8 @@ igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, i
     rel = rr0 > 0 ? std::sqrt(rr / rr0) : 0.0;
     if (rr0 == 0.0 || (tol > 0 && rel <= tol)) break;
     if (total >= c->opt.max_iter || outer >= 60) { st = tol > 0 ? IGAMG_ERR_NOT_CONVERGED : IGAMG_OK; break; }
-    // scaled FP32 residual (norm 1) so FP32 range never matters
+    // canonical distributed form, then the scaled FP32 residual (norm 1)
+    CK(launch_canonicalize<double>(s, L.n_if, L.if_ptr, L.if_idx, c->Rr));
     double scale = 1.0 / std::sqrt(rr);
     CK(launch_convert_f64_f32(s, T, c->Rr, scale, L.n32.F));
     double irel = 0.0;
@@ -1221,6 +1240,9 @@ igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, i
     int it = pcg_core<float>(c, c->X32, c->P32, c->W32, c->opt.inner_tol, c->opt.max_iter - total, &irel, &stalled);
     total += it;
     ++outer;
+    if (c->verbose)
+      std::fprintf(stderr, "[igamg] refinement %d: ||r||/||r0|| = %.3e, inner %d its, inner reduction %.3e%s\n", outer,
+                   rel, it, irel, stalled ? " (stalled)" : "");
     CK(launch_add_scaled_f32(s, T, c->X32, 1.0 / scale, c->X));
     if (it == 0) { st = IGAMG_ERR_NUMERIC; break; }
   }
@@ -1283,15 +1305,20 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     B.tA = tr(A.tA);
     B.tB = tr(A.tB);
     int64_t nb = c->band_count[l];
+    const bool finest = l + 1 == c->lv.size();
+    float* b32 = nullptr;
+    if (!bf16_bands || finest) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
+      b32 = c->mem.alloc<float>(nb);
+      CK(launch_convert_f64_f32(s, nb, L.band, 1.0, b32));
+      B.band_op = b32;
+    }
     if (bf16_bands) {
       __nv_bfloat16* bb = c->mem.alloc<__nv_bfloat16>(nb);
       CK(launch_convert_f64_bf16(s, nb, L.band, bb));
       B.band = bb;
       B.bf16 = true;
     } else {
-      float* bb = c->mem.alloc<float>(nb);
-      CK(launch_convert_f64_f32(s, nb, L.band, 1.0, bb));
-      B.band = bb;
+      B.band = b32;
     }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
     tr_set(A.st3, B.st3);
@@ -1312,6 +1339,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
   c->X32 = c->mem.alloc<float>(Tf);
   c->P32 = c->mem.alloc<float>(Tf);
   c->W32 = c->mem.alloc<float>(Tf);
+  c->Zold32 = c->mem.alloc<float>(Tf);
   c->low = true;
   c->low_bf16 = bf16_bands;
   CK(cudaStreamSynchronize(s));
@@ -1357,6 +1385,7 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
   if (!prob) { g_setup_error = "problem is NULL"; return IGAMG_ERR_ARG; }
   igamg_ctx* c = new igamg_ctx();
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->verbose = std::getenv("IGAMG_VERBOSE") != nullptr;
   igamg_default_options(&c->opt);
   if (opt) c->opt = *opt;
   double t0 = now_ms();

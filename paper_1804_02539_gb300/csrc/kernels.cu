@@ -254,6 +254,20 @@ __global__ void k_iface_scatter(int64_t n, const int64_t* __restrict__ ptr, cons
   }
 }
 
+// Canonical distributed form: for every interface node the sum of its copies goes to the
+// first copy and the other copies become zero (same global vector, no cancellation
+// between copies).
+template <class T>
+__global__ void k_canonicalize(int64_t n, const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                               T* __restrict__ v) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T s = 0;
+    for (int64_t c = ptr[i]; c < ptr[i + 1]; ++c) s += v[idx[c]];
+    v[idx[ptr[i]]] = s;
+    for (int64_t c = ptr[i] + 1; c < ptr[i + 1]; ++c) v[idx[c]] = T(0);
+  }
+}
+
 static int grid_for(int64_t n, int threads, int cap = 4 * 152 * 8) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -276,6 +290,15 @@ cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t*
   k_iface_scatter<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, Z, G, vscale, tau, add, u);
   return cudaGetLastError();
 }
+template <class T>
+cudaError_t launch_canonicalize(cudaStream_t s, int64_t n_nodes, const int64_t* ptr, const int64_t* idx, T* v) {
+  if (n_nodes <= 0) return cudaSuccess;
+  k_canonicalize<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, ptr, idx, v);
+  return cudaGetLastError();
+}
+template cudaError_t launch_canonicalize<double>(cudaStream_t, int64_t, const int64_t*, const int64_t*, double*);
+template cudaError_t launch_canonicalize<float>(cudaStream_t, int64_t, const int64_t*, const int64_t*, float*);
+
 #define INST_IF(T)                                                                                          \
   template cudaError_t launch_iface_gather<T>(cudaStream_t, int64_t, const int64_t*, const int64_t*, const T*, T*); \
   template cudaError_t launch_iface_scatter<T>(cudaStream_t, int64_t, const int64_t*, const int64_t*, const T*,     \
@@ -460,6 +483,30 @@ template cudaError_t launch_pcg_xr<float>(cudaStream_t, int64_t, const double*, 
                                           const float*);
 template cudaError_t launch_pcg_p<double>(cudaStream_t, int64_t, double*, double*, const double*);
 template cudaError_t launch_pcg_p<float>(cudaStream_t, int64_t, double*, float*, const float*);
+
+// Flexible CG (Polak-Ribiere): beta = (rz_new - (r_new, z_old)) / rz_old; scal[5] = beta,
+// scal[0] = rz_new.
+__global__ void k_fcg_beta(double* scal) {
+  scal[5] = (scal[2] - scal[4]) / scal[0];
+  scal[0] = scal[2];
+}
+
+template <class T>
+__global__ void k_p_update(int64_t n, const double* __restrict__ beta_p, T* __restrict__ p, const T* __restrict__ z,
+                           T* __restrict__ zold) {
+  const T beta = T(*beta_p);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T zi = z[i];
+    p[i] = fma(beta, p[i], zi);
+    zold[i] = zi;
+  }
+}
+
+cudaError_t launch_fcg_p(cudaStream_t s, int64_t n, double* scal, float* p, const float* z, float* zold) {
+  k_fcg_beta<<<1, 1, 0, s>>>(scal);
+  k_p_update<float><<<grid_for(n, 256), 256, 0, s>>>(n, scal + 5, p, z, zold);
+  return cudaGetLastError();
+}
 
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)

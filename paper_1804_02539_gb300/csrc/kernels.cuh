@@ -73,6 +73,10 @@ template <class T>
 cudaError_t launch_iface_scatter(cudaStream_t s, int64_t n_nodes, const int64_t* ptr, const int64_t* idx,
                                  const T* Z, const T* G, const T* vscale, T tau, int add, T* u);
 
+// Canonical distributed form of v on the interface nodes (sum of copies in the first copy).
+template <class T>
+cudaError_t launch_canonicalize(cudaStream_t s, int64_t n_nodes, const int64_t* ptr, const int64_t* idx, T* v);
+
 // One direction of a tensor transfer: out has `nout` entries along the direction, in has
 // `nin`; outer/inner are the products of the sizes before/after it.
 template <class T>
@@ -123,6 +127,9 @@ cudaError_t launch_pcg_xr(cudaStream_t s, int64_t n, const double* scal, T* x, T
 template <class T>
 cudaError_t launch_pcg_p(cudaStream_t s, int64_t n, double* scal, T* p, const T* z);
 cudaError_t launch_axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y);
+// Flexible CG direction update: beta from scal[2] (r.z new), scal[4] (r.z_old), scal[0]
+// (r.z old); p = z + beta p; z_old = z.
+cudaError_t launch_fcg_p(cudaStream_t s, int64_t n, double* scal, float* p, const float* z, float* zold);
 
 // Precision conversions for iterative refinement.
 cudaError_t launch_convert_f64_f32(cudaStream_t s, int64_t n, const double* src, double scale, float* dst);
