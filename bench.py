@@ -278,7 +278,47 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+# Table II (iteration counts to 1e-8, PCG + V(1,1), Fichera corner, K = 448): rows l, columns p
+TABLE_II_IT = {1: {2: 30, 3: 31, 4: 31, 5: 26, 6: 22}, 2: {2: 33, 3: 32, 4: 33, 5: 31, 6: 28},
+               3: {2: 39, 3: 38, 4: 37, 5: 33, 6: 30}, 4: {2: 44, 3: 44, 4: 42, 5: 37, 6: 35}}
+
+
+def fichera_table(cases):
+    """Sec. 5.2 experiment: -Laplace u = 75 pi^2 sin(5 pi x) sin(5 pi y) sin(5 pi z) on the
+    Fichera corner, Dirichlet on xyz = 0, PCG + V(1,1) to 1e-8; the source enters as its
+    quasi-interpolant at the Greville points.  Prints one JSON line per case."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1804_02539_gb300 import igamg
+    for split, lev, p, mu in cases:
+        pr = workloads.fichera_corner(split, p, 2 ** lev, lev + 1)
+        opts = igamg.igamg_default_options()
+        opts.mu = mu
+        t0 = time.perf_counter()
+        ctx = igamg.Context(pr, opts)
+        t_setup = time.perf_counter() - t0
+        X = ctx.greville_points()
+        f = 75 * np.pi ** 2 * np.sin(5 * np.pi * X[:, 0]) * np.sin(5 * np.pi * X[:, 1]) * np.sin(5 * np.pi * X[:, 2])
+        coef = torch.tensor(f, device="cuda")
+        b = torch.empty_like(coef)
+        ctx.rhs_from_coefs(coef, b)
+        x = torch.zeros_like(b)
+        res, st = ctx.solve(b, x, TOL)
+        paper = TABLE_II_IT.get(lev, {}).get(p) if split == 4 and mu == 1 else None
+        print(json.dumps({"K": pr.num_patches, "l": lev, "p": p, "cycle": "V" if mu == 1 else "W",
+                          "dofs": ctx.num_dofs(), "coarse_dofs": ctx.num_dofs(0), "iters": res.iters,
+                          "paper_iters": paper, "relres": res.relres, "setup_s": round(t_setup, 2),
+                          "solve_ms": round(res.t_solve_ms, 1)}), flush=True)
+        ctx.free()
+
+
 def main():
+    if "--fichera" in sys.argv:
+        cases = [(4, l, 2, 1) for l in (1, 2, 3, 4)] + [(4, l, 2, 2) for l in (1, 2, 3)]
+        cases += [(2, l, p, 1) for p in (3, 4) for l in (1, 2, 3, 4)]
+        fichera_table(cases)
+        return
     if "--_oracle" in sys.argv:
         print(json.dumps(oracle_sample_json()))
         return

@@ -118,6 +118,13 @@ igamg_status igamg_num_local(const igamg_ctx* ctx, int level, int64_t* n);
  * Dirichlet side (Sec. 2 dof mapper). */
 igamg_status igamg_dof_map(const igamg_ctx* ctx, int level, int64_t* local_to_global);
 
+/* Physical coordinates of the Greville point of every active dof of level l (-1 =
+ * finest): xyz[g*dim + a], host array of N_l * dim doubles.  The Greville abscissa of
+ * B_i is (t_{i+1} + ... + t_{i+p}) / p per direction, mapped by the patch geometry G_k
+ * (Sec. 2); a source f given as a function can be turned into spline coefficients
+ * c_g = f(xyz_g) (Schoenberg's quasi-interpolant) for igamg_rhs_from_coefs. */
+igamg_status igamg_greville_points(const igamg_ctx* ctx, int level, double* xyz);
+
 /* Load vector b_i = (f_h, phi_i)_{L2(Omega)} of the source f_h = sum_j c_j phi_j given by
  * its spline coefficients c on the active dofs of the finest level (Sec. 2 right-hand side
  * (f, v)), by Gauss quadrature with the geometry.  Both device vectors of length N_L. */

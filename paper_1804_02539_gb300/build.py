@@ -44,14 +44,14 @@ def build(verbose: bool = False) -> str:
     for src in CPP_SOURCES:
         obj = os.path.join(OUT_DIR, src + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-c", os.path.join(CSRC, src), "-o", obj])
+        jobs.append(["g++", "-std=c++17", "-O3", "-fPIC", "-fopenmp", "-c", os.path.join(CSRC, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:
         for o in outs:
             if o.strip():
                 print(o)
-    _run([nvcc, "-shared", ARCH, "-o", LIB] + objs + ["-lcudart"])
+    _run([nvcc, "-shared", ARCH, "-Xcompiler", "-fopenmp", "-o", LIB] + objs + ["-lcudart", "-lgomp"])
     return LIB
 
 

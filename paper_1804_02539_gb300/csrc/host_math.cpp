@@ -159,27 +159,33 @@ Mat prolongation_1d(int mc, int p) {
 }
 
 bool cholesky(int n, Mat& A) {
+  // right-looking column Cholesky; the update of the trailing rows is parallel
   for (int j = 0; j < n; ++j) {
     double s = A[size_t(j) * n + j];
     for (int k = 0; k < j; ++k) s -= A[size_t(j) * n + k] * A[size_t(j) * n + k];
     if (!(s > 0.0)) return false;
     double ljj = std::sqrt(s);
     A[size_t(j) * n + j] = ljj;
+    const double* rj = &A[size_t(j) * n];
+#pragma omp parallel for schedule(static) if (n - j > 256)
     for (int i = j + 1; i < n; ++i) {
-      double v = A[size_t(i) * n + j];
-      for (int k = 0; k < j; ++k) v -= A[size_t(i) * n + k] * A[size_t(j) * n + k];
-      A[size_t(i) * n + j] = v / ljj;
+      double* ri = &A[size_t(i) * n];
+      double v = ri[j];
+      for (int k = 0; k < j; ++k) v -= ri[k] * rj[k];
+      ri[j] = v / ljj;
     }
-    for (int i = 0; i < j; ++i) A[size_t(i) * n + j] = 0.0;
   }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) A[size_t(i) * n + j] = 0.0;
   return true;
 }
 
 void cholesky_solve(int n, const Mat& L, double* b) {
   for (int i = 0; i < n; ++i) {
     double v = b[i];
-    for (int k = 0; k < i; ++k) v -= L[size_t(i) * n + k] * b[k];
-    b[i] = v / L[size_t(i) * n + i];
+    const double* ri = &L[size_t(i) * n];
+    for (int k = 0; k < i; ++k) v -= ri[k] * b[k];
+    b[i] = v / ri[i];
   }
   for (int i = n - 1; i >= 0; --i) {
     double v = b[i];
@@ -189,11 +195,30 @@ void cholesky_solve(int n, const Mat& L, double* b) {
 }
 
 void cholesky_solve_many(int n, const Mat& L, Mat& B, int ncols) {
-  std::vector<double> col(n);
-  for (int c = 0; c < ncols; ++c) {
-    for (int i = 0; i < n; ++i) col[i] = B[size_t(i) * ncols + c];
-    cholesky_solve(n, L, col.data());
-    for (int i = 0; i < n; ++i) B[size_t(i) * ncols + c] = col[i];
+  // independent right-hand sides in parallel; the back substitution uses L^T stored by rows
+  Mat LT(size_t(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k <= i; ++k) LT[size_t(k) * n + i] = L[size_t(i) * n + k];
+#pragma omp parallel
+  {
+    std::vector<double> col(n);
+#pragma omp for schedule(dynamic, 8)
+    for (int c = 0; c < ncols; ++c) {
+      for (int i = 0; i < n; ++i) col[i] = B[size_t(i) * ncols + c];
+      for (int i = 0; i < n; ++i) {
+        double v = col[i];
+        const double* ri = &L[size_t(i) * n];
+        for (int k = 0; k < i; ++k) v -= ri[k] * col[k];
+        col[i] = v / ri[i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double v = col[i];
+        const double* ri = &LT[size_t(i) * n];
+        for (int k = i + 1; k < n; ++k) v -= ri[k] * col[k];
+        col[i] = v / ri[i];
+      }
+      for (int i = 0; i < n; ++i) B[size_t(i) * ncols + c] = col[i];
+    }
   }
 }
 

@@ -1441,6 +1441,40 @@ igamg_status igamg_dof_map(const igamg_ctx* c, int level, int64_t* l2g) {
   return IGAMG_OK;
 }
 
+igamg_status igamg_greville_points(const igamg_ctx* c, int level, double* xyz) {
+  if (!c || !xyz) return IGAMG_ERR_ARG;
+  int NL = int(c->lv.size());
+  int l = level == -1 ? NL - 1 : level;
+  if (l < 0 || l >= NL) return IGAMG_ERR_ARG;
+  const LevelTopo& T = c->lv[l].topo;
+  const int d = c->pd.dim, nc = 1 << d;
+  for (int64_t g = 0; g < T.N; ++g) {
+    int64_t t = T.g2t[T.g2t_ptr[g]];
+    int k = int(std::upper_bound(T.off.begin(), T.off.end(), t) - T.off.begin()) - 1;
+    int64_t li = t - T.off[k];
+    double xi[3] = {0, 0, 0};
+    for (int j = d - 1; j >= 0; --j) {
+      int n = T.n[k * d + j], p = c->pd.p[k * d + j], m = n - p;
+      int i = int(li % n);
+      li /= n;
+      std::vector<double> kn = uniform_knots(m, p);
+      double s = 0.0;
+      for (int q = 1; q <= p; ++q) s += kn[i + q];
+      xi[j] = s / p;
+    }
+    for (int a = 0; a < d; ++a) {
+      double v = 0.0;
+      for (int cc = 0; cc < nc; ++cc) {
+        double w = 1.0;
+        for (int j = 0; j < d; ++j) w *= ((cc >> j) & 1) ? xi[j] : 1.0 - xi[j];
+        v += w * c->pd.corners[(size_t(k) * nc + cc) * d + a];
+      }
+      xyz[g * d + a] = v;
+    }
+  }
+  return IGAMG_OK;
+}
+
 igamg_status igamg_apply(igamg_ctx* c, int level, const double* x, double* y) {
   return guarded(c, [&]() {
     if (!x || !y) throw Fail{IGAMG_ERR_ARG, "NULL vector"};

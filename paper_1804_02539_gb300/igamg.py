@@ -48,6 +48,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_num_local": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
         "igamg_dof_map": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
         "igamg_rhs_from_coefs": ([P, P, P], C.c_int),
+        "igamg_greville_points": ([P, C.c_int, P], C.c_int),
         "igamg_solve": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
         "igamg_solve_host": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
         "igamg_apply": ([P, C.c_int, P, P], C.c_int),
@@ -177,6 +178,12 @@ class Context:
     def dof_map(self, level=-1) -> np.ndarray:
         out = np.empty(self.num_local(level), dtype=np.int64)
         self._check(lib().igamg_dof_map(self.h, level, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def greville_points(self, level=-1) -> np.ndarray:
+        d = int(self.problem.struct.dim)
+        out = np.empty((self.num_dofs(level), d))
+        self._check(lib().igamg_greville_points(self.h, level, out.ctypes.data_as(C.c_void_p)))
         return out
 
     def rhs_from_coefs(self, coef, rhs):

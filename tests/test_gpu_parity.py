@@ -214,6 +214,45 @@ def test_mixed_precision_refinement(name, prec):
     cm.free()
 
 
+@pytest.mark.parametrize("name", ["grid3x3_p3_m16", "cube_p2_m4", "fichera_p2_m4"])
+def test_w_cycle_parity(name):
+    """mu = 2 (W-cycle of Algorithm 1): one cycle and PCG counts against the oracle."""
+    from paper_1804_02539_gb300 import igamg
+    pr, H, ctx, perms = setup_case(name)
+    Hw = solver.build_hierarchy(pr, mu=2)
+    opts = igamg.igamg_default_options()
+    opts.mu = 2
+    cw = igamg.Context(pr, opts)
+    r = np.random.default_rng(21).normal(size=H.levels[-1].space.N)
+    z = torch.empty_like(dev(r))
+    cw.precondition(dev(to_lib(perms[-1], r)), z)
+    assert rel(from_lib(perms[-1], host(z)), solver.precondition(Hw, r)) < 1e-11
+    b = workloads.rhs_coefficients(H.levels[-1].space.N, 22)
+    x = torch.zeros_like(z)
+    res, st = cw.solve(dev(to_lib(perms[-1], b)), x, 1e-8)
+    ref = solver.pcg(Hw, b, tol=1e-8)
+    assert abs(res.iters - ref.iters) <= 1
+    assert rel(from_lib(perms[-1], host(x)), ref.x) < 1e-7
+    cw.free()
+
+
+def test_greville_points():
+    pr, H, ctx, perms = setup_case("grid2x2_p5_m32_ragged")
+    xyz = ctx.greville_points()
+    sp_ = H.levels[-1].space
+    # every dof's point lies on the image of its Greville abscissae in each owner patch
+    from oracle import patch as opatch
+    for k in range(pr.num_patches):
+        t = sp_.knots[k][0]
+        p = int(sp_.p[k, 0])
+        g1 = np.array([t[i + 1:i + p + 1].mean() for i in range(len(t) - p - 1)])
+        grid = np.stack([a.ravel() for a in np.meshgrid(g1, g1, indexing="ij")], 1)
+        X, _ = opatch.geometry(np.asarray(pr.corners[k]), grid)
+        ids = sp_.l2g[k].ravel()
+        keep = ids >= 0
+        np.testing.assert_allclose(xyz[perms[-1][ids[keep]]], X[keep], atol=1e-13)
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
