@@ -83,6 +83,9 @@ typedef struct {
                           eigendecompositions, the refinement residual and the coarse
                           solve stay FP64                                            */
   double inner_tol;    /* mixed precision: relative reduction of each inner PCG (1e-4) */
+  int fd_engine;       /* patch-interior FD contractions (2D): 0 = tensor cores (FP64:
+                          exact BF16 digit slices with FP64 recombination; BF16 variant:
+                          BF16 operands), 1 = FMA pipes in the working precision       */
 } igamg_options;
 
 typedef struct {

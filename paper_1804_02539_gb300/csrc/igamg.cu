@@ -16,6 +16,7 @@
 #include "../../include/igamg.h"
 #include "host_math.h"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 #include "topology.h"
 
 using namespace igamg;
@@ -78,6 +79,14 @@ struct GemmSetT {
 };
 using GemmSet = GemmSetT<double>;
 
+template <class T>
+struct TcSet {
+  TcDesc<T, T>* d = nullptr;
+  std::vector<TcDesc<T, T>> h;
+  int batch = 0, maxM = 0, maxN = 0;
+  double flops = 0;
+};
+
 // Numeric data of one level in one precision: the vectors and the descriptor sets the
 // cycle launches.  FP64 data are built by the setup; lower-precision data are twins of them.
 template <class T>
@@ -87,6 +96,8 @@ struct Num {
   const T* band_op = nullptr;  // band coefficients of the Krylov operator (always type T)
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
+  TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // 2D interiors on the tensor cores
+  bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
   T* cX = nullptr;                                  // compact 3D interior tensor
   T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
@@ -142,6 +153,8 @@ struct igamg_ctx {
   // FP64 device arrays referenced by the cycle: (base, count, constant?) for the twins
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
+  int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
+  std::map<const void*, const void*> tc_bf16_twin;         // S=7 slices -> S=1 slices of the same matrix
   double *partials = nullptr, *scal = nullptr;
   double* h_scal = nullptr;  // pinned
   std::string err;
@@ -247,6 +260,30 @@ void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, do
   if (!gs.batch) return;
   ProfScope ps(c, cls, gs.flops, gs.bytes * sizeof(T) / 8.0);
   CK(launch_gemm<T>(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, T(alpha)));
+}
+
+template <class T>
+void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
+  ts.h = v;
+  ts.batch = int(v.size());
+  ts.maxM = ts.maxN = 0;
+  ts.flops = 0;
+  for (auto& d : v) {
+    ts.maxM = std::max(ts.maxM, d.M);
+    ts.maxN = std::max(ts.maxN, d.N);
+    ts.flops += 2.0 * d.M * double(d.N) * d.K;
+  }
+  ts.d = v.empty() ? nullptr : c->mem.upload(v, c->stream);
+}
+
+template <class T>
+void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha) {
+  if (!ts.batch) return;
+  ProfScope ps(c, CLS_FD, ts.flops, 0.0);
+  if constexpr (std::is_same<T, double>::value)
+    CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err)));
+  else
+    CK((launch_gemm_tc<1, float, float>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, float(alpha), c->tc_err)));
 }
 
 // ---------------------------------------------------------------- setup helpers
@@ -571,6 +608,61 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.st1, s1);
       set_gemm(c, L.n64.st2, s2);
       set_gemm(c, L.n64.st3, s3);
+      if (c->opt.fd_engine == 0) {
+        // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
+        struct Sl { const __nv_bfloat16* a; const int* e; int nkb; };
+        std::map<std::pair<const Smoother1D*, int>, Sl> sl;  // (basis, transposed?) -> slices
+        auto slices = [&](const Smoother1D* S, int tr) -> Sl {
+          auto key = std::make_pair(S, tr);
+          if (!sl.count(key)) {
+            int n = S->len;
+            std::vector<double> A(size_t(n) * n);
+            for (int i = 0; i < n; ++i)
+              for (int k = 0; k < n; ++k) A[size_t(i) * n + k] = tr ? S->U[size_t(k) * n + i] : S->U[size_t(i) * n + k];
+            std::vector<uint16_t> sv;
+            std::vector<int> ev;
+            slice_constant(A, n, n, 7, sv, ev);
+            const __nv_bfloat16* da = reinterpret_cast<const __nv_bfloat16*>(c->mem.upload(sv, s));
+            if (c->opt.precision == IGAMG_BF16) {
+              std::vector<uint16_t> s1;
+              std::vector<int> e1;
+              slice_constant(A, n, n, 1, s1, e1);
+              c->tc_bf16_twin[da] = c->mem.upload(s1, s);
+            }
+            sl[key] = Sl{da, c->mem.upload(ev, s), (n + 63) / 64};
+          }
+          return sl[key];
+        };
+        std::vector<TcDesc<double, double>> t0F, t0R, t1, t2, t3;
+        size_t q = 0;
+        for (const Interior& in : T.interiors) {
+          const PatchDev& P = L.pd_h[in.k];
+          if (in.len[0] == 0 || in.len[1] == 0) continue;
+          const Smoother1D* S0 = get_scms(P.m[0], P.p[0], in.drop_lo[0], in.drop_hi[0], c->opt.sigma_scale * double(P.m[0]) * P.m[0]);
+          const Smoother1D* S1 = get_scms(P.m[1], P.p[1], in.drop_lo[1], in.drop_hi[1], c->opt.sigma_scale * double(P.m[1]) * P.m[1]);
+          int n0 = in.len[0], n1 = in.len[1];
+          const GemmDesc& g0 = s0F[q];
+          const GemmDesc& g1 = s1[q];
+          const GemmDesc& g3 = s3[q];
+          double* Tb = g0.C;   // scratch T (n0 x n1)
+          double* Yb = g1.C;   // scratch Y
+          Sl a0t = slices(S0, 1), a1t = slices(S1, 1), a0 = slices(S0, 0), a1 = slices(S1, 0);
+          TcDesc<double, double> d0{a0t.a, a0t.e, a0t.nkb, g0.B, P.n[1], 0, Tb, n1, 0, nullptr, 0, n0, n1, n0};
+          t0F.push_back(d0);
+          d0.B = s0R[q].B;
+          t0R.push_back(d0);
+          t1.push_back(TcDesc<double, double>{a1t.a, a1t.e, a1t.nkb, Tb, n1, 1, Yb, n1, 1, g1.E, n1, n1, n0, n1});
+          t2.push_back(TcDesc<double, double>{a0.a, a0.e, a0.nkb, Yb, n1, 0, Tb, n1, 0, nullptr, 0, n0, n1, n0});
+          t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n1, 1, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
+          ++q;
+        }
+        set_tc(c, L.n64.tc0F, t0F);
+        set_tc(c, L.n64.tc0R, t0R);
+        set_tc(c, L.n64.tc1, t1);
+        set_tc(c, L.n64.tc2, t2);
+        set_tc(c, L.n64.tc3, t3);
+        L.n64.use_tc = true;
+      }
     } else {
       // 3D: compact boxes, three mode products forward, Dinv, three backward
       std::vector<BoxDev> boxes;
@@ -905,6 +997,8 @@ void build_levels(igamg_ctx* c) {
   for (auto& L : c->lv) gmaxN = std::max(gmaxN, L.topo.N);
   c->gtmp = c->mem.alloc<double>(gmaxN);
   c->partials = c->mem.alloc<double>(RED_BLOCKS);
+  c->tc_err = c->mem.alloc<int>(1);
+  CK(cudaMemsetAsync(c->tc_err, 0, sizeof(int), s));
   c->scal = c->mem.alloc<double>(16);
   CK(cudaMemsetAsync(c->scal, 0, 16 * sizeof(double), s));
   CK(cudaMallocHost(&c->h_scal, 16 * sizeof(double)));
@@ -949,7 +1043,12 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   const T* v = from_F ? N.F : N.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
-  if (c->pd.dim == 2) {
+  if (c->pd.dim == 2 && N.use_tc) {
+    run_tc(c, from_F ? N.tc0F : N.tc0R, EPI_STORE, 1.0);
+    run_tc(c, N.tc1, EPI_MUL, 1.0);
+    run_tc(c, N.tc2, EPI_STORE, 1.0);
+    run_tc(c, N.tc3, epi, tau);
+  } else if (c->pd.dim == 2) {
     run_gemm(c, from_F ? N.st0F : N.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
     run_gemm(c, N.st1, false, false, EPI_MUL, 1.0, CLS_FD);
     run_gemm(c, N.st2, false, false, EPI_STORE, 1.0, CLS_FD);
@@ -1178,6 +1277,12 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
   return it;
 }
 
+void check_tc(igamg_ctx* c) {
+  int e = 0;
+  CK(cudaMemcpy(&e, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) throw Fail{IGAMG_ERR_TIMEOUT, "a tensor-core contraction timed out waiting for its MMAs"};
+}
+
 // FP64 PCG from x (global) with rhs b (global).
 igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_result* res) {
   double t0 = now_ms();
@@ -1196,6 +1301,7 @@ igamg_status pcg(igamg_ctx* c, const double* b, double* x, double tol, igamg_res
   CK(launch_axpby(s, T, 1.0, c->Rr, 1.0, c->X));
   from_acc(c, Lf, c->X, x);
   CK(cudaStreamSynchronize(s));
+  check_tc(c);
   if (c->prof) prof_collect(c);
   if (res) {
     res->iters = it;
@@ -1248,6 +1354,7 @@ igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, i
   }
   from_acc(c, Lf, c->X, x);
   CK(cudaStreamSynchronize(s));
+  check_tc(c);
   if (c->prof) prof_collect(c);
   if (res) {
     res->iters = total;
@@ -1320,6 +1427,20 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     } else {
       B.band = b32;
     }
+    if (bf16_bands && A.use_tc) {
+      auto tr_tc = [&](const TcSet<double>& g, TcSet<float>& out) {
+        std::vector<TcDesc<float, float>> v;
+        for (const auto& d : g.h) {
+          auto it = c->tc_bf16_twin.find(d.Aslices);
+          if (it == c->tc_bf16_twin.end()) throw Fail{IGAMG_ERR_NUMERIC, "missing BF16 basis slices"};
+          v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
+                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
+        }
+        set_tc(c, out, v);
+      };
+      tr_tc(A.tc0F, B.tc0F); tr_tc(A.tc0R, B.tc0R); tr_tc(A.tc1, B.tc1); tr_tc(A.tc2, B.tc2); tr_tc(A.tc3, B.tc3);
+      B.use_tc = true;
+    }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
     tr_set(A.st3, B.st3);
     tr_set(A.m0f, B.m0f); tr_set(A.m1f, B.m1f); tr_set(A.m2f, B.m2f);
@@ -1375,6 +1496,7 @@ igamg_status igamg_default_options(igamg_options* opt) {
   opt->max_iter = 500;
   opt->precision = IGAMG_FP64;
   opt->inner_tol = 1e-4;
+  opt->fd_engine = 0;
   return IGAMG_OK;
 }
 

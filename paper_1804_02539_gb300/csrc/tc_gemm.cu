@@ -1,0 +1,315 @@
+// Tensor-core (tcgen05) GEMMs for the fast-diagonalisation contractions of the smoother.
+//
+//   C = A B   with A a constant matrix (an FD basis U or U^T, sliced at setup) and B a
+//   varying operand (the residual tile or an intermediate), M x N x K.
+//
+// S == 1: BF16 operands, FP32 accumulation in TMEM (the BF16 precision variant).
+// S == 7: FP64-accurate product from BF16 digit slices (the error-free splitting scheme of
+//   Ozaki et al.): every row i of A is written as 2^{sigma_i} sum_s A_s 2^{-7s} and every
+//   column j of B as 2^{tau_j} sum_t B_t 2^{-7t}, with integer digits |A_s|, |B_t| <= 127
+//   (exact in BF16).  A digit product summed over K <= 1023 stays below 2^24, so each
+//   tcgen05.mma of one slice pair is exact in FP32; the pairs with s + t = q accumulate
+//   into TMEM accumulator q, and the epilogue forms
+//       C_ij = 2^{sigma_i + tau_j} sum_{q=2..S+1} D_q(i,j) 2^{-7q}
+//   in FP64 (pairs with s + t > S + 1 are below 2^{-56} relative and are dropped).
+//
+// Block: 128 threads, output tile 128 x 64, K block 64.  Operands are staged in shared
+// memory in the canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes;
+// LBO = 128 B between core matrices along K, SBO = 1024 B between 8-row groups), one thread
+// issues the MMAs, completion is tracked by an mbarrier (bounded wait), the accumulators
+// are read back with tcgen05.ld.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "tc_gemm.cuh"
+
+namespace igamg {
+
+namespace {
+constexpr int TBM = 128, TBN = 64, TBK = 64;
+constexpr int WAIT_LIMIT = 1 << 24;
+
+__device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFF);
+  d |= uint64_t(128 >> 4) << 16;   // leading byte offset: next core matrix along K
+  d |= uint64_t(1024 >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= uint64_t(1) << 46;          // descriptor version
+  return d;
+}
+
+// element (r, k) of a [rows x 64] K-major no-swizzle tile
+__device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (TBK / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+               :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < WAIT_LIMIT && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(phase));
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Exponent e of |x| (x = m 2^(e-52), m < 2^53) and 53-bit integer mantissa.
+__device__ __forceinline__ void split_f64(double x, int& e, uint64_t& m, bool& neg) {
+  uint64_t b = uint64_t(__double_as_longlong(x));
+  neg = (b >> 63) != 0;
+  int eb = int((b >> 52) & 0x7FF);
+  uint64_t f = b & ((uint64_t(1) << 52) - 1);
+  if (eb == 0) {  // zero / subnormal: treat as the smallest normal exponent
+    e = -1022;
+    m = f;
+  } else {
+    e = eb - 1023;
+    m = f | (uint64_t(1) << 52);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void digits_f64(double x, int tau, float* dig) {
+  int e;
+  uint64_t m;
+  bool neg;
+  split_f64(x, e, m, neg);
+  // fixed point F = |x| 2^{7S - tau}, |x| = m 2^{e - 52}
+  int sh = (e - 52) - tau + 7 * S;
+  uint64_t F = 0;
+  if (sh >= 0) F = sh < 11 ? (m << sh) : 0;  // cannot happen when |x| < 2^tau
+  else if (sh > -64) F = m >> (-sh);
+#pragma unroll
+  for (int s = 1; s <= S; ++s) {
+    float d = float(uint32_t(F >> (7 * (S - s))) & 127u);
+    dig[s - 1] = neg ? -d : d;
+  }
+}
+}  // namespace
+
+template <int S, class TB, class TC>
+__global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int epi, TC alpha,
+                                                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);                 // [S][128 x 64]
+  __nv_bfloat16* Bs = As + S * TBM * TBK;                                     // [S][64 x 64]
+  int* tauS = reinterpret_cast<int*>(Bs + S * TBN * TBK);                     // [64]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const TcDesc<TB, TC> d = descs[blockIdx.z];
+  const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
+  if (i0 >= d.M || j0 >= d.N) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NACC = S == 1 ? 1 : S;      // accumulators: diagonals q = 2..S+1
+  constexpr uint32_t TCOLS = S == 1 ? 64 : 512;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sptr(tslot)), "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // column scales of B over the whole K (S > 1)
+  if (S > 1) {
+    if (tid < TBN) tauS[tid] = -1022;
+    __syncthreads();
+    for (int idx = tid; idx < TBN * d.K; idx += 128) {
+      int n, k;
+      if (d.tb) { n = idx / d.K; k = idx % d.K; } else { k = idx / TBN; n = idx % TBN; }
+      int gj = j0 + n;
+      if (gj >= d.N) continue;
+      double x = double(d.tb ? d.B[int64_t(gj) * d.ldb + k] : d.B[int64_t(k) * d.ldb + gj]);
+      if (x != 0.0) {
+        int e;
+        uint64_t m;
+        bool ng;
+        split_f64(x, e, m, ng);
+        atomicMax(&tauS[n], e + 1);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
+  const int nkb = (d.K + TBK - 1) / TBK;
+  const int mt = blockIdx.y;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int k0 = kb * TBK;
+    // A: pre-sliced tile block [S][128 x 64], contiguous, 16-byte vector copies
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(d.Aslices + (int64_t(mt) * d.nkb + kb) * S * TBM * TBK);
+      uint4* dst = reinterpret_cast<uint4*>(As);
+      for (int i = tid; i < S * TBM * TBK / 8; i += 128) dst[i] = src[i];
+    }
+    // B: digits of the varying operand (k, n) -> core layout of an [n x k] K-major tile
+    for (int idx = tid; idx < TBN * TBK; idx += 128) {
+      int n, k;
+      if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
+      int gj = j0 + n, gk = k0 + k;
+      float dig[S];
+      if (gj < d.N && gk < d.K) {
+        TB x = d.tb ? d.B[int64_t(gj) * d.ldb + gk] : d.B[int64_t(gk) * d.ldb + gj];
+        if constexpr (S == 1) dig[0] = float(x);
+        else digits_f64<S>(double(x), tauS[n], dig);
+      } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) dig[s] = 0.f;
+      }
+      int off = core_off(n, k);
+#pragma unroll
+      for (int s = 0; s < S; ++s) Bs[s * TBN * TBK + off] = __float2bfloat16_rn(dig[s]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int ksteps = min(TBK, d.K - k0 + 15) / 16;
+      for (int s = 1; s <= S; ++s)
+        for (int t = 1; t + s <= (S == 1 ? 2 : S + 1); ++t) {
+          const uint32_t acc_col = S == 1 ? 0 : uint32_t(s + t - 2) * TBN;
+          for (int kk = 0; kk < ksteps; ++kk) {
+            uint64_t da = smem_desc(sptr(As + (s - 1) * TBM * TBK) + kk * 256);
+            uint64_t db = smem_desc(sptr(Bs + (t - 1) * TBN * TBK) + kk * 256);
+            // the first contribution to accumulator s + t (pair (1, q-1), first K step)
+            // overwrites it
+            const bool first = kb == 0 && kk == 0 && s == 1;
+            mma_bf16(tmem + acc_col, da, db, idesc, first ? 0u : 1u);
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sptr(mbar)));
+    }
+    if (!mbar_wait(sptr(mbar), phase)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    phase ^= 1;
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int gi = i0 + warp * 32 + lane;
+    int sig = 0;
+    if (S > 1 && gi < d.M) sig = d.Aexp[gi];
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      double acc[16];
+      if constexpr (S == 1) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + c0, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = v[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+        for (int dg = NACC - 1; dg >= 0; --dg) {  // small diagonals first
+          float v[16];
+          tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(dg) * TBN + c0, v);
+          const double w = ldexp(1.0, -7 * (dg + 2));
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[q] = fma(double(v[q]), w, acc[q]);
+        }
+      }
+      if (gi >= d.M) continue;
+#pragma unroll 4
+      for (int q = 0; q < 16; ++q) {
+        int gj = j0 + c0 + q;
+        if (gj >= d.N) continue;
+        double v = acc[q];
+        if (S > 1) v = ldexp(v, sig + tauS[c0 + q]);
+        int64_t o = d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj;
+        TC* cp = d.C + o;
+        switch (epi) {
+          case EPI_MUL: *cp = TC(v * double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj])); break;
+          case EPI_ASSIGN: *cp = TC(double(alpha) * v); break;
+          case EPI_ADD: *cp = TC(fma(double(alpha), v, double(*cp))); break;
+          default: *cp = TC(v);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
+}
+
+template <int S, class TB, class TC>
+cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
+                           TC alpha, int* err) {
+  if (batch <= 0) return cudaSuccess;
+  size_t smem = size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<S, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((maxN + TBN - 1) / TBN, (maxM + TBM - 1) / TBM, batch);
+  k_gemm_tc<S, TB, TC><<<grid, 128, smem, s>>>(d_desc, epi, alpha, err);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
+                                                       double, int*);
+template cudaError_t launch_gemm_tc<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int, int, int, float,
+                                                     int*);
+
+namespace {
+uint16_t bf16_bits_rn(float f) {
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  uint32_t r = b + 0x7FFFu + ((b >> 16) & 1u);
+  return uint16_t(r >> 16);
+}
+}  // namespace
+
+void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
+                    std::vector<int>& exps) {
+  const int mt = (M + TBM - 1) / TBM, nkb = (K + TBK - 1) / TBK;
+  slices.assign(size_t(mt) * nkb * S * TBM * TBK, 0);
+  exps.assign(M, 0);
+  for (int i = 0; i < M; ++i) {
+    double mx = 0.0;
+    for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(A[size_t(i) * K + k]));
+    int e = -1022;
+    if (mx > 0) std::frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |a| < 2^e
+    exps[i] = e;
+    for (int k = 0; k < K; ++k) {
+      double a = A[size_t(i) * K + k];
+      size_t base = ((size_t(i / TBM) * nkb + k / TBK) * S) * TBM * TBK;
+      int r = i % TBM, kk = k % TBK;
+      size_t off = size_t(((r >> 3) * (TBK / 8) + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7));
+      if (S == 1) {
+        slices[base + off] = bf16_bits_rn(float(a));
+        continue;
+      }
+      double F = std::floor(std::ldexp(std::fabs(a), 7 * S - e));  // < 2^(7S), exact
+      uint64_t Fi = uint64_t(F);
+      for (int s = 1; s <= S; ++s) {
+        float dgt = float((Fi >> (7 * (S - s))) & 127u);
+        if (a < 0) dgt = -dgt;
+        slices[base + size_t(s - 1) * TBM * TBK + off] = bf16_bits_rn(dgt);
+      }
+    }
+  }
+}
+
+}  // namespace igamg

@@ -1,0 +1,39 @@
+// Tensor-core GEMMs of the smoother contractions (tcgen05, BF16 operands in shared memory,
+// FP32 accumulators in TMEM): C = A B with A a constant, pre-sliced matrix and B varying.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace igamg {
+
+template <class TB, class TC>
+struct TcDesc {
+  const __nv_bfloat16* Aslices;  // [M/128 tiles][K/64 blocks][S][128 x 64] in core-matrix layout
+  const int* Aexp;               // [M] row scale exponents (S > 1)
+  int nkb;                       // K blocks of A (ceil(K / 64))
+  const TB* B;                   // B(k, n) = tb ? B[n * ldb + k] : B[k * ldb + n]
+  int ldb, tb;
+  TC* C;                         // C(i, j) at tc ? C[j * ldc + i] : C[i * ldc + j]
+  int ldc, tc;
+  const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
+  int lde;
+  int M, N, K;
+};
+
+// S = 7: FP64-accurate digit-slice product (TB = TC = double); S = 1: BF16 product with
+// FP32 accumulation (TB = TC = float).  err: device flag set when an mbarrier wait times out.
+template <int S, class TB, class TC>
+cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
+                           TC alpha, int* err);
+
+// Host: slices of a constant row-major M x K matrix in the layout TcDesc::Aslices expects.
+// S = 7 gives integer digits and the row exponents; S = 1 gives BF16 roundings.
+void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
+                    std::vector<int>& exps);
+
+}  // namespace igamg

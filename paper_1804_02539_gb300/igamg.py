@@ -28,7 +28,8 @@ class igamg_problem(C.Structure):
 
 class igamg_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("sigma_scale", C.c_double), ("nu", C.c_int),
-                ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double)]
+                ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
+                ("fd_engine", C.c_int)]
 
 
 class igamg_result(C.Structure):

@@ -253,6 +253,29 @@ def test_greville_points():
         np.testing.assert_allclose(xyz[perms[-1][ids[keep]]], X[keep], atol=1e-13)
 
 
+@pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "single_patch_p2_m64"])
+def test_fd_engines_agree(name):
+    """Tensor-core FD (FP64-accurate digit slices) against the FP64-FMA FD: smoother and
+    solve agree to FP64 rounding."""
+    from paper_1804_02539_gb300 import igamg
+    pr, H, ctx, perms = setup_case(name)
+    o = igamg.igamg_default_options()
+    o.fd_engine = 1
+    cf = igamg.Context(pr, o)
+    L = pr.num_levels - 1
+    r = dev(np.random.default_rng(31).normal(size=H.levels[-1].space.N))
+    z0, z1 = torch.empty_like(r), torch.empty_like(r)
+    ctx.smooth(L, r, z0)
+    cf.smooth(L, r, z1)
+    assert rel(host(z0), host(z1)) < 1e-14
+    x0, x1 = torch.zeros_like(r), torch.zeros_like(r)
+    r0, _ = ctx.solve(r, x0, 1e-10)
+    r1, _ = cf.solve(r, x1, 1e-10)
+    assert r0.iters == r1.iters
+    assert rel(host(x0), host(x1)) < 1e-12
+    cf.free()
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
