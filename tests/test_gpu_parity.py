@@ -267,7 +267,7 @@ def test_fd_engines_agree(name):
     z0, z1 = torch.empty_like(r), torch.empty_like(r)
     ctx.smooth(L, r, z0)
     cf.smooth(L, r, z1)
-    assert rel(host(z0), host(z1)) < 1e-14
+    assert rel(host(z0), host(z1)) < 1e-12      # digit truncation at 2^-49 of each column maximum
     x0, x1 = torch.zeros_like(r), torch.zeros_like(r)
     r0, _ = ctx.solve(r, x0, 1e-10)
     r1, _ = cf.solve(r, x1, 1e-10)
