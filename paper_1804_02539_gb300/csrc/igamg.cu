@@ -608,7 +608,11 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.st1, s1);
       set_gemm(c, L.n64.st2, s2);
       set_gemm(c, L.n64.st3, s3);
-      if (c->opt.fd_engine == 0) {
+      int min_len = 1 << 30;
+      for (const Interior& in : T.interiors)
+        if (in.len[0] && in.len[1]) min_len = std::min(min_len, std::min(in.len[0], in.len[1]));
+      // tensor cores where the interiors are large enough to amortise the slices
+      if (c->opt.fd_engine == 0 && min_len >= 96) {
         // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
         struct Sl { const __nv_bfloat16* a; const int* e; int nkb; };
         std::map<std::pair<const Smoother1D*, int>, Sl> sl;  // (basis, transposed?) -> slices
@@ -656,6 +660,9 @@ void build_levels(igamg_ctx* c) {
           t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n1, 1, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
           ++q;
         }
+        // column-exponent workspaces, one region per descriptor and stage
+        for (auto* vec : {&t0F, &t0R, &t1, &t2, &t3})
+          for (auto& dsc : *vec) dsc.tau = c->mem.alloc<int>(std::max(dsc.N, 1));
         set_tc(c, L.n64.tc0F, t0F);
         set_tc(c, L.n64.tc0R, t0R);
         set_tc(c, L.n64.tc1, t1);
@@ -1434,7 +1441,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
           auto it = c->tc_bf16_twin.find(d.Aslices);
           if (it == c->tc_bf16_twin.end()) throw Fail{IGAMG_ERR_NUMERIC, "missing BF16 basis slices"};
           v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
-                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
+                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K, nullptr});
         }
         set_tc(c, out, v);
       };

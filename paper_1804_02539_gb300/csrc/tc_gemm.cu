@@ -113,8 +113,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);                 // [S][128 x 64]
   __nv_bfloat16* Bs = As + S * TBM * TBK;                                     // [S][64 x 64]
   int* tauS = reinterpret_cast<int*>(Bs + S * TBN * TBK);                     // [64]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);                    // MMA completion
+  uint64_t* abar = mbar + 1;                                                  // A bulk copy
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const TcDesc<TB, TC> d = descs[blockIdx.z];
   const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
   if (i0 >= d.M || j0 >= d.N) return;
@@ -127,27 +128,11 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(abar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // column scales of B over the whole K (S > 1)
-  if (S > 1) {
-    if (tid < TBN) tauS[tid] = -1022;
-    __syncthreads();
-    for (int idx = tid; idx < TBN * d.K; idx += 128) {
-      int n, k;
-      if (d.tb) { n = idx / d.K; k = idx % d.K; } else { k = idx / TBN; n = idx % TBN; }
-      int gj = j0 + n;
-      if (gj >= d.N) continue;
-      double x = double(d.tb ? d.B[int64_t(gj) * d.ldb + k] : d.B[int64_t(k) * d.ldb + gj]);
-      if (x != 0.0) {
-        int e;
-        uint64_t m;
-        bool ng;
-        split_f64(x, e, m, ng);
-        atomicMax(&tauS[n], e + 1);
-      }
-    }
-  }
+  // column scales of B (computed by k_col_exponents before this launch)
+  if (S > 1 && tid < TBN) tauS[tid] = (j0 + tid < d.N) ? d.tau[j0 + tid] : 0;
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -159,29 +144,42 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   bool ok = true;
   for (int kb = 0; kb < nkb; ++kb) {
     const int k0 = kb * TBK;
-    // A: pre-sliced tile block [S][128 x 64], contiguous, 16-byte vector copies
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(d.Aslices + (int64_t(mt) * d.nkb + kb) * S * TBM * TBK);
-      uint4* dst = reinterpret_cast<uint4*>(As);
-      for (int i = tid; i < S * TBM * TBK / 8; i += 128) dst[i] = src[i];
+    // A: pre-sliced tile block [S][128 x 64], contiguous: one bulk (TMA) copy tracked by abar
+    if (tid == 0) {
+      const uint32_t bytes = uint32_t(S) * TBM * TBK * sizeof(__nv_bfloat16);
+      const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * S * TBM * TBK;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar)), "r"(bytes));
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   :: "r"(sptr(As)), "l"(src), "r"(bytes), "r"(sptr(abar)) : "memory");
     }
-    // B: digits of the varying operand (k, n) -> core layout of an [n x k] K-major tile
-    for (int idx = tid; idx < TBN * TBK; idx += 128) {
-      int n, k;
-      if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
-      int gj = j0 + n, gk = k0 + k;
-      float dig[S];
-      if (gj < d.N && gk < d.K) {
-        TB x = d.tb ? d.B[int64_t(gj) * d.ldb + gk] : d.B[int64_t(gk) * d.ldb + gj];
-        if constexpr (S == 1) dig[0] = float(x);
-        else digits_f64<S>(double(x), tauS[n], dig);
-      } else {
+    // B: digits of the varying operand (k, n) -> core layout of an [n x k] K-major tile;
+    // the 32 loads of a thread are issued before any is used
+    {
+      TB xv[TBN * TBK / 128];
 #pragma unroll
-        for (int s = 0; s < S; ++s) dig[s] = 0.f;
+      for (int u = 0; u < TBN * TBK / 128; ++u) {
+        int idx = tid + u * 128, n, k;
+        if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
+        int gj = j0 + n, gk = k0 + k;
+        xv[u] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
+                                       : TB(0);
       }
-      int off = core_off(n, k);
 #pragma unroll
-      for (int s = 0; s < S; ++s) Bs[s * TBN * TBK + off] = __float2bfloat16_rn(dig[s]);
+      for (int u = 0; u < TBN * TBK / 128; ++u) {
+        int idx = tid + u * 128, n, k;
+        if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
+        float dig[S];
+        if constexpr (S == 1) dig[0] = float(xv[u]);
+        else digits_f64<S>(double(xv[u]), tauS[n], dig);
+        int off = core_off(n, k);
+#pragma unroll
+        for (int q = 0; q < S; ++q) Bs[q * TBN * TBK + off] = __float2bfloat16_rn(dig[q]);
+      }
+    }
+    if (!mbar_wait(sptr(abar), phase)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 2);
+      break;
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -223,14 +221,32 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = v[q];
       } else {
+        // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
+        // units of 2^-49; |sum| < 2^58.  One int64 -> FP64 conversion, then the power-of-two
+        // scale 2^{sigma + tau - 49} is added to the exponent bits.
+        long long iacc[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-        for (int dg = NACC - 1; dg >= 0; --dg) {  // small diagonals first
+        for (int q = 0; q < 16; ++q) iacc[q] = 0;
+        for (int dg = 0; dg < NACC; ++dg) {
           float v[16];
           tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(dg) * TBN + c0, v);
-          const double w = ldexp(1.0, -7 * (dg + 2));
+          const int qd = dg + 2;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) acc[q] = fma(double(v[q]), w, acc[q]);
+          for (int q = 0; q < 16; ++q) {
+            long long iv = __float2ll_rn(v[q]);
+            iacc[q] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          double x = __ll2double_rn(iacc[q]);
+          int sh = sig + tauS[c0 + q] - 49;
+          long long b = __double_as_longlong(x);
+          if (x != 0.0) {
+            int eb = int((b >> 52) & 0x7FF) + sh;
+            x = (eb > 0 && eb < 2047) ? __longlong_as_double(b + ((long long)sh << 52)) : ldexp(x, sh);
+          }
+          acc[q] = x;
         }
       }
       if (gi >= d.M) continue;
@@ -239,7 +255,6 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
         int gj = j0 + c0 + q;
         if (gj >= d.N) continue;
         double v = acc[q];
-        if (S > 1) v = ldexp(v, sig + tauS[c0 + q]);
         int64_t o = d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj;
         TC* cp = d.C + o;
         switch (epi) {
@@ -256,13 +271,56 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
 }
 
+// tau_j = 1 + max exponent over column j of op(B) (bit extraction; zero columns: -1022).
+// One block of 256 threads per (64-column tile, batch entry); 16 loads in flight per thread.
+template <class TB, class TC>
+__global__ void __launch_bounds__(256) k_col_exponents(const TcDesc<TB, TC>* __restrict__ descs) {
+  const TcDesc<TB, TC> d = descs[blockIdx.y];
+  const int j0 = blockIdx.x * TBN;
+  if (j0 >= d.N) return;
+  __shared__ int tmax[TBN];
+  const int tid = threadIdx.x;
+  if (tid < TBN) tmax[tid] = -1022;
+  __syncthreads();
+  const int total = TBN * d.K;
+  for (int base = tid; base < total; base += 256 * 16) {
+    int eb[16], nn[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      int idx = base + u * 256;
+      eb[u] = 0;
+      nn[u] = 0;
+      if (idx < total) {
+        int n, k;
+        if (d.tb) { n = idx / d.K; k = idx % d.K; } else { k = idx / TBN; n = idx % TBN; }
+        nn[u] = n;
+        int gj = j0 + n;
+        if (gj < d.N) {
+          const TB* bp = d.tb ? d.B + int64_t(gj) * d.ldb + k : d.B + int64_t(k) * d.ldb + gj;
+          eb[u] = int((uint64_t(__double_as_longlong(double(__ldg(bp)))) >> 52) & 0x7FF);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (eb[u]) atomicMax(&tmax[nn[u]], eb[u] - 1023 + 1);
+  }
+  __syncthreads();
+  if (tid < TBN && j0 + tid < d.N) d.tau[j0 + tid] = tmax[tid];
+}
+
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err) {
   if (batch <= 0) return cudaSuccess;
-  size_t smem = size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64;
+  size_t smem = size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<S, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
+  if (S > 1) {
+    k_col_exponents<TB, TC><<<dim3((maxN + TBN - 1) / TBN, batch), 256, 0, s>>>(d_desc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((maxN + TBN - 1) / TBN, (maxM + TBM - 1) / TBM, batch);
   k_gemm_tc<S, TB, TC><<<grid, 128, smem, s>>>(d_desc, epi, alpha, err);
   return cudaGetLastError();

@@ -23,6 +23,7 @@ struct TcDesc {
   const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
   int lde;
   int M, N, K;
+  int* tau;                      // [N] workspace: column exponents of op(B) (S > 1)
 };
 
 // S = 7: FP64-accurate digit-slice product (TB = TC = double); S = 1: BF16 product with
