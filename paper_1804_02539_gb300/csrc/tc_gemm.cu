@@ -32,6 +32,7 @@ namespace igamg {
 
 namespace {
 constexpr int TBM = 128, TBN = 64, TBK = 64;
+constexpr int NT = 512;  // threads per CTA: 16 warps, 4 per TMEM lane quarter
 constexpr int WAIT_LIMIT = 1 << 24;
 
 __device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -107,7 +108,7 @@ __device__ __forceinline__ void digits_f64(double x, int tau, float* dig) {
 }  // namespace
 
 template <int S, class TB, class TC>
-__global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int epi, TC alpha,
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int epi, TC alpha,
                                                  int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);                 // [S][128 x 64]
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
   if (i0 >= d.M || j0 >= d.N) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, colgrp = warp >> 2;  // TMEM lanes 32*quarter.., columns 16*colgrp..
   constexpr int NACC = S == 1 ? 1 : S;      // accumulators: diagonals q = 2..S+1
   constexpr uint32_t TCOLS = S == 1 ? 64 : 512;
   if (warp == 0) {
@@ -155,18 +157,18 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
     // B: digits of the varying operand (k, n) -> core layout of an [n x k] K-major tile;
     // the 32 loads of a thread are issued before any is used
     {
-      TB xv[TBN * TBK / 128];
+      TB xv[TBN * TBK / NT];
 #pragma unroll
-      for (int u = 0; u < TBN * TBK / 128; ++u) {
-        int idx = tid + u * 128, n, k;
+      for (int u = 0; u < TBN * TBK / NT; ++u) {
+        int idx = tid + u * NT, n, k;
         if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
         int gj = j0 + n, gk = k0 + k;
         xv[u] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
                                        : TB(0);
       }
 #pragma unroll
-      for (int u = 0; u < TBN * TBK / 128; ++u) {
-        int idx = tid + u * 128, n, k;
+      for (int u = 0; u < TBN * TBK / NT; ++u) {
+        int idx = tid + u * NT, n, k;
         if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
         float dig[S];
         if constexpr (S == 1) dig[0] = float(xv[u]);
@@ -210,14 +212,14 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    const int gi = i0 + warp * 32 + lane;
+    const int gi = i0 + quarter * 32 + lane;
     int sig = 0;
     if (S > 1 && gi < d.M) sig = d.Aexp[gi];
-    for (int c0 = 0; c0 < TBN; c0 += 16) {
+    for (int c0 = colgrp * 16; c0 < colgrp * 16 + 16; c0 += 16) {
       double acc[16];
       if constexpr (S == 1) {
         float v[16];
-        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + c0, v);
+        tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + c0, v);
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = v[q];
       } else {
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const TcDesc<TB, TC>* __restric
         for (int q = 0; q < 16; ++q) iacc[q] = 0;
         for (int dg = 0; dg < NACC; ++dg) {
           float v[16];
-          tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(dg) * TBN + c0, v);
+          tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(dg) * TBN + c0, v);
           const int qd = dg + 2;
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -322,7 +324,7 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
     if (e != cudaSuccess) return e;
   }
   dim3 grid((maxN + TBN - 1) / TBN, (maxM + TBM - 1) / TBM, batch);
-  k_gemm_tc<S, TB, TC><<<grid, 128, smem, s>>>(d_desc, epi, alpha, err);
+  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, epi, alpha, err);
   return cudaGetLastError();
 }
 template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
