@@ -158,8 +158,18 @@ def run_ours(args, rank, world, local_rank):
             x.zero_()
             res, st = ctx.solve(b, x, TOL)
         iters = res.iters if args.warmup else None
+        # pass 1 (untimed): per-class breakdown of one solve, every class timed with events
+        ctx.profile_enable(0x3F)
+        x.zero_()
+        ctx.solve(b, x, TOL)
+        prof1 = ctx.profile_read()
+        dom = max(prof1, key=lambda k: prof1[k]["ms"])
+        dom_bit = 1 << igamg.Context.PROFILE_CLASSES.index(dom)
+        ctx.profile_enable(0)
+        # timed region: the solves as a user runs them (graph-replayed PCG iterations),
+        # with CUDA events only around the dominant class's launches
         sampler = ClockSampler(local_rank)
-        ctx.profile_enable(True)
+        ctx.profile_enable(dom_bit)
         if dist:
             tdist.barrier()
         torch.cuda.synchronize()
@@ -176,7 +186,7 @@ def run_ours(args, rank, world, local_rank):
         ms_total = e0.elapsed_time(e1)
         clocks = sampler.stop()
         prof = ctx.profile_read()
-        ctx.profile_enable(False)
+        ctx.profile_enable(0)
         iters = res.iters
         outer = res.outer_iters
         relres = res.relres
@@ -208,11 +218,10 @@ def run_ours(args, rank, world, local_rank):
         assemble_ms = res.t_assemble_ms
     ms_step = ms_total / args.steps
     value = N * world / (ms_step * 1e-3) / 1e6
-    # dominant kernel class and its roofline
-    dom = max(prof, key=lambda k: prof[k]["ms"])
+    # dominant kernel class (from the breakdown pass) and its roofline, timed in the timed region
     d = prof[dom]
     pk, src = peaks()
-    if dom in ("interior_fd", "interface", "coarse"):
+    if dom in ("interior_fd", "interface", "coarse") or (dom == "apply" and args.precision == "fp64"):
         ach = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
@@ -223,10 +232,9 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": src, "kernel": dom, "traffic": None}
     roof["avg_launch_ms"] = round(d["ms"] / max(d["launches"], 1), 5)
-    breakdown = {k: {"ms_per_step": round(v["ms"] / args.steps, 3),
-                     "launches_per_step": v["launches"] // args.steps,
-                     "gflop_per_step": round(v["flops"] / args.steps / 1e9, 4),
-                     "gbyte_per_step": round(v["bytes"] / args.steps / 1e9, 4)} for k, v in prof.items()}
+    breakdown = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"],
+                     "gflop_per_step": round(v["flops"] / 1e9, 4),
+                     "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items()}
     launches = sum(v["launches"] for v in prof.values())
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": world,

@@ -86,6 +86,9 @@ typedef struct {
   int fd_engine;       /* patch-interior FD contractions (2D): 0 = tensor cores (FP64:
                           exact BF16 digit slices with FP64 recombination; BF16 variant:
                           BF16 operands), 1 = FMA pipes in the working precision       */
+  int graphs;          /* 1: each PCG iteration after the first is captured once as a
+                          CUDA graph and replayed (same launches, same order, same
+                          results); 0: launched one by one                            */
 } igamg_options;
 
 typedef struct {
@@ -206,8 +209,11 @@ igamg_status igamg_fd_apply_noalloc(int n0, int n1, const double* U0, const doub
  * algorithmic FLOPs and bytes of those launches (the operands the method itself must
  * read and write once: band coefficients, vectors, smoother bases).  Classes: 0 stiffness apply/residual, 1 patch-interior smoother contractions,
  * 2 interface smoothers (gather, edge contractions, scatter), 3 transfers, 4 coarse solve,
- * 5 vector operations (reductions, PCG updates, conversions).  Enabling resets the
- * counters.  Reading synchronises the stream. */
+ * 5 vector operations (reductions, PCG updates, conversions).  `enable` is a bit mask of
+ * the classes whose launches are bracketed by events (bit c = class c; 0 disables; launches,
+ * flops and bytes are counted for every class while enabled).  While enabled the PCG
+ * iterations run as individual launches instead of a replayed CUDA graph.  Enabling resets
+ * the counters.  Reading synchronises the stream. */
 igamg_status igamg_profile_enable(igamg_ctx* ctx, int enable);
 igamg_status igamg_profile_read(igamg_ctx* ctx, int cls, int64_t* launches, double* ms,
                                 double* flops, double* bytes);

@@ -154,6 +154,15 @@ struct igamg_ctx {
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
   int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
+  // PCG iteration body replayed as a CUDA graph (index 0 FP64, 1 FP32 inner), captured on a
+  // private stream (the legacy stream cannot capture) and launched on `stream`
+  cudaGraphExec_t iter_graph[2] = {nullptr, nullptr};
+  unsigned graph_key[2] = {0, 0};                         // profiling mode it was captured in
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> graph_ev[2];  // timing nodes inside it
+  int64_t graph_launch[2][8] = {};                        // per-replay launch accounting
+  double graph_flops[2][8] = {}, graph_bytes[2][8] = {};
+  cudaStream_t cap_stream = nullptr;
+  int capturing = -1, pending_graph = -1;
   std::map<const void*, const void*> tc_bf16_twin;         // S=7 slices -> S=1 slices of the same matrix
   double *partials = nullptr, *scal = nullptr;
   double* h_scal = nullptr;  // pinned
@@ -161,6 +170,7 @@ struct igamg_ctx {
   double t_setup_ms = 0, t_assemble_ms = 0;
   // per-class launch accounting (igamg_profile_*)
   bool prof = false;
+  unsigned prof_mask = 0;  // classes whose launches get timing events
   int64_t prof_launch[8] = {0};
   double prof_ms[8] = {0}, prof_flops[8] = {0}, prof_bytes[8] = {0};
   std::vector<cudaEvent_t> ev_free;
@@ -210,14 +220,21 @@ struct ProfScope {
     c->prof_launch[cls] += launches;
     c->prof_flops[cls] += flops;
     c->prof_bytes[cls] += bytes;
+    if (!((c->prof_mask >> cls) & 1u)) return;
     a = prof_event(c);
-    CK(cudaEventRecord(a, c->stream));
+    record(a);
+  }
+  void record(cudaEvent_t e) {
+    // inside a graph capture the event becomes a record node that fires on every replay
+    if (c->capturing >= 0) CK(cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal));
+    else CK(cudaEventRecord(e, c->stream));
   }
   ~ProfScope() noexcept(false) {
     if (!a) return;
     cudaEvent_t b = prof_event(c);
-    CK(cudaEventRecord(b, c->stream));
-    c->ev_open.emplace_back(cls, a, b);
+    record(b);
+    if (c->capturing >= 0) c->graph_ev[c->capturing].emplace_back(cls, a, b);
+    else c->ev_open.emplace_back(cls, a, b);
   }
 };
 
@@ -231,6 +248,79 @@ void prof_collect(igamg_ctx* c) {
     c->ev_free.push_back(std::get<2>(t));
   }
   c->ev_open.clear();
+  if (c->pending_graph >= 0) {  // timing nodes of the last graph replay
+    for (auto& t : c->graph_ev[c->pending_graph]) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
+      c->prof_ms[std::get<0>(t)] += ms;
+    }
+    c->pending_graph = -1;
+  }
+}
+
+void drop_graph(igamg_ctx* c, int gi) {
+  if (c->iter_graph[gi]) CK(cudaGraphExecDestroy(c->iter_graph[gi]));
+  c->iter_graph[gi] = nullptr;
+  for (auto& t : c->graph_ev[gi]) {
+    c->ev_free.push_back(std::get<1>(t));
+    c->ev_free.push_back(std::get<2>(t));
+  }
+  c->graph_ev[gi].clear();
+}
+
+// Runs `body` as the replay of a graph captured from it on the first call (and again when
+// the profiling mode changed).  The body must launch onto c->stream only and touch the same
+// buffers with the same host arguments every time.
+template <class F>
+void graph_run(igamg_ctx* c, int gi, F&& body) {
+  const unsigned key = c->prof ? (0x100u | c->prof_mask) : 0u;
+  if (c->iter_graph[gi] && c->graph_key[gi] != key) drop_graph(c, gi);
+  if (!c->iter_graph[gi]) {
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    int64_t l0[8];
+    double f0[8], b0[8];
+    std::copy(c->prof_launch, c->prof_launch + 8, l0);
+    std::copy(c->prof_flops, c->prof_flops + 8, f0);
+    std::copy(c->prof_bytes, c->prof_bytes + 8, b0);
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    c->capturing = gi;
+    cudaGraph_t g = nullptr;
+    try {
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+      body();
+      CK(cudaStreamEndCapture(c->stream, &g));
+    } catch (...) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(c->stream, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      c->stream = user;
+      c->capturing = -1;
+      throw;
+    }
+    c->stream = user;
+    c->capturing = -1;
+    CK(cudaGraphInstantiate(&c->iter_graph[gi], g, 0));
+    CK(cudaGraphDestroy(g));
+    c->graph_key[gi] = key;
+    for (int k = 0; k < 8; ++k) {  // the capture launched nothing: count per replay instead
+      c->graph_launch[gi][k] = c->prof_launch[k] - l0[k];
+      c->graph_flops[gi][k] = c->prof_flops[k] - f0[k];
+      c->graph_bytes[gi][k] = c->prof_bytes[k] - b0[k];
+    }
+    std::copy(l0, l0 + 8, c->prof_launch);
+    std::copy(f0, f0 + 8, c->prof_flops);
+    std::copy(b0, b0 + 8, c->prof_bytes);
+  }
+  CK(cudaGraphLaunch(c->iter_graph[gi], c->stream));
+  if (c->prof) {
+    for (int k = 0; k < 8; ++k) {
+      c->prof_launch[k] += c->graph_launch[gi][k];
+      c->prof_flops[k] += c->graph_flops[gi][k];
+      c->prof_bytes[k] += c->graph_bytes[gi][k];
+    }
+    c->pending_graph = gi;
+  }
 }
 
 template <class T>
@@ -1244,7 +1334,23 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
   CK(cudaMemcpyAsync(p, N.U, T_ * sizeof(T), cudaMemcpyDeviceToDevice, s));
   if (flexible) CK(cudaMemcpyAsync(c->Zold32, N.U, T_ * sizeof(T), cudaMemcpyDeviceToDevice, s));
   vdot<T>(c, N.F, N.U, T_, c->scal + 0);
-  while (!(tol > 0 && rel <= tol) && it < max_iter) {
+  // one PCG step after the convergence check: z = B r, beta, p, w = A p, alpha, x, r, ||r||
+  auto body = [&](bool with_precondition) {
+    cudaStream_t s = c->stream;  // the capture stream while a graph is recorded
+    if (with_precondition) {
+      precondition<T>(c);
+      vdot<T>(c, N.F, N.U, T_, c->scal + 2);
+      if (flexible) {
+        if constexpr (std::is_same<T, float>::value) {
+          vdot<T>(c, N.F, c->Zold32, T_, c->scal + 4);
+          ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 4.0 * sizeof(T) * T_, 2);
+          CK(launch_fcg_p(s, T_, c->scal, p, N.U, c->Zold32));
+        }
+      } else {
+        ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 3.0 * sizeof(T) * T_, 2);
+        CK(launch_pcg_p<T>(s, T_, c->scal, p, N.U));
+      }
+    }
     residual<T>(c, Lf, nullptr, p, w, true);
     if (flexible) {  // keep the low-precision residual free of cancellation between copies
       ProfScope ps(c, CLS_VECTOR, 0.0, 3.0 * sizeof(T) * L.n_if);
@@ -1255,8 +1361,19 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
       ProfScope ps(c, CLS_VECTOR, 4.0 * T_, 6.0 * sizeof(T) * T_);
       CK(launch_pcg_xr<T>(s, T_, c->scal, x, N.F, p, w));
     }
-    ++it;
     vnorm_dist<T>(c, Lf, N.F, c->scal + 3);
+  };
+  const int gi = sizeof(T) == 8 ? 0 : 1;
+  while (!(tol > 0 && rel <= tol) && it < max_iter) {
+    if (it == 0) {
+      body(false);
+    } else if (c->opt.graphs) {
+      // the step touches fixed buffers only: capture it once, replay it every iteration
+      graph_run(c, gi, [&] { body(true); });
+    } else {
+      body(true);
+    }
+    ++it;
     double rr = read_scalar(c, 3);
     if (!std::isfinite(rr)) throw Fail{IGAMG_ERR_NUMERIC, "non-finite residual in PCG"};
     rel = std::sqrt(rr / rr0);
@@ -1265,19 +1382,6 @@ int pcg_core(igamg_ctx* c, T* x, T* p, T* w, double tol, int max_iter, double* r
     if (flexible && it >= 8 && rel > 0.5 * hist[it - 8]) {
       *stalled = true;
       break;
-    }
-    if ((tol > 0 && rel <= tol) || it >= max_iter) break;
-    precondition<T>(c);
-    vdot<T>(c, N.F, N.U, T_, c->scal + 2);
-    if (flexible) {
-      if constexpr (std::is_same<T, float>::value) {
-        vdot<T>(c, N.F, c->Zold32, T_, c->scal + 4);
-        ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 4.0 * sizeof(T) * T_, 2);
-        CK(launch_fcg_p(s, T_, c->scal, p, N.U, c->Zold32));
-      }
-    } else {
-      ProfScope ps(c, CLS_VECTOR, 2.0 * T_, 3.0 * sizeof(T) * T_, 2);
-      CK(launch_pcg_p<T>(s, T_, c->scal, p, N.U));
     }
   }
   *rel_out = rel;
@@ -1504,6 +1608,7 @@ igamg_status igamg_default_options(igamg_options* opt) {
   opt->precision = IGAMG_FP64;
   opt->inner_tol = 1e-4;
   opt->fd_engine = 0;
+  opt->graphs = 1;
   return IGAMG_OK;
 }
 
@@ -1740,6 +1845,7 @@ igamg_status igamg_profile_enable(igamg_ctx* c, int enable) {
     CK(cudaStreamSynchronize(c->stream));
     prof_collect(c);
     c->prof = enable != 0;
+    c->prof_mask = unsigned(enable);
     for (int i = 0; i < 8; ++i) {
       c->prof_launch[i] = 0;
       c->prof_ms[i] = c->prof_flops[i] = c->prof_bytes[i] = 0.0;
@@ -1800,6 +1906,14 @@ igamg_status igamg_free(igamg_ctx* c) {
   if (!c) return IGAMG_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (int gi = 0; gi < 2; ++gi) {
+    if (c->iter_graph[gi]) cudaGraphExecDestroy(c->iter_graph[gi]);
+    for (auto& t : c->graph_ev[gi]) {
+      cudaEventDestroy(std::get<1>(t));
+      cudaEventDestroy(std::get<2>(t));
+    }
+  }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& t : c->ev_open) {
     cudaEventDestroy(std::get<1>(t));
     cudaEventDestroy(std::get<2>(t));

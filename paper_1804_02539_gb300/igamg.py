@@ -29,7 +29,8 @@ class igamg_problem(C.Structure):
 class igamg_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("sigma_scale", C.c_double), ("nu", C.c_int),
                 ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
-                ("fd_engine", C.c_int)]
+                ("fd_engine", C.c_int),
+                ("graphs", C.c_int)]
 
 
 class igamg_result(C.Structure):
@@ -221,8 +222,9 @@ class Context:
 
     PROFILE_CLASSES = ("apply", "interior_fd", "interface", "transfer", "coarse", "vector")
 
-    def profile_enable(self, on=True):
-        self._check(lib().igamg_profile_enable(self.h, 1 if on else 0))
+    def profile_enable(self, mask=0x3F):
+        """mask: bit c times class c with CUDA events (0 disables profiling)."""
+        self._check(lib().igamg_profile_enable(self.h, int(mask)))
 
     def profile_read(self):
         out = {}

@@ -276,6 +276,40 @@ def test_fd_engines_agree(name):
     cf.free()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("name", ["grid2x2_p5_m32_ragged", "cube_p2_m4"])
+def test_graph_replay_identical(name, prec):
+    """PCG iterations replayed from a captured CUDA graph launch the same kernels in the same
+    order as the one-by-one launches: identical iterations and bit-identical solutions,
+    also while the profiler times one class inside the graph and on a second solve."""
+    from paper_1804_02539_gb300 import igamg
+    pr = cases()[name]()
+    o = igamg.igamg_default_options()
+    o.precision = prec
+    o.graphs = 0
+    ce = igamg.Context(pr, o)
+    o.graphs = 1
+    cg = igamg.Context(pr, o)
+    N = ce.num_dofs()
+    b = dev(workloads.rhs_coefficients(N, 41))
+    xe = torch.zeros_like(b)
+    re_, _ = ce.solve(b, xe, 1e-10)
+    for mask in (0, 0x2, 0x3F):
+        cg.profile_enable(mask)
+        xg = torch.zeros_like(b)
+        rg, _ = cg.solve(b, xg, 1e-10)
+        assert rg.iters == re_.iters and rg.outer_iters == re_.outer_iters
+        assert torch.equal(xg, xe)
+        if mask:
+            prof = cg.profile_read()
+            assert prof["interior_fd"]["ms"] > 0 and prof["apply"]["launches"] > 0
+            if mask == 0x2:
+                assert prof["apply"]["ms"] == 0
+    cg.profile_enable(0)
+    ce.free()
+    cg.free()
+
+
 def test_nonzero_initial_guess_and_zero_rhs():
     pr, H, ctx, perms = setup_case("grid3x3_p3_m16")
     N = H.levels[-1].space.N
