@@ -321,7 +321,182 @@ def fichera_table(cases):
         ctx.free()
 
 
+# ---------------------------------------------------------------- batched workload
+
+BATCH_COUNT, BATCH_SEED = 512, 4
+BATCH_DESC = ("512 independent 2D Poisson problems (seed 4): sqrt(K) x sqrt(K) rectangle patches on [0,1]^2, "
+              "K in {4,9,16,25,36}, p in {2..6}, m in {16,32,64,128} intervals per patch direction, iid uniform; "
+              "all Dirichlet, f = 2 pi^2 sin(pi x) sin(pi y) through its Greville interpolant; FP64 PCG + V(1,1) "
+              "to 1e-8 each, all resident, solved concurrently")
+BATCH_ORACLE_SAMPLE = 6   # the oracle solves the first problems of the batch with m <= 32
+
+
+def sin_rhs_coefs(X):
+    import numpy as np
+    return 2 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
+
+
+def oracle_greville(pr, sp):
+    """Greville points of the oracle's dofs (oracle numbering): Greville abscissae of the
+    owning patch's finest knot vectors through its bilinear map."""
+    import numpy as np
+    from oracle import patch as opatch
+    X = np.zeros((sp.N, 2))
+    for k in range(pr.num_patches):
+        ids = sp.l2g[k].ravel()
+        keep = ids >= 0
+        g = []
+        for j in range(2):
+            t = sp.knots[k][j]
+            p = int(sp.p[k, j])
+            g.append(np.array([t[i + 1:i + p + 1].mean() for i in range(len(t) - p - 1)]))
+        grid = np.stack([a.ravel() for a in np.meshgrid(g[0], g[1], indexing="ij")], 1)
+        Xk, _ = opatch.geometry(np.asarray(pr.corners[k]), grid)
+        X[ids[keep]] = Xk[keep]
+    return X
+
+
+def oracle_batch_json():
+    """Subprocess, one thread: oracle setup (untimed) and one PCG solve each (timed) of the
+    first BATCH_ORACLE_SAMPLE problems of the batch with at most 32 intervals."""
+    import workloads
+    from oracle import multipatch, solver
+    probs = [p for p in workloads.batch_problems(BATCH_COUNT, BATCH_SEED) if int(p.name.split("_m")[-1]) <= 32]
+    probs = probs[:BATCH_ORACLE_SAMPLE]
+    N = 0
+    t = 0.0
+    its = []
+    for pr in probs:
+        H = solver.build_hierarchy(pr)
+        sp = H.levels[-1].space
+        _, Mg = multipatch.stiffness(pr, sp, want_mass=True)
+        b = Mg @ sin_rhs_coefs(oracle_greville(pr, sp))
+        t0 = time.perf_counter()
+        its.append(solver.pcg(H, b, tol=TOL).iters)
+        t += time.perf_counter() - t0
+        N += sp.N
+    return {"N": N, "t_solve_s": t, "iters": its, "problems": [p.name for p in probs]}
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1804_02539_gb300 import igamg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    probs = workloads.batch_problems(BATCH_COUNT, BATCH_SEED)
+    opts = igamg.igamg_default_options()
+    opts.precision = {"fp64": igamg.IGAMG_FP64, "fp32": igamg.IGAMG_FP32, "bf16": igamg.IGAMG_BF16}[args.precision]
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        B = igamg.Batch(probs, opts, workers=args.workers, stream=stream)
+        t_setup = time.perf_counter() - t0
+        Ns = [c.num_dofs() for c in B.contexts]
+        rhs, xs = [], []
+        for c in B.contexts:
+            coef = torch.tensor(sin_rhs_coefs(c.greville_points()), device="cuda")
+            b = torch.empty_like(coef)
+            c.rhs_from_coefs(coef, b)
+            rhs.append(b)
+            xs.append(torch.zeros_like(b))
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            for x in xs:
+                x.zero_()
+            B.solve(rhs, xs, TOL)
+        sampler = ClockSampler(0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for x in xs:
+                x.zero_()
+            st, res, sts = B.solve(rhs, xs, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_total = e0.elapsed_time(e1)
+        clocks = sampler.stop()
+        assert st == 0, sts
+        # profiled pass (untimed): launches and algorithmic work per class over the batch
+        for c in B.contexts:
+            c.profile_enable(0x3F)
+        for x in xs:
+            x.zero_()
+        B.solve(rhs, xs, TOL)
+        prof = {}
+        for c in B.contexts:
+            for k, v in c.profile_read().items():
+                acc = prof.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                for f in acc:
+                    acc[f] += v[f]
+            c.profile_enable(0)
+        # end to end: pinned host rhs in, solutions out, inside the timed region
+        e2e = None
+        if not args.no_e2e:
+            hb = [r.cpu().pin_memory() for r in rhs]
+            hx = [torch.empty(n, dtype=torch.float64).pin_memory() for n in Ns]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                for h, r in zip(hb, rhs):
+                    r.copy_(h, non_blocking=True)
+                for x in xs:
+                    x.zero_()
+                B.solve(rhs, xs, TOL)
+                for h, x in zip(hx, xs):
+                    h.copy_(x, non_blocking=True)
+                torch.cuda.synchronize()
+            e2e = (time.perf_counter() - t0) / args.steps
+    ms_step = ms_total / args.steps
+    Ntot = sum(Ns)
+    value = Ntot / (ms_step * 1e-3) / 1e6
+    flops = sum(v["flops"] for v in prof.values())
+    byts = sum(v["bytes"] for v in prof.values())
+    ach = flops / (ms_step * 1e-3) / 1e12
+    pk, src = peaks()
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32 (f64 refinement)",
+                                       "bf16": "bf16 bands, f32 (f64 refinement)"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "batch512_2d_rect", "description": BATCH_DESC, "problems": len(probs),
+                   "dofs_total": Ntot, "dofs_min": min(Ns), "dofs_max": max(Ns), "workers": min(args.workers or 16, len(probs)),
+                   "iters_min": min(r.iters for r in res), "iters_max": max(r.iters for r in res),
+                   "setup_s": round(t_setup, 1), "l2": "inputs larger than L2 (vectors of 5.3e7 dofs)"},
+        "e2e": {"value": None if e2e is None else round(Ntot / e2e / 1e6, 4), "unit": "MDOF/s",
+                "h2d_bytes_per_step": 8 * Ntot, "d2h_bytes_per_step": 8 * Ntot},
+        "gpu_launches": int(sum(v["launches"] for v in prof.values()) * args.steps),
+        "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                     "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "kernel": "whole batch step (all classes, concurrent streams)",
+                     "hbm_gbs": round(byts / (ms_step * 1e-3) / 1e9, 1), "hbm_peak": pk["hbm_gbs"],
+                     "traffic": None},
+        "clocks": clocks,
+        "kernel_breakdown": {k: {"launches_per_step": v["launches"], "gflop_per_step": round(v["flops"] / 1e9, 3),
+                                 "gbyte_per_step": round(v["bytes"] / 1e9, 3)} for k, v in prof.items()},
+    }
+    if not args.no_cpu_baseline:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        o = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle_batch"], env=env,
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1800)
+        if o.returncode == 0:
+            d = json.loads(o.stdout.strip().splitlines()[-1])
+            out["cpu_baseline"] = {"value": round(d["N"] / d["t_solve_s"] / 1e6, 6), "unit": "MDOF/s", "cores": 1,
+                                   "kind": "oracle", "sample": f"the first {BATCH_ORACLE_SAMPLE} problems of the "
+                                   "batch with m <= 32, one PCG solve each, setup excluded, 1 thread",
+                                   "sample_dofs": d["N"], "sample_iters": d["iters"]}
+    print(json.dumps(out), flush=True)
+    B.free()
+
+
 def main():
+    if "--_oracle_batch" in sys.argv:
+        print(json.dumps(oracle_batch_json()))
+        return
     if "--fichera" in sys.argv:
         cases = [(4, l, 2, 1) for l in (1, 2, 3, 4)] + [(4, l, 2, 2) for l in (1, 2, 3)]
         cases += [(2, l, p, 1) for p in (3, 4) for l in (1, 2, 3, 4)]
@@ -339,7 +514,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="key of workloads.CONFIGS")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--batch", action="store_true", help="the 512-problem batched workload")
+    ap.add_argument("--workers", type=int, default=16, help="host worker threads of the batch")
     args = ap.parse_args()
+    if args.batch:
+        run_batch(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

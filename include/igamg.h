@@ -83,12 +83,22 @@ typedef struct {
                           eigendecompositions, the refinement residual and the coarse
                           solve stay FP64                                            */
   double inner_tol;    /* mixed precision: relative reduction of each inner PCG (1e-4) */
-  int fd_engine;       /* patch-interior FD contractions (2D): 0 = tensor cores (FP64:
-                          exact BF16 digit slices with FP64 recombination; BF16 variant:
-                          BF16 operands), 1 = FMA pipes in the working precision       */
+  int fd_engine;       /* patch-interior FD contractions: 0 = automatic (the autotuner's
+                          choice per level, else tensor cores on 2D interiors of >= 96
+                          dofs per direction), 1 = FMA pipes in the working precision,
+                          2 = tensor cores on every 2D level (FP64: exact BF16 digit
+                          slices with integer recombination; BF16 variant: BF16 operands) */
   int graphs;          /* 1: each PCG iteration after the first is captured once as a
                           CUDA graph and replayed (same launches, same order, same
                           results); 0: launched one by one                            */
+  int apply_engine;    /* stiffness apply above the coarsest level (2D): 0 = a Kronecker
+                          sum of the 1D stiffness and mass when every patch is a
+                          rectangle (no band storage), stored bands otherwise;
+                          1 = stored bands always                                     */
+  int autotune;        /* with fd_engine 0: time the FD candidates of every level once at
+                          setup (FMA tile factors 1, 2, 4; tensor cores on 2D interiors of
+                          >= 32) and keep the fastest; choices are cached per interior
+                          shape for the life of the process                           */
 } igamg_options;
 
 typedef struct {
@@ -227,6 +237,39 @@ igamg_status igamg_free(igamg_ctx* ctx);
 /* Message of the last error on this context; with ctx == NULL, of the last failed setup
  * or context-free call on the calling thread.  Never NULL; valid until the next call. */
 const char* igamg_last_error(const igamg_ctx* ctx);
+
+/* ---------------------------------------------------------------- batched solves
+ * Many independent problems (each the model problem of Sec. 2 on its own multi-patch
+ * domain) solved concurrently on one device.  Each problem keeps its own context: its
+ * hierarchy stays resident between solves.  The solves run on `workers` host threads, each
+ * with its own CUDA stream, taking problems in decreasing order of estimated work; a
+ * problem's result is bit-identical to igamg_solve on that problem alone.  The paper solves
+ * one problem at a time and has no counterpart of this layer. */
+typedef struct igamg_batch igamg_batch;
+
+/* Sets up `count` problems (host array, read during the call) with the same options.
+ * workers <= 0 selects 16 (capped at count).  The contexts use `cuda_stream` outside
+ * igamg_solve_batch.  On failure nothing is kept and igamg_last_error(NULL) names the first
+ * failing problem. */
+igamg_status igamg_setup_batch(const igamg_problem* problems, int count, const igamg_options* opt, int workers,
+                               void* cuda_stream, igamg_batch** out);
+
+/* The context of problem i (owned by the batch; do not free): for igamg_num_dofs,
+ * igamg_dof_map, igamg_rhs_from_coefs, igamg_solve and the other per-context calls. */
+igamg_status igamg_batch_context(igamg_batch* batch, int i, igamg_ctx** ctx);
+
+/* Solves problem i for rhs[i] into x[i] (host arrays of `count` device pointers, each of
+ * that problem's igamg_num_dofs; x[i] holds the initial guess on entry), every problem to
+ * the relative tolerance tol.  Starts after the work queued on the batch's stream and
+ * returns when every solve is done.  res and status (host arrays of `count`, or NULL)
+ * receive each problem's result and status.  Returns IGAMG_OK if every solve converged,
+ * else the first other status by problem index, an error taking precedence over
+ * IGAMG_ERR_NOT_CONVERGED. */
+igamg_status igamg_solve_batch(igamg_batch* batch, const double* const* rhs, double* const* x, double tol,
+                               igamg_result* res, igamg_status* status);
+
+/* Releases every context of the batch and its streams.  NULL is accepted. */
+igamg_status igamg_free_batch(igamg_batch* batch);
 
 #ifdef __cplusplus
 }

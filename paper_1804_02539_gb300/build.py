@@ -13,7 +13,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libigamg.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["kernels.cu", "igamg.cu", "noalloc.cu", "tc_gemm.cu"]
+CU_SOURCES = ["kernels.cu", "igamg.cu", "noalloc.cu", "tc_gemm.cu", "batch.cu"]
 CPP_SOURCES = ["host_math.cpp", "topology.cpp"]
 
 
@@ -51,7 +51,7 @@ def build(verbose: bool = False) -> str:
         for o in outs:
             if o.strip():
                 print(o)
-    _run([nvcc, "-shared", ARCH, "-Xcompiler", "-fopenmp", "-o", LIB] + objs + ["-lcudart", "-lgomp"])
+    _run([nvcc, "-shared", ARCH, "-Xcompiler", "-fopenmp", "-o", LIB] + objs + ["-lcudart", "-lgomp", "-lpthread"])
     return LIB
 
 

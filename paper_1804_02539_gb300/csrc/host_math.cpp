@@ -1,9 +1,14 @@
 #include "host_math.h"
 
+#include <omp.h>
+
 #include <algorithm>
 #include <cmath>
 
 namespace igamg {
+
+void set_host_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+
 
 std::vector<double> uniform_knots(int m, int p) {
   std::vector<double> t;

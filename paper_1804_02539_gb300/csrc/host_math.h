@@ -30,6 +30,10 @@ void mass_stiffness_1d(int m, int p, Mat& M, Mat& K);
 // interpolating the coarse B-splines at the fine Greville abscissae.
 Mat prolongation_1d(int mc, int p);
 
+// Threads the dense routines below may use when called from the current thread
+// (OpenMP team size; 1 inside a pool of setup workers).
+void set_host_threads(int n);
+
 // Dense linear algebra.
 bool cholesky(int n, Mat& A);                               // A = L L^T, L in lower part
 void cholesky_solve(int n, const Mat& L, double* b);         // in place

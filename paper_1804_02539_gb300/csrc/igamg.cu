@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <type_traits>
 #include <string>
 #include <tuple>
@@ -75,6 +76,7 @@ struct GemmSetT {
   GemmDescT<T>* d = nullptr;
   std::vector<GemmDescT<T>> h;  // host copy (FP64 sets are translated into lower precision)
   int batch = 0, maxM = 0, maxN = 0;
+  int R = 0;                    // FMA tile factor (0: size heuristic; the autotuner may set it)
   double flops = 0, bytes = 0;  // algorithmic work of one launch
 };
 using GemmSet = GemmSetT<double>;
@@ -94,6 +96,7 @@ struct Num {
   const void* band = nullptr;  // band coefficients of the cycle: T, or __nv_bfloat16 when bf16
   bool bf16 = false;
   const T* band_op = nullptr;  // band coefficients of the Krylov operator (always type T)
+  KronDevT<T>* kd = nullptr;   // rectangle patches: Kronecker-sum operator per patch
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
   TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // 2D interiors on the tensor cores
@@ -114,7 +117,12 @@ struct Level {
   int max_n[3] = {1, 1, 1}, max_p = 1;
   int64_t* l2g = nullptr;
   int64_t *g2t_ptr = nullptr, *g2t = nullptr;
-  double* band = nullptr;  // FP64 band coefficients
+  double* band = nullptr;  // FP64 band coefficients (none when kron)
+  bool kron = false;       // every patch a rectangle: A applied as a Kronecker sum of 1D K, M
+  unsigned char* active = nullptr;  // kron: 1 for non-eliminated tile nodes
+  std::vector<KronDevT<double>> kd_h;
+  int64_t band_doubles = 0;  // size of a band array in this layout (mass bands of the rhs)
+  bool tc_ok = false;        // tensor-core FD stage sets built (the FD engine may switch)
   Num<double> n64;
   Num<float> n32;
   // 3D interior boxes (shared by all precisions)
@@ -153,6 +161,7 @@ struct igamg_ctx {
   // FP64 device arrays referenced by the cycle: (base, count, constant?) for the twins
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
+  std::map<std::tuple<int, int>, std::pair<double*, double*>> kron_1d;  // (m, p) -> banded K, M
   int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
   // PCG iteration body replayed as a CUDA graph (index 0 FP64, 1 FP32 inner), captured on a
   // private stream (the legacy stream cannot capture) and launched on `stream`
@@ -184,6 +193,14 @@ static thread_local std::string g_setup_error = "no error";
 namespace igamg {
 // Message returned by igamg_last_error(NULL) on this thread.
 void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
+// Stream a context launches on (the batch driver lends contexts to its worker streams).
+cudaStream_t ctx_stream(const igamg_ctx* c) { return c->stream; }
+void ctx_set_stream(igamg_ctx* c, cudaStream_t s) { c->stream = s; }
+// Scheduling weight of one solve: finest-level tile nodes times (degree + 2).
+double ctx_work_estimate(const igamg_ctx* c) {
+  const LevelTopo& T = c->lv.back().topo;
+  return double(T.T) * (c->pd.p[0] + 2);
+}
 }  // namespace igamg
 
 namespace {
@@ -349,7 +366,7 @@ template <class T>
 void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, double alpha, int cls) {
   if (!gs.batch) return;
   ProfScope ps(c, cls, gs.flops, gs.bytes * sizeof(T) / 8.0);
-  CK(launch_gemm<T>(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, T(alpha)));
+  CK(launch_gemm<T>(c->stream, gs.d, gs.batch, gs.maxM, gs.maxN, ta, tb, epi, T(alpha), gs.R));
 }
 
 template <class T>
@@ -584,6 +601,36 @@ void assemble_level(igamg_ctx* c, Level& L, std::map<std::tuple<int, int>, DevTa
   }
 }
 
+// A 2D patch whose bilinear map is affine with orthogonal Jacobian columns (a rectangle,
+// any orientation) has the constant metric C = |det J| J^{-1} J^{-T} = diag(c0, c1) with
+// c_j = |det J| / |J e_j|^2 (Sec. 2: the patch stiffness integrand grad^T C grad).
+bool rect_metric(const double* X, double* c0, double* c1) {
+  double a[2] = {X[2] - X[0], X[3] - X[1]}, b[2] = {X[4] - X[0], X[5] - X[1]};
+  double la = std::hypot(a[0], a[1]), lb = std::hypot(b[0], b[1]);
+  double gap = std::hypot(X[6] - X[0] - a[0] - b[0], X[7] - X[1] - a[1] - b[1]);
+  if (!(la > 0 && lb > 0) || gap > 1e-14 * (la + lb) || std::fabs(a[0] * b[0] + a[1] * b[1]) > 1e-14 * la * lb)
+    return false;
+  double det = std::fabs(a[0] * b[1] - a[1] * b[0]);
+  *c0 = det / (la * la);
+  *c1 = det / (lb * lb);
+  return true;
+}
+
+// Row-banded copy [n][2p+1] of a dense symmetric n x n banded 1D matrix.
+std::vector<double> row_band(const Mat& A, int n, int p) {
+  std::vector<double> b(size_t(n) * (2 * p + 1), 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int t = 0; t <= 2 * p; ++t) {
+      int j = i - p + t;
+      if (j >= 0 && j < n) b[size_t(i) * (2 * p + 1) + t] = A[size_t(i) * n + j];
+    }
+  return b;
+}
+
+// Interior sizes from which the tensor-core FD is built (a candidate of the autotuner) and
+// from which it is used when the autotuner is off.
+constexpr int kTcMinLen = 32, kTcMinLenStatic = 96;
+
 void build_levels(igamg_ctx* c) {
   cudaStream_t s = c->stream;
   const int d = c->pd.dim, K = c->pd.K;
@@ -634,7 +681,48 @@ void build_levels(igamg_ctx* c) {
     L.l2g = c->mem.upload(T.l2g, s);
     L.g2t_ptr = c->mem.upload(T.g2t_ptr, s);
     L.g2t = c->mem.upload(T.g2t, s);
-    L.band = c->mem.alloc<double>(band_total);
+    L.band_doubles = band_total;
+    // rectangle patches (2D, above the coarsest level): no bands, Kronecker-sum apply
+    L.kron = d == 2 && l > 0 && c->opt.apply_engine == 0;
+    std::vector<double> cc(2 * K);
+    for (int k = 0; k < K && L.kron; ++k)
+      L.kron = rect_metric(c->pd.corners.data() + size_t(k) * 8, &cc[2 * k], &cc[2 * k + 1]);
+    if (L.kron) {
+      std::vector<unsigned char> act(T.T);
+      for (int64_t t = 0; t < T.T; ++t) act[t] = T.l2g[t] >= 0 ? 1 : 0;
+      L.active = c->mem.upload(act, s);
+      L.apply_flops = 0;
+      L.band_bytes = 0;
+      for (int k = 0; k < K; ++k) {
+        const PatchDev& P = L.pd_h[k];
+        KronDevT<double> kd{P.off, P.n[0], P.n[1], P.p[0], P.p[1], nullptr, nullptr, nullptr, nullptr,
+                            cc[2 * k], cc[2 * k + 1]};
+        const double* KM[2][2];
+        for (int j = 0; j < 2; ++j) {
+          auto key = std::make_tuple(P.m[j], P.p[j]);
+          if (!c->kron_1d.count(key)) {
+            Mat M1, K1;
+            mass_stiffness_1d(P.m[j], P.p[j], M1, K1);
+            int n = P.m[j] + P.p[j];
+            std::vector<double> kb = row_band(K1, n, P.p[j]), mb = row_band(M1, n, P.p[j]);
+            c->kron_1d[key] = {reg_const(c, c->mem.upload(kb, s), kb.size()),
+                               reg_const(c, c->mem.upload(mb, s), mb.size())};
+          }
+          KM[j][0] = c->kron_1d[key].first;
+          KM[j][1] = c->kron_1d[key].second;
+        }
+        kd.K0 = KM[0][0];
+        kd.M0 = KM[0][1];
+        kd.K1 = KM[1][0];
+        kd.M1 = KM[1][1];
+        L.kd_h.push_back(kd);
+        double nn = double(P.n[0]) * P.n[1];
+        L.apply_flops += nn * 4.0 * (2 * P.p[0] + 1 + 2 * P.p[1] + 1);  // 4d(2p+1) per node
+      }
+      L.n64.kd = c->mem.upload(L.kd_h, s);
+      band_total = 0;
+    }
+    L.band = band_total ? c->mem.alloc<double>(band_total) : nullptr;
     L.n64.F = reg_work(c, c->mem.alloc<double>(T.T), T.T);
     L.n64.U = reg_work(c, c->mem.alloc<double>(T.T), T.T);
     L.n64.R = reg_work(c, c->mem.alloc<double>(T.T), T.T);
@@ -644,9 +732,11 @@ void build_levels(igamg_ctx* c) {
     L.n64.band = L.band;
     L.n64.band_op = L.band;
     c->band_count.push_back(band_total);
-    CK(cudaMemsetAsync(L.band, 0, band_total * sizeof(double), s));
     double ta0 = now_ms();
-    assemble_level(c, L, dtabs, tabs, dcorn, false, L.band);
+    if (!L.kron) {
+      CK(cudaMemsetAsync(L.band, 0, band_total * sizeof(double), s));
+      assemble_level(c, L, dtabs, tabs, dcorn, false, L.band);
+    }
     CK(cudaStreamSynchronize(s));
     c->t_assemble_ms += now_ms() - ta0;
     if (l == 0) continue;
@@ -702,7 +792,8 @@ void build_levels(igamg_ctx* c) {
       for (const Interior& in : T.interiors)
         if (in.len[0] && in.len[1]) min_len = std::min(min_len, std::min(in.len[0], in.len[1]));
       // tensor cores where the interiors are large enough to amortise the slices
-      if (c->opt.fd_engine == 0 && min_len >= 96) {
+      const bool want_tc = c->opt.fd_engine == 2 ? min_len >= 1 : c->opt.fd_engine == 0 && min_len >= kTcMinLen;
+      if (want_tc) {
         // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
         struct Sl { const __nv_bfloat16* a; const int* e; int nkb; };
         std::map<std::pair<const Smoother1D*, int>, Sl> sl;  // (basis, transposed?) -> slices
@@ -758,7 +849,9 @@ void build_levels(igamg_ctx* c) {
         set_tc(c, L.n64.tc1, t1);
         set_tc(c, L.n64.tc2, t2);
         set_tc(c, L.n64.tc3, t3);
-        L.n64.use_tc = true;
+        L.tc_ok = true;
+        // without the autotuner: the tensor cores from interiors of kTcMinLenStatic up
+        L.n64.use_tc = c->opt.fd_engine == 2 || min_len >= kTcMinLenStatic;
       }
     } else {
       // 3D: compact boxes, three mode products forward, Dinv, three backward
@@ -1110,6 +1203,11 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
   Num<T>& N = num<T>(L);
   const bool bf = N.bf16 && !krylov;
   double bb = bf ? 0.25 : double(sizeof(T)) / 8.0;  // band bytes relative to FP64
+  if (L.kron) {
+    ProfScope ps(c, CLS_APPLY, L.apply_flops, (double(sizeof(T)) * (f ? 3 : 2) + 1.0) * L.topo.T);
+    CK(launch_kron_apply_2d<T>(c->stream, N.kd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, L.active, u, f, r));
+    return;
+  }
   ProfScope ps(c, CLS_APPLY, L.apply_flops, L.band_bytes * bb + double(sizeof(T)) * L.topo.T * (f ? 3 : 2));
   if (bf) {
     if constexpr (std::is_same<T, float>::value) {
@@ -1478,6 +1576,86 @@ igamg_status pcg_refined(igamg_ctx* c, const double* b, double* x, double tol, i
   return st;
 }
 
+// ---------------------------------------------------------------- FD autotuner
+
+// Per level, the patch-interior FD contractions run on the candidate that times fastest on
+// this device: the FMA GEMM with an 8R x 8R output tile per block (R = 1, 2, 4) or the
+// tensor cores (where their stage sets were built).  A level's choice depends only on its
+// interior shapes and degrees, so it is kept process-wide under that signature: later
+// contexts with the same shapes (a batch of similar problems) reuse it without timing, and
+// two contexts in one process always make the same choice.
+struct FdChoice {
+  bool tc;
+  int R;
+};
+std::mutex g_tune_mu;
+std::map<std::string, FdChoice> g_tune_cache;
+
+std::string fd_signature(const igamg_ctx* c, const Level& L) {
+  std::string k = "d" + std::to_string(c->pd.dim) + (L.tc_ok ? "t" : "f");
+  for (const Interior& in : L.topo.interiors) {
+    k += "|" + std::to_string(c->pd.p[in.k * c->pd.dim]);
+    for (int j = 0; j < c->pd.dim; ++j) k += "x" + std::to_string(in.len[j]);
+  }
+  return k;
+}
+
+void apply_choice(Level& L, const FdChoice& ch) {
+  Num<double>& N = L.n64;
+  N.use_tc = ch.tc && L.tc_ok;
+  for (GemmSet* g : {&N.st0F, &N.st0R, &N.st1, &N.st2, &N.st3, &N.m0f, &N.m1f, &N.m2f, &N.m0b, &N.m1b, &N.m2b})
+    g->R = ch.R;
+}
+
+void autotune(igamg_ctx* c) {
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int l = 1; l < int(c->lv.size()); ++l) {
+    Level& L = c->lv[l];
+    if (!L.n64.st0F.batch && !L.n64.m0f.batch) continue;  // no patch interiors on this level
+    const std::string key = fd_signature(c, L);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        apply_choice(L, it->second);
+        continue;
+      }
+    }
+    std::vector<FdChoice> cand{{false, 1}, {false, 2}, {false, 4}};
+    if (L.tc_ok) cand.push_back({true, 0});
+    FdChoice best{false, 0};
+    float best_ms = 1e30f;
+    for (const FdChoice& ch : cand) {
+      apply_choice(L, ch);
+      smooth<double>(c, l, true, false);  // warm-up
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) smooth<double>(c, l, true, false);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ch;
+      }
+    }
+    if (c->verbose)
+      std::fprintf(stderr, "[igamg] autotune level %d: %s R=%d (%.3f ms per smoother)\n", l, best.tc ? "tensor" : "fma",
+                   best.R, best_ms / 3);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    // a context that tuned the same signature concurrently may have stored first: use
+    // the stored choice, so that every context of the process agrees
+    apply_choice(L, g_tune_cache.emplace(key, best).first->second);
+  }
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  CK(cudaMemsetAsync(c->lv.back().n64.U, 0, c->lv.back().topo.T * sizeof(double), s));
+  check_tc(c);
+}
+
 // Twins of the FP64 numerics in FP32 (bands in FP32 or BF16): every registered FP64 array
 // gets an FP32 copy (constants converted, work buffers allocated) and every FP64
 // descriptor is translated pointer by pointer.
@@ -1508,6 +1686,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     for (const GemmDesc& d : g.h)
       v.push_back(GemmDescT<float>{tr(d.A), tr(d.B), tr(d.C), tr(d.E), d.lda, d.ldb, d.ldc, d.lde, d.M, d.N, d.K});
     set_gemm(c, out, v);
+    out.R = g.R;
   };
   for (size_t l = 0; l < c->lv.size(); ++l) {
     Level& L = c->lv[l];
@@ -1525,12 +1704,18 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     int64_t nb = c->band_count[l];
     const bool finest = l + 1 == c->lv.size();
     float* b32 = nullptr;
-    if (!bf16_bands || finest) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
+    if (L.kron) {  // FP32 1D factors in every variant (no bands to round to BF16)
+      std::vector<KronDevT<float>> kf;
+      for (const auto& k : L.kd_h)
+        kf.push_back(KronDevT<float>{k.off, k.n0, k.n1, k.p0, k.p1, tr(k.K0), tr(k.M0), tr(k.K1), tr(k.M1),
+                                     float(k.c0), float(k.c1)});
+      B.kd = c->mem.upload(kf, s);
+    } else if (!bf16_bands || finest) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
       b32 = c->mem.alloc<float>(nb);
       CK(launch_convert_f64_f32(s, nb, L.band, 1.0, b32));
       B.band_op = b32;
     }
-    if (bf16_bands) {
+    if (bf16_bands && !L.kron) {
       __nv_bfloat16* bb = c->mem.alloc<__nv_bfloat16>(nb);
       CK(launch_convert_f64_bf16(s, nb, L.band, bb));
       B.band = bb;
@@ -1538,7 +1723,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     } else {
       B.band = b32;
     }
-    if (bf16_bands && A.use_tc) {
+    if (bf16_bands && L.tc_ok && (A.use_tc || c->opt.fd_engine == 0)) {  // BF16 operands: one MMA per product
       auto tr_tc = [&](const TcSet<double>& g, TcSet<float>& out) {
         std::vector<TcDesc<float, float>> v;
         for (const auto& d : g.h) {
@@ -1609,6 +1794,8 @@ igamg_status igamg_default_options(igamg_options* opt) {
   opt->inner_tol = 1e-4;
   opt->fd_engine = 0;
   opt->graphs = 1;
+  opt->apply_engine = 0;
+  opt->autotune = 1;
   return IGAMG_OK;
 }
 
@@ -1635,6 +1822,7 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
                                   prob->num_levels, c->pd, &code);
     if (!e.empty()) throw Fail{igamg_status(code), e};
     build_levels(c);
+    if (c->opt.autotune && c->opt.fd_engine == 0) autotune(c);
     if (c->opt.precision != IGAMG_FP64) build_low(c, c->opt.precision == IGAMG_BF16);
   } catch (const Fail& e) {
     g_setup_error = e.msg;
@@ -1795,8 +1983,8 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs)
     Level& L = c->lv[Lf];
     cudaStream_t s = c->stream;
     double* mband = nullptr;
-    CK(cudaMallocAsync(&mband, size_t(L.band_bytes), s));
-    CK(cudaMemsetAsync(mband, 0, size_t(L.band_bytes), s));
+    CK(cudaMallocAsync(&mband, size_t(L.band_doubles) * sizeof(double), s));
+    CK(cudaMemsetAsync(mband, 0, size_t(L.band_doubles) * sizeof(double), s));
     size_t mark = c->mem.ptrs.size();
     std::map<std::tuple<int, int>, Tables1D> tabs;
     std::map<std::tuple<int, int>, DevTables> dtabs;

@@ -7,7 +7,27 @@
 // (j - i + p) over (2p+1)^d, tap-major so that a warp reads 32 consecutive rows of one tap.
 #include "kernels.cuh"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace igamg {
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;  // within the default limit
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[std::make_pair(dev, func)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 
 namespace {
 constexpr int AX = 32, AY = 8;  // band-apply block: 32 x 8 outputs
@@ -97,6 +117,97 @@ template cudaError_t launch_band_apply_2d<float, float>(cudaStream_t, const Patc
 template cudaError_t launch_band_apply_2d<float, __nv_bfloat16>(cudaStream_t, const PatchDev*, int, int, int, int,
                                                                 const __nv_bfloat16*, const float*, const float*,
                                                                 float*);
+
+// ---------------------------------------------------------------- Kronecker-sum apply
+
+// One block computes KY x AX outputs of one rectangle patch.  Pass 1 contracts the u halo
+// (KY + 2p0 rows) along direction 1 with M_1 and K_1; pass 2 contracts those along
+// direction 0 with K_0 and M_0: 4(2p1+1)(1 + 2p0/KY) + 4(2p0+1) flops per output and no
+// operator traffic beyond the 1D bands (L1-resident).
+constexpr int KY = 16;
+
+size_t kron_apply_smem(int elem_size, int max_p) {
+  return size_t(elem_size) * ((KY + 2 * max_p) * (AX + 2 * max_p) + 2 * (KY + 2 * max_p) * AX);
+}
+
+template <class T>
+__global__ void __launch_bounds__(AX * AY) k_kron_apply_2d(const KronDevT<T>* __restrict__ kds,
+                                                           const unsigned char* __restrict__ active,
+                                                           const T* __restrict__ u, const T* __restrict__ f,
+                                                           T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const KronDevT<T> kd = kds[blockIdx.z];
+  const int n0 = kd.n0, n1 = kd.n1, p0 = kd.p0, p1 = kd.p1;
+  const int i0b = blockIdx.y * KY, i1b = blockIdx.x * AX;
+  if (i0b >= n0 || i1b >= n1) return;
+  const int H0 = KY + 2 * p0, H1 = AX + 2 * p1;
+  T* su = reinterpret_cast<T*>(smraw);
+  T* sa = su + H0 * H1;  // M_1-contracted halo rows
+  T* sb = sa + H0 * AX;  // K_1-contracted halo rows
+  const int tid = threadIdx.y * AX + threadIdx.x;
+  const T* ut = u + kd.off;
+  const unsigned char* at = active + kd.off;
+  for (int idx = tid; idx < H0 * H1; idx += AX * AY) {
+    int r = idx / H1, cc = idx % H1;
+    int g0 = i0b - p0 + r, g1 = i1b - p1 + cc;
+    T v = T(0);
+    if (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1) {
+      int64_t node = int64_t(g0) * n1 + g1;
+      if (at[node]) v = ut[node];
+    }
+    su[idx] = v;
+  }
+  __syncthreads();
+  const int w1 = 2 * p1 + 1, w0 = 2 * p0 + 1;
+  {
+    const int cx = threadIdx.x, i1 = i1b + cx;
+    const T* mrow = kd.M1 + int64_t(min(i1, n1 - 1)) * w1;
+    const T* krow = kd.K1 + int64_t(min(i1, n1 - 1)) * w1;
+    for (int r = threadIdx.y; r < H0; r += AY) {
+      const T* srow = su + r * H1 + cx;
+      T a = T(0), b = T(0);
+      for (int t = 0; t < w1; ++t) {
+        T v = srow[t];
+        a = fma(mrow[t], v, a);
+        b = fma(krow[t], v, b);
+      }
+      sa[r * AX + cx] = a;
+      sb[r * AX + cx] = b;
+    }
+  }
+  __syncthreads();
+  const int i1 = i1b + threadIdx.x;
+  if (i1 >= n1) return;
+  for (int r = threadIdx.y; r < KY; r += AY) {
+    const int i0 = i0b + r;
+    if (i0 >= n0) break;
+    const T* krow = kd.K0 + int64_t(i0) * w0;
+    const T* mrow = kd.M0 + int64_t(i0) * w0;
+    T a = T(0), b = T(0);
+    for (int t = 0; t < w0; ++t) {
+      a = fma(krow[t], sa[(r + t) * AX + threadIdx.x], a);
+      b = fma(mrow[t], sb[(r + t) * AX + threadIdx.x], b);
+    }
+    const int64_t node = kd.off + int64_t(i0) * n1 + i1;
+    T acc = active[node] ? kd.c0 * a + kd.c1 * b : T(0);
+    y[node] = f ? f[node] - acc : acc;
+  }
+}
+
+template <class T>
+cudaError_t launch_kron_apply_2d(cudaStream_t s, const KronDevT<T>* kd, int K, int max_n0, int max_n1, int max_p,
+                                 const unsigned char* active, const T* u, const T* f, T* y) {
+  dim3 grid((max_n1 + AX - 1) / AX, (max_n0 + KY - 1) / KY, K);
+  size_t sm = kron_apply_smem(sizeof(T), max_p);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_kron_apply_2d<T>), sm);
+  if (e != cudaSuccess) return e;
+  k_kron_apply_2d<T><<<grid, dim3(AX, AY), sm, s>>>(kd, active, u, f, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_kron_apply_2d<double>(cudaStream_t, const KronDevT<double>*, int, int, int, int,
+                                                  const unsigned char*, const double*, const double*, double*);
+template cudaError_t launch_kron_apply_2d<float>(cudaStream_t, const KronDevT<float>*, int, int, int, int,
+                                                 const unsigned char*, const float*, const float*, float*);
 
 // ---------------------------------------------------------------- batched GEMM
 
@@ -207,17 +318,20 @@ static int pick_r(int maxM, int maxN, int batch) {
 
 template <class T>
 cudaError_t launch_gemm(cudaStream_t s, const GemmDescT<T>* d_desc, int batch, int maxM, int maxN,
-                        bool transA, bool transB, int epi, T alpha) {
+                        bool transA, bool transB, int epi, T alpha, int R) {
   if (batch <= 0) return cudaSuccess;
-  int R = pick_r(maxM, maxN, batch), bt = 8 * R;
+  if (R != 1 && R != 2 && R != 4) R = pick_r(maxM, maxN, batch);
+  const int bt = 8 * R;
   dim3 grid((maxN + bt - 1) / bt, (maxM + bt - 1) / bt, batch);
   if (R == 4) k_gemm<4, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
   else if (R == 2) k_gemm<2, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
   else k_gemm<1, T><<<grid, 64, 0, s>>>(d_desc, transA, transB, epi, alpha);
   return cudaGetLastError();
 }
-template cudaError_t launch_gemm<double>(cudaStream_t, const GemmDescT<double>*, int, int, int, bool, bool, int, double);
-template cudaError_t launch_gemm<float>(cudaStream_t, const GemmDescT<float>*, int, int, int, bool, bool, int, float);
+template cudaError_t launch_gemm<double>(cudaStream_t, const GemmDescT<double>*, int, int, int, bool, bool, int, double,
+                                         int);
+template cudaError_t launch_gemm<float>(cudaStream_t, const GemmDescT<float>*, int, int, int, bool, bool, int, float,
+                                        int);
 
 cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
                             double alpha) {
@@ -732,8 +846,8 @@ cudaError_t launch_assemble_elem(cudaStream_t s, const ElemAsm& base) {
   const int D = base.dim, P = base.p + 1;
   size_t smem = elem_asm_smem(D, base.p, base.mass);
   cudaError_t e;
-  if (D == 2) e = cudaFuncSetAttribute(k_assemble_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  else e = cudaFuncSetAttribute(k_assemble_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (D == 2) e = ensure_smem(reinterpret_cast<const void*>(k_assemble_elem<2>), smem);
+  else e = ensure_smem(reinterpret_cast<const void*>(k_assemble_elem<3>), smem);
   if (e != cudaSuccess) return e;
   int ncol = 1;
   for (int j = 0; j < D; ++j) ncol *= P;
@@ -805,7 +919,7 @@ cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, 
   int t1 = (max_n[1] + BY3 - 1) / BY3, t0 = (max_n[0] + BZ3 - 1) / BZ3;
   dim3 grid((max_n[2] + BX3 - 1) / BX3, t0 * t1, K);
   size_t sm = sizeof(TV) * (BZ3 + 2 * max_p) * (BY3 + 2 * max_p) * (BX3 + 2 * max_p);
-  cudaError_t e = cudaFuncSetAttribute(k_band_apply_3d<TV, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_band_apply_3d<TV, TB>), sm);
   if (e != cudaSuccess) return e;
   k_band_apply_3d<TV, TB><<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
   return cudaGetLastError();

@@ -9,6 +9,11 @@
 
 namespace igamg {
 
+// Raises `func`'s dynamic shared memory limit on the current device to at least `bytes` and
+// never lowers it, so launches of the same kernel from concurrent host threads with
+// smaller needs stay valid.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+
 // Per-patch descriptor of one level's tile layout and band storage.
 struct PatchDev {
   int64_t off;       // tile offset (nodes)
@@ -53,13 +58,31 @@ size_t elem_asm_smem(int D, int p, bool mass);
 template <class TV, class TB>
 cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0, int max_n1, int max_p,
                                  const TB* band, const TV* u, const TV* f, TV* y);
+// Rectangle patch with constant metric C = |det J| J^{-1} J^{-T} = diag(c0, c1): the stiffness
+// is the Kronecker sum A = c0 K_0 (x) M_1 + c1 M_0 (x) K_1 of the 1D stiffness K_j and mass
+// M_j on (0,1).  The 1D matrices are stored row-banded, [n_j][2p_j+1] with entry (i, t) =
+// X(i, i - p_j + t) (0 outside the matrix).
+template <class T>
+struct KronDevT {
+  int64_t off;  // tile offset (nodes)
+  int n0, n1, p0, p1;
+  const T *K0, *M0, *K1, *M1;
+  T c0, c1;
+};
+// y = f - A u (f != NULL) or y = A u per tile; rows and columns of eliminated (Dirichlet)
+// nodes, active[node] == 0, are dropped: their u is read as 0 and their y is f or 0.
+template <class T>
+cudaError_t launch_kron_apply_2d(cudaStream_t s, const KronDevT<T>* kd, int K, int max_n0, int max_n1, int max_p,
+                                 const unsigned char* active, const T* u, const T* f, T* y);
+size_t kron_apply_smem(int elem_size, int max_p);
+
 template <class TV, class TB>
 cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
                                  const TB* band, const TV* u, const TV* f, TV* y);
 
 template <class T>
 cudaError_t launch_gemm(cudaStream_t s, const GemmDescT<T>* d_desc, int batch, int maxM, int maxN,
-                        bool transA, bool transB, int epi, T alpha);
+                        bool transA, bool transB, int epi, T alpha, int R = 0);
 // One FP64 GEMM with the descriptor passed by value (no device-side descriptor array).
 cudaError_t launch_gemm_one(cudaStream_t s, const GemmDesc& d, bool transA, bool transB, int epi,
                             double alpha);

@@ -26,6 +26,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "kernels.cuh"
 #include "tc_gemm.cuh"
 
 namespace igamg {
@@ -316,7 +317,7 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
                            TC alpha, int* err) {
   if (batch <= 0) return cudaSuccess;
   size_t smem = size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<S, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
   if (S > 1) {
     k_col_exponents<TB, TC><<<dim3((maxN + TBN - 1) / TBN, batch), 256, 0, s>>>(d_desc);

@@ -30,7 +30,9 @@ class igamg_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("sigma_scale", C.c_double), ("nu", C.c_int),
                 ("mu", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double),
                 ("fd_engine", C.c_int),
-                ("graphs", C.c_int)]
+                ("graphs", C.c_int),
+                ("apply_engine", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class igamg_result(C.Structure):
@@ -68,6 +70,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                    C.c_int),
         "igamg_free": ([P], C.c_int),
         "igamg_last_error": ([P], C.c_char_p),
+        "igamg_setup_batch": ([P, C.c_int, C.POINTER(igamg_options), C.c_int, P, C.POINTER(P)], C.c_int),
+        "igamg_batch_context": ([P, C.c_int, C.POINTER(P)], C.c_int),
+        "igamg_solve_batch": ([P, C.POINTER(P), C.POINTER(P), C.c_double, C.POINTER(igamg_result),
+                               C.POINTER(C.c_int)], C.c_int),
+        "igamg_free_batch": ([P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -148,6 +155,16 @@ def igamg_default_options() -> igamg_options:
 
 class Context:
     """Owns one igamg_ctx.  Methods are the ABI entry points without the igamg_ prefix."""
+
+    @classmethod
+    def borrowed(cls, handle, problem, stream):
+        """Wrapper of a context owned elsewhere (a batch): free() leaves it alone."""
+        self = cls.__new__(cls)
+        self.problem = problem
+        self.stream = stream
+        self.h = handle
+        self._borrowed = True
+        return self
 
     def __init__(self, problem, options: igamg_options | None = None, stream=None):
         import torch
@@ -239,7 +256,65 @@ class Context:
 
     def free(self):
         if getattr(self, "h", None):
-            lib().igamg_free(self.h)
+            if not getattr(self, "_borrowed", False):
+                lib().igamg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one igamg_batch: independent problems set up together and solved concurrently
+    by `workers` host threads with a CUDA stream each.  contexts[i] is problem i's context
+    (borrowed: it lives as long as the batch)."""
+
+    def __init__(self, problems, options: igamg_options | None = None, workers=0, stream=None):
+        import torch
+        self.problems = [Problem(p) for p in problems]
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (igamg_problem * len(self.problems))(*[p.struct for p in self.problems])
+        self._arr = arr
+        h = C.c_void_p()
+        st = lib().igamg_setup_batch(arr, len(self.problems), C.byref(options) if options else None, int(workers),
+                                     C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != IGAMG_OK:
+            raise IgamgError(st, lib().igamg_last_error(None).decode())
+        self.h = h
+        self.contexts = []
+        for i, pr in enumerate(self.problems):
+            ch = C.c_void_p()
+            lib().igamg_batch_context(h, i, C.byref(ch))
+            self.contexts.append(Context.borrowed(ch, pr, stream))
+
+    def __len__(self):
+        return len(self.contexts)
+
+    def solve(self, rhs, xs, tol=1e-8):
+        """rhs, xs: sequences of contiguous CUDA float64 tensors (xs hold the initial guesses).
+        Returns (overall status, [igamg_result], [status])."""
+        n = len(self.contexts)
+        assert len(rhs) == n and len(xs) == n
+        bp = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
+        xp = (C.c_void_p * n)(*[t.data_ptr() for t in xs])
+        res = (igamg_result * n)()
+        sts = (C.c_int * n)()
+        st = lib().igamg_solve_batch(self.h, bp, xp, tol, res, sts)
+        if st not in (IGAMG_OK, IGAMG_ERR_NOT_CONVERGED):
+            bad = next(i for i in range(n) if sts[i] not in (IGAMG_OK, IGAMG_ERR_NOT_CONVERGED))
+            raise IgamgError(st, f"problem {bad}: " + lib().igamg_last_error(self.contexts[bad].h).decode())
+        return st, list(res), list(sts)
+
+    def free(self):
+        if getattr(self, "h", None):
+            for c in self.contexts:
+                c.h = None
+            lib().igamg_free_batch(self.h)
             self.h = None
 
     def __del__(self):

@@ -15,6 +15,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+def transposed_rect_grid():
+    """2x2 rectangles with patch 0's parameter directions swapped (its direction 0 runs
+    along y): the Kronecker-sum metric must follow the patch's own axes."""
+    pr = workloads.perturbed_grid_2d(2, 2, 8, 4, 3, amp=0.0)
+    pr.corners[0] = pr.corners[0][[0, 2, 1, 3]]
+    pr.side_bc[0] = pr.side_bc[0][[2, 3, 0, 1]]
+    return pr
+
+
 def cases():
     return {
         "square_p2_m8": lambda: workloads.unit_square_quadrants(8, 2, 4),
@@ -27,6 +36,8 @@ def cases():
         "cube_p3_m8": lambda: workloads.perturbed_cube_3d(2, 3, 8, 4, 3),
         "fichera_p2_m4": lambda: workloads.fichera_corner(1, 2, 4, 3),
         "cube_p4_m4_single": lambda: workloads.perturbed_cube_3d(1, 4, 4, 3, 5),
+        "rect3x3_p3_m16_mixed_bc": lambda: workloads.perturbed_grid_2d(3, 3, 16, 5, 31, amp=0.0),
+        "rect2x2_p2_m8_transposed": transposed_rect_grid,
     }
 
 
@@ -253,27 +264,88 @@ def test_greville_points():
         np.testing.assert_allclose(xyz[perms[-1][ids[keep]]], X[keep], atol=1e-13)
 
 
-@pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "single_patch_p2_m64"])
+@pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "single_patch_p2_m64",
+                                  "grid2x2_p1_m8"])
 def test_fd_engines_agree(name):
-    """Tensor-core FD (FP64-accurate digit slices) against the FP64-FMA FD: smoother and
-    solve agree to FP64 rounding."""
+    """Tensor-core FD forced on every level (FP64-accurate digit slices; ragged sizes from
+    1 to 66, far from the 128 x 64 tile) against the FP64-FMA FD, and the autotuned default
+    against both: smoother and solve agree to FP64 rounding on every level."""
+    from paper_1804_02539_gb300 import igamg
+    pr, H, ctx, perms = setup_case(name)
+    ctxs = {}
+    for eng in (1, 2):
+        o = igamg.igamg_default_options()
+        o.fd_engine = eng
+        ctxs[eng] = igamg.Context(pr, o)
+    rng = np.random.default_rng(31)
+    for l in range(1, pr.num_levels):
+        r = dev(rng.normal(size=H.levels[l].space.N))
+        z = {}
+        for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2])):
+            z[k] = torch.empty_like(r)
+            c.smooth(l, r, z[k])
+        # digit truncation at 2^-49 of each column maximum
+        assert rel(host(z["tc"]), host(z["fma"])) < 1e-12, l
+        assert rel(host(z["auto"]), host(z["fma"])) < 1e-12, l
+    r = dev(rng.normal(size=H.levels[-1].space.N))
+    xs, its = {}, {}
+    for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2])):
+        xs[k] = torch.zeros_like(r)
+        res, _ = c.solve(r, xs[k], 1e-10)
+        its[k] = res.iters
+    assert its["tc"] == its["fma"] == its["auto"]
+    assert rel(host(xs["tc"]), host(xs["fma"])) < 1e-11
+    for c in ctxs.values():
+        c.free()
+
+
+def test_autotuned_choice_is_reused():
+    """Two contexts of one problem in one process make the same FD choices (the tuning
+    cache), so their solves are bit-identical; with the autotuner off the result agrees to
+    rounding."""
+    from paper_1804_02539_gb300 import igamg
+    pr = cases()["grid2x2_p5_m32_ragged"]()
+    a, b = igamg.Context(pr), igamg.Context(pr)
+    o = igamg.igamg_default_options()
+    o.autotune = 0
+    c = igamg.Context(pr, o)
+    rhs = dev(workloads.rhs_coefficients(a.num_dofs(), 3))
+    xs = []
+    for ctx in (a, b, c):
+        x = torch.zeros_like(rhs)
+        ctx.solve(rhs, x, 1e-10)
+        xs.append(x)
+    assert torch.equal(xs[0], xs[1])
+    assert rel(host(xs[0]), host(xs[2])) < 1e-11
+    for ctx in (a, b, c):
+        ctx.free()
+
+
+@pytest.mark.parametrize("name", ["square_p2_m8", "rect3x3_p3_m16_mixed_bc", "rect2x2_p2_m8_transposed",
+                                  "single_patch_p2_m64"])
+def test_apply_engines_agree(name):
+    """Rectangle patches: the Kronecker-sum apply (no bands) and the assembled bands give
+    the same operator on every level, and the same solve."""
     from paper_1804_02539_gb300 import igamg
     pr, H, ctx, perms = setup_case(name)
     o = igamg.igamg_default_options()
-    o.fd_engine = 1
-    cf = igamg.Context(pr, o)
-    L = pr.num_levels - 1
-    r = dev(np.random.default_rng(31).normal(size=H.levels[-1].space.N))
-    z0, z1 = torch.empty_like(r), torch.empty_like(r)
-    ctx.smooth(L, r, z0)
-    cf.smooth(L, r, z1)
-    assert rel(host(z0), host(z1)) < 1e-12      # digit truncation at 2^-49 of each column maximum
-    x0, x1 = torch.zeros_like(r), torch.zeros_like(r)
-    r0, _ = ctx.solve(r, x0, 1e-10)
-    r1, _ = cf.solve(r, x1, 1e-10)
-    assert r0.iters == r1.iters
-    assert rel(host(x0), host(x1)) < 1e-12
-    cf.free()
+    o.apply_engine = 1
+    cb = igamg.Context(pr, o)
+    rng = np.random.default_rng(7)
+    for l in range(pr.num_levels):
+        n = H.levels[l].space.N
+        x = dev(rng.normal(size=n))
+        y0, y1 = torch.empty_like(x), torch.empty_like(x)
+        ctx.apply(l, x, y0)
+        cb.apply(l, x, y1)
+        assert rel(host(y0), host(y1)) < 1e-13, l
+    b = dev(workloads.rhs_coefficients(H.levels[-1].space.N, 5))
+    x0, x1 = torch.zeros_like(b), torch.zeros_like(b)
+    r0, _ = ctx.solve(b, x0, 1e-10)
+    r1, _ = cb.solve(b, x1, 1e-10)
+    assert abs(r0.iters - r1.iters) <= 1
+    assert rel(host(x0), host(x1)) < 1e-9
+    cb.free()
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])

@@ -153,15 +153,16 @@ def rhs_coefficients(num_dofs: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, num_dofs)
 
 
-def batch_problems(count: int = 512, seed: int = 4) -> List[Problem]:
+def batch_problems(count: int = 512, seed: int = 4, m_choices=(16, 32, 64, 128),
+                   K_choices=(4, 9, 16, 25, 36), p_range=(2, 6)) -> List[Problem]:
     """Independent 2D problems like the quadrant workload: sqrt(K) x sqrt(K) affine grid
     on [0,1]^2, all Dirichlet, with K, p and intervals per direction drawn uniformly."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
-        K = int(rng.choice([4, 9, 16, 25, 36]))
-        p = int(rng.integers(2, 7))
-        m = int(rng.choice([16, 32, 64, 128]))
+        K = int(rng.choice(list(K_choices)))
+        p = int(rng.integers(p_range[0], p_range[1] + 1))
+        m = int(rng.choice(list(m_choices)))
         nper = int(round(K ** 0.5))
         levels = int(np.log2(m)) + 1
         verts = _vertex_lattice(2, nper, 1.0)
