@@ -166,27 +166,36 @@ def run_ours(args, rank, world, local_rank):
         dom = max(prof1, key=lambda k: prof1[k]["ms"])
         dom_bit = 1 << igamg.Context.PROFILE_CLASSES.index(dom)
         ctx.profile_enable(0)
-        # timed region: the solves as a user runs them (graph-replayed PCG iterations),
-        # with CUDA events only around the dominant class's launches
-        sampler = ClockSampler(local_rank)
+        # both graph variants of the PCG iteration (plain, and with timing nodes around the
+        # dominant class) are captured before the timed region
         ctx.profile_enable(dom_bit)
+        x.zero_()
+        ctx.solve(b, x, TOL)
+        ctx.profile_enable(0)
+        # timed region: the solves as a user runs them (graph-replayed PCG iterations); the
+        # first timed solve carries CUDA-event nodes around the dominant class's launches
+        sampler = ClockSampler(local_rank)
         if dist:
             tdist.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        prof = None
+        for step in range(args.steps):
+            if step == 0:
+                ctx.profile_enable(dom_bit)
             x.zero_()
             res, st = ctx.solve(b, x, TOL)
+            if step == 0:
+                prof = ctx.profile_read()
+                ctx.profile_enable(0)
         e1.record(stream)
         torch.cuda.synchronize()
         if dist:
             tdist.barrier()
         ms_total = e0.elapsed_time(e1)
         clocks = sampler.stop()
-        prof = ctx.profile_read()
-        ctx.profile_enable(0)
         iters = res.iters
         outer = res.outer_iters
         relres = res.relres
@@ -232,10 +241,12 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": src, "kernel": dom, "traffic": None}
     roof["avg_launch_ms"] = round(d["ms"] / max(d["launches"], 1), 5)
+    roof["timing"] = ("CUDA-event nodes around each launch of the class in the first timed solve "
+                      f"({d['launches']} launches), on the solve's stream")
     breakdown = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"],
                      "gflop_per_step": round(v["flops"] / 1e9, 4),
                      "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items()}
-    launches = sum(v["launches"] for v in prof.values())
+    launches = sum(v["launches"] for v in prof.values()) * args.steps
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -493,6 +504,47 @@ def run_batch(args):
     B.free()
 
 
+# ---------------------------------------------------------------- smoother micro-benchmark
+
+def run_micro_fd(args):
+    """The finest-level smoother of the workload (patch-interior FD contractions plus the
+    interface pieces) applied `steps` times after `warmup`, timed with CUDA events; with
+    --no-autotune the static engine rule applies (tensor cores on the 2D interiors)."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1804_02539_gb300 import igamg
+    torch.cuda.set_device(0)
+    pr = workloads.CONFIGS[args.workload]()
+    o = igamg.igamg_default_options()
+    o.autotune = 0 if args.no_autotune else 1
+    o.fd_engine = args.fd_engine
+    ctx = igamg.Context(pr, o)
+    L = pr.num_levels - 1
+    r = torch.tensor(np.random.default_rng(1).normal(size=ctx.num_dofs()), device="cuda")
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        ctx.smooth(L, r, z)
+    ctx.profile_enable(0x3F)
+    ctx.smooth(L, r, z)
+    prof = ctx.profile_read()
+    ctx.profile_enable(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.smooth(L, r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fd = prof["interior_fd"]
+    print(json.dumps({"micro": "finest smoother", "workload": args.workload, "fd_engine": args.fd_engine,
+                      "autotune": o.autotune, "ms_per_smoother": round(ms, 4),
+                      "fd_ms_profiled": round(fd["ms"], 4), "fd_launches": fd["launches"],
+                      "fd_fp64_tflops": round(fd["flops"] / (fd["ms"] * 1e-3) / 1e12, 3)}), flush=True)
+    ctx.free()
+
+
 def main():
     if "--_oracle_batch" in sys.argv:
         print(json.dumps(oracle_batch_json()))
@@ -516,7 +568,13 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--batch", action="store_true", help="the 512-problem batched workload")
     ap.add_argument("--workers", type=int, default=16, help="host worker threads of the batch")
+    ap.add_argument("--micro", choices=["fd"], help="micro-benchmark of one kernel class instead of the solve")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fd-engine", type=int, default=0)
     args = ap.parse_args()
+    if args.micro:
+        run_micro_fd(args)
+        return
     if args.batch:
         run_batch(args)
         return

@@ -165,11 +165,13 @@ struct igamg_ctx {
   int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
   // PCG iteration body replayed as a CUDA graph (index 0 FP64, 1 FP32 inner), captured on a
   // private stream (the legacy stream cannot capture) and launched on `stream`
-  cudaGraphExec_t iter_graph[2] = {nullptr, nullptr};
-  unsigned graph_key[2] = {0, 0};                         // profiling mode it was captured in
-  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> graph_ev[2];  // timing nodes inside it
-  int64_t graph_launch[2][8] = {};                        // per-replay launch accounting
-  double graph_flops[2][8] = {}, graph_bytes[2][8] = {};
+  // slot 2 * index + (1 while profiling): the plain graph and the one with timing nodes
+  // are kept side by side, so switching the profiler between solves costs no capture
+  cudaGraphExec_t iter_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned graph_key[4] = {0, 0, 0, 0};                   // profiling mode it was captured in
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> graph_ev[4];  // timing nodes inside it
+  int64_t graph_launch[4][8] = {};                        // per-replay launch accounting
+  double graph_flops[4][8] = {}, graph_bytes[4][8] = {};
   cudaStream_t cap_stream = nullptr;
   int capturing = -1, pending_graph = -1;
   std::map<const void*, const void*> tc_bf16_twin;         // S=7 slices -> S=1 slices of the same matrix
@@ -289,8 +291,9 @@ void drop_graph(igamg_ctx* c, int gi) {
 // the profiling mode changed).  The body must launch onto c->stream only and touch the same
 // buffers with the same host arguments every time.
 template <class F>
-void graph_run(igamg_ctx* c, int gi, F&& body) {
+void graph_run(igamg_ctx* c, int index, F&& body) {
   const unsigned key = c->prof ? (0x100u | c->prof_mask) : 0u;
+  const int gi = 2 * index + (c->prof ? 1 : 0);
   if (c->iter_graph[gi] && c->graph_key[gi] != key) drop_graph(c, gi);
   if (!c->iter_graph[gi]) {
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -2094,7 +2097,7 @@ igamg_status igamg_free(igamg_ctx* c) {
   if (!c) return IGAMG_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (int gi = 0; gi < 2; ++gi) {
+  for (int gi = 0; gi < 4; ++gi) {
     if (c->iter_graph[gi]) cudaGraphExecDestroy(c->iter_graph[gi]);
     for (auto& t : c->graph_ev[gi]) {
       cudaEventDestroy(std::get<1>(t));

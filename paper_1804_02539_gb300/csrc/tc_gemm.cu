@@ -143,6 +143,23 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
   const int nkb = (d.K + TBK - 1) / TBK;
   const int mt = blockIdx.y;
+  // B staging: thread -> (column bn, chunk bkc of 8 consecutive k).  The mapping keeps the
+  // global loads coalesced for either storage order of B and lets every thread write one
+  // 16-byte core-matrix row per digit plane (8 lanes of a store phase hit 8 bank groups).
+  int bn, bkc;
+  if (d.tb) { bn = (tid & 7) | ((tid >> 6) << 3); bkc = (tid >> 3) & 7; }
+  else { bn = tid & 63; bkc = tid >> 6; }
+  const int gj = j0 + bn;
+  TB xv[8];
+  auto load_b = [&](int k0) {
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int gk = k0 + bkc * 8 + kk;
+      xv[kk] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
+                                      : TB(0);
+    }
+  };
+  load_b(0);
   uint32_t phase = 0;
   bool ok = true;
   for (int kb = 0; kb < nkb; ++kb) {
@@ -155,30 +172,32 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                    :: "r"(sptr(As)), "l"(src), "r"(bytes), "r"(sptr(abar)) : "memory");
     }
-    // B: digits of the varying operand (k, n) -> core layout of an [n x k] K-major tile;
-    // the 32 loads of a thread are issued before any is used
+    // B: digit planes of this k-block from the registers (the previous MMAs are complete)
     {
-      TB xv[TBN * TBK / NT];
+      uint32_t pk[S][4];
 #pragma unroll
-      for (int u = 0; u < TBN * TBK / NT; ++u) {
-        int idx = tid + u * NT, n, k;
-        if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
-        int gj = j0 + n, gk = k0 + k;
-        xv[u] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
-                                       : TB(0);
+      for (int kk = 0; kk < 8; kk += 2) {
+        float d0[S], d1[S];
+        if constexpr (S == 1) {
+          d0[0] = float(xv[kk]);
+          d1[0] = float(xv[kk + 1]);
+        } else {
+          digits_f64<S>(double(xv[kk]), tauS[bn], d0);
+          digits_f64<S>(double(xv[kk + 1]), tauS[bn], d1);
+        }
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(d0[q], d1[q]);
+          pk[q][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
+        }
       }
+      const int off = core_off(bn, bkc * 8);
 #pragma unroll
-      for (int u = 0; u < TBN * TBK / NT; ++u) {
-        int idx = tid + u * NT, n, k;
-        if (d.tb) { n = idx / TBK; k = idx % TBK; } else { k = idx / TBN; n = idx % TBN; }
-        float dig[S];
-        if constexpr (S == 1) dig[0] = float(xv[u]);
-        else digits_f64<S>(double(xv[u]), tauS[n], dig);
-        int off = core_off(n, k);
-#pragma unroll
-        for (int q = 0; q < S; ++q) Bs[q * TBN * TBK + off] = __float2bfloat16_rn(dig[q]);
-      }
+      for (int q = 0; q < S; ++q)
+        *reinterpret_cast<uint4*>(Bs + q * TBN * TBK + off) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
     }
+    // the next k-block's operand loads are in flight during this block's MMAs
+    if (kb + 1 < nkb) load_b((kb + 1) * TBK);
     if (!mbar_wait(sptr(abar), phase)) {
       ok = false;
       if (tid == 0) atomicExch(err, 2);
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
           const int qd = dg + 2;
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            long long iv = __float2ll_rn(v[q]);
+            long long iv = __float2int_rn(v[q]);  // exact: |D_q| < 2^24
             iacc[q] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
           }
         }

@@ -171,8 +171,19 @@ def batch_problems(count: int = 512, seed: int = 4, m_choices=(16, 32, 64, 128),
     return out
 
 
+def rect_grid_2d(nper: int = 4, p: int = 4, m: int = 64) -> Problem:
+    """One member of the batched workload's family, fixed: nper x nper rectangle patches on
+    [0,1]^2, all Dirichlet, degree p, m intervals per patch direction."""
+    verts = _vertex_lattice(2, nper, 1.0)
+    levels = int(np.log2(m)) + 1
+    return _grid_problem(2, nper, p, m, levels, verts, lambda j, e: SIDE_DIRICHLET,
+                         f"rect2d_K{nper*nper}_p{p}_m{m}")
+
+
 CONFIGS = {
     "square2x2_p2_m8": lambda: unit_square_quadrants(8, 2, 4),
+    "rect2d_K16_p4_m64": lambda: rect_grid_2d(4, 4, 64),
+    "rect2d_K36_p6_m128": lambda: rect_grid_2d(6, 6, 128),
     "grid2d_K16_p4_m256": lambda: perturbed_grid_2d(4, 4, 256, 9, 2),
     "grid2d_K16_p4_m128": lambda: perturbed_grid_2d(4, 4, 128, 8, 2),
     "cube3d_K8_p3_m64": lambda: perturbed_cube_3d(2, 3, 64, 7, 3),
