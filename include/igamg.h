@@ -271,6 +271,60 @@ igamg_status igamg_solve_batch(igamg_batch* batch, const double* const* rhs, dou
 /* Releases every context of the batch and its streams.  NULL is accepted. */
 igamg_status igamg_free_batch(igamg_batch* batch);
 
+/* ---------------------------------------------------------------- serving
+ * A request is one right-hand side of a registered model (a problem as in igamg_setup).
+ * Requests are answered by `workers` host threads with a CUDA stream each, in arrival
+ * order, except that a request waits while another worker uses its model's hierarchy.
+ * Hierarchies stay resident between requests; a model's hierarchy is built on its first
+ * request when its estimated size fits the device-memory budget, after freeing the least
+ * recently used idle hierarchies.  Times are milliseconds since igamg_server_create.  The
+ * paper solves one problem at a time and has no counterpart of this layer. */
+typedef struct igamg_server igamg_server;
+
+typedef struct {
+  int status;           /* igamg_status of the solve (IGAMG_ERR_OOM: the model never fits) */
+  int iters;            /* PCG iterations */
+  double relres;        /* ||b - A x|| / ||b|| at exit                                 */
+  double t_submit_ms;   /* igamg_server_submit                                       */
+  double t_start_ms;    /* a worker took the request                                 */
+  double t_done_ms;     /* solution copied to x                                      */
+  double setup_ms;      /* hierarchy built for this request (0 if it was resident)    */
+} igamg_request_info;
+
+typedef struct {
+  int models, resident;
+  int64_t device_bytes;  /* hierarchies (measured; estimates while being built)        */
+  int64_t setups, evictions, completed, waiting;
+} igamg_server_counters;
+
+/* Starts the workers.  opt (NULL = defaults) applies to every model; hbm_budget_bytes
+ * bounds the device memory of the resident hierarchies. */
+igamg_status igamg_server_create(const igamg_options* opt, int workers, int64_t hbm_budget_bytes,
+                                 igamg_server** out);
+
+/* Registers a problem (copied; nothing is built yet) and returns its model id, the length
+ * of its right-hand side and solution (the library's dof order of igamg_dof_map) and the
+ * estimated device bytes of its hierarchy used for admission until it is first built
+ * (num_dofs and est_bytes may be NULL). */
+igamg_status igamg_server_add_model(igamg_server* server, const igamg_problem* problem, int* model,
+                                    int64_t* num_dofs, int64_t* est_bytes);
+
+/* Queues a solve of model `model` for the load vector rhs (host, num_dofs values) from
+ * x = 0 to the relative tolerance tol; the solution is written to x (host).  Both arrays
+ * must stay valid until igamg_server_wait returns for the request. */
+igamg_status igamg_server_submit(igamg_server* server, int model, const double* rhs, double* x, double tol,
+                                 int64_t* request);
+
+/* Blocks until the request is answered and returns its record (each request is waited
+ * for exactly once). */
+igamg_status igamg_server_wait(igamg_server* server, int64_t request, igamg_request_info* info);
+
+igamg_status igamg_server_stats(igamg_server* server, igamg_server_counters* stats);
+
+/* Stops the workers (after the requests they are running) and frees every hierarchy.
+ * Requests still queued are dropped: wait for them first.  NULL is accepted. */
+igamg_status igamg_server_free(igamg_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,12 +44,14 @@ double now_ms() {
 // Device allocation registry of a context.
 struct DevMem {
   std::vector<void*> ptrs;
+  std::vector<size_t> sizes;  // bytes of each allocation
   template <class T>
   T* alloc(size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
     CK(cudaMalloc(&p, count * sizeof(T)));
     ptrs.push_back(p);
+    sizes.push_back(count * sizeof(T));
     return static_cast<T*>(p);
   }
   template <class T>
@@ -58,10 +60,17 @@ struct DevMem {
     if (!h.empty()) CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return d;
   }
-  void release() {
-    for (void* p : ptrs) cudaFree(p);
-    ptrs.clear();
+  void truncate(size_t mark) {  // frees the allocations made after `mark`
+    for (size_t i = mark; i < ptrs.size(); ++i) cudaFree(ptrs[i]);
+    ptrs.resize(mark);
+    sizes.resize(mark);
   }
+  size_t bytes() const {
+    size_t b = 0;
+    for (size_t x : sizes) b += x;
+    return b;
+  }
+  void release() { truncate(0); }
 };
 
 struct Smoother1D {  // subspace-corrected mass smoother data of one direction signature
@@ -198,6 +207,8 @@ void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
 // Stream a context launches on (the batch driver lends contexts to its worker streams).
 cudaStream_t ctx_stream(const igamg_ctx* c) { return c->stream; }
 void ctx_set_stream(igamg_ctx* c, cudaStream_t s) { c->stream = s; }
+// Device memory the context holds (its own allocations).
+size_t ctx_device_bytes(const igamg_ctx* c) { return c->mem.bytes(); }
 // Scheduling weight of one solve: finest-level tile nodes times (degree + 2).
 double ctx_work_estimate(const igamg_ctx* c) {
   const LevelTopo& T = c->lv.back().topo;
@@ -2003,8 +2014,7 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs)
     from_dist(c, Lf, L.n64.R, rhs);
     CK(cudaFreeAsync(mband, s));
     CK(cudaStreamSynchronize(s));
-    for (size_t i = mark; i < c->mem.ptrs.size(); ++i) cudaFree(c->mem.ptrs[i]);  // temporary tables
-    c->mem.ptrs.resize(mark);
+    c->mem.truncate(mark);  // temporary tables
     return IGAMG_OK;
   });
 }

@@ -40,6 +40,16 @@ class igamg_result(C.Structure):
                 ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double)]
 
 
+class igamg_request_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("relres", C.c_double), ("t_submit_ms", C.c_double),
+                ("t_start_ms", C.c_double), ("t_done_ms", C.c_double), ("setup_ms", C.c_double)]
+
+
+class igamg_server_counters(C.Structure):
+    _fields_ = [("models", C.c_int), ("resident", C.c_int), ("device_bytes", C.c_int64), ("setups", C.c_int64),
+                ("evictions", C.c_int64), ("completed", C.c_int64), ("waiting", C.c_int64)]
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libigamg.so not built ({path}); run __graft_entry__.build()")
@@ -75,6 +85,13 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_solve_batch": ([P, C.POINTER(P), C.POINTER(P), C.c_double, C.POINTER(igamg_result),
                                C.POINTER(C.c_int)], C.c_int),
         "igamg_free_batch": ([P], C.c_int),
+        "igamg_server_create": ([C.POINTER(igamg_options), C.c_int, C.c_int64, C.POINTER(P)], C.c_int),
+        "igamg_server_add_model": ([P, C.POINTER(igamg_problem), C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)], C.c_int),
+        "igamg_server_submit": ([P, C.c_int, P, P, C.c_double, C.POINTER(C.c_int64)], C.c_int),
+        "igamg_server_wait": ([P, C.c_int64, C.POINTER(igamg_request_info)], C.c_int),
+        "igamg_server_stats": ([P, C.POINTER(igamg_server_counters)], C.c_int),
+        "igamg_server_free": ([P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -315,6 +332,66 @@ class Batch:
             for c in self.contexts:
                 c.h = None
             lib().igamg_free_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns one igamg_server: models are registered problems, requests are load vectors
+    (host float64 arrays in the model's dof order) answered by worker threads."""
+
+    def __init__(self, options: igamg_options | None = None, workers=8, hbm_budget_bytes=64 << 30):
+        h = C.c_void_p()
+        st = lib().igamg_server_create(C.byref(options) if options else None, int(workers),
+                                       int(hbm_budget_bytes), C.byref(h))
+        if st != IGAMG_OK:
+            raise IgamgError(st, lib().igamg_last_error(None).decode())
+        self.h = h
+        self._problems = []
+        self._live = {}  # request id -> (rhs, x): kept alive until waited for
+
+    def add_model(self, problem):
+        """Returns (model id, number of dofs, estimated device bytes of its hierarchy)."""
+        pr = Problem(problem)
+        m, n, e = C.c_int(), C.c_int64(), C.c_int64()
+        st = lib().igamg_server_add_model(self.h, C.byref(pr.struct), C.byref(m), C.byref(n), C.byref(e))
+        if st != IGAMG_OK:
+            raise IgamgError(st, lib().igamg_last_error(None).decode())
+        self._problems.append(pr)
+        return m.value, n.value, e.value
+
+    def submit(self, model, rhs: np.ndarray, tol=1e-8):
+        """Queues a solve; returns (request id, x) with x filled once waited for."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.zeros_like(rhs)
+        rid = C.c_int64()
+        st = lib().igamg_server_submit(self.h, int(model), _host_ptr(rhs), _host_ptr(x), tol, C.byref(rid))
+        if st != IGAMG_OK:
+            raise IgamgError(st, "igamg_server_submit failed")
+        self._live[rid.value] = (rhs, x)
+        return rid.value, x
+
+    def wait(self, request):
+        info = igamg_request_info()
+        st = lib().igamg_server_wait(self.h, int(request), C.byref(info))
+        if st != IGAMG_OK:
+            raise IgamgError(st, "igamg_server_wait: unknown request")
+        self._live.pop(request, None)
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def stats(self):
+        s = igamg_server_counters()
+        lib().igamg_server_stats(self.h, C.byref(s))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().igamg_server_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -38,6 +38,8 @@ def cases():
         "cube_p4_m4_single": lambda: workloads.perturbed_cube_3d(1, 4, 4, 3, 5),
         "rect3x3_p3_m16_mixed_bc": lambda: workloads.perturbed_grid_2d(3, 3, 16, 5, 31, amp=0.0),
         "rect2x2_p2_m8_transposed": transposed_rect_grid,
+        "cube_p2_m12_coarse3": lambda: workloads.perturbed_cube_3d(2, 2, 12, 3, 3),    # 3 elements per
+        "grid2x2_p3_m20_coarse5": lambda: workloads.perturbed_grid_2d(2, 3, 20, 3, 5),  # coarsest direction
     }
 
 

@@ -1,0 +1,88 @@
+"""Serving layer (igamg_server_*): requests of several models (2D and 3D, different
+sizes) submitted together and answered by concurrent workers.
+
+  * each answer is bit-identical to solving that request alone through igamg_solve
+    (the served solve is the single-problem path on a resident hierarchy);
+  * with a device-memory budget that holds one hierarchy at a time, hierarchies are
+    evicted and rebuilt and the answers are unchanged;
+  * a model larger than the budget is answered with IGAMG_ERR_OOM, the others are served;
+  * latency bookkeeping is ordered (submit <= start <= done)."""
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def models():
+    return [workloads.rect_grid_2d(2, 3, 16), workloads.perturbed_grid_2d(2, 4, 16, 5, 4),
+            workloads.perturbed_cube_3d(2, 2, 4, 3, 3), workloads.rect_grid_2d(3, 2, 32),
+            workloads.perturbed_cube_3d(2, 2, 12, 3, 3)]
+
+
+def alone(pr, b):
+    from paper_1804_02539_gb300 import igamg
+    c = igamg.Context(pr)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    res, st = c.solve(torch.tensor(b, device="cuda"), x, 1e-8)
+    out = x.cpu().numpy()
+    c.free()
+    return out, res.iters
+
+
+def estimates():
+    from paper_1804_02539_gb300 import igamg
+    srv = igamg.Server(workers=1)
+    est = [srv.add_model(pr)[2] for pr in models()]
+    srv.free()
+    return est
+
+
+def serve(budget, reqs, workers=3):
+    from paper_1804_02539_gb300 import igamg
+    srv = igamg.Server(workers=workers, hbm_budget_bytes=budget)
+    ids = [srv.add_model(pr) for pr in models()]
+    sub = []
+    for m, seed in reqs:
+        b = np.random.default_rng(seed).uniform(-1, 1, ids[m][1])
+        rid, x = srv.submit(ids[m][0], b, 1e-8)
+        sub.append((m, b, rid, x))
+    out = [(m, b, x, srv.wait(rid)) for m, b, rid, x in sub]
+    stats = srv.stats()
+    srv.free()
+    return out, stats
+
+
+REQS = [(i % 5, 100 + i) for i in range(15)]
+
+
+def test_served_answers_match_single_solves():
+    out, stats = serve(8 << 30, REQS)
+    assert stats["completed"] == len(REQS) and stats["setups"] == 5 and stats["evictions"] == 0
+    prs = models()
+    for m, b, x, info in out:
+        ref, its = alone(prs[m], b)
+        assert info["status"] == 0 and info["iters"] == its
+        assert np.array_equal(x, ref)
+        assert info["t_submit_ms"] <= info["t_start_ms"] <= info["t_done_ms"]
+
+
+def test_eviction_under_a_small_budget():
+    # room for the largest hierarchy, not for all of them
+    est = estimates()
+    out, stats = serve(int(1.2 * max(est)), REQS, workers=2)
+    assert stats["evictions"] > 0 and stats["completed"] == len(REQS)
+    prs = models()
+    for m, b, x, info in out[:6]:
+        ref, _ = alone(prs[m], b)
+        assert info["status"] == 0 and np.array_equal(x, ref)
+
+
+def test_model_larger_than_budget_is_refused():
+    est = estimates()
+    assert est[4] > est[0]
+    out, stats = serve((est[0] + est[4]) // 2, [(0, 1), (4, 2), (0, 3)], workers=1)
+    statuses = [info["status"] for _, _, _, info in out]
+    assert statuses == [0, 4, 0]  # IGAMG_ERR_OOM for the model that never fits

@@ -171,6 +171,42 @@ def batch_problems(count: int = 512, seed: int = 4, m_choices=(16, 32, 64, 128),
     return out
 
 
+def serving_models():
+    """Model catalog of the served workload: every 2D problem of the batched family (K in
+    {4,9,16,25,36}, p in {2..6}, m in {16,32,64,128}; 100 models) and the 2x2x2 perturbed
+    unit cube with p in {2,3}, m in {16,24,32,40,48} (10 models; the coarsest level keeps
+    m / 2^k elements per patch direction once m is odd).  Returns (problems, is_3d)."""
+    probs, is3d = [], []
+    for K in (4, 9, 16, 25, 36):
+        for p in range(2, 7):
+            for m in (16, 32, 64, 128):
+                probs.append(rect_grid_2d(int(round(K ** 0.5)), p, m))
+                is3d.append(False)
+    for p in (2, 3):
+        for m in (16, 24, 32, 40, 48):
+            levels, mm = 1, m
+            while mm % 2 == 0:
+                mm //= 2
+                levels += 1
+            probs.append(perturbed_cube_3d(2, p, m, levels, 3))
+            is3d.append(True)
+    return probs, is3d
+
+
+def serving_requests(is3d, rate: float, count: int, seed: int = 5):
+    """Poisson arrivals at `rate` per second: (arrival time s, model index, rhs seed) for
+    `count` requests; 80% of the requests pick a 2D model, 20% a 3D model, uniformly."""
+    rng = np.random.default_rng([seed, int(rate)])
+    two = [i for i, t in enumerate(is3d) if not t]
+    three = [i for i, t in enumerate(is3d) if t]
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    out = []
+    for i in range(count):
+        pool = three if rng.random() < 0.2 else two
+        out.append((float(t[i]), int(pool[rng.integers(len(pool))]), int(rng.integers(1 << 30))))
+    return out
+
+
 def rect_grid_2d(nper: int = 4, p: int = 4, m: int = 64) -> Problem:
     """One member of the batched workload's family, fixed: nper x nper rectangle patches on
     [0,1]^2, all Dirichlet, degree p, m intervals per patch direction."""
