@@ -202,6 +202,21 @@ struct igamg_ctx {
 static thread_local std::string g_setup_error = "no error";
 
 namespace igamg {
+// A 2D patch whose bilinear map is affine with orthogonal Jacobian columns (a rectangle,
+// any orientation) has the constant metric C = |det J| J^{-1} J^{-T} = diag(c0, c1) with
+// c_j = |det J| / |J e_j|^2 (Sec. 2: the patch stiffness integrand grad^T C grad).
+bool rect_metric(const double* X, double* c0, double* c1) {
+  double a[2] = {X[2] - X[0], X[3] - X[1]}, b[2] = {X[4] - X[0], X[5] - X[1]};
+  double la = std::hypot(a[0], a[1]), lb = std::hypot(b[0], b[1]);
+  double gap = std::hypot(X[6] - X[0] - a[0] - b[0], X[7] - X[1] - a[1] - b[1]);
+  if (!(la > 0 && lb > 0) || gap > 1e-14 * (la + lb) || std::fabs(a[0] * b[0] + a[1] * b[1]) > 1e-14 * la * lb)
+    return false;
+  double det = std::fabs(a[0] * b[1] - a[1] * b[0]);
+  *c0 = det / (la * la);
+  *c1 = det / (lb * lb);
+  return true;
+}
+
 // Message returned by igamg_last_error(NULL) on this thread.
 void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
 // Stream a context launches on (the batch driver lends contexts to its worker streams).
@@ -615,21 +630,6 @@ void assemble_level(igamg_ctx* c, Level& L, std::map<std::tuple<int, int>, DevTa
   }
 }
 
-// A 2D patch whose bilinear map is affine with orthogonal Jacobian columns (a rectangle,
-// any orientation) has the constant metric C = |det J| J^{-1} J^{-T} = diag(c0, c1) with
-// c_j = |det J| / |J e_j|^2 (Sec. 2: the patch stiffness integrand grad^T C grad).
-bool rect_metric(const double* X, double* c0, double* c1) {
-  double a[2] = {X[2] - X[0], X[3] - X[1]}, b[2] = {X[4] - X[0], X[5] - X[1]};
-  double la = std::hypot(a[0], a[1]), lb = std::hypot(b[0], b[1]);
-  double gap = std::hypot(X[6] - X[0] - a[0] - b[0], X[7] - X[1] - a[1] - b[1]);
-  if (!(la > 0 && lb > 0) || gap > 1e-14 * (la + lb) || std::fabs(a[0] * b[0] + a[1] * b[1]) > 1e-14 * la * lb)
-    return false;
-  double det = std::fabs(a[0] * b[1] - a[1] * b[0]);
-  *c0 = det / (la * la);
-  *c1 = det / (lb * lb);
-  return true;
-}
-
 // Row-banded copy [n][2p+1] of a dense symmetric n x n banded 1D matrix.
 std::vector<double> row_band(const Mat& A, int n, int p) {
   std::vector<double> b(size_t(n) * (2 * p + 1), 0.0);
@@ -828,7 +828,7 @@ void build_levels(igamg_ctx* c) {
               slice_constant(A, n, n, 1, s1, e1);
               c->tc_bf16_twin[da] = c->mem.upload(s1, s);
             }
-            sl[key] = Sl{da, c->mem.upload(ev, s), (n + 63) / 64};
+            sl[key] = Sl{da, c->mem.upload(ev, s), tc_kblocks(n)};
           }
           return sl[key];
         };

@@ -29,6 +29,7 @@ namespace igamg {
 void set_context_free_error(const std::string& msg);
 void ctx_set_stream(igamg_ctx* c, cudaStream_t s);
 size_t ctx_device_bytes(const igamg_ctx* c);
+bool rect_metric(const double* X, double* c0, double* c1);
 }  // namespace igamg
 
 namespace {
@@ -115,30 +116,43 @@ struct igamg_server {
 
 namespace {
 
-// Device bytes of a hierarchy, estimated from the finest level's tile size: vectors, maps
-// and FD work arrays (~80 B per tile node), band coefficients ((2p+1)^d doubles per node),
-// twice that for the precision variant's twins, over all levels (geometric sum).
+// Device bytes of a hierarchy, estimated from the level topologies: vectors, maps, FD and
+// transfer work arrays (~80 B per tile node, 40 B more on the finest level for the PCG
+// vectors), band coefficients ((2p+1)^d doubles per node; none above the coarsest level
+// when every 2D patch is a rectangle), the dense coarse inverse, and ~1.6x that for the
+// precision variant's twins.
 int64_t estimate_bytes(const igamg_problem& p, const igamg_options& opt, int64_t* ndofs, std::string* err) {
   igamg::ProblemDesc pd;
   int code = 0;
   std::string e = igamg::parse_problem(p.dim, p.num_patches, p.degree, p.num_knots, p.knots, p.geo_degree,
                                        p.geo_num_ctrl, p.geo_ctrl, p.side_bc, p.num_levels, pd, &code);
-  if (e.empty()) {
-    igamg::LevelTopo T;
-    e = igamg::build_level(pd, pd.levels - 1, T, &code);
-    if (e.empty()) {
-      *ndofs = T.N;
-      int pmax = 1;
-      for (int q : pd.p) pmax = std::max(pmax, q);
-      double band = 8.0 * std::pow(2.0 * pmax + 1.0, pd.dim);
-      double per_node = 80.0 + band;
-      if (opt.precision != IGAMG_FP64) per_node *= 1.6;
-      double levels = double(1 << pd.dim) / double((1 << pd.dim) - 1);
-      return int64_t(double(T.T) * per_node * levels) + (8 << 20);
-    }
+  if (!e.empty()) {
+    *err = e;
+    return -1;
   }
-  *err = e;
-  return -1;
+  bool kron = pd.dim == 2 && opt.apply_engine == 0;
+  for (int k = 0; k < pd.K && kron; ++k) {
+    double c0, c1;
+    kron = igamg::rect_metric(pd.corners.data() + size_t(k) * 8, &c0, &c1);
+  }
+  int pmax = 1;
+  for (int q : pd.p) pmax = std::max(pmax, q);
+  const double band = 8.0 * std::pow(2.0 * pmax + 1.0, pd.dim);
+  double total = 1 << 20;
+  for (int l = 0; l < pd.levels; ++l) {
+    igamg::LevelTopo T;
+    e = igamg::build_level(pd, l, T, &code);
+    if (!e.empty()) {
+      *err = e;
+      return -1;
+    }
+    double per_node = 80.0 + ((kron && l > 0) ? 1.0 : band) + (l == pd.levels - 1 ? 40.0 : 0.0);
+    total += double(T.T) * per_node;
+    if (l == 0) total += 8.0 * double(T.N) * double(T.N);
+    if (l == pd.levels - 1) *ndofs = T.N;
+  }
+  if (opt.precision != IGAMG_FP64) total *= 1.6;
+  return int64_t(total);
 }
 
 void ensure_staging(Worker& w, int64_t n) {

@@ -32,7 +32,7 @@
 namespace igamg {
 
 namespace {
-constexpr int TBM = 128, TBN = 64, TBK = 64;
+constexpr int TBM = 128, TBN = 64, TBK = 32;  // K block of one pipeline stage
 constexpr int NT = 512;  // threads per CTA: 16 warps, 4 per TMEM lane quarter
 constexpr int WAIT_LIMIT = 1 << 24;
 
@@ -42,7 +42,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= uint64_t((saddr >> 4) & 0x3FFF);
   d |= uint64_t(128 >> 4) << 16;   // leading byte offset: next core matrix along K
-  d |= uint64_t(1024 >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= uint64_t((TBK / 8 * 128) >> 4) << 32;  // stride byte offset: next 8-row group
   d |= uint64_t(1) << 46;          // descriptor version
   return d;
 }
@@ -112,12 +112,14 @@ template <int S, class TB, class TC>
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int epi, TC alpha,
                                                  int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);                 // [S][128 x 64]
-  __nv_bfloat16* Bs = As + S * TBM * TBK;                                     // [S][64 x 64]
-  int* tauS = reinterpret_cast<int*>(Bs + S * TBN * TBK);                     // [64]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);                    // MMA completion
-  uint64_t* abar = mbar + 1;                                                  // A bulk copy
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  // two pipeline stages, each [S][128 x TBK] of A and [S][64 x TBK] of B
+  constexpr int ASZ = S * TBM * TBK, BSZ = S * TBN * TBK;
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Bs = As + 2 * ASZ;
+  int* tauS = reinterpret_cast<int*>(Bs + 2 * BSZ);                           // [64]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);                    // [2] MMAs of a stage done
+  uint64_t* abar = mbar + 2;                                                  // [2] A bulk copy landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
   const TcDesc<TB, TC> d = descs[blockIdx.z];
   const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
   if (i0 >= d.M || j0 >= d.N) return;
@@ -130,8 +132,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(abar)), "r"(1));
+    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar + q)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   // column scales of B (computed by k_col_exponents before this launch)
@@ -143,62 +144,64 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
   const int nkb = (d.K + TBK - 1) / TBK;
   const int mt = blockIdx.y;
-  // B staging: thread -> (column bn, chunk bkc of 8 consecutive k).  The mapping keeps the
-  // global loads coalesced for either storage order of B and lets every thread write one
-  // 16-byte core-matrix row per digit plane (8 lanes of a store phase hit 8 bank groups).
-  int bn, bkc;
-  if (d.tb) { bn = (tid & 7) | ((tid >> 6) << 3); bkc = (tid >> 3) & 7; }
-  else { bn = tid & 63; bkc = tid >> 6; }
+  // B staging: thread -> (column bn, 4 consecutive k at bk).  Bits of tid, high to low:
+  // bn / 8 (3), k chunk of 8 (2), bn % 8 (3), half chunk (1).  A half-warp stores 16
+  // distinct 8-byte pieces of one 128-byte core matrix per digit plane (conflict-free), and
+  // the loads are 32-byte sectors fully used for either storage order of B.
+  const int bn = ((tid >> 6) << 3) | ((tid >> 1) & 7);
+  const int bk = ((tid >> 4) & 3) * 8 + (tid & 1) * 4;
   const int gj = j0 + bn;
-  TB xv[8];
+  TB xv[4];
   auto load_b = [&](int k0) {
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const int gk = k0 + bkc * 8 + kk;
+    for (int kk = 0; kk < 4; ++kk) {
+      const int gk = k0 + bk + kk;
       xv[kk] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
                                       : TB(0);
     }
   };
-  load_b(0);
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int k0 = kb * TBK;
-    // A: pre-sliced tile block [S][128 x 64], contiguous: one bulk (TMA) copy tracked by abar
-    if (tid == 0) {
-      const uint32_t bytes = uint32_t(S) * TBM * TBK * sizeof(__nv_bfloat16);
-      const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * S * TBM * TBK;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar)), "r"(bytes));
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   :: "r"(sptr(As)), "l"(src), "r"(bytes), "r"(sptr(abar)) : "memory");
-    }
-    // B: digit planes of this k-block from the registers (the previous MMAs are complete)
-    {
-      uint32_t pk[S][4];
+  // digit planes of the registers into stage st of B
+  auto stage_b = [&](int st) {
+    uint32_t pk[S][2];
 #pragma unroll
-      for (int kk = 0; kk < 8; kk += 2) {
-        float d0[S], d1[S];
-        if constexpr (S == 1) {
-          d0[0] = float(xv[kk]);
-          d1[0] = float(xv[kk + 1]);
-        } else {
-          digits_f64<S>(double(xv[kk]), tauS[bn], d0);
-          digits_f64<S>(double(xv[kk + 1]), tauS[bn], d1);
-        }
-#pragma unroll
-        for (int q = 0; q < S; ++q) {
-          __nv_bfloat162 h = __floats2bfloat162_rn(d0[q], d1[q]);
-          pk[q][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
-        }
+    for (int kk = 0; kk < 4; kk += 2) {
+      float d0[S], d1[S];
+      if constexpr (S == 1) {
+        d0[0] = float(xv[kk]);
+        d1[0] = float(xv[kk + 1]);
+      } else {
+        digits_f64<S>(double(xv[kk]), tauS[bn], d0);
+        digits_f64<S>(double(xv[kk + 1]), tauS[bn], d1);
       }
-      const int off = core_off(bn, bkc * 8);
 #pragma unroll
-      for (int q = 0; q < S; ++q)
-        *reinterpret_cast<uint4*>(Bs + q * TBN * TBK + off) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+      for (int q = 0; q < S; ++q) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(d0[q], d1[q]);
+        pk[q][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
+      }
     }
-    // the next k-block's operand loads are in flight during this block's MMAs
-    if (kb + 1 < nkb) load_b((kb + 1) * TBK);
-    if (!mbar_wait(sptr(abar), phase)) {
+    const int off = core_off(bn, bk);
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      *reinterpret_cast<uint2*>(Bs + st * BSZ + q * TBN * TBK + off) = make_uint2(pk[q][0], pk[q][1]);
+  };
+  // A: the pre-sliced block [S][128 x TBK] is contiguous: one bulk (TMA) copy per stage
+  auto copy_a = [&](int kb, int st) {
+    const uint32_t bytes = uint32_t(ASZ) * sizeof(__nv_bfloat16);
+    const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar + st)), "r"(bytes));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(sptr(As + st * ASZ)), "l"(src), "r"(bytes), "r"(sptr(abar + st)) : "memory");
+  };
+  bool ok = true;
+  // prologue: stage 0 holds block 0; the registers hold block 1
+  if (tid == 0) copy_a(0, 0);
+  load_b(0);
+  stage_b(0);
+  if (nkb > 1) load_b(TBK);
+  for (int kb = 0; kb < nkb && ok; ++kb) {
+    const int st = kb & 1;
+    const uint32_t par = uint32_t(kb >> 1) & 1u;  // completion count parity of stage st's barriers
+    if (!mbar_wait(sptr(abar + st), par)) {
       ok = false;
       if (tid == 0) atomicExch(err, 2);
       break;
@@ -207,29 +210,42 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int ksteps = min(TBK, d.K - k0 + 15) / 16;
+      const int ksteps = min(TBK, d.K - kb * TBK + 15) / 16;
+      const __nv_bfloat16* a = As + st * ASZ;
+      const __nv_bfloat16* b = Bs + st * BSZ;
       for (int s = 1; s <= S; ++s)
         for (int t = 1; t + s <= (S == 1 ? 2 : S + 1); ++t) {
           const uint32_t acc_col = S == 1 ? 0 : uint32_t(s + t - 2) * TBN;
           for (int kk = 0; kk < ksteps; ++kk) {
-            uint64_t da = smem_desc(sptr(As + (s - 1) * TBM * TBK) + kk * 256);
-            uint64_t db = smem_desc(sptr(Bs + (t - 1) * TBN * TBK) + kk * 256);
+            uint64_t da = smem_desc(sptr(a + (s - 1) * TBM * TBK) + kk * 256);
+            uint64_t db = smem_desc(sptr(b + (t - 1) * TBN * TBK) + kk * 256);
             // the first contribution to accumulator s + t (pair (1, q-1), first K step)
             // overwrites it
             const bool first = kb == 0 && kk == 0 && s == 1;
             mma_bf16(tmem + acc_col, da, db, idesc, first ? 0u : 1u);
           }
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sptr(mbar)));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sptr(mbar + st)));
     }
-    if (!mbar_wait(sptr(mbar), phase)) {
-      ok = false;
-      if (tid == 0) atomicExch(err, 1);
-      break;
+    // while these MMAs run: stage the next block into the other buffers, once the MMAs
+    // that read them (block kb - 1) are complete
+    if (kb + 1 < nkb) {
+      if (kb >= 1 && !mbar_wait(sptr(mbar + (st ^ 1)), uint32_t((kb - 1) >> 1) & 1u)) {
+        ok = false;
+        if (tid == 0) atomicExch(err, 1);
+        break;
+      }
+      if (tid == 0) copy_a(kb + 1, st ^ 1);
+      stage_b(st ^ 1);
+      if (kb + 2 < nkb) load_b((kb + 2) * TBK);
     }
-    phase ^= 1;
-    __syncthreads();
   }
+  // the last commit arrives after every MMA of this thread is complete
+  if (ok && !mbar_wait(sptr(mbar + ((nkb - 1) & 1)), uint32_t((nkb - 1) >> 1) & 1u)) {
+    ok = false;
+    if (tid == 0) atomicExch(err, 1);
+  }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     const int gi = i0 + quarter * 32 + lane;
@@ -335,7 +351,7 @@ template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err) {
   if (batch <= 0) return cudaSuccess;
-  size_t smem = size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
+  size_t smem = 2 * size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
   if (S > 1) {
@@ -360,6 +376,8 @@ uint16_t bf16_bits_rn(float f) {
   return uint16_t(r >> 16);
 }
 }  // namespace
+
+int tc_kblocks(int K) { return (K + TBK - 1) / TBK; }
 
 void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
                     std::vector<int>& exps) {

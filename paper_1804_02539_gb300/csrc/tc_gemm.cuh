@@ -13,9 +13,9 @@ namespace igamg {
 
 template <class TB, class TC>
 struct TcDesc {
-  const __nv_bfloat16* Aslices;  // [M/128 tiles][K/64 blocks][S][128 x 64] in core-matrix layout
+  const __nv_bfloat16* Aslices;  // [M/128 tiles][K blocks][S][128 x 32] in core-matrix layout
   const int* Aexp;               // [M] row scale exponents (S > 1)
-  int nkb;                       // K blocks of A (ceil(K / 64))
+  int nkb;                       // K blocks of A (tc_kblocks(K))
   const TB* B;                   // B(k, n) = tb ? B[n * ldb + k] : B[k * ldb + n]
   int ldb, tb;
   TC* C;                         // C(i, j) at tc ? C[j * ldc + i] : C[i * ldc + j]
@@ -31,6 +31,9 @@ struct TcDesc {
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err);
+
+// K blocks of the slice layout for inner dimension K.
+int tc_kblocks(int K);
 
 // Host: slices of a constant row-major M x K matrix in the layout TcDesc::Aslices expects.
 // S = 7 gives integer digits and the row exponents; S = 1 gives BF16 roundings.

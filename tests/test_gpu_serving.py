@@ -32,18 +32,23 @@ def alone(pr, b):
     return out, res.iters
 
 
-def estimates():
+def similar_models():
+    return [workloads.rect_grid_2d(2, p, 32) for p in range(2, 7)]
+
+
+def estimates(mods):
     from paper_1804_02539_gb300 import igamg
     srv = igamg.Server(workers=1)
-    est = [srv.add_model(pr)[2] for pr in models()]
+    est = [srv.add_model(pr)[2] for pr in mods]
     srv.free()
     return est
 
 
-def serve(budget, reqs, workers=3):
+def serve(budget, reqs, workers=3, mods=None):
     from paper_1804_02539_gb300 import igamg
+    mods = mods or models()
     srv = igamg.Server(workers=workers, hbm_budget_bytes=budget)
-    ids = [srv.add_model(pr) for pr in models()]
+    ids = [srv.add_model(pr) for pr in mods]
     sub = []
     for m, seed in reqs:
         b = np.random.default_rng(seed).uniform(-1, 1, ids[m][1])
@@ -70,18 +75,21 @@ def test_served_answers_match_single_solves():
 
 
 def test_eviction_under_a_small_budget():
-    # room for the largest hierarchy, not for all of them
-    est = estimates()
-    out, stats = serve(int(1.2 * max(est)), REQS, workers=2)
+    """Five hierarchies of similar size; the budget holds the largest estimate, which is
+    less than all five together: every hierarchy is evicted and rebuilt at least once."""
+    mods = similar_models()
+    est = estimates(mods)
+    out, full = serve(8 << 30, REQS[:5], mods=mods)
+    assert full["device_bytes"] > 1.1 * max(est)   # all five do not fit the budget below
+    out, stats = serve(int(1.05 * max(est)), REQS, workers=2, mods=mods)
     assert stats["evictions"] > 0 and stats["completed"] == len(REQS)
-    prs = models()
-    for m, b, x, info in out[:6]:
-        ref, _ = alone(prs[m], b)
+    for m, b, x, info in out:
+        ref, _ = alone(mods[m], b)
         assert info["status"] == 0 and np.array_equal(x, ref)
 
 
 def test_model_larger_than_budget_is_refused():
-    est = estimates()
+    est = estimates(models())
     assert est[4] > est[0]
     out, stats = serve((est[0] + est[4]) // 2, [(0, 1), (4, 2), (0, 3)], workers=1)
     statuses = [info["status"] for _, _, _, info in out]
