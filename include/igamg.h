@@ -213,17 +213,18 @@ igamg_status igamg_fd_apply_noalloc(int n0, int n1, const double* U0, const doub
                                     const double* Dinv, const double* R, int ldr, double tau,
                                     double* Z, int ldz, void* cuda_stream);
 
-/* Per-kernel-class accounting for measurement.  While enabled, every kernel the context
- * launches is bracketed by CUDA events on its stream and counted; igamg_profile_read
- * returns, for class `cls`, the launches, the summed device time in ms, and the
- * algorithmic FLOPs and bytes of those launches (the operands the method itself must
- * read and write once: band coefficients, vectors, smoother bases).  Classes: 0 stiffness apply/residual, 1 patch-interior smoother contractions,
- * 2 interface smoothers (gather, edge contractions, scatter), 3 transfers, 4 coarse solve,
- * 5 vector operations (reductions, PCG updates, conversions).  `enable` is a bit mask of
- * the classes whose launches are bracketed by events (bit c = class c; 0 disables; launches,
- * flops and bytes are counted for every class while enabled).  While enabled the PCG
- * iterations run as individual launches instead of a replayed CUDA graph.  Enabling resets
- * the counters.  Reading synchronises the stream. */
+/* Per-kernel-class accounting for measurement.  While enabled, the context counts every
+ * kernel it launches; igamg_profile_read returns, for class `cls`, the launches, the summed
+ * device time in ms, and the algorithmic FLOPs and bytes of those launches (the operands
+ * the method itself must read and write once: band coefficients, vectors, smoother bases).
+ * Classes: 0 stiffness apply/residual, 1 patch-interior smoother contractions, 2 interface
+ * smoothers (gather, edge contractions, scatter), 3 transfers, 4 coarse solve, 5 vector
+ * operations (reductions, PCG updates, conversions); class 6 counts no launches and holds in
+ * `flops` the BF16 tensor-core FLOPs the class-1 tensor-core contractions execute (digit
+ * pairs and tile padding included).  `enable` is a bit mask of the classes whose launches
+ * are bracketed by CUDA events on the context's stream (bit c = class c; 0 disables); the
+ * PCG iterations then replay a graph variant with event-record nodes (captured once per
+ * mask).  Enabling resets the counters.  Reading synchronises the stream. */
 igamg_status igamg_profile_enable(igamg_ctx* ctx, int enable);
 igamg_status igamg_profile_read(igamg_ctx* ctx, int cls, int64_t* launches, double* ms,
                                 double* flops, double* bytes);

@@ -95,7 +95,8 @@ struct TcSet {
   TcDesc<T, T>* d = nullptr;
   std::vector<TcDesc<T, T>> h;
   int batch = 0, maxM = 0, maxN = 0;
-  double flops = 0;
+  double flops = 0;       // algorithmic (the GEMMs' own)
+  double exec_flops = 0;  // BF16 MMA work issued
 };
 
 // Numeric data of one level in one precision: the vectors and the descriptor sets the
@@ -242,7 +243,7 @@ double* reg_work(igamg_ctx* c, double* p, int64_t n) {
   return p;
 }
 
-enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5 };
+enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5, CLS_TENSOR_EXEC = 6 };
 
 cudaEvent_t prof_event(igamg_ctx* c) {
   if (!c->ev_free.empty()) {
@@ -404,10 +405,12 @@ void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
   ts.batch = int(v.size());
   ts.maxM = ts.maxN = 0;
   ts.flops = 0;
+  ts.exec_flops = 0;
   for (auto& d : v) {
     ts.maxM = std::max(ts.maxM, d.M);
     ts.maxN = std::max(ts.maxN, d.N);
     ts.flops += 2.0 * d.M * double(d.N) * d.K;
+    ts.exec_flops += tc_exec_flops(d.M, d.N, d.K, sizeof(T) == 8 ? 7 : 1);
   }
   ts.d = v.empty() ? nullptr : c->mem.upload(v, c->stream);
 }
@@ -415,6 +418,7 @@ void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
 template <class T>
 void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha) {
   if (!ts.batch) return;
+  if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
   ProfScope ps(c, CLS_FD, ts.flops, 0.0);
   if constexpr (std::is_same<T, double>::value)
     CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err)));
@@ -855,9 +859,6 @@ void build_levels(igamg_ctx* c) {
           t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n1, 1, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
           ++q;
         }
-        // column-exponent workspaces, one region per descriptor and stage
-        for (auto* vec : {&t0F, &t0R, &t1, &t2, &t3})
-          for (auto& dsc : *vec) dsc.tau = c->mem.alloc<int>(std::max(dsc.N, 1));
         set_tc(c, L.n64.tc0F, t0F);
         set_tc(c, L.n64.tc0R, t0R);
         set_tc(c, L.n64.tc1, t1);
@@ -1744,7 +1745,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
           auto it = c->tc_bf16_twin.find(d.Aslices);
           if (it == c->tc_bf16_twin.end()) throw Fail{IGAMG_ERR_NUMERIC, "missing BF16 basis slices"};
           v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
-                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K, nullptr});
+                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
         }
         set_tc(c, out, v);
       };

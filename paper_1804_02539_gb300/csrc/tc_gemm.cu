@@ -135,8 +135,34 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar + q)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // column scales of B (computed by k_col_exponents before this launch)
-  if (S > 1 && tid < TBN) tauS[tid] = (j0 + tid < d.N) ? d.tau[j0 + tid] : 0;
+  // column scales of B: tau_j = 1 + the largest exponent in column j of op(B) over all of K
+  // (bit extraction; zero columns give -1022).  Every CTA of a column panel reads the panel
+  // once here (L2-resident for the panel's other CTAs), eight loads in flight per thread.
+  if constexpr (S > 1) {
+    if (tid < TBN) tauS[tid] = 0;  // biased exponent field while reducing
+    __syncthreads();
+    int n, kq;
+    if (d.tb) { n = tid >> 3; kq = tid & 7; }  // 8 lanes along k of one column
+    else { n = tid & 63; kq = tid >> 6; }      // 32 lanes along the columns
+    const int gn = j0 + n;
+    int emax = 0;
+    if (gn < d.N) {
+      for (int k0 = kq; k0 < d.K; k0 += 64) {
+        TB v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + 8 * u;
+          v[u] = k < d.K ? __ldg(d.tb ? d.B + int64_t(gn) * d.ldb + k : d.B + int64_t(k) * d.ldb + gn) : TB(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          emax = max(emax, int((uint64_t(__double_as_longlong(double(v[u]))) >> 52) & 0x7FF));
+      }
+    }
+    atomicMax(&tauS[n], emax);
+    __syncthreads();
+    if (tid < TBN) tauS[tid] = tauS[tid] ? tauS[tid] - 1023 + 1 : -1022;
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -309,44 +335,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
 }
 
-// tau_j = 1 + max exponent over column j of op(B) (bit extraction; zero columns: -1022).
-// One block of 256 threads per (64-column tile, batch entry); 16 loads in flight per thread.
-template <class TB, class TC>
-__global__ void __launch_bounds__(256) k_col_exponents(const TcDesc<TB, TC>* __restrict__ descs) {
-  const TcDesc<TB, TC> d = descs[blockIdx.y];
-  const int j0 = blockIdx.x * TBN;
-  if (j0 >= d.N) return;
-  __shared__ int tmax[TBN];
-  const int tid = threadIdx.x;
-  if (tid < TBN) tmax[tid] = -1022;
-  __syncthreads();
-  const int total = TBN * d.K;
-  for (int base = tid; base < total; base += 256 * 16) {
-    int eb[16], nn[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      int idx = base + u * 256;
-      eb[u] = 0;
-      nn[u] = 0;
-      if (idx < total) {
-        int n, k;
-        if (d.tb) { n = idx / d.K; k = idx % d.K; } else { k = idx / TBN; n = idx % TBN; }
-        nn[u] = n;
-        int gj = j0 + n;
-        if (gj < d.N) {
-          const TB* bp = d.tb ? d.B + int64_t(gj) * d.ldb + k : d.B + int64_t(k) * d.ldb + gj;
-          eb[u] = int((uint64_t(__double_as_longlong(double(__ldg(bp)))) >> 52) & 0x7FF);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 16; ++u)
-      if (eb[u]) atomicMax(&tmax[nn[u]], eb[u] - 1023 + 1);
-  }
-  __syncthreads();
-  if (tid < TBN && j0 + tid < d.N) d.tau[j0 + tid] = tmax[tid];
-}
-
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err) {
@@ -354,11 +342,6 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
   size_t smem = 2 * size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
-  if (S > 1) {
-    k_col_exponents<TB, TC><<<dim3((maxN + TBN - 1) / TBN, batch), 256, 0, s>>>(d_desc);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   dim3 grid((maxN + TBN - 1) / TBN, (maxM + TBM - 1) / TBM, batch);
   k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, epi, alpha, err);
   return cudaGetLastError();
@@ -378,6 +361,14 @@ uint16_t bf16_bits_rn(float f) {
 }  // namespace
 
 int tc_kblocks(int K) { return (K + TBK - 1) / TBK; }
+
+double tc_exec_flops(int M, int N, int K, int S) {
+  const double tiles = double((M + TBM - 1) / TBM) * ((N + TBN - 1) / TBN);
+  const int pairs = S == 1 ? 1 : S * (S + 1) / 2;
+  double ksteps = 0;
+  for (int k0 = 0; k0 < K; k0 += TBK) ksteps += std::min(TBK, K - k0 + 15) / 16;
+  return tiles * pairs * ksteps * 2.0 * TBM * TBN * 16;
+}
 
 void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
                     std::vector<int>& exps) {

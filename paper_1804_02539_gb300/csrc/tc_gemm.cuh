@@ -23,7 +23,6 @@ struct TcDesc {
   const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
   int lde;
   int M, N, K;
-  int* tau;                      // [N] workspace: column exponents of op(B) (S > 1)
 };
 
 // S = 7: FP64-accurate digit-slice product (TB = TC = double); S = 1: BF16 product with
@@ -34,6 +33,8 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
 
 // K blocks of the slice layout for inner dimension K.
 int tc_kblocks(int K);
+// BF16 MMA FLOPs one launch issues for an M x N x K product with S digit slices.
+double tc_exec_flops(int M, int N, int K, int S);
 
 // Host: slices of a constant row-major M x K matrix in the layout TcDesc::Aslices expects.
 // S = 7 gives integer digits and the row exponents; S = 1 gives BF16 roundings.

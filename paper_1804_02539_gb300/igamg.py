@@ -255,6 +255,7 @@ class Context:
         self._check(lib().igamg_precondition(self.h, _ptr(r), _ptr(z)))
 
     PROFILE_CLASSES = ("apply", "interior_fd", "interface", "transfer", "coarse", "vector")
+    TENSOR_EXEC_CLASS = 6  # flops only: BF16 MMA work of the tensor-core FD
 
     def profile_enable(self, mask=0x3F):
         """mask: bit c times class c with CUDA events (0 disables profiling)."""
@@ -262,7 +263,7 @@ class Context:
 
     def profile_read(self):
         out = {}
-        for i, name in enumerate(self.PROFILE_CLASSES):
+        for i, name in list(enumerate(self.PROFILE_CLASSES)) + [(self.TENSOR_EXEC_CLASS, "tensor_exec")]:
             n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
             self._check(lib().igamg_profile_read(self.h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
             out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
