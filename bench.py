@@ -256,6 +256,10 @@ def run_ours(args, rank, world, local_rank):
                      "gflop_per_step": round(v["flops"] / 1e9, 4),
                      "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items() if k != "tensor_exec"}
     launches = sum(v["launches"] for v in prof.values()) * args.steps
+    # whole-solve HBM view: algorithmic bytes of every class (bands, vectors, bases) per solve
+    gb = sum(v["bytes"] for k, v in prof1.items() if k != "tensor_exec") / 1e9
+    hbm = {"algorithmic_gb_per_step": round(gb, 3), "achieved_gbs": round(gb / (ms_step * 1e-3), 1),
+           "peak": pk["hbm_gbs"], "frac": round(gb / (ms_step * 1e-3) / pk["hbm_gbs"], 4)}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "MDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -272,6 +276,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "hbm_whole_solve": hbm,
         "clocks": clocks,
         "kernel_breakdown": breakdown,
     }
@@ -519,8 +524,9 @@ def run_batch(args):
 SERVE_DESC = ("Poisson arrivals of single-rhs requests over a catalog of 110 models: the 100 2D problems of the "
               "batched family (K in {4,9,16,25,36}, p in {2..6}, m in {16,32,64,128}) drawn with 80% probability "
               "and 10 perturbed 2x2x2 cubes (p in {2,3}, m in {16,24,32,40,48}) with 20%; rhs = U(-1,1) load "
-              "vectors; FP64 PCG + V(1,1) to 1e-8; hierarchies resident under the device-memory budget "
-              "(one untimed warm-up request per model builds them)")
+              "vectors; PCG + V(1,1) to relative residual 1e-8 (mixed precision: FP64 iterative refinement); "
+              "hierarchies resident under the device-memory budget (one untimed warm-up request per model "
+              "builds them)")
 
 
 def run_serve(args):
@@ -530,6 +536,7 @@ def run_serve(args):
     from paper_1804_02539_gb300 import igamg
     probs, is3d = workloads.serving_models()
     opts = igamg.igamg_default_options()
+    opts.precision = {"fp64": igamg.IGAMG_FP64, "fp32": igamg.IGAMG_FP32, "bf16": igamg.IGAMG_BF16}[args.precision]
     srv = igamg.Server(opts, workers=args.workers, hbm_budget_bytes=int(args.budget_gb * (1 << 30)))
     ids = [srv.add_model(p) for p in probs]
     rng = np.random.default_rng(5)
@@ -578,8 +585,11 @@ def run_serve(args):
     best = max(lines, key=lambda l: l["mdof_per_s"])
     out = {"metric": METRIC, "value": best["mdof_per_s"], "unit": "MDOF/s", "n_gpus": 1,
            "steps": len(args.rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32 (f64 refinement)", "bf16": "bf16 bands, f32 (f64 refinement)"}[args.precision],
+           "data": "synthetic",
            "config": {"workload": "serve_110_models", "description": SERVE_DESC, "workers": args.workers,
+                      "precision": args.precision,
                       "budget_gb": args.budget_gb, "warmup_s": round(t_warm, 1), "models": len(probs),
                       "resident": st["resident"], "setups": st["setups"], "evictions": st["evictions"],
                       "l2": "inputs larger than L2 (resident hierarchies of GBs)"},
@@ -653,7 +663,7 @@ def main():
     ap.add_argument("--workers", type=int, default=16, help="host worker threads of the batch")
     ap.add_argument("--micro", choices=["fd"], help="micro-benchmark of one kernel class instead of the solve")
     ap.add_argument("--serve", action="store_true", help="the served workload (Poisson arrivals)")
-    ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 200.0, 2000.0])
+    ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 200.0, 500.0, 2000.0])
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=96.0)
     ap.add_argument("--no-autotune", action="store_true")
