@@ -226,6 +226,7 @@ def run_ours(args, rank, world, local_rank):
             e2e_s = (time.perf_counter() - t0) / args.steps
         setup_ms = res.t_setup_ms
         assemble_ms = res.t_assemble_ms
+        dev_bytes = ctx.device_bytes()
     ms_step = ms_total / args.steps
     value = N * world / (ms_step * 1e-3) / 1e6
     # dominant kernel class (from the breakdown pass) and its roofline, timed in the timed region
@@ -271,6 +272,7 @@ def run_ours(args, rank, world, local_rank):
                    "precision": args.precision, "rel_err_vs_fp64_solution": err_vs_fp64,
                    "relres": relres, "tol": TOL, "l2": "inputs larger than L2 (operator bands 0.94 GB)",
                    "parallelism": f"replicas x{world}", "setup_ms": round(setup_ms, 1),
+                   "device_gb": round(dev_bytes / 1e9, 3),
                    "assemble_ms": round(assemble_ms, 1)},
         "e2e": {"value": None if e2e_s != e2e_s else round(N * world / e2e_s / 1e6, 4), "unit": "MDOF/s",
                 "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N},
@@ -491,7 +493,8 @@ def run_batch(args):
         "config": {"workload": "batch512_2d_rect", "description": BATCH_DESC, "problems": len(probs),
                    "dofs_total": Ntot, "dofs_min": min(Ns), "dofs_max": max(Ns), "workers": min(args.workers or 16, len(probs)),
                    "iters_min": min(r.iters for r in res), "iters_max": max(r.iters for r in res),
-                   "setup_s": round(t_setup, 1), "l2": "inputs larger than L2 (vectors of 5.3e7 dofs)"},
+                   "setup_s": round(t_setup, 1), "l2": "inputs larger than L2 (vectors of 5.3e7 dofs)",
+                   "device_gb": round(sum(c.device_bytes() for c in B.contexts) / 1e9, 3)},
         "e2e": {"value": None if e2e is None else round(Ntot / e2e / 1e6, 4), "unit": "MDOF/s",
                 "h2d_bytes_per_step": 8 * Ntot, "d2h_bytes_per_step": 8 * Ntot},
         "gpu_launches": int(sum(v["launches"] for v in prof.values()) * args.steps),
@@ -592,6 +595,7 @@ def run_serve(args):
                       "precision": args.precision,
                       "budget_gb": args.budget_gb, "warmup_s": round(t_warm, 1), "models": len(probs),
                       "resident": st["resident"], "setups": st["setups"], "evictions": st["evictions"],
+                      "device_gb": round(st["device_bytes"] / 1e9, 3),
                       "l2": "inputs larger than L2 (resident hierarchies of GBs)"},
            "serving": lines}
     print(json.dumps(out), flush=True)

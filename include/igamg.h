@@ -126,6 +126,9 @@ igamg_status igamg_setup(const igamg_problem* problem, const igamg_options* opt,
 /* Number of active (non-Dirichlet) dofs N_l of level l (-1 = finest). */
 igamg_status igamg_num_dofs(const igamg_ctx* ctx, int level, int64_t* n);
 
+/* Device memory the context holds (hierarchy, work vectors, graphs excluded), in bytes. */
+igamg_status igamg_device_bytes(const igamg_ctx* ctx, int64_t* bytes);
+
 /* Total number of patch-local basis functions sum_k prod_j n_kj at level l. */
 igamg_status igamg_num_local(const igamg_ctx* ctx, int level, int64_t* n);
 

@@ -1860,6 +1860,12 @@ igamg_status igamg_num_dofs(const igamg_ctx* c, int level, int64_t* n) {
   return IGAMG_OK;
 }
 
+igamg_status igamg_device_bytes(const igamg_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return IGAMG_ERR_ARG;
+  *bytes = int64_t(c->mem.bytes());
+  return IGAMG_OK;
+}
+
 igamg_status igamg_num_local(const igamg_ctx* c, int level, int64_t* n) {
   if (!c || !n) return IGAMG_ERR_ARG;
   int NL = int(c->lv.size());

@@ -63,15 +63,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
-  uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t ta, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                : "r"(ta));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+// Waits for the thread's outstanding TMEM loads; the registers are operands so that no use
+// of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
 }
 
 // Exponent e of |x| (x = m 2^(e-52), m < 2^53) and 53-bit integer mantissa.
@@ -236,19 +239,23 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int ksteps = min(TBK, d.K - kb * TBK + 15) / 16;
-      const __nv_bfloat16* a = As + st * ASZ;
-      const __nv_bfloat16* b = Bs + st * BSZ;
+      const bool two = d.K - kb * TBK > 16;  // second 16-wide K step of this block present
+      const uint64_t a0 = smem_desc(sptr(As + st * ASZ)), b0 = smem_desc(sptr(Bs + st * BSZ));
+#pragma unroll
       for (int s = 1; s <= S; ++s)
+#pragma unroll
         for (int t = 1; t + s <= (S == 1 ? 2 : S + 1); ++t) {
           const uint32_t acc_col = S == 1 ? 0 : uint32_t(s + t - 2) * TBN;
-          for (int kk = 0; kk < ksteps; ++kk) {
-            uint64_t da = smem_desc(sptr(a + (s - 1) * TBM * TBK) + kk * 256);
-            uint64_t db = smem_desc(sptr(b + (t - 1) * TBN * TBK) + kk * 256);
+#pragma unroll
+          for (int kk = 0; kk < TBK / 16; ++kk) {
+            if (kk > 0 && !two) continue;
+            // descriptors differ from the stage's by the operand offsets (address field, 16 B units)
+            const uint64_t da = a0 + uint64_t(((s - 1) * TBM * TBK * 2) >> 4) + uint64_t(kk * 16);
+            const uint64_t db = b0 + uint64_t(((t - 1) * TBN * TBK * 2) >> 4) + uint64_t(kk * 16);
             // the first contribution to accumulator s + t (pair (1, q-1), first K step)
             // overwrites it
-            const bool first = kb == 0 && kk == 0 && s == 1;
-            mma_bf16(tmem + acc_col, da, db, idesc, first ? 0u : 1u);
+            const uint32_t accum = (kb > 0 || kk > 0 || s > 1) ? 1u : 0u;
+            mma_bf16(tmem + acc_col, da, db, idesc, accum);
           }
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sptr(mbar + st)));
@@ -277,54 +284,72 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     const int gi = i0 + quarter * 32 + lane;
     int sig = 0;
     if (S > 1 && gi < d.M) sig = d.Aexp[gi];
-    for (int c0 = colgrp * 16; c0 < colgrp * 16 + 16; c0 += 16) {
-      double acc[16];
-      if constexpr (S == 1) {
-        float v[16];
-        tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + c0, v);
+    const int c0 = colgrp * 16;
+    const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0);
+    double acc[16];
+    if constexpr (S == 1) {
+      uint32_t r[16];
+      tmem_ld16_issue(trow, r);
+      tmem_ld_wait(r);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = v[q];
-      } else {
-        // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
-        // units of 2^-49; |sum| < 2^58.  One int64 -> FP64 conversion, then the power-of-two
-        // scale 2^{sigma + tau - 49} is added to the exponent bits.
-        long long iacc[16];
+      for (int q = 0; q < 16; ++q) acc[q] = __uint_as_float(r[q]);
+    } else {
+      // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
+      // units of 2^-49; |sum| < 2^58.  One int64 -> FP64 conversion, then the power-of-two
+      // scale 2^{sigma + tau - 49} is added to the exponent bits.  The TMEM load of the next
+      // diagonal is in flight while one is converted.
+      long long iacc[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) iacc[q] = 0;
-        for (int dg = 0; dg < NACC; ++dg) {
-          float v[16];
-          tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(dg) * TBN + c0, v);
-          const int qd = dg + 2;
+      for (int q = 0; q < 16; ++q) iacc[q] = 0;
+      uint32_t r[2][16];
+      tmem_ld16_issue(trow, r[0]);
+      tmem_ld_wait(r[0]);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            long long iv = __float2int_rn(v[q]);  // exact: |D_q| < 2^24
-            iacc[q] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
-          }
-        }
+      for (int dg = 0; dg < NACC; ++dg) {
+        if (dg + 1 < NACC) tmem_ld16_issue(trow + uint32_t(dg + 1) * TBN, r[(dg + 1) & 1]);
+        const int qd = dg + 2;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          double x = __ll2double_rn(iacc[q]);
-          int sh = sig + tauS[c0 + q] - 49;
-          long long b = __double_as_longlong(x);
-          if (x != 0.0) {
-            int eb = int((b >> 52) & 0x7FF) + sh;
-            x = (eb > 0 && eb < 2047) ? __longlong_as_double(b + ((long long)sh << 52)) : ldexp(x, sh);
-          }
-          acc[q] = x;
+          long long iv = __float2int_rn(__uint_as_float(r[dg & 1][q]));  // exact: |D_q| < 2^24
+          iacc[q] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
+        }
+        if (dg + 1 < NACC) tmem_ld_wait(r[(dg + 1) & 1]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        double x = __ll2double_rn(iacc[q]);
+        int sh = sig + tauS[c0 + q] - 49;
+        long long b = __double_as_longlong(x);
+        if (x != 0.0) {
+          int eb = int((b >> 52) & 0x7FF) + sh;
+          x = (eb > 0 && eb < 2047) ? __longlong_as_double(b + ((long long)sh << 52)) : ldexp(x, sh);
+        }
+        acc[q] = x;
+      }
+    }
+    if (gi < d.M) {
+      // epilogue operands first (16 loads in flight), then the stores
+      double e[16];
+      const bool needs = epi == EPI_MUL || epi == EPI_ADD;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int gj = j0 + c0 + q;
+        e[q] = 0.0;
+        if (needs && gj < d.N) {
+          if (epi == EPI_MUL) e[q] = double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
+          else e[q] = double(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
         }
       }
-      if (gi >= d.M) continue;
-#pragma unroll 4
+#pragma unroll
       for (int q = 0; q < 16; ++q) {
-        int gj = j0 + c0 + q;
+        const int gj = j0 + c0 + q;
         if (gj >= d.N) continue;
-        double v = acc[q];
-        int64_t o = d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj;
-        TC* cp = d.C + o;
+        const double v = acc[q];
+        TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
         switch (epi) {
-          case EPI_MUL: *cp = TC(v * double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj])); break;
+          case EPI_MUL: *cp = TC(v * e[q]); break;
           case EPI_ASSIGN: *cp = TC(double(alpha) * v); break;
-          case EPI_ADD: *cp = TC(fma(double(alpha), v, double(*cp))); break;
+          case EPI_ADD: *cp = TC(fma(double(alpha), v, e[q])); break;
           default: *cp = TC(v);
         }
       }

@@ -60,6 +60,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_setup": ([C.POINTER(igamg_problem), C.POINTER(igamg_options), P, C.POINTER(P)], C.c_int),
         "igamg_num_dofs": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
         "igamg_num_local": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
+        "igamg_device_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
         "igamg_dof_map": ([P, C.c_int, C.POINTER(C.c_int64)], C.c_int),
         "igamg_rhs_from_coefs": ([P, P, P], C.c_int),
         "igamg_greville_points": ([P, C.c_int, P], C.c_int),
@@ -204,6 +205,11 @@ class Context:
     def num_dofs(self, level=-1) -> int:
         n = C.c_int64()
         self._check(lib().igamg_num_dofs(self.h, level, C.byref(n)))
+        return n.value
+
+    def device_bytes(self) -> int:
+        n = C.c_int64()
+        self._check(lib().igamg_device_bytes(self.h, C.byref(n)))
         return n.value
 
     def num_local(self, level=-1) -> int:
