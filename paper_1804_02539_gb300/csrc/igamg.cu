@@ -109,7 +109,8 @@ struct Num {
   KronDevT<T>* kd = nullptr;   // rectangle patches: Kronecker-sum operator per patch
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
-  TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // 2D interiors on the tensor cores
+  TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // interiors on the tensor cores (2D: 4
+  TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
   bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
   T* cX = nullptr;                                  // compact 3D interior tensor
@@ -125,6 +126,7 @@ struct Level {
   std::vector<PatchDev> pd_h;
   PatchDev* pd = nullptr;
   int max_n[3] = {1, 1, 1}, max_p = 1;
+  int uniform_p = 0;  // the degree shared by every patch and direction, else 0
   int64_t* l2g = nullptr;
   int64_t *g2t_ptr = nullptr, *g2t = nullptr;
   double* band = nullptr;  // FP64 band coefficients (none when kron)
@@ -695,6 +697,9 @@ void build_levels(igamg_ctx* c) {
       L.apply_flops += 2.0 * double(nn) * nb;
       L.band_bytes += 8.0 * double(nn) * nb;
     }
+    L.uniform_p = L.max_p;
+    for (int q = 0; q < K * d; ++q)
+      if (c->pd.p[q] != L.max_p) L.uniform_p = 0;
     L.pd = c->mem.upload(L.pd_h, s);
     L.l2g = c->mem.upload(T.l2g, s);
     L.g2t_ptr = c->mem.upload(T.g2t_ptr, s);
@@ -761,6 +766,31 @@ void build_levels(igamg_ctx* c) {
 
     // ---------------- patch-interior smoother
     std::map<std::string, double*> dinv_cache;
+    // digit slices of an FD basis (or its transpose) for the tensor-core contractions,
+    // uploaded once per (basis, orientation)
+    struct Sl { const __nv_bfloat16* a; const int* e; int nkb; };
+    std::map<std::pair<const Smoother1D*, int>, Sl> sl;
+    auto slices = [&](const Smoother1D* S, int tr) -> Sl {
+      auto key = std::make_pair(S, tr);
+      if (!sl.count(key)) {
+        int n = S->len;
+        std::vector<double> A(size_t(n) * n);
+        for (int i = 0; i < n; ++i)
+          for (int k = 0; k < n; ++k) A[size_t(i) * n + k] = tr ? S->U[size_t(k) * n + i] : S->U[size_t(i) * n + k];
+        std::vector<uint16_t> sv;
+        std::vector<int> ev;
+        slice_constant(A, n, n, 7, sv, ev);
+        const __nv_bfloat16* da = reinterpret_cast<const __nv_bfloat16*>(c->mem.upload(sv, s));
+        if (c->opt.precision == IGAMG_BF16) {
+          std::vector<uint16_t> s1;
+          std::vector<int> e1;
+          slice_constant(A, n, n, 1, s1, e1);
+          c->tc_bf16_twin[da] = c->mem.upload(s1, s);
+        }
+        sl[key] = Sl{da, c->mem.upload(ev, s), tc_kblocks(n)};
+      }
+      return sl[key];
+    };
     if (d == 2) {
       int64_t fd_total = 0;
       std::vector<GemmDesc> s0F, s0R, s1, s2, s3;
@@ -813,29 +843,6 @@ void build_levels(igamg_ctx* c) {
       const bool want_tc = c->opt.fd_engine == 2 ? min_len >= 1 : c->opt.fd_engine == 0 && min_len >= kTcMinLen;
       if (want_tc) {
         // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
-        struct Sl { const __nv_bfloat16* a; const int* e; int nkb; };
-        std::map<std::pair<const Smoother1D*, int>, Sl> sl;  // (basis, transposed?) -> slices
-        auto slices = [&](const Smoother1D* S, int tr) -> Sl {
-          auto key = std::make_pair(S, tr);
-          if (!sl.count(key)) {
-            int n = S->len;
-            std::vector<double> A(size_t(n) * n);
-            for (int i = 0; i < n; ++i)
-              for (int k = 0; k < n; ++k) A[size_t(i) * n + k] = tr ? S->U[size_t(k) * n + i] : S->U[size_t(i) * n + k];
-            std::vector<uint16_t> sv;
-            std::vector<int> ev;
-            slice_constant(A, n, n, 7, sv, ev);
-            const __nv_bfloat16* da = reinterpret_cast<const __nv_bfloat16*>(c->mem.upload(sv, s));
-            if (c->opt.precision == IGAMG_BF16) {
-              std::vector<uint16_t> s1;
-              std::vector<int> e1;
-              slice_constant(A, n, n, 1, s1, e1);
-              c->tc_bf16_twin[da] = c->mem.upload(s1, s);
-            }
-            sl[key] = Sl{da, c->mem.upload(ev, s), tc_kblocks(n)};
-          }
-          return sl[key];
-        };
         std::vector<TcDesc<double, double>> t0F, t0R, t1, t2, t3;
         size_t q = 0;
         for (const Interior& in : T.interiors) {
@@ -936,6 +943,40 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.m0b, b0);
       set_gemm(c, L.n64.m1b, b1);
       set_gemm(c, L.n64.m2b, b2);
+      int min_len = 1 << 30;
+      for (const Pend& pe : pend) min_len = std::min(min_len, std::min(pe.n0, std::min(pe.n1, pe.n2)));
+      const bool want_tc =
+          !pend.empty() && (c->opt.fd_engine == 2 ? true : c->opt.fd_engine == 0 && min_len >= kTcMinLen);
+      if (want_tc) {
+        // tensor cores: each stage contracts the leading mode and rotates it to the back,
+        // C(i1, i2, j0) = sum_i0 U(i0, j0) X(i0, i1, i2), an n x n^2 product stored
+        // transposed; three stages restore the order (j0, j1, j2), where Dinv is applied.
+        std::vector<TcDesc<double, double>> tf[3], tb[3];
+        for (const Pend& pe : pend) {
+          const int n[3] = {pe.n0, pe.n1, pe.n2};
+          const int64_t vol = int64_t(pe.n0) * pe.n1 * pe.n2;
+          double *X = L.n64.cX + pe.base, *B1 = cB1 + pe.base, *B2 = cB2 + pe.base;
+          double* fin[3] = {X, B1, B2};
+          double* fout[3] = {B1, B2, B1};
+          double* bin[3] = {B1, B2, B1};
+          double* bout[3] = {B2, B1, X};
+          for (int j = 0; j < 3; ++j) {
+            const int m = n[j], rest = int(vol / m);
+            const Sl at = slices(pe.S[j], 1), a = slices(pe.S[j], 0);
+            const double* E = j == 2 ? pe.Dinv : nullptr;
+            tf[j].push_back(TcDesc<double, double>{at.a, at.e, at.nkb, fin[j], rest, 0, fout[j], m, 1, E, m, m, rest, m});
+            tb[j].push_back(TcDesc<double, double>{a.a, a.e, a.nkb, bin[j], rest, 0, bout[j], m, 1, nullptr, 0, m, rest, m});
+          }
+        }
+        set_tc(c, L.n64.tc0F, tf[0]);
+        set_tc(c, L.n64.tc1, tf[1]);
+        set_tc(c, L.n64.tc2, tf[2]);
+        set_tc(c, L.n64.tc3, tb[0]);
+        set_tc(c, L.n64.tc4, tb[1]);
+        set_tc(c, L.n64.tc5, tb[2]);
+        L.tc_ok = true;
+        L.n64.use_tc = c->opt.fd_engine == 2 || min_len >= kTcMinLenStatic;
+      }
     }
 
     // ---------------- interface pieces: vertices; edges and faces grouped by signature
@@ -1231,7 +1272,8 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
         CK((launch_band_apply_2d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p,
                                                          band, u, f, r)));
       else
-        CK((launch_band_apply_3d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r)));
+        CK((launch_band_apply_3d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r,
+                                                         L.uniform_p)));
     }
     return;
   }
@@ -1239,7 +1281,7 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
   if (c->pd.dim == 2)
     CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r)));
   else
-    CK((launch_band_apply_3d<T, T>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r)));
+    CK((launch_band_apply_3d<T, T>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r, L.uniform_p)));
 }
 
 // u (=|+=) tau L^{-1} v for a distributed v (F or R of the level): patch interiors by
@@ -1268,12 +1310,21 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
       ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
       CK(launch_box_copy<T>(c->stream, L.boxes, L.nbox, L.max_box, v, N.cX, 1, T(1), 0));
     }
-    run_gemm(c, N.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, N.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, N.m2f, false, false, EPI_MUL, 1.0, CLS_FD);
-    run_gemm(c, N.m0b, false, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, N.m1b, false, false, EPI_STORE, 1.0, CLS_FD);
-    run_gemm(c, N.m2b, false, true, EPI_STORE, 1.0, CLS_FD);
+    if (N.use_tc) {
+      run_tc(c, N.tc0F, EPI_STORE, 1.0);
+      run_tc(c, N.tc1, EPI_STORE, 1.0);
+      run_tc(c, N.tc2, EPI_MUL, 1.0);
+      run_tc(c, N.tc3, EPI_STORE, 1.0);
+      run_tc(c, N.tc4, EPI_STORE, 1.0);
+      run_tc(c, N.tc5, EPI_STORE, 1.0);
+    } else {
+      run_gemm(c, N.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
+      run_gemm(c, N.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
+      run_gemm(c, N.m2f, false, false, EPI_MUL, 1.0, CLS_FD);
+      run_gemm(c, N.m0b, false, false, EPI_STORE, 1.0, CLS_FD);
+      run_gemm(c, N.m1b, false, false, EPI_STORE, 1.0, CLS_FD);
+      run_gemm(c, N.m2b, false, true, EPI_STORE, 1.0, CLS_FD);
+    }
     ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
     CK(launch_box_copy<T>(c->stream, L.boxes, L.nbox, L.max_box, N.cX, N.U, 0, T(tau), add ? 1 : 0));
   }
@@ -1750,6 +1801,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
         set_tc(c, out, v);
       };
       tr_tc(A.tc0F, B.tc0F); tr_tc(A.tc0R, B.tc0R); tr_tc(A.tc1, B.tc1); tr_tc(A.tc2, B.tc2); tr_tc(A.tc3, B.tc3);
+      tr_tc(A.tc4, B.tc4); tr_tc(A.tc5, B.tc5);
       B.use_tc = true;
     }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);

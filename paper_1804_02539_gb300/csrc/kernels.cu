@@ -876,7 +876,9 @@ namespace {
 constexpr int BX3 = 32, BY3 = 4, BZ3 = 2;
 }
 
-template <class TV, class TB>
+// P > 0: every patch of the launch has degree P in all directions (the tap loops are
+// unrolled, so a thread has a plane of (2P+1)^2 band loads in flight); P = 0: any degrees.
+template <class TV, class TB, int P>
 __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDev* __restrict__ pds,
                                                                    const TB* __restrict__ band,
                                                                    const TV* __restrict__ u,
@@ -885,7 +887,8 @@ __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDe
   extern __shared__ __align__(16) unsigned char smraw[];
   TV* su = reinterpret_cast<TV*>(smraw);
   const PatchDev pd = pds[blockIdx.z];
-  const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2], p0 = pd.p[0], p1 = pd.p[1], p2 = pd.p[2];
+  const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2];
+  const int p0 = P ? P : pd.p[0], p1 = P ? P : pd.p[1], p2 = P ? P : pd.p[2];
   const int i0b = (blockIdx.y / tiles1) * BZ3, i1b = (blockIdx.y % tiles1) * BY3, i2b = blockIdx.x * BX3;
   if (i0b >= n0 || i1b >= n1 || i2b >= n2) return;
   const int H0 = BZ3 + 2 * p0, H1 = BY3 + 2 * p1, H2 = BX3 + 2 * p2;
@@ -902,35 +905,59 @@ __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDe
   if (i0 >= n0 || i1 >= n1 || i2 >= n2) return;
   const int64_t nn = int64_t(n0) * n1 * n2, node = (int64_t(i0) * n1 + i1) * n2 + i2;
   const TB* bp = band + pd.band_off + node;
-  const int w1 = 2 * p1 + 1, w2 = 2 * p2 + 1;
   TV acc = 0;
-  int t = 0;
-  for (int t0 = 0; t0 <= 2 * p0; ++t0)
-    for (int t1 = 0; t1 < w1; ++t1) {
-      const TV* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
-      for (int t2 = 0; t2 < w2; ++t2, ++t) acc = fma(band_val<TV, TB>(bp + int64_t(t) * nn), srow[t2], acc);
+  if constexpr (P > 0) {
+    constexpr int W = 2 * P + 1;
+#pragma unroll 1
+    for (int t0 = 0; t0 < W; ++t0) {
+      const TB* bq = bp + int64_t(t0 * W * W) * nn;
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1) {
+        const TV* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
+#pragma unroll
+        for (int t2 = 0; t2 < W; ++t2) acc = fma(band_val<TV, TB>(bq + int64_t(t1 * W + t2) * nn), srow[t2], acc);
+      }
     }
+  } else {
+    const int w1 = 2 * p1 + 1, w2 = 2 * p2 + 1;
+    int t = 0;
+    for (int t0 = 0; t0 <= 2 * p0; ++t0)
+      for (int t1 = 0; t1 < w1; ++t1) {
+        const TV* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
+        for (int t2 = 0; t2 < w2; ++t2, ++t) acc = fma(band_val<TV, TB>(bp + int64_t(t) * nn), srow[t2], acc);
+      }
+  }
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
+}
+
+template <class TV, class TB, int P>
+static cudaError_t launch_apply_3d_p(cudaStream_t s, dim3 grid, size_t sm, const PatchDev* pd_dev, const TB* band,
+                                     const TV* u, const TV* f, TV* y, int t1) {
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_band_apply_3d<TV, TB, P>), sm);
+  if (e != cudaSuccess) return e;
+  k_band_apply_3d<TV, TB, P><<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
+  return cudaGetLastError();
 }
 
 template <class TV, class TB>
 cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
-                                 const TB* band, const TV* u, const TV* f, TV* y) {
+                                 const TB* band, const TV* u, const TV* f, TV* y, int uniform_p) {
   int t1 = (max_n[1] + BY3 - 1) / BY3, t0 = (max_n[0] + BZ3 - 1) / BZ3;
   dim3 grid((max_n[2] + BX3 - 1) / BX3, t0 * t1, K);
   size_t sm = sizeof(TV) * (BZ3 + 2 * max_p) * (BY3 + 2 * max_p) * (BX3 + 2 * max_p);
-  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_band_apply_3d<TV, TB>), sm);
-  if (e != cudaSuccess) return e;
-  k_band_apply_3d<TV, TB><<<grid, dim3(BX3, BY3, BZ3), sm, s>>>(pd_dev, band, u, f, y, t1);
-  return cudaGetLastError();
-}
-template cudaError_t launch_band_apply_3d<double, double>(cudaStream_t, const PatchDev*, int, const int*, int,
-                                                          const double*, const double*, const double*, double*);
+  switch (uniform_p) {
+    case 2: return launch_apply_3d_p<TV, TB, 2>(s, grid, sm, pd_dev, band, u, f, y, t1);
+    case 3: return launch_apply_3d_p<TV, TB, 3>(s, grid, sm, pd_dev, band, u, f, y, t1);
+    case 4: return launch_apply_3d_p<TV, TB, 4>(s, grid, sm, pd_dev, band, u, f, y, t1);
+    default: return launch_apply_3d_p<TV, TB, 0>(s, grid, sm, pd_dev, band, u, f, y, t1);
+  }
+}template cudaError_t launch_band_apply_3d<double, double>(cudaStream_t, const PatchDev*, int, const int*, int,
+                                                          const double*, const double*, const double*, double*, int);
 template cudaError_t launch_band_apply_3d<float, float>(cudaStream_t, const PatchDev*, int, const int*, int,
-                                                        const float*, const float*, const float*, float*);
+                                                        const float*, const float*, const float*, float*, int);
 template cudaError_t launch_band_apply_3d<float, __nv_bfloat16>(cudaStream_t, const PatchDev*, int, const int*, int,
                                                                 const __nv_bfloat16*, const float*, const float*,
-                                                                float*);
+                                                                float*, int);
 
 // ---------------------------------------------------------------- 1D transfer along one direction
 

@@ -76,9 +76,11 @@ cudaError_t launch_kron_apply_2d(cudaStream_t s, const KronDevT<T>* kd, int K, i
                                  const unsigned char* active, const T* u, const T* f, T* y);
 size_t kron_apply_smem(int elem_size, int max_p);
 
+// uniform_p: the common degree of every patch and direction (selects an unrolled kernel
+// for 2, 3, 4), or 0.
 template <class TV, class TB>
 cudaError_t launch_band_apply_3d(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int max_p,
-                                 const TB* band, const TV* u, const TV* f, TV* y);
+                                 const TB* band, const TV* u, const TV* f, TV* y, int uniform_p = 0);
 
 template <class T>
 cudaError_t launch_gemm(cudaStream_t s, const GemmDescT<T>* d_desc, int batch, int maxM, int maxN,

@@ -267,7 +267,7 @@ def test_greville_points():
 
 
 @pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "single_patch_p2_m64",
-                                  "grid2x2_p1_m8"])
+                                  "grid2x2_p1_m8", "cube_p3_m8", "cube_p2_m12_coarse3", "fichera_p2_m4"])
 def test_fd_engines_agree(name):
     """Tensor-core FD forced on every level (FP64-accurate digit slices; ragged sizes from
     1 to 66, far from the 128 x 64 tile) against the FP64-FMA FD, and the autotuned default
