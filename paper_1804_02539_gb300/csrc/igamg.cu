@@ -111,6 +111,7 @@ struct Num {
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
   TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // interiors on the tensor cores (2D: 4
   TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
+  TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
   bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
   T* cX = nullptr;                                  // compact 3D interior tensor
@@ -418,10 +419,10 @@ void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
 }
 
 template <class T>
-void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha) {
+void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha, int cls = CLS_FD) {
   if (!ts.batch) return;
-  if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
-  ProfScope ps(c, CLS_FD, ts.flops, 0.0);
+  if (c->prof && cls == CLS_FD) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
+  ProfScope ps(c, cls, ts.flops, 0.0);
   if constexpr (std::is_same<T, double>::value)
     CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err)));
   else
@@ -993,6 +994,8 @@ void build_levels(igamg_ctx* c) {
     std::vector<int64_t> ptr{0}, idx;
     std::vector<double> vsc;
     std::vector<GemmDesc> eA, eB, q0, q1, q2, q3;
+    std::vector<TcDesc<double, double>> tqd[4];
+    bool face_tc = true;
     int64_t face_tot = 0;
     for (auto& kv : groups) {
       int kind = std::get<0>(kv.first);
@@ -1034,12 +1037,32 @@ void build_levels(igamg_ctx* c) {
           for (int b = 0; b < len1; ++b)
             Dv[size_t(a) * len1 + b] = 1.0 / ((h / p) * (S0->mu[a] + S1->mu[b] + double(p) * p / (h * h)));
         double* Dinv = reg_const(c, c->mem.upload(Dv, s), Dv.size());
+        const bool tcf = c->opt.fd_engine == 2 || (c->opt.fd_engine == 0 && std::min(len0, len1) >= kTcMinLen);
+        face_tc = face_tc && tcf;
+        Sl a0t{}, a1t{}, a0{}, a1{};
+        if (tcf) {
+          a0t = slices(S0, 1);
+          a1t = slices(S1, 1);
+          a0 = slices(S0, 0);
+          a1 = slices(S1, 0);
+        }
         for (int f = 0; f < np; ++f) {
           int64_t off = gbase + int64_t(f) * len0 * len1, tb = face_tot + int64_t(f) * len0 * len1;
           q0.push_back(GemmDesc{S0->dU, (double*)(intptr_t)off, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
           q1.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)tb, Dinv, len1, len1, len1, len1, len0, len1, len1});
           q2.push_back(GemmDesc{S0->dU, (double*)(intptr_t)tb, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
           q3.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)off, nullptr, len1, len1, len1, 0, len0, len1, len1});
+          if (tcf) {  // the interior formulation on the face block (offsets resolved below)
+            using TD = TcDesc<double, double>;
+            tqd[0].push_back(TD{a0t.a, a0t.e, a0t.nkb, (double*)(intptr_t)off, len1, 0, (double*)(intptr_t)tb, len1, 0,
+                                nullptr, 0, len0, len1, len0});
+            tqd[1].push_back(TD{a1t.a, a1t.e, a1t.nkb, (double*)(intptr_t)tb, len1, 1, (double*)(intptr_t)tb, len1, 1,
+                                Dinv, len1, len1, len0, len1});
+            tqd[2].push_back(TD{a0.a, a0.e, a0.nkb, (double*)(intptr_t)tb, len1, 0, (double*)(intptr_t)tb, len1, 0,
+                                nullptr, 0, len0, len1, len0});
+            tqd[3].push_back(TD{a1.a, a1.e, a1.nkb, (double*)(intptr_t)tb, len1, 1, (double*)(intptr_t)off, len1, 1,
+                                nullptr, 0, len1, len0, len1});
+          }
         }
         face_tot += int64_t(np) * len0 * len1;
       }
@@ -1066,6 +1089,17 @@ void build_levels(igamg_ctx* c) {
     set_gemm(c, L.n64.face1, q1);
     set_gemm(c, L.n64.face2, q2);
     set_gemm(c, L.n64.face3, q3);
+    if (face_tc && !q0.empty()) {
+      // stage 0 reads G, 1 reads T writes Y, 2 reads Y writes T, 3 reads T writes Z
+      for (auto& t : tqd[0]) { t.B = L.n64.G + (intptr_t)t.B; t.C = fT + (intptr_t)t.C; }
+      for (auto& t : tqd[1]) { t.B = fT + (intptr_t)t.B; t.C = fY + (intptr_t)t.C; }
+      for (auto& t : tqd[2]) { t.B = fY + (intptr_t)t.B; t.C = fT + (intptr_t)t.C; }
+      for (auto& t : tqd[3]) { t.B = fT + (intptr_t)t.B; t.C = L.n64.Z + (intptr_t)t.C; }
+      set_tc(c, L.n64.tq0, tqd[0]);
+      set_tc(c, L.n64.tq1, tqd[1]);
+      set_tc(c, L.n64.tq2, tqd[2]);
+      set_tc(c, L.n64.tq3, tqd[3]);
+    }
 
     // ---------------- transfers from level l-1 (one 1D pass per direction)
     const Level& C = c->lv[l - 1];
@@ -1335,10 +1369,17 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   }
   run_gemm(c, N.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
   run_gemm(c, N.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
-  run_gemm(c, N.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
-  run_gemm(c, N.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  if (N.use_tc && N.tq0.batch) {  // faces follow the interiors' engine
+    run_tc(c, N.tq0, EPI_STORE, 1.0, CLS_IFACE);
+    run_tc(c, N.tq1, EPI_MUL, 1.0, CLS_IFACE);
+    run_tc(c, N.tq2, EPI_STORE, 1.0, CLS_IFACE);
+    run_tc(c, N.tq3, EPI_STORE, 1.0, CLS_IFACE);
+  } else {
+    run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
+    run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
+    run_gemm(c, N.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
+    run_gemm(c, N.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  }
   {
     ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 3.0 * sizeof(T) * L.n_if);
     CK(launch_iface_scatter<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, N.Z, N.G, N.vscale, T(tau), add ? 1 : 0, N.U));
@@ -1802,6 +1843,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       };
       tr_tc(A.tc0F, B.tc0F); tr_tc(A.tc0R, B.tc0R); tr_tc(A.tc1, B.tc1); tr_tc(A.tc2, B.tc2); tr_tc(A.tc3, B.tc3);
       tr_tc(A.tc4, B.tc4); tr_tc(A.tc5, B.tc5);
+      tr_tc(A.tq0, B.tq0); tr_tc(A.tq1, B.tq1); tr_tc(A.tq2, B.tq2); tr_tc(A.tq3, B.tq3);
       B.use_tc = true;
     }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
