@@ -1304,7 +1304,7 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
       const __nv_bfloat16* band = static_cast<const __nv_bfloat16*>(N.band);
       if (c->pd.dim == 2)
         CK((launch_band_apply_2d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p,
-                                                         band, u, f, r)));
+                                                         band, u, f, r, L.uniform_p)));
       else
         CK((launch_band_apply_3d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r,
                                                          L.uniform_p)));
@@ -1313,7 +1313,8 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
   }
   const T* band = krylov ? N.band_op : static_cast<const T*>(N.band);
   if (c->pd.dim == 2)
-    CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r)));
+    CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r,
+                                   L.uniform_p)));
   else
     CK((launch_band_apply_3d<T, T>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r, L.uniform_p)));
 }

@@ -67,7 +67,9 @@ __device__ __forceinline__ TV band_val(const TB* p) {
   else return TV(to_acc<TB>(*p));
 }
 
-template <class TV, class TB>
+// P > 0: every patch has degree P (taps unrolled; one partial sum per tap row, so a thread
+// runs 2P+1 independent FMA chains); P = 0: any degrees.
+template <class TV, class TB, int P>
 __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __restrict__ pds,
                                                            const TB* __restrict__ band,
                                                            const TV* __restrict__ u,
@@ -76,7 +78,8 @@ __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __res
   extern __shared__ __align__(16) unsigned char smraw[];
   TV* su = reinterpret_cast<TV*>(smraw);
   const PatchDev pd = pds[blockIdx.z];
-  const int n0 = pd.n[0], n1 = pd.n[1], p0 = pd.p[0], p1 = pd.p[1];
+  const int n0 = pd.n[0], n1 = pd.n[1];
+  const int p0 = P ? P : pd.p[0], p1 = P ? P : pd.p[1];
   const int i0b = blockIdx.y * AY, i1b = blockIdx.x * AX;
   if (i0b >= n0 || i1b >= n1) return;
   const int H0 = AY + 2 * p0, H1 = AX + 2 * p1;
@@ -91,32 +94,61 @@ __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __res
   if (i0 >= n0 || i1 >= n1) return;
   const int64_t nn = int64_t(n0) * n1, node = int64_t(i0) * n1 + i1;
   const TB* bp = band + pd.band_off + node;
-  const int w1 = 2 * p1 + 1;
   TV acc = 0;
-  for (int t0 = 0; t0 <= 2 * p0; ++t0) {
-    const TV* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
-    const TB* brow = bp + int64_t(t0 * w1) * nn;
-    for (int t1 = 0; t1 < w1; ++t1) acc = fma(band_val<TV, TB>(brow + int64_t(t1) * nn), srow[t1], acc);
+  if constexpr (P > 0) {
+    constexpr int W = 2 * P + 1;
+    TV part[W];
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) {
+      const TV* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
+      part[t0] = TV(0);
+#pragma unroll
+      for (int t1 = 0; t1 < W; ++t1)
+        part[t0] = fma(band_val<TV, TB>(bp + int64_t(t0 * W + t1) * nn), srow[t1], part[t0]);
+    }
+#pragma unroll
+    for (int t0 = 0; t0 < W; ++t0) acc += part[t0];
+  } else {
+    const int w1 = 2 * p1 + 1;
+    for (int t0 = 0; t0 <= 2 * p0; ++t0) {
+      const TV* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
+      const TB* brow = bp + int64_t(t0 * w1) * nn;
+      for (int t1 = 0; t1 < w1; ++t1) acc = fma(band_val<TV, TB>(brow + int64_t(t1) * nn), srow[t1], acc);
+    }
   }
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
+}
+
+template <class TV, class TB, int P>
+static void launch_apply_2d_p(cudaStream_t s, dim3 grid, size_t sm, const PatchDev* pd_dev, const TB* band,
+                              const TV* u, const TV* f, TV* y) {
+  k_band_apply_2d<TV, TB, P><<<grid, dim3(AX, AY), sm, s>>>(pd_dev, band, u, f, y);
 }
 
 template <class TV, class TB>
 cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0,
                                  int max_n1, int max_p, const TB* band, const TV* u,
-                                 const TV* f, TV* y) {
+                                 const TV* f, TV* y, int uniform_p) {
   dim3 grid((max_n1 + AX - 1) / AX, (max_n0 + AY - 1) / AY, K);
   size_t sm = sizeof(TV) * (AY + 2 * max_p) * (AX + 2 * max_p);
-  k_band_apply_2d<TV, TB><<<grid, dim3(AX, AY), sm, s>>>(pd_dev, band, u, f, y);
+  switch (uniform_p) {
+    case 1: launch_apply_2d_p<TV, TB, 1>(s, grid, sm, pd_dev, band, u, f, y); break;
+    case 2: launch_apply_2d_p<TV, TB, 2>(s, grid, sm, pd_dev, band, u, f, y); break;
+    case 3: launch_apply_2d_p<TV, TB, 3>(s, grid, sm, pd_dev, band, u, f, y); break;
+    case 4: launch_apply_2d_p<TV, TB, 4>(s, grid, sm, pd_dev, band, u, f, y); break;
+    case 5: launch_apply_2d_p<TV, TB, 5>(s, grid, sm, pd_dev, band, u, f, y); break;
+    case 6: launch_apply_2d_p<TV, TB, 6>(s, grid, sm, pd_dev, band, u, f, y); break;
+    default: launch_apply_2d_p<TV, TB, 0>(s, grid, sm, pd_dev, band, u, f, y);
+  }
   return cudaGetLastError();
 }
 template cudaError_t launch_band_apply_2d<double, double>(cudaStream_t, const PatchDev*, int, int, int, int,
-                                                          const double*, const double*, const double*, double*);
+                                                          const double*, const double*, const double*, double*, int);
 template cudaError_t launch_band_apply_2d<float, float>(cudaStream_t, const PatchDev*, int, int, int, int,
-                                                        const float*, const float*, const float*, float*);
+                                                        const float*, const float*, const float*, float*, int);
 template cudaError_t launch_band_apply_2d<float, __nv_bfloat16>(cudaStream_t, const PatchDev*, int, int, int, int,
                                                                 const __nv_bfloat16*, const float*, const float*,
-                                                                float*);
+                                                                float*, int);
 
 // ---------------------------------------------------------------- Kronecker-sum apply
 
@@ -877,7 +909,8 @@ constexpr int BX3 = 32, BY3 = 4, BZ3 = 2;
 }
 
 // P > 0: every patch of the launch has degree P in all directions (the tap loops are
-// unrolled, so a thread has a plane of (2P+1)^2 band loads in flight); P = 0: any degrees.
+// unrolled, so a thread has a plane of (2P+1)^2 band loads in flight; one FMA chain, which
+// measured faster than per-row partial sums here); P = 0: any degrees.
 template <class TV, class TB, int P>
 __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDev* __restrict__ pds,
                                                                    const TB* __restrict__ band,

@@ -55,9 +55,10 @@ size_t elem_asm_smem(int D, int p, bool mass);
 
 // y = f - A u per tile (residual) or y = A u when f == NULL (apply).  TV vector type,
 // TB band storage type: (double, double), (float, float), (float, __nv_bfloat16).
+// uniform_p: the common degree of every patch (selects an unrolled kernel for 1..6), or 0.
 template <class TV, class TB>
 cudaError_t launch_band_apply_2d(cudaStream_t s, const PatchDev* pd_dev, int K, int max_n0, int max_n1, int max_p,
-                                 const TB* band, const TV* u, const TV* f, TV* y);
+                                 const TB* band, const TV* u, const TV* f, TV* y, int uniform_p = 0);
 // Rectangle patch with constant metric C = |det J| J^{-1} J^{-T} = diag(c0, c1): the stiffness
 // is the Kronecker sum A = c0 K_0 (x) M_1 + c1 M_0 (x) K_1 of the 1D stiffness K_j and mass
 // M_j on (0,1).  The 1D matrices are stored row-banded, [n_j][2p_j+1] with entry (i, t) =

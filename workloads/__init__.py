@@ -223,4 +223,5 @@ CONFIGS = {
     "grid2d_K16_p4_m256": lambda: perturbed_grid_2d(4, 4, 256, 9, 2),
     "grid2d_K16_p4_m128": lambda: perturbed_grid_2d(4, 4, 128, 8, 2),
     "cube3d_K8_p3_m64": lambda: perturbed_cube_3d(2, 3, 64, 7, 3),
+    "cube3d_K8_p3_m32": lambda: perturbed_cube_3d(2, 3, 32, 6, 3),
 }
