@@ -86,8 +86,10 @@ typedef struct {
   int fd_engine;       /* patch-interior FD contractions: 0 = automatic (the autotuner's
                           choice per level, else tensor cores on 2D interiors of >= 96
                           dofs per direction), 1 = FMA pipes in the working precision,
-                          2 = tensor cores on every 2D level (FP64: exact BF16 digit
-                          slices with integer recombination; BF16 variant: BF16 operands) */
+                          2 = tensor cores on every level (FP64: exact BF16 digit slices
+                          with integer recombination; BF16 variant: BF16 operands),
+                          3 = one block per 2D interior of <= 32 x 32 (all four
+                          contractions in shared memory), FMA GEMMs elsewhere          */
   int graphs;          /* 1: each PCG iteration after the first is captured once as a
                           CUDA graph and replayed (same launches, same order, same
                           results); 0: launched one by one                            */
@@ -96,9 +98,10 @@ typedef struct {
                           rectangle (no band storage), stored bands otherwise;
                           1 = stored bands always                                     */
   int autotune;        /* with fd_engine 0: time the FD candidates of every level once at
-                          setup (FMA tile factors 1, 2, 4; tensor cores on 2D interiors of
-                          >= 32) and keep the fastest; choices are cached per interior
-                          shape for the life of the process                           */
+                          setup (FMA tile factors 1, 2, 4; tensor cores on interiors of
+                          >= 32; the one-block kernel on 2D interiors of <= 32) and keep
+                          the fastest; choices are cached per interior shape for the life
+                          of the process                                               */
 } igamg_options;
 
 typedef struct {

@@ -112,6 +112,10 @@ struct Num {
   TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // interiors on the tensor cores (2D: 4
   TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
   TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
+  FdSmallT<T>* fsmall = nullptr;                    // small 2D interiors, one block each
+  int nfsmall = 0;
+  bool use_fused = false;
+  double fsmall_flops = 0;
   bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
   T* cX = nullptr;                                  // compact 3D interior tensor
@@ -136,6 +140,8 @@ struct Level {
   std::vector<KronDevT<double>> kd_h;
   int64_t band_doubles = 0;  // size of a band array in this layout (mass bands of the rhs)
   bool tc_ok = false;        // tensor-core FD stage sets built (the FD engine may switch)
+  bool fused_ok = false;     // every 2D interior fits the one-block FD kernel
+  std::vector<FdSmallT<double>> fs_h;
   Num<double> n64;
   Num<float> n32;
   // 3D interior boxes (shared by all precisions)
@@ -837,6 +843,32 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.st1, s1);
       set_gemm(c, L.n64.st2, s2);
       set_gemm(c, L.n64.st3, s3);
+      // one-block FD for small interiors (a candidate of the autotuner)
+      {
+        bool ok = !s0F.empty();
+        std::vector<FdSmallT<double>> fs;
+        size_t q = 0;
+        double fl = 0;
+        for (const Interior& in : T.interiors) {
+          if (in.len[0] == 0 || in.len[1] == 0) continue;
+          const PatchDev& P = L.pd_h[in.k];
+          const int n0 = in.len[0], n1 = in.len[1];
+          ok = ok && n0 <= kFdSmallMax && n1 <= kFdSmallMax;
+          const int64_t xoff = P.off + int64_t(in.lo[0]) * P.n[1] + in.lo[1];
+          fs.push_back(FdSmallT<double>{s0F[q].A, s1[q].B, s1[q].E, L.n64.F + xoff, L.n64.R + xoff, L.n64.U + xoff, n0,
+                                        n1, P.n[1]});
+          fl += 4.0 * n0 * n1 * double(n0 + n1);
+          ++q;
+        }
+        if (ok) {
+          L.fused_ok = true;
+          L.fs_h = fs;
+          L.n64.fsmall = c->mem.upload(fs, s);
+          L.n64.nfsmall = int(fs.size());
+          L.n64.fsmall_flops = fl;
+          L.n64.use_fused = c->opt.fd_engine == 3;
+        }
+      }
       int min_len = 1 << 30;
       for (const Interior& in : T.interiors)
         if (in.len[0] && in.len[1]) min_len = std::min(min_len, std::min(in.len[0], in.len[1]));
@@ -1330,7 +1362,10 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   const T* v = from_F ? N.F : N.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
-  if (c->pd.dim == 2 && N.use_tc) {
+  if (c->pd.dim == 2 && N.use_fused) {
+    ProfScope ps(c, CLS_FD, N.fsmall_flops, 0.0);
+    CK(launch_fd_small<T>(c->stream, N.fsmall, N.nfsmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
+  } else if (c->pd.dim == 2 && N.use_tc) {
     run_tc(c, from_F ? N.tc0F : N.tc0R, EPI_STORE, 1.0);
     run_tc(c, N.tc1, EPI_MUL, 1.0);
     run_tc(c, N.tc2, EPI_STORE, 1.0);
@@ -1700,7 +1735,7 @@ std::mutex g_tune_mu;
 std::map<std::string, FdChoice> g_tune_cache;
 
 std::string fd_signature(const igamg_ctx* c, const Level& L) {
-  std::string k = "d" + std::to_string(c->pd.dim) + (L.tc_ok ? "t" : "f");
+  std::string k = "d" + std::to_string(c->pd.dim) + (L.tc_ok ? "t" : "f") + (L.fused_ok ? "s" : "");
   for (const Interior& in : L.topo.interiors) {
     k += "|" + std::to_string(c->pd.p[in.k * c->pd.dim]);
     for (int j = 0; j < c->pd.dim; ++j) k += "x" + std::to_string(in.len[j]);
@@ -1711,8 +1746,9 @@ std::string fd_signature(const igamg_ctx* c, const Level& L) {
 void apply_choice(Level& L, const FdChoice& ch) {
   Num<double>& N = L.n64;
   N.use_tc = ch.tc && L.tc_ok;
+  N.use_fused = ch.R < 0 && L.fused_ok;  // R = -1: the one-block kernel
   for (GemmSet* g : {&N.st0F, &N.st0R, &N.st1, &N.st2, &N.st3, &N.m0f, &N.m1f, &N.m2f, &N.m0b, &N.m1b, &N.m2b})
-    g->R = ch.R;
+    g->R = ch.R > 0 ? ch.R : 0;
 }
 
 void autotune(igamg_ctx* c) {
@@ -1734,6 +1770,7 @@ void autotune(igamg_ctx* c) {
     }
     std::vector<FdChoice> cand{{false, 1}, {false, 2}, {false, 4}};
     if (L.tc_ok) cand.push_back({true, 0});
+    if (L.fused_ok) cand.push_back({false, -1});
     FdChoice best{false, 0};
     float best_ms = 1e30f;
     for (const FdChoice& ch : cand) {
@@ -1751,8 +1788,8 @@ void autotune(igamg_ctx* c) {
       }
     }
     if (c->verbose)
-      std::fprintf(stderr, "[igamg] autotune level %d: %s R=%d (%.3f ms per smoother)\n", l, best.tc ? "tensor" : "fma",
-                   best.R, best_ms / 3);
+      std::fprintf(stderr, "[igamg] autotune level %d: %s R=%d (%.3f ms per smoother)\n", l,
+                   best.tc ? "tensor" : best.R < 0 ? "one-block" : "fma", best.R, best_ms / 3);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     // a context that tuned the same signature concurrently may have stored first: use
     // the stored choice, so that every context of the process agrees
@@ -1847,6 +1884,15 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       tr_tc(A.tq0, B.tq0); tr_tc(A.tq1, B.tq1); tr_tc(A.tq2, B.tq2); tr_tc(A.tq3, B.tq3);
       B.use_tc = true;
     }
+    if (L.fused_ok) {
+      std::vector<FdSmallT<float>> fs;
+      for (const auto& f : L.fs_h)
+        fs.push_back(FdSmallT<float>{tr(f.U0), tr(f.U1), tr(f.Dinv), tr(f.vF), tr(f.vR), tr(f.u), f.n0, f.n1, f.ld});
+      B.fsmall = c->mem.upload(fs, s);
+      B.nfsmall = int(fs.size());
+      B.fsmall_flops = A.fsmall_flops;
+      B.use_fused = A.use_fused;
+    }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
     tr_set(A.st3, B.st3);
     tr_set(A.m0f, B.m0f); tr_set(A.m1f, B.m1f); tr_set(A.m2f, B.m2f);
@@ -1922,6 +1968,7 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
   double t0 = now_ms();
   try {
     if (c->opt.precision < IGAMG_FP64 || c->opt.precision > IGAMG_BF16) throw Fail{IGAMG_ERR_ARG, "bad precision"};
+    if (c->opt.fd_engine < 0 || c->opt.fd_engine > 3) throw Fail{IGAMG_ERR_ARG, "bad fd_engine"};
     if (c->opt.precision != IGAMG_FP64 && !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1))
       throw Fail{IGAMG_ERR_ARG, "inner_tol must be in (0, 1)"};
     if (c->opt.nu < 1 || c->opt.mu < 1 || c->opt.mu > 2 || c->opt.max_iter < 0 || !(c->opt.tau > 0))

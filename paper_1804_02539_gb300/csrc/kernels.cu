@@ -241,6 +241,58 @@ template cudaError_t launch_kron_apply_2d<double>(cudaStream_t, const KronDevT<d
 template cudaError_t launch_kron_apply_2d<float>(cudaStream_t, const KronDevT<float>*, int, int, int, int,
                                                  const unsigned char*, const float*, const float*, float*);
 
+// ---------------------------------------------------------------- small-interior FD
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fd_small(const FdSmallT<T>* __restrict__ ds, int from_F, T tau, int add) {
+  constexpr int M = kFdSmallMax;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  const FdSmallT<T> d = ds[blockIdx.x];
+  const int n0 = d.n0, n1 = d.n1, tid = threadIdx.x;
+  const T* v = from_F ? d.vF : d.vR;
+  for (int i = tid; i < n0 * n0; i += 256) U0[i] = d.U0[i];
+  for (int i = tid; i < n1 * n1; i += 256) U1[i] = d.U1[i];
+  for (int i = tid; i < n0 * n1; i += 256) X[i] = v[int64_t(i / n1) * d.ld + i % n1];
+  __syncthreads();
+  for (int i = tid; i < n0 * n1; i += 256) {  // T = U0^T X
+    const int a = i / n1, b = i % n1;
+    T acc = 0;
+    for (int k = 0; k < n0; ++k) acc = fma(U0[k * n0 + a], X[k * n1 + b], acc);
+    Tm[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < n0 * n1; i += 256) {  // Y = (T U1) .* Dinv
+    const int a = i / n1, b = i % n1;
+    T acc = 0;
+    for (int k = 0; k < n1; ++k) acc = fma(Tm[a * n1 + k], U1[k * n1 + b], acc);
+    X[i] = acc * d.Dinv[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < n0 * n1; i += 256) {  // S = U0 Y
+    const int a = i / n1, b = i % n1;
+    T acc = 0;
+    for (int k = 0; k < n0; ++k) acc = fma(U0[a * n0 + k], X[k * n1 + b], acc);
+    Tm[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < n0 * n1; i += 256) {  // u (=|+=) tau S U1^T
+    const int a = i / n1, b = i % n1;
+    T acc = 0;
+    for (int k = 0; k < n1; ++k) acc = fma(Tm[a * n1 + k], U1[b * n1 + k], acc);
+    T* up = d.u + int64_t(a) * d.ld + b;
+    *up = add ? fma(tau, acc, *up) : tau * acc;
+  }
+}
+
+template <class T>
+cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int from_F, T tau, int add) {
+  if (count <= 0) return cudaSuccess;
+  k_fd_small<T><<<count, 256, 0, s>>>(d, from_F, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fd_small<double>(cudaStream_t, const FdSmallT<double>*, int, int, double, int);
+template cudaError_t launch_fd_small<float>(cudaStream_t, const FdSmallT<float>*, int, int, float, int);
+
 // ---------------------------------------------------------------- batched GEMM
 
 // C = op(A) op(B) with an epilogue, one output tile of 8R x 8R per block of 64 threads;

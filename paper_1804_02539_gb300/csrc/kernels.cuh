@@ -117,6 +117,19 @@ cudaError_t launch_transfer_1d(cudaStream_t s, const XferT<T>* xs, int npatch, i
                                int add, const int64_t* mask);
 
 // Interior box of a tile <-> compact tensor.
+// Whole patch-interior smoother of one small 2D interior in one block (the four FD
+// contractions in shared memory): u (=|+=) tau U0 ((U0^T v U1) .* Dinv) U1^T.
+constexpr int kFdSmallMax = 32;
+template <class T>
+struct FdSmallT {
+  const T *U0, *U1, *Dinv;  // n0 x n0, n1 x n1 (columns = FD basis), n0 x n1
+  const T *vF, *vR;         // the interior block in the F and R tiles (row stride ld)
+  T* u;                     // the interior block in the U tile
+  int n0, n1, ld;
+};
+template <class T>
+cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int from_F, T tau, int add);
+
 struct BoxDev {
   int64_t tile_off, compact_off;
   int n[3], lo[3], len[3];

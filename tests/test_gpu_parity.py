@@ -275,7 +275,7 @@ def test_fd_engines_agree(name):
     from paper_1804_02539_gb300 import igamg
     pr, H, ctx, perms = setup_case(name)
     ctxs = {}
-    for eng in (1, 2):
+    for eng in (1, 2, 3):
         o = igamg.igamg_default_options()
         o.fd_engine = eng
         ctxs[eng] = igamg.Context(pr, o)
@@ -283,12 +283,13 @@ def test_fd_engines_agree(name):
     for l in range(1, pr.num_levels):
         r = dev(rng.normal(size=H.levels[l].space.N))
         z = {}
-        for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2])):
+        for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2]), ("block", ctxs[3])):
             z[k] = torch.empty_like(r)
             c.smooth(l, r, z[k])
         # digit truncation at 2^-49 of each column maximum
         assert rel(host(z["tc"]), host(z["fma"])) < 1e-12, l
         assert rel(host(z["auto"]), host(z["fma"])) < 1e-12, l
+        assert rel(host(z["block"]), host(z["fma"])) < 1e-13, l
     r = dev(rng.normal(size=H.levels[-1].space.N))
     xs, its = {}, {}
     for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2])):
