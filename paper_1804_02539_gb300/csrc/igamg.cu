@@ -113,6 +113,8 @@ struct Num {
   TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
   TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
   FdSmallT<T>* fsmall = nullptr;                    // small 2D interiors, one block each
+  SmoothSmallT<T> ssmall{};                         // + edges and vertices in the same launch
+  double ssmall_flops = 0;
   int nfsmall = 0;
   bool use_fused = false;
   double fsmall_flops = 0;
@@ -141,6 +143,8 @@ struct Level {
   int64_t band_doubles = 0;  // size of a band array in this layout (mass bands of the rhs)
   bool tc_ok = false;        // tensor-core FD stage sets built (the FD engine may switch)
   bool fused_ok = false;     // every 2D interior fits the one-block FD kernel
+  bool small_ok = false;     // ... and every edge too: the whole smoother is one launch
+  std::vector<EdgeSmallT<double>> es_h;
   std::vector<FdSmallT<double>> fs_h;
   Num<double> n64;
   Num<float> n32;
@@ -1028,6 +1032,9 @@ void build_levels(igamg_ctx* c) {
     std::vector<GemmDesc> eA, eB, q0, q1, q2, q3;
     std::vector<TcDesc<double, double>> tqd[4];
     bool face_tc = true;
+    std::vector<EdgeSmallT<double>> es;
+    bool edges_small = d == 2;
+    int64_t vtx_beg = 0, vtx_end = 0;
     int64_t face_tot = 0;
     for (auto& kv : groups) {
       int kind = std::get<0>(kv.first);
@@ -1051,12 +1058,18 @@ void build_levels(igamg_ctx* c) {
       int m = std::get<1>(kv.first), p = std::get<2>(kv.first);
       int len0 = std::get<3>(kv.first), len1 = std::get<4>(kv.first);
       int np = int(kv.second.size());
+      if (kind == PIECE_VERTEX) {
+        vtx_beg = gbase;
+        vtx_end = int64_t(vsc.size());
+      }
       if (kind == PIECE_EDGE && len0 > 0) {
         Mat U;
         std::vector<double> dv;
         edge_fd(d, m, p, U, dv);
         double* dU = reg_const(c, c->mem.upload(U, s), U.size());
         double* ddv = reg_const(c, c->mem.upload(dv, s), dv.size());
+        edges_small = edges_small && len0 <= kFdSmallMax;
+        for (int j = 0; j < np; ++j) es.push_back(EdgeSmallT<double>{dU, ddv, gbase + int64_t(j) * len0, len0});
         eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len0, len0, len0, 0, np, len0, len0});
         eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len0, len0, len0, 0, np, len0, len0});
       } else if (kind == PIECE_FACE && len0 > 0 && len1 > 0) {
@@ -1117,6 +1130,26 @@ void build_levels(igamg_ctx* c) {
     for (auto& g : q3) { g.A = fT + (intptr_t)g.A; g.C = L.n64.Z + (intptr_t)g.C; }
     set_gemm(c, L.n64.edgeA, eA);
     set_gemm(c, L.n64.edgeB, eB);
+    if (L.fused_ok && edges_small) {  // the whole smoother of this level in one launch
+      L.small_ok = true;
+      L.es_h = es;
+      SmoothSmallT<double>& q = L.n64.ssmall;
+      q.fd = L.n64.fsmall;
+      q.nfd = L.n64.nfsmall;
+      q.edges = es.empty() ? nullptr : c->mem.upload(es, s);
+      q.nedges = int(es.size());
+      q.ptr = L.if_ptr;
+      q.idx = L.if_idx;
+      q.vscale = L.n64.vscale;
+      q.vbeg = vtx_beg;
+      q.vend = vtx_end;
+      q.vF = L.n64.F;
+      q.vR = L.n64.R;
+      q.u = L.n64.U;
+      double fl = L.n64.fsmall_flops;
+      for (const auto& e : es) fl += 4.0 * e.len * double(e.len);
+      L.n64.ssmall_flops = fl;
+    }
     set_gemm(c, L.n64.face0, q0);
     set_gemm(c, L.n64.face1, q1);
     set_gemm(c, L.n64.face2, q2);
@@ -1362,6 +1395,11 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
   const T* v = from_F ? N.F : N.R;
   double tau = c->opt.tau;
   int epi = add ? EPI_ADD : EPI_ASSIGN;
+  if (c->pd.dim == 2 && N.use_fused && L.small_ok) {  // interiors, edges and vertices: one launch
+    ProfScope ps(c, CLS_FD, N.ssmall_flops, 0.0);
+    CK(launch_smooth_small<T>(c->stream, N.ssmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
+    return;
+  }
   if (c->pd.dim == 2 && N.use_fused) {
     ProfScope ps(c, CLS_FD, N.fsmall_flops, 0.0);
     CK(launch_fd_small<T>(c->stream, N.fsmall, N.nfsmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
@@ -1892,6 +1930,25 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       B.nfsmall = int(fs.size());
       B.fsmall_flops = A.fsmall_flops;
       B.use_fused = A.use_fused;
+      if (L.small_ok) {
+        std::vector<EdgeSmallT<float>> es;
+        for (const auto& e : L.es_h) es.push_back(EdgeSmallT<float>{tr(e.U), tr(e.dinv), e.first, e.len});
+        SmoothSmallT<float>& q = B.ssmall;
+        const SmoothSmallT<double>& a = A.ssmall;
+        q.fd = B.fsmall;
+        q.nfd = B.nfsmall;
+        q.edges = es.empty() ? nullptr : c->mem.upload(es, s);
+        q.nedges = int(es.size());
+        q.ptr = a.ptr;
+        q.idx = a.idx;
+        q.vscale = tr(a.vscale);
+        q.vbeg = a.vbeg;
+        q.vend = a.vend;
+        q.vF = tr(a.vF);
+        q.vR = tr(a.vR);
+        q.u = tr(a.u);
+        B.ssmall_flops = A.ssmall_flops;
+      }
     }
     tr_set(A.st0F, B.st0F); tr_set(A.st0R, B.st0R); tr_set(A.st1, B.st1); tr_set(A.st2, B.st2);
     tr_set(A.st3, B.st3);

@@ -244,10 +244,7 @@ template cudaError_t launch_kron_apply_2d<float>(cudaStream_t, const KronDevT<fl
 // ---------------------------------------------------------------- small-interior FD
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fd_small(const FdSmallT<T>* __restrict__ ds, int from_F, T tau, int add) {
-  constexpr int M = kFdSmallMax;
-  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
-  const FdSmallT<T> d = ds[blockIdx.x];
+__device__ void fd_small_block(const FdSmallT<T>& d, int from_F, T tau, int add, T* U0, T* U1, T* X, T* Tm) {
   const int n0 = d.n0, n1 = d.n1, tid = threadIdx.x;
   const T* v = from_F ? d.vF : d.vR;
   for (int i = tid; i < n0 * n0; i += 256) U0[i] = d.U0[i];
@@ -283,6 +280,73 @@ __global__ void __launch_bounds__(256) k_fd_small(const FdSmallT<T>* __restrict_
     *up = add ? fma(tau, acc, *up) : tau * acc;
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fd_small(const FdSmallT<T>* __restrict__ ds, int from_F, T tau, int add) {
+  constexpr int M = kFdSmallMax;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  fd_small_block<T>(ds[blockIdx.x], from_F, tau, add, U0, U1, X, Tm);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_small(const SmoothSmallT<T> p, int from_F, T tau, int add) {
+  constexpr int M = kFdSmallMax;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const T* v = from_F ? p.vF : p.vR;
+  if (b < p.nfd) {
+    fd_small_block<T>(p.fd[b], from_F, tau, add, U0, U1, X, Tm);
+    return;
+  }
+  if (b < p.nfd + p.nedges) {
+    const EdgeSmallT<T> e = p.edges[b - p.nfd];
+    const int n = e.len;
+    for (int i = tid; i < n * n; i += 256) U0[i] = e.U[i];
+    for (int i = tid; i < n; i += 256) {  // gather: the sum of the copies
+      const int64_t g = e.first + i;
+      T acc = 0;
+      for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) acc += v[p.idx[c]];
+      X[i] = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += 256) {  // y = (g^T U) .* dinv
+      T acc = 0;
+      for (int i = 0; i < n; ++i) acc = fma(X[i], U0[i * n + j], acc);
+      Tm[j] = acc * e.dinv[j];
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += 256) {  // z = U y, scattered to every copy
+      T acc = 0;
+      for (int j = 0; j < n; ++j) acc = fma(Tm[j], U0[i * n + j], acc);
+      const T val = tau * acc;
+      const int64_t g = e.first + i;
+      for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) {
+        T* up = p.u + p.idx[c];
+        *up = add ? *up + val : val;
+      }
+    }
+    return;
+  }
+  for (int64_t g = p.vbeg + tid; g < p.vend; g += 256) {  // vertices
+    T acc = 0;
+    for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) acc += v[p.idx[c]];
+    const T val = tau * (p.vscale[g] * acc);
+    for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) {
+      T* up = p.u + p.idx[c];
+      *up = add ? *up + val : val;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_smooth_small(cudaStream_t s, const SmoothSmallT<T>& p, int from_F, T tau, int add) {
+  const int blocks = p.nfd + p.nedges + (p.vend > p.vbeg ? 1 : 0);
+  if (blocks <= 0) return cudaSuccess;
+  k_smooth_small<T><<<blocks, 256, 0, s>>>(p, from_F, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_smooth_small<double>(cudaStream_t, const SmoothSmallT<double>&, int, double, int);
+template cudaError_t launch_smooth_small<float>(cudaStream_t, const SmoothSmallT<float>&, int, float, int);
 
 template <class T>
 cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int from_F, T tau, int add) {

@@ -130,6 +130,32 @@ struct FdSmallT {
 template <class T>
 cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int from_F, T tau, int add);
 
+// The whole smoother of a small 2D level in one launch: blocks [0, nfd) are the interiors
+// (as launch_fd_small), the next nedges blocks one edge each (gather of the copies, 1D FD
+// with U (len x len, columns = basis) and dinv, scatter tau z to the copies), the last
+// block the vertices (z = vscale * gathered value).  Interface nodes are numbered as the
+// gather/scatter CSR (ptr, idx) numbers them.
+template <class T>
+struct EdgeSmallT {
+  const T *U, *dinv;
+  int64_t first;  // first interface node of the edge
+  int len;
+};
+template <class T>
+struct SmoothSmallT {
+  const FdSmallT<T>* fd;
+  int nfd;
+  const EdgeSmallT<T>* edges;
+  int nedges;
+  const int64_t *ptr, *idx;
+  const T* vscale;
+  int64_t vbeg, vend;  // vertex nodes
+  const T *vF, *vR;    // level vectors (tiles)
+  T* u;
+};
+template <class T>
+cudaError_t launch_smooth_small(cudaStream_t s, const SmoothSmallT<T>& p, int from_F, T tau, int add);
+
 struct BoxDev {
   int64_t tile_off, compact_off;
   int n[3], lo[3], len[3];
