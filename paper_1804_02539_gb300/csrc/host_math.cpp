@@ -166,9 +166,10 @@ Mat prolongation_1d(int mc, int p) {
 bool cholesky(int n, Mat& A) {
   // right-looking column Cholesky; the update of the trailing rows is parallel
   for (int j = 0; j < n; ++j) {
-    double s = A[size_t(j) * n + j];
+    const double diag = A[size_t(j) * n + j];
+    double s = diag;
     for (int k = 0; k < j; ++k) s -= A[size_t(j) * n + k] * A[size_t(j) * n + k];
-    if (!(s > 0.0)) return false;
+    if (!(s > 1e-13 * diag)) return false;  // not positive definite to working accuracy
     double ljj = std::sqrt(s);
     A[size_t(j) * n + j] = ljj;
     const double* rj = &A[size_t(j) * n];

@@ -100,3 +100,18 @@ def test_batch_reports_failing_problem():
     with pytest.raises(igamg.IgamgError) as e:
         igamg.Batch([good, good, bad, good], workers=2)
     assert "problem 2" in str(e.value)
+
+
+def test_batch_of_one_and_more_workers_than_problems():
+    from paper_1804_02539_gb300 import igamg
+    pr = workloads.unit_square_quadrants(8, 2, 4)
+    b = igamg.Batch([pr], workers=8)
+    rhs = [torch.tensor(workloads.rhs_coefficients(b.contexts[0].num_dofs(), 1), device="cuda")]
+    xs = [torch.zeros_like(rhs[0])]
+    st, res, sts = b.solve(rhs, xs, 1e-8)
+    c = igamg.Context(pr)
+    x = torch.zeros_like(rhs[0])
+    c.solve(rhs[0], x, 1e-8)
+    assert st == 0 and torch.equal(x, xs[0])
+    c.free()
+    b.free()

@@ -432,3 +432,32 @@ def test_errors_are_reported():
     ctx = setup_case("square_p2_m8")[2]
     with pytest.raises(igamg.IgamgError):
         ctx.smooth(0, dev(np.zeros(9)), dev(np.zeros(9)))
+
+
+def test_degenerate_problems_are_reported():
+    """A problem without Dirichlet data is singular (constants are in the kernel): the
+    coarse factorisation fails and setup reports IGAMG_ERR_NUMERIC; bad options are
+    rejected before any device work; a one-level hierarchy is a direct solve."""
+    from paper_1804_02539_gb300 import igamg
+    pr = workloads.perturbed_grid_2d(2, 2, 8, 4, 3)
+    pr.side_bc[:] = np.where(pr.side_bc == workloads.SIDE_DIRICHLET, workloads.SIDE_NEUMANN, pr.side_bc)
+    with pytest.raises(igamg.IgamgError) as e:
+        igamg.Context(pr)
+    assert e.value.status == 6
+    pr = workloads.unit_square_quadrants(8, 2, 4)
+    for field, val in (("fd_engine", 7), ("nu", 0), ("mu", 3), ("precision", 5)):
+        o = igamg.igamg_default_options()
+        setattr(o, field, val)
+        with pytest.raises(igamg.IgamgError) as e:
+            igamg.Context(pr, o)
+        assert e.value.status == 1, field
+    one = workloads.unit_square_quadrants(2, 2, 1)        # the coarsest level only
+    H = solver.build_hierarchy(one)
+    c = igamg.Context(one)
+    b = workloads.rhs_coefficients(H.levels[-1].space.N, 4)
+    perm = permutation(H.levels[-1].space, c.dof_map())
+    x = dev(np.zeros(len(b)))
+    res, st = c.solve(dev(to_lib(perm, b)), x, 1e-10)
+    assert st == 0 and res.iters <= 2
+    assert rel(from_lib(perm, host(x)), solver.direct_solve(H.levels[-1].A, b)) < 1e-10
+    c.free()

@@ -94,3 +94,20 @@ def test_model_larger_than_budget_is_refused():
     out, stats = serve((est[0] + est[4]) // 2, [(0, 1), (4, 2), (0, 3)], workers=1)
     statuses = [info["status"] for _, _, _, info in out]
     assert statuses == [0, 4, 0]  # IGAMG_ERR_OOM for the model that never fits
+
+
+def test_bad_requests_are_rejected():
+    from paper_1804_02539_gb300 import igamg
+    srv = igamg.Server(workers=1, hbm_budget_bytes=1 << 30)
+    m, n, _ = srv.add_model(workloads.unit_square_quadrants(8, 2, 4))
+    with pytest.raises(igamg.IgamgError):
+        srv.submit(m + 1, np.zeros(n))             # unknown model
+    with pytest.raises(igamg.IgamgError):
+        srv.wait(12345)                            # unknown request
+    bad = workloads.unit_square_quadrants(6, 2, 4)  # 6 intervals cannot make 4 levels
+    with pytest.raises(igamg.IgamgError):
+        srv.add_model(bad)
+    rid, x = srv.submit(m, np.zeros(n))            # zero load: zero answer, no iterations
+    info = srv.wait(rid)
+    assert info["status"] == 0 and info["iters"] == 0 and not x.any()
+    srv.free()
