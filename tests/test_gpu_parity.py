@@ -40,6 +40,7 @@ def cases():
         "rect2x2_p2_m8_transposed": transposed_rect_grid,
         "cube_p2_m12_coarse3": lambda: workloads.perturbed_cube_3d(2, 2, 12, 3, 3),    # 3 elements per
         "grid2x2_p3_m20_coarse5": lambda: workloads.perturbed_grid_2d(2, 3, 20, 3, 5),  # coarsest direction
+        "single_patch_p4_m128": lambda: workloads.perturbed_grid_2d(1, 4, 128, 8, 3),  # interior 130 = 128 + 2
     }
 
 
@@ -267,7 +268,8 @@ def test_greville_points():
 
 
 @pytest.mark.parametrize("name", ["grid4x4_p4_m16", "grid2x2_p5_m32_ragged", "single_patch_p2_m64",
-                                  "grid2x2_p1_m8", "cube_p3_m8", "cube_p2_m12_coarse3", "fichera_p2_m4"])
+                                  "grid2x2_p1_m8", "cube_p3_m8", "cube_p2_m12_coarse3", "fichera_p2_m4",
+                                  "single_patch_p4_m128"])
 def test_fd_engines_agree(name):
     """Tensor-core FD forced on every level (FP64-accurate digit slices; ragged sizes from
     1 to 66, far from the 128 x 64 tile) against the FP64-FMA FD, and the autotuned default
