@@ -185,6 +185,8 @@ struct igamg_ctx {
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
   std::map<std::tuple<int, int>, std::pair<double*, double*>> kron_1d;  // (m, p) -> banded K, M
+  struct SliceSrc { const double* U; int n, tr; };
+  std::map<const void*, SliceSrc> slice_src;  // digit slices -> the FP64 basis they cut
   int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
   // PCG iteration body replayed as a CUDA graph (index 0 FP64, 1 FP32 inner), captured on a
   // private stream (the legacy stream cannot capture) and launched on `stream`
@@ -413,7 +415,16 @@ void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, do
 }
 
 template <class T>
-void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
+void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v0) {
+  std::vector<TcDesc<T, T>> v = v0;
+  if constexpr (std::is_same<T, double>::value)
+    for (auto& d : v) {  // the FP64 basis behind the slices, for remainder row tiles
+      auto it = c->slice_src.find(d.Aslices);
+      if (it == c->slice_src.end()) continue;
+      d.Af = it->second.U;
+      d.lda = it->second.n;
+      d.tra = it->second.tr;
+    }
   ts.h = v;
   ts.batch = int(v.size());
   ts.maxM = ts.maxN = 0;
@@ -799,6 +810,7 @@ void build_levels(igamg_ctx* c) {
           c->tc_bf16_twin[da] = c->mem.upload(s1, s);
         }
         sl[key] = Sl{da, c->mem.upload(ev, s), tc_kblocks(n)};
+        c->slice_src[da] = igamg_ctx::SliceSrc{S->dU, n, tr};
       }
       return sl[key];
     };
@@ -1913,7 +1925,8 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
           auto it = c->tc_bf16_twin.find(d.Aslices);
           if (it == c->tc_bf16_twin.end()) throw Fail{IGAMG_ERR_NUMERIC, "missing BF16 basis slices"};
           v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
-                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
+                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K,
+                                            tr(d.Af), d.lda, d.tra});
         }
         set_tc(c, out, v);
       };

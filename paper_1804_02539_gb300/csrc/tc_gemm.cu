@@ -35,6 +35,7 @@ namespace {
 constexpr int TBM = 128, TBN = 64, TBK = 32;  // K block of one pipeline stage
 constexpr int NT = 512;  // threads per CTA: 16 warps, 4 per TMEM lane quarter
 constexpr int WAIT_LIMIT = 1 << 24;
+constexpr int kLightRows = 32;  // a row tile this sparse skips the tensor cores
 
 __device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -127,6 +128,28 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
   if (i0 >= d.M || j0 >= d.N) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (d.Af && d.M - i0 <= kLightRows) {
+    // a tile of a few remainder rows: plain FMAs over K instead of 128-row MMAs
+    const int rows = d.M - i0;
+    for (int o = tid; o < rows * TBN; o += NT) {
+      const int gi = i0 + o / TBN, gj = j0 + o % TBN;
+      if (gj >= d.N) continue;
+      TC acc = TC(0);
+      for (int k = 0; k < d.K; ++k) {
+        const TC a = TC(d.tra ? d.Af[int64_t(k) * d.lda + gi] : d.Af[int64_t(gi) * d.lda + k]);
+        const TC b = TC(d.tb ? d.B[int64_t(gj) * d.ldb + k] : d.B[int64_t(k) * d.ldb + gj]);
+        acc = fma(a, b, acc);
+      }
+      TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
+      switch (epi) {
+        case EPI_MUL: *cp = acc * d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]; break;
+        case EPI_ASSIGN: *cp = alpha * acc; break;
+        case EPI_ADD: *cp = fma(alpha, acc, *cp); break;
+        default: *cp = acc;
+      }
+    }
+    return;
+  }
   const int quarter = warp & 3, colgrp = warp >> 2;  // TMEM lanes 32*quarter.., columns 16*colgrp..
   constexpr int NACC = S == 1 ? 1 : S;      // accumulators: diagonals q = 2..S+1
   constexpr uint32_t TCOLS = S == 1 ? 64 : 512;

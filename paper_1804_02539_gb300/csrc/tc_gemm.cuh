@@ -23,6 +23,10 @@ struct TcDesc {
   const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
   int lde;
   int M, N, K;
+  // the constant operand in the working precision (optional): A(i, k) = tra ? Af[k * lda + i]
+  // : Af[i * lda + k]; a 128-row tile with at most 32 valid rows is then computed with FMAs
+  const TB* Af = nullptr;
+  int lda = 0, tra = 0;
 };
 
 // S = 7: FP64-accurate digit-slice product (TB = TC = double); S = 1: BF16 product with
