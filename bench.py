@@ -642,6 +642,29 @@ def run_micro_fd(args):
     ctx.free()
 
 
+def run_micro_fp64():
+    """FP64 reference rate of this GPU: cuBLAS DGEMM (torch.matmul in float64, 8192^3),
+    best of 5 after warm-up; the denominator the FP64 roofline fractions are compared with."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    print(json.dumps({"micro": "fp64 dgemm", "n": n, "ms": round(best, 3),
+                      "tflops": round(2 * n ** 3 / (best * 1e-3) / 1e12, 4),
+                      "derived_fma_peak_tflops": round(FP64_PEAK_TFLOPS, 4)}), flush=True)
+
+
 def main():
     if "--_oracle_batch" in sys.argv:
         print(json.dumps(oracle_batch_json()))
@@ -665,7 +688,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--batch", action="store_true", help="the 512-problem batched workload")
     ap.add_argument("--workers", type=int, default=16, help="host worker threads of the batch")
-    ap.add_argument("--micro", choices=["fd"], help="micro-benchmark of one kernel class instead of the solve")
+    ap.add_argument("--micro", choices=["fd", "fp64"], help="micro-benchmark instead of the solve")
     ap.add_argument("--serve", action="store_true", help="the served workload (Poisson arrivals)")
     ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 200.0, 500.0, 2000.0])
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -673,6 +696,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fd-engine", type=int, default=0)
     args = ap.parse_args()
+    if args.micro == "fp64":
+        run_micro_fp64()
+        return
     if args.micro:
         run_micro_fd(args)
         return

@@ -35,7 +35,7 @@ namespace {
 constexpr int TBM = 128, TBN = 64, TBK = 32;  // K block of one pipeline stage
 constexpr int NT = 512;  // threads per CTA: 16 warps, 4 per TMEM lane quarter
 constexpr int WAIT_LIMIT = 1 << 24;
-constexpr int kLightRows = 32;  // a row tile this sparse skips the tensor cores
+constexpr int kLightRows = 32;  // a tile with this few valid rows or columns skips the tensor cores
 
 __device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -124,16 +124,40 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);                    // [2] MMAs of a stage done
   uint64_t* abar = mbar + 2;                                                  // [2] A bulk copy landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
-  const TcDesc<TB, TC> d = descs[blockIdx.z];
-  const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
-  if (i0 >= d.M || j0 >= d.N) return;
+  const TcDesc<TB, TC> d = descs[blockIdx.x];
+  // tile blockIdx.y of this product; the tiles that run on the tensor cores come first, so
+  // that (with the batch as the fastest grid dimension) they fill the first waves and the
+  // light tiles (few valid rows or columns, FMA path) the remainder
+  const int tiles_m = (d.M + TBM - 1) / TBM, tiles_n = (d.N + TBN - 1) / TBN;
+  int t = blockIdx.y;
+  if (t >= tiles_m * tiles_n) return;
+  int Mh = tiles_m, Nh = tiles_n;
+  if (d.Af) {
+    Mh = d.M / TBM + (d.M % TBM > kLightRows ? 1 : 0);
+    Nh = d.N / TBN + (d.N % TBN > kLightRows ? 1 : 0);
+  }
+  int mt, nt;
+  if (t < Mh * Nh) {
+    mt = t / Nh;
+    nt = t % Nh;
+  } else {  // the k-th light tile in row-major order
+    int k = t - Mh * Nh;
+    mt = 0;
+    nt = 0;
+    for (int q = 0; q < tiles_m * tiles_n; ++q) {
+      const int a = q / tiles_n, b = q % tiles_n;
+      if (a < Mh && b < Nh) continue;
+      if (k-- == 0) { mt = a; nt = b; break; }
+    }
+  }
+  const int i0 = mt * TBM, j0 = nt * TBN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (d.Af && d.M - i0 <= kLightRows) {
-    // a tile of a few remainder rows: plain FMAs over K instead of 128-row MMAs
-    const int rows = d.M - i0;
-    for (int o = tid; o < rows * TBN; o += NT) {
-      const int gi = i0 + o / TBN, gj = j0 + o % TBN;
-      if (gj >= d.N) continue;
+  const int rows = min(TBM, d.M - i0), cols = min(TBN, d.N - j0);
+  if (d.Af && (rows <= kLightRows || cols <= kLightRows)) {
+    // a tile of a few remainder rows or columns: plain FMAs over K instead of MMAs on a
+    // mostly empty 128 x 64 tile (this also keeps such tiles out of the waves of full ones)
+    for (int o = tid; o < rows * cols; o += NT) {
+      const int gi = i0 + o / cols, gj = j0 + o % cols;
       TC acc = TC(0);
       for (int k = 0; k < d.K; ++k) {
         const TC a = TC(d.tra ? d.Af[int64_t(k) * d.lda + gi] : d.Af[int64_t(gi) * d.lda + k]);
@@ -195,7 +219,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   const uint32_t tmem = *tslot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
   const int nkb = (d.K + TBK - 1) / TBK;
-  const int mt = blockIdx.y;
   // B staging: thread -> (column bn, 4 consecutive k at bk).  Bits of tid, high to low:
   // bn / 8 (3), k chunk of 8 (2), bn % 8 (3), half chunk (1).  A half-warp stores 16
   // distinct 8-byte pieces of one 128-byte core matrix per digit plane (conflict-free), and
@@ -390,7 +413,7 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
   size_t smem = 2 * size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((maxN + TBN - 1) / TBN, (maxM + TBM - 1) / TBM, batch);
+  dim3 grid(batch, ((maxN + TBN - 1) / TBN) * ((maxM + TBM - 1) / TBM));
   k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, epi, alpha, err);
   return cudaGetLastError();
 }

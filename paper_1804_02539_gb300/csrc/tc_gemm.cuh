@@ -24,7 +24,8 @@ struct TcDesc {
   int lde;
   int M, N, K;
   // the constant operand in the working precision (optional): A(i, k) = tra ? Af[k * lda + i]
-  // : Af[i * lda + k]; a 128-row tile with at most 32 valid rows is then computed with FMAs
+  // : Af[i * lda + k]; a 128 x 64 tile with at most 32 valid rows or columns is then computed
+  // with FMAs
   const TB* Af = nullptr;
   int lda = 0, tra = 0;
 };
