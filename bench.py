@@ -128,6 +128,21 @@ def sample_desc():
             f"one full PCG+V(1,1) solve to 1e-8, setup excluded, 1 thread")
 
 
+# ---------------------------------------------------------------- replicas over ranks
+
+def combine_over_ranks(ms_total, dofs, tdist=None, device="cpu"):
+    """Replicas: every rank solves its own copy.  The job time is the slowest rank's; the
+    work is the sum of the ranks' dofs.  Returns (max ms, total dofs)."""
+    if tdist is None:
+        return ms_total, dofs
+    import torch
+    t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    n = torch.tensor([dofs], dtype=torch.float64, device=device)
+    tdist.all_reduce(n, op=tdist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_ours(args, rank, world, local_rank):
@@ -209,10 +224,7 @@ def run_ours(args, rank, world, local_rank):
             ref.solve(b, xr, 1e-12)
             err_vs_fp64 = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
             ref.free()
-        if dist:
-            t = torch.tensor([ms_total], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            ms_total = float(t.item())
+        ms_total, dofs_all = combine_over_ranks(ms_total, N, tdist if dist else None, dev)
         # end to end: host vectors, H2D + D2H inside the timed region
         e2e_s = float("nan")
         if not args.no_e2e:
@@ -228,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
         assemble_ms = res.t_assemble_ms
         dev_bytes = ctx.device_bytes()
     ms_step = ms_total / args.steps
-    value = N * world / (ms_step * 1e-3) / 1e6
+    value = dofs_all / (ms_step * 1e-3) / 1e6
     # dominant kernel class (from the breakdown pass) and its roofline, timed in the timed region
     d = prof[dom]
     pk, src = peaks()
