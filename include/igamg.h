@@ -89,7 +89,9 @@ typedef struct {
                           2 = tensor cores on every level (FP64: exact BF16 digit slices
                           with integer recombination; BF16 variant: BF16 operands),
                           3 = one block per 2D interior of <= 32 x 32 (all four
-                          contractions in shared memory), FMA GEMMs elsewhere          */
+                          contractions in shared memory), FMA GEMMs elsewhere,
+                          4 = 2D interiors in two launches over blocks of 8 rows (each
+                          fusing two of the products), FMA GEMMs in 3D               */
   int graphs;          /* 1: each PCG iteration after the first is captured once as a
                           CUDA graph and replayed (same launches, same order, same
                           results); 0: launched one by one                            */
@@ -99,7 +101,8 @@ typedef struct {
                           1 = stored bands always                                     */
   int autotune;        /* with fd_engine 0: time the FD candidates of every level once at
                           setup (FMA tile factors 1, 2, 4; tensor cores on interiors of
-                          >= 32; the one-block kernel on 2D interiors of <= 32) and keep
+                          >= 32; the one-block kernel on 2D interiors of <= 32; the
+                          row-block kernel on 2D interiors) and keep
                           the fastest; choices are cached per interior shape for the life
                           of the process                                               */
 } igamg_options;

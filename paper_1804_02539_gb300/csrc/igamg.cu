@@ -114,6 +114,9 @@ struct Num {
   TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
   FdSmallT<T>* fsmall = nullptr;                    // small 2D interiors, one block each
   SmoothSmallT<T> ssmall{};                         // + edges and vertices in the same launch
+  FdRowsT<T>* frows = nullptr;                      // 2D interiors by row blocks (two launches)
+  int nfrows = 0, frows_n0 = 0, frows_n1 = 0;
+  bool use_rows = false;
   double ssmall_flops = 0;
   int nfsmall = 0;
   bool use_fused = false;
@@ -144,6 +147,7 @@ struct Level {
   bool tc_ok = false;        // tensor-core FD stage sets built (the FD engine may switch)
   bool fused_ok = false;     // every 2D interior fits the one-block FD kernel
   bool small_ok = false;     // ... and every edge too: the whole smoother is one launch
+  std::vector<FdRowsT<double>> fr_h;
   std::vector<EdgeSmallT<double>> es_h;
   std::vector<FdSmallT<double>> fs_h;
   Num<double> n64;
@@ -859,6 +863,30 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.st1, s1);
       set_gemm(c, L.n64.st2, s2);
       set_gemm(c, L.n64.st3, s3);
+      // row-block FD (a candidate of the autotuner), Y in the stage-1 scratch of each interior
+      {
+        std::vector<FdRowsT<double>> fr;
+        size_t q = 0;
+        int mx0 = 0, mx1 = 0;
+        for (const Interior& in : T.interiors) {
+          if (in.len[0] == 0 || in.len[1] == 0) continue;
+          const PatchDev& P = L.pd_h[in.k];
+          const int64_t xoff = P.off + int64_t(in.lo[0]) * P.n[1] + in.lo[1];
+          fr.push_back(FdRowsT<double>{s0F[q].A, s1[q].B, s1[q].E, L.n64.F + xoff, L.n64.R + xoff, L.n64.U + xoff,
+                                       s1[q].C, in.len[0], in.len[1], P.n[1]});
+          mx0 = std::max(mx0, in.len[0]);
+          mx1 = std::max(mx1, in.len[1]);
+          ++q;
+        }
+        if (!fr.empty()) {
+          L.fr_h = fr;
+          L.n64.frows = c->mem.upload(fr, s);
+          L.n64.nfrows = int(fr.size());
+          L.n64.frows_n0 = mx0;
+          L.n64.frows_n1 = mx1;
+          L.n64.use_rows = c->opt.fd_engine == 4;
+        }
+      }
       // one-block FD for small interiors (a candidate of the autotuner)
       {
         bool ok = !s0F.empty();
@@ -1412,7 +1440,13 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
     CK(launch_smooth_small<T>(c->stream, N.ssmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
     return;
   }
-  if (c->pd.dim == 2 && N.use_fused) {
+  if (c->pd.dim == 2 && N.use_rows) {
+    for (int pass = 1; pass <= 2; ++pass) {
+      ProfScope ps(c, CLS_FD, 2.0 * N.st1.flops, 0.0);  // two of the four products per pass
+      CK(launch_fd_rows<T>(c->stream, N.frows, N.nfrows, N.frows_n0, N.frows_n1, pass, from_F ? 1 : 0, T(tau),
+                           add ? 1 : 0));
+    }
+  } else if (c->pd.dim == 2 && N.use_fused) {
     ProfScope ps(c, CLS_FD, N.fsmall_flops, 0.0);
     CK(launch_fd_small<T>(c->stream, N.fsmall, N.nfsmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
   } else if (c->pd.dim == 2 && N.use_tc) {
@@ -1785,7 +1819,7 @@ std::mutex g_tune_mu;
 std::map<std::string, FdChoice> g_tune_cache;
 
 std::string fd_signature(const igamg_ctx* c, const Level& L) {
-  std::string k = "d" + std::to_string(c->pd.dim) + (L.tc_ok ? "t" : "f") + (L.fused_ok ? "s" : "");
+  std::string k = "d" + std::to_string(c->pd.dim) + (L.tc_ok ? "t" : "f") + (L.fused_ok ? "s" : "") + "r";
   for (const Interior& in : L.topo.interiors) {
     k += "|" + std::to_string(c->pd.p[in.k * c->pd.dim]);
     for (int j = 0; j < c->pd.dim; ++j) k += "x" + std::to_string(in.len[j]);
@@ -1796,7 +1830,8 @@ std::string fd_signature(const igamg_ctx* c, const Level& L) {
 void apply_choice(Level& L, const FdChoice& ch) {
   Num<double>& N = L.n64;
   N.use_tc = ch.tc && L.tc_ok;
-  N.use_fused = ch.R < 0 && L.fused_ok;  // R = -1: the one-block kernel
+  N.use_fused = ch.R == -1 && L.fused_ok;  // R = -1: the one-block kernel
+  N.use_rows = ch.R == -2 && N.nfrows > 0;  // R = -2: the row-block kernel
   for (GemmSet* g : {&N.st0F, &N.st0R, &N.st1, &N.st2, &N.st3, &N.m0f, &N.m1f, &N.m2f, &N.m0b, &N.m1b, &N.m2b})
     g->R = ch.R > 0 ? ch.R : 0;
 }
@@ -1821,6 +1856,7 @@ void autotune(igamg_ctx* c) {
     std::vector<FdChoice> cand{{false, 1}, {false, 2}, {false, 4}};
     if (L.tc_ok) cand.push_back({true, 0});
     if (L.fused_ok) cand.push_back({false, -1});
+    if (L.n64.nfrows && c->pd.dim == 2) cand.push_back({false, -2});
     FdChoice best{false, 0};
     float best_ms = 1e30f;
     for (const FdChoice& ch : cand) {
@@ -1839,7 +1875,8 @@ void autotune(igamg_ctx* c) {
     }
     if (c->verbose)
       std::fprintf(stderr, "[igamg] autotune level %d: %s R=%d (%.3f ms per smoother)\n", l,
-                   best.tc ? "tensor" : best.R < 0 ? "one-block" : "fma", best.R, best_ms / 3);
+                   best.tc ? "tensor" : best.R == -1 ? "one-block" : best.R == -2 ? "row-block" : "fma", best.R,
+                   best_ms / 3);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     // a context that tuned the same signature concurrently may have stored first: use
     // the stored choice, so that every context of the process agrees
@@ -1934,6 +1971,17 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       tr_tc(A.tc4, B.tc4); tr_tc(A.tc5, B.tc5);
       tr_tc(A.tq0, B.tq0); tr_tc(A.tq1, B.tq1); tr_tc(A.tq2, B.tq2); tr_tc(A.tq3, B.tq3);
       B.use_tc = true;
+    }
+    if (!L.fr_h.empty()) {
+      std::vector<FdRowsT<float>> fr;
+      for (const auto& f : L.fr_h)
+        fr.push_back(FdRowsT<float>{tr(f.U0), tr(f.U1), tr(f.Dinv), tr(f.vF), tr(f.vR), tr(f.u), tr(f.Y), f.n0, f.n1,
+                                    f.ld});
+      B.frows = c->mem.upload(fr, s);
+      B.nfrows = int(fr.size());
+      B.frows_n0 = A.frows_n0;
+      B.frows_n1 = A.frows_n1;
+      B.use_rows = A.use_rows;
     }
     if (L.fused_ok) {
       std::vector<FdSmallT<float>> fs;
@@ -2038,7 +2086,7 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
   double t0 = now_ms();
   try {
     if (c->opt.precision < IGAMG_FP64 || c->opt.precision > IGAMG_BF16) throw Fail{IGAMG_ERR_ARG, "bad precision"};
-    if (c->opt.fd_engine < 0 || c->opt.fd_engine > 3) throw Fail{IGAMG_ERR_ARG, "bad fd_engine"};
+    if (c->opt.fd_engine < 0 || c->opt.fd_engine > 4) throw Fail{IGAMG_ERR_ARG, "bad fd_engine"};
     if (c->opt.precision != IGAMG_FP64 && !(c->opt.inner_tol > 0 && c->opt.inner_tol < 1))
       throw Fail{IGAMG_ERR_ARG, "inner_tol must be in (0, 1)"};
     if (c->opt.nu < 1 || c->opt.mu < 1 || c->opt.mu > 2 || c->opt.max_iter < 0 || !(c->opt.tau > 0))

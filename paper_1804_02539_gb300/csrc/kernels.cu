@@ -357,6 +357,64 @@ cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int
 template cudaError_t launch_fd_small<double>(cudaStream_t, const FdSmallT<double>*, int, int, double, int);
 template cudaError_t launch_fd_small<float>(cudaStream_t, const FdSmallT<float>*, int, int, float, int);
 
+// ---------------------------------------------------------------- row-block FD
+
+constexpr int FR_RB = 8;  // rows per block
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fd_rows(const FdRowsT<T>* __restrict__ ds, int pass, int from_F, T tau,
+                                                 int add) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* rowsS = reinterpret_cast<T*>(smraw);  // FR_RB x n1: this block's rows of T (pass 1) or S (pass 2)
+  const FdRowsT<T> d = ds[blockIdx.y];
+  const int n0 = d.n0, n1 = d.n1, a0 = blockIdx.x * FR_RB;
+  if (a0 >= n0) return;
+  const int rb = min(FR_RB, n0 - a0), tid = threadIdx.x;
+  // first product: rows a0.. of U0^T X (pass 1) or U0 Y (pass 2), contracted over all n0 rows
+  const T* src = pass == 1 ? (from_F ? d.vF : d.vR) : d.Y;
+  const int lds = pass == 1 ? d.ld : n1;
+  for (int o = tid; o < rb * n1; o += 256) {
+    const int r = o / n1, b = o % n1, a = a0 + r;
+    T acc = 0;
+    for (int k = 0; k < n0; ++k) {
+      const T u0 = pass == 1 ? d.U0[k * n0 + a] : d.U0[a * n0 + k];
+      acc = fma(u0, src[int64_t(k) * lds + b], acc);
+    }
+    rowsS[r * n1 + b] = acc;
+  }
+  __syncthreads();
+  // second product: these rows times U1 (pass 1, then .* Dinv into Y) or U1^T (pass 2, into u)
+  for (int o = tid; o < rb * n1; o += 256) {
+    const int r = o / n1, b = o % n1, a = a0 + r;
+    T acc = 0;
+    for (int k = 0; k < n1; ++k) {
+      const T u1 = pass == 1 ? d.U1[k * n1 + b] : d.U1[b * n1 + k];
+      acc = fma(rowsS[r * n1 + k], u1, acc);
+    }
+    if (pass == 1) {
+      d.Y[a * n1 + b] = acc * d.Dinv[a * n1 + b];
+    } else {
+      T* up = d.u + int64_t(a) * d.ld + b;
+      *up = add ? fma(tau, acc, *up) : tau * acc;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_fd_rows(cudaStream_t s, const FdRowsT<T>* d, int count, int max_n0, int max_n1, int pass,
+                           int from_F, T tau, int add) {
+  if (count <= 0) return cudaSuccess;
+  const size_t sm = sizeof(T) * FR_RB * size_t(max_n1);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_fd_rows<T>), sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((max_n0 + FR_RB - 1) / FR_RB, count);
+  k_fd_rows<T><<<grid, 256, sm, s>>>(d, pass, from_F, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fd_rows<double>(cudaStream_t, const FdRowsT<double>*, int, int, int, int, int, double,
+                                            int);
+template cudaError_t launch_fd_rows<float>(cudaStream_t, const FdRowsT<float>*, int, int, int, int, int, float, int);
+
 // ---------------------------------------------------------------- batched GEMM
 
 // C = op(A) op(B) with an epilogue, one output tile of 8R x 8R per block of 64 threads;

@@ -130,6 +130,21 @@ struct FdSmallT {
 template <class T>
 cudaError_t launch_fd_small(cudaStream_t s, const FdSmallT<T>* d, int count, int from_F, T tau, int add);
 
+// Patch-interior FD of a 2D level in two launches over blocks of RB rows: pass 1 computes
+// rows of T = U0^T X and then of Y = (T U1) .* Dinv; pass 2 rows of S = U0 Y and then of
+// u (=|+=) tau S U1^T.  Y is a scratch n0 x n1 block per interior.
+template <class T>
+struct FdRowsT {
+  const T *U0, *U1, *Dinv;
+  const T *vF, *vR;  // interior block in the F and R tiles (row stride ld)
+  T* u;              // interior block in the U tile
+  T* Y;              // scratch, n0 x n1 contiguous
+  int n0, n1, ld;
+};
+template <class T>
+cudaError_t launch_fd_rows(cudaStream_t s, const FdRowsT<T>* d, int count, int max_n0, int max_n1, int pass,
+                           int from_F, T tau, int add);
+
 // The whole smoother of a small 2D level in one launch: blocks [0, nfd) are the interiors
 // (as launch_fd_small), the next nedges blocks one edge each (gather of the copies, 1D FD
 // with U (len x len, columns = basis) and dinv, scatter tau z to the copies), the last

@@ -277,7 +277,7 @@ def test_fd_engines_agree(name):
     from paper_1804_02539_gb300 import igamg
     pr, H, ctx, perms = setup_case(name)
     ctxs = {}
-    for eng in (1, 2, 3):
+    for eng in (1, 2, 3, 4):
         o = igamg.igamg_default_options()
         o.fd_engine = eng
         ctxs[eng] = igamg.Context(pr, o)
@@ -285,13 +285,14 @@ def test_fd_engines_agree(name):
     for l in range(1, pr.num_levels):
         r = dev(rng.normal(size=H.levels[l].space.N))
         z = {}
-        for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2]), ("block", ctxs[3])):
+        for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2]), ("block", ctxs[3]), ("rows", ctxs[4])):
             z[k] = torch.empty_like(r)
             c.smooth(l, r, z[k])
         # digit truncation at 2^-49 of each column maximum
         assert rel(host(z["tc"]), host(z["fma"])) < 1e-12, l
         assert rel(host(z["auto"]), host(z["fma"])) < 1e-12, l
         assert rel(host(z["block"]), host(z["fma"])) < 1e-13, l
+        assert rel(host(z["rows"]), host(z["fma"])) < 1e-13, l
     r = dev(rng.normal(size=H.levels[-1].space.N))
     xs, its = {}, {}
     for k, c in (("auto", ctx), ("fma", ctxs[1]), ("tc", ctxs[2])):
@@ -447,7 +448,7 @@ def test_degenerate_problems_are_reported():
         igamg.Context(pr)
     assert e.value.status == 6
     pr = workloads.unit_square_quadrants(8, 2, 4)
-    for field, val in (("fd_engine", 7), ("nu", 0), ("mu", 3), ("precision", 5)):
+    for field, val in (("fd_engine", 5), ("nu", 0), ("mu", 3), ("precision", 5)):
         o = igamg.igamg_default_options()
         setattr(o, field, val)
         with pytest.raises(igamg.IgamgError) as e:
