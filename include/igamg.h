@@ -19,6 +19,11 @@
  *  - Host arrays passed to igamg_setup are read during the call only.
  *  - The context owns the grid hierarchy (band coefficients, smoother bases, transfer
  *    tables, coarse factor) and its device workspaces; only igamg_free releases them.
+ *  - A context is used by one host thread at a time (its work buffers and captured CUDA
+ *    graphs are per context); different contexts may be used concurrently from different
+ *    threads, as the batch and server layers below do.
+ *  - igamg_solve synchronises the stream once per PCG iteration (the convergence test
+ *    reads the residual norm on the host) and at its end.
  */
 #ifndef IGAMG_H
 #define IGAMG_H
