@@ -768,7 +768,10 @@ template cudaError_t launch_norm2_dist<float>(cudaStream_t, int64_t, const int64
 template <class T>
 __global__ void k_pcg_xr(int64_t n, const double* __restrict__ scal, T* __restrict__ x,
                          T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ w) {
-  const T alpha = T(scal[0] / scal[1]);
+  __shared__ T alpha_s;  // one FP64 division per block, not per thread
+  if (threadIdx.x == 0) alpha_s = T(scal[0] / scal[1]);
+  __syncthreads();
+  const T alpha = alpha_s;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
     r[i] = fma(-alpha, w[i], r[i]);
@@ -778,7 +781,10 @@ __global__ void k_pcg_xr(int64_t n, const double* __restrict__ scal, T* __restri
 template <class T>
 __global__ void k_pcg_p(int64_t n, const double* __restrict__ scal, T* __restrict__ p,
                         const T* __restrict__ z) {
-  const T beta = T(scal[2] / scal[0]);
+  __shared__ T beta_s;
+  if (threadIdx.x == 0) beta_s = T(scal[2] / scal[0]);
+  __syncthreads();
+  const T beta = beta_s;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     p[i] = fma(beta, p[i], z[i]);
 }

@@ -193,7 +193,7 @@ cudaError_t launch_tile_to_global(cudaStream_t s, int64_t N, const int64_t* ptr,
                                   T* xg, int sum_copies);
 
 // Deterministic reductions (FP64 partials): fixed grid of RED_BLOCKS partial sums, then one block.
-constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs: enough loads in flight to stream HBM
 template <class T>
 cudaError_t launch_dot(cudaStream_t s, const T* a, const T* b, int64_t n, double* partials, double* out);
 // sum over active dofs of (sum of copies of v)^2 for a distributed vector v
