@@ -239,6 +239,24 @@ def run_ours(args, rank, world, local_rank):
         setup_ms = res.t_setup_ms
         assemble_ms = res.t_assemble_ms
         dev_bytes = ctx.device_bytes()
+        # one FP64 cycle alone (igamg_precondition, launched one by one): its algorithmic
+        # bytes (all classes) against its time, the V-cycle's HBM roofline fraction
+        zc = torch.empty_like(b)
+        ctx.profile_enable(0x3F)
+        ctx.precondition(b, zc)
+        pv = ctx.profile_read()
+        ctx.profile_enable(0)
+        gb_v = sum(v["bytes"] for k, v in pv.items() if k != "tensor_exec") / 1e9
+        for _ in range(2):
+            ctx.precondition(b, zc)
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(10):
+            ctx.precondition(b, zc)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        ms_v = v0.elapsed_time(v1) / 10
     ms_step = ms_total / args.steps
     value = dofs_all / (ms_step * 1e-3) / 1e6
     # dominant kernel class (from the breakdown pass) and its roofline, timed in the timed region
@@ -291,6 +309,10 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": roof,
         "hbm_whole_solve": hbm,
+        "vcycle": {"ms": round(ms_v, 4), "algorithmic_gb": round(gb_v, 4),
+                   "achieved_gbs": round(gb_v / (ms_v * 1e-3), 1), "peak_gbs": pk["hbm_gbs"],
+                   "hbm_frac": round(gb_v / (ms_v * 1e-3) / pk["hbm_gbs"], 4),
+                   "note": "one FP64 cycle via igamg_precondition, launched one by one (no graph)"},
         "clocks": clocks,
         "kernel_breakdown": breakdown,
     }
