@@ -917,7 +917,11 @@ void build_levels(igamg_ctx* c) {
       for (const Interior& in : T.interiors)
         if (in.len[0] && in.len[1]) min_len = std::min(min_len, std::min(in.len[0], in.len[1]));
       // tensor cores where the interiors are large enough to amortise the slices
-      const bool want_tc = c->opt.fd_engine == 2 ? min_len >= 1 : c->opt.fd_engine == 0 && min_len >= kTcMinLen;
+      int max_len = 0;
+      for (const Interior& in : T.interiors) max_len = std::max(max_len, std::max(in.len[0], in.len[1]));
+      // (FP64 digit sums are exact up to K = kTcMaxK)
+      const bool want_tc = max_len <= kTcMaxK &&
+                           (c->opt.fd_engine == 2 ? min_len >= 1 : c->opt.fd_engine == 0 && min_len >= kTcMinLen);
       if (want_tc) {
         // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
         std::vector<TcDesc<double, double>> t0F, t0R, t1, t2, t3;
@@ -1022,8 +1026,10 @@ void build_levels(igamg_ctx* c) {
       set_gemm(c, L.n64.m2b, b2);
       int min_len = 1 << 30;
       for (const Pend& pe : pend) min_len = std::min(min_len, std::min(pe.n0, std::min(pe.n1, pe.n2)));
-      const bool want_tc =
-          !pend.empty() && (c->opt.fd_engine == 2 ? true : c->opt.fd_engine == 0 && min_len >= kTcMinLen);
+      int max_len = 0;
+      for (const Pend& pe : pend) max_len = std::max(max_len, std::max(pe.n0, std::max(pe.n1, pe.n2)));
+      const bool want_tc = !pend.empty() && max_len <= kTcMaxK &&
+                           (c->opt.fd_engine == 2 ? true : c->opt.fd_engine == 0 && min_len >= kTcMinLen);
       if (want_tc) {
         // tensor cores: each stage contracts the leading mode and rotates it to the back,
         // C(i1, i2, j0) = sum_i0 U(i0, j0) X(i0, i1, i2), an n x n^2 product stored
@@ -1122,7 +1128,8 @@ void build_levels(igamg_ctx* c) {
           for (int b = 0; b < len1; ++b)
             Dv[size_t(a) * len1 + b] = 1.0 / ((h / p) * (S0->mu[a] + S1->mu[b] + double(p) * p / (h * h)));
         double* Dinv = reg_const(c, c->mem.upload(Dv, s), Dv.size());
-        const bool tcf = c->opt.fd_engine == 2 || (c->opt.fd_engine == 0 && std::min(len0, len1) >= kTcMinLen);
+        const bool tcf = std::max(len0, len1) <= kTcMaxK &&
+                         (c->opt.fd_engine == 2 || (c->opt.fd_engine == 0 && std::min(len0, len1) >= kTcMinLen));
         face_tc = face_tc && tcf;
         Sl a0t{}, a1t{}, a0{}, a1{};
         if (tcf) {

@@ -13,11 +13,19 @@
 //       C_ij = 2^{sigma_i + tau_j} sum_{q=2..S+1} D_q(i,j) 2^{-7q}
 //   in FP64 (pairs with s + t > S + 1 are below 2^{-56} relative and are dropped).
 //
-// Block: 128 threads, output tile 128 x 64, K block 64.  Operands are staged in shared
-// memory in the canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes;
-// LBO = 128 B between core matrices along K, SBO = 1024 B between 8-row groups), one thread
-// issues the MMAs, completion is tracked by an mbarrier (bounded wait), the accumulators
-// are read back with tcgen05.ld.
+// The epilogue recombines the diagonals exactly in 64-bit integers (units of 2^-49 of the
+// row and column scales), converts once to FP64 and applies the smoother's epilogue.
+//
+// Block: 512 threads (16 warps, 4 per TMEM lane quarter), one 128 x 64 output tile.  A
+// pre-pass finds the column exponents of the tile's 64-column panel.  Then a two-stage
+// pipeline over K blocks of 32: A's slices, pre-arranged on the host in the canonical
+// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes; LBO = 128 B between core
+// matrices along K, SBO = 512 B between 8-row groups), arrive by one bulk TMA copy per
+// stage; B's digits are produced by all threads from register-prefetched operands; one
+// thread issues the MMAs of a block and commits them to the stage's mbarrier while the
+// others stage the next block.  Every mbarrier wait is bounded.  Tiles with at most 32
+// valid rows or columns skip the tensor cores and use FMAs on the FP64 basis; such tiles
+// are scheduled after the full ones.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

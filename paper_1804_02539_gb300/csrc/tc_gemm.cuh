@@ -30,8 +30,10 @@ struct TcDesc {
   int lda = 0, tra = 0;
 };
 
-// S = 7: FP64-accurate digit-slice product (TB = TC = double); S = 1: BF16 product with
-// FP32 accumulation (TB = TC = float).  err: device flag set when an mbarrier wait times out.
+// S = 7: FP64-accurate digit-slice product (TB = TC = double), exact digit sums for
+// K <= kTcMaxK; S = 1: BF16 product with FP32 accumulation (TB = TC = float).  err: device
+// flag set when an mbarrier wait times out.
+constexpr int kTcMaxK = 1023;
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err);
