@@ -1,8 +1,13 @@
-"""Benchmark: FP64 multigrid-preconditioned CG (one V(1,1)-cycle per iteration, tau=0.25,
-sigma=5h^-2) on the 2D multi-patch workload, solved from x0 = 0 to relative residual
-1e-8 through the C ABI.  One step = one complete solve.  Prints ONE JSON line.
+"""Benchmark: multigrid-preconditioned CG (one V(1,1)-cycle per iteration, tau=0.25,
+sigma=5h^-2) solved from x0 = 0 to relative residual 1e-8 through the C ABI.  One step =
+one complete solve.  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|fp32|bf16] [--workload KEY]
+
+Default: FP64 on the 2D multi-patch workload grid2d_K16_p4_m256 (1,073,296 dofs).  Other
+modes: --batch (512 independent problems), --serve (Poisson arrivals, p50/p99 latency),
+--fichera (the Table II runs), --micro fd|fp64 (the finest smoother alone, the DGEMM rate).
 
 --impl reference times the CPU oracle (FP64 NumPy/SciPy restatement of the method) on
 the host cores, one thread, on a bounded sample of the same workload family."""

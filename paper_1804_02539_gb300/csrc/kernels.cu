@@ -1,4 +1,5 @@
-// FP64 device kernels of the multi-patch multigrid solver (2D tiles).
+// Device kernels of the multi-patch multigrid solver (2D and 3D tiles; FP64, and FP32 /
+// BF16-band twins for the precision variant), except the tensor-core GEMM (tc_gemm.cu).
 //
 // Layout: a level vector is the concatenation of per-patch tiles (C order, last direction
 // fastest); a global dof shared by several patches has one copy per owner (Sec. 4: the

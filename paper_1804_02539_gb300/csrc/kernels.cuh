@@ -1,4 +1,5 @@
-// Device kernels of the multigrid-preconditioned CG (FP64 path) and their launchers.
+// Device kernels of the multigrid-preconditioned CG and their launchers (FP64, and the FP32
+// twins of the precision variant).
 // Every launcher takes the stream explicitly and returns the launch status.
 #pragma once
 #include <cuda_bf16.h>
