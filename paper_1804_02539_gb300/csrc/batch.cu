@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -102,8 +103,28 @@ igamg_status igamg_setup_batch(const igamg_problem* problems, int count, const i
   std::vector<std::string> msg(count);
   int dev = 0;
   cudaGetDevice(&dev);
-  run_pool(W, count, [&](int w, int i) {
+  // Phase 1, one thread: the first problem of every (dim, patches, degree, knots, levels)
+  // class, so that the FD autotuner times its candidates on an otherwise idle device and
+  // caches the choices.  Phase 2, the pool: the rest, which find their choices cached.
+  std::vector<int> first, rest;
+  {
+    std::map<std::vector<int>, int> seen;
+    for (int i = 0; i < count; ++i) {
+      const igamg_problem& p = problems[i];
+      std::vector<int> key{p.dim, p.num_patches, p.num_levels, p.degree ? p.degree[0] : 0,
+                           p.num_knots ? p.num_knots[0] : 0};
+      if (seen.emplace(key, i).second) first.push_back(i);
+      else rest.push_back(i);
+    }
+  }
+  igamg::set_host_threads(0);
+  for (int i : first) {
+    st[i] = igamg_setup(&problems[i], opt, b->streams[0], &b->ctx[i]);
+    if (st[i] != IGAMG_OK) msg[i] = igamg_last_error(nullptr);
+  }
+  run_pool(W, int(rest.size()), [&](int w, int k) {
     cudaSetDevice(dev);
+    const int i = rest[k];
     st[i] = igamg_setup(&problems[i], opt, b->streams[w], &b->ctx[i]);
     if (st[i] != IGAMG_OK) msg[i] = igamg_last_error(nullptr);
   });

@@ -7,7 +7,7 @@
 
 namespace igamg {
 
-void set_host_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+void set_host_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
 
 
 std::vector<double> uniform_knots(int m, int p) {

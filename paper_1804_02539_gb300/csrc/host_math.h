@@ -31,7 +31,7 @@ void mass_stiffness_1d(int m, int p, Mat& M, Mat& K);
 Mat prolongation_1d(int mc, int p);
 
 // Threads the dense routines below may use when called from the current thread
-// (OpenMP team size; 1 inside a pool of setup workers).
+// (OpenMP team size; 1 inside a pool of setup workers; n <= 0: every core).
 void set_host_threads(int n);
 
 // Dense linear algebra.
