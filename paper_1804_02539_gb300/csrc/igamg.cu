@@ -127,6 +127,8 @@ struct Num {
   T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
   GemmSetT<T> edgeA, edgeB, face0, face1, face2, face3;
   XferT<T>* rpass[3] = {nullptr, nullptr, nullptr};
+  Xfer2T<T>* r2 = nullptr;
+  Xfer2T<T>* p2 = nullptr;
   XferT<T>* ppass[3] = {nullptr, nullptr, nullptr};
   T *tA = nullptr, *tB = nullptr;
 };
@@ -161,6 +163,8 @@ struct Level {
   int64_t *if_ptr = nullptr, *if_idx = nullptr;
   // transfer from level l-1 (valid for level >= 1): host descriptors per pass
   std::vector<XferT<double>> rp_h[3], pp_h[3];
+  std::vector<Xfer2T<double>> r2_h, p2_h;  // 2D: both passes fused (when the tables allow)
+  int x2_rout0 = 0, x2_rout1 = 0, x2_pout0 = 0, x2_pout1 = 0, x2_rw1 = 0, x2_pw1 = 0;
   int64_t rmax[3] = {0, 0, 0}, pmax[3] = {0, 0, 0};
   double apply_flops = 0, band_bytes = 0, xfer_flops = 0, xfer_bytes = 0;
 };
@@ -1216,6 +1220,7 @@ void build_levels(igamg_ctx* c) {
     // ---------------- transfers from level l-1 (one 1D pass per direction)
     const Level& C = c->lv[l - 1];
     std::map<std::tuple<int, int>, std::vector<void*>> ptabs;
+    std::map<std::tuple<int, int>, std::pair<std::vector<int>, std::vector<int>>> pstart_h;  // rs, ps
     auto tables = [&](int mc, int p) -> std::vector<void*>& {
       auto key = std::make_tuple(mc, p);
       if (!ptabs.count(key)) {
@@ -1244,6 +1249,7 @@ void build_levels(igamg_ctx* c) {
         ptabs[key] = {reg_const(c, c->mem.upload(rw, s), rw.size()), c->mem.upload(rs, s),
                       reg_const(c, c->mem.upload(pw, s), pw.size()), c->mem.upload(ps, s),
                       (void*)(intptr_t)wr, (void*)(intptr_t)wp};
+        pstart_h[key] = {rs, ps};
       }
       return ptabs[key];
     };
@@ -1325,6 +1331,44 @@ void build_levels(igamg_ctx* c) {
       L.pp_h[j] = pp[j];
       L.n64.rpass[j] = c->mem.upload(rp[j], s);
       L.n64.ppass[j] = c->mem.upload(pp[j], s);
+    }
+    if (d == 2) {
+      // both passes in one launch; each block's input columns must fit its shared buffer
+      // (2 x 32 + width): checked on the start tables
+      auto fits = [](const std::vector<int>& st, int nout, int width) {
+        for (int o = 0; o < nout; o += 32) {
+          const int e = std::min(o + 32, nout) - 1;
+          if (st[e] + width - st[o] > 64 + width) return false;
+        }
+        return true;
+      };
+      bool ok = true;
+      std::vector<Xfer2T<double>> r2, p2;
+      for (int k = 0; k < K; ++k) {
+        const PatchDev &Pf = L.pd_h[k], &Pc = C.pd_h[k];
+        auto& t0 = tables(Pc.m[0], Pc.p[0]);
+        auto& t1 = tables(Pc.m[1], Pc.p[1]);
+        const auto& h1 = pstart_h[std::make_tuple(Pc.m[1], Pc.p[1])];
+        const int wr0 = int((intptr_t)t0[4]), wr1 = int((intptr_t)t1[4]);
+        const int wp0 = int((intptr_t)t0[5]), wp1 = int((intptr_t)t1[5]);
+        ok = ok && fits(h1.first, Pc.n[1], wr1) && fits(h1.second, Pf.n[1], wp1);
+        r2.push_back(Xfer2T<double>{Pf.off, Pc.off, Pf.n[0], Pf.n[1], Pc.n[0], Pc.n[1], (const double*)t0[0],
+                                    (const double*)t1[0], (const int*)t0[1], (const int*)t1[1], wr0, wr1});
+        p2.push_back(Xfer2T<double>{Pc.off, Pf.off, Pc.n[0], Pc.n[1], Pf.n[0], Pf.n[1], (const double*)t0[2],
+                                    (const double*)t1[2], (const int*)t0[3], (const int*)t1[3], wp0, wp1});
+        L.x2_rout0 = std::max(L.x2_rout0, Pc.n[0]);
+        L.x2_rout1 = std::max(L.x2_rout1, Pc.n[1]);
+        L.x2_pout0 = std::max(L.x2_pout0, Pf.n[0]);
+        L.x2_pout1 = std::max(L.x2_pout1, Pf.n[1]);
+        L.x2_rw1 = std::max(L.x2_rw1, wr1);
+        L.x2_pw1 = std::max(L.x2_pw1, wp1);
+      }
+      if (ok) {
+        L.r2_h = r2;
+        L.p2_h = p2;
+        L.n64.r2 = c->mem.upload(r2, s);
+        L.n64.p2 = c->mem.upload(p2, s);
+      }
     }
   }
   // coarse solver: dense A_0 from the level-0 bands, Cholesky, explicit inverse
@@ -1520,6 +1564,11 @@ void restrict_to_coarse(igamg_ctx* c, int l, const T* rf) {
   Level& C = c->lv[l - 1];
   Num<T>& N = num<T>(L);
   const int d = c->pd.dim, K = c->pd.K;
+  if (N.r2) {
+    ProfScope pr(c, CLS_TRANSFER, L.xfer_flops / 3, L.xfer_bytes / 3 * sizeof(T) / 8.0, 1);
+    CK(launch_transfer_2d<T>(c->stream, N.r2, K, L.x2_rout0, L.x2_rout1, L.x2_rw1, rf, num<T>(C).F, 0, C.l2g));
+    return;
+  }
   ProfScope pr(c, CLS_TRANSFER, L.xfer_flops / 3, L.xfer_bytes / 3 * sizeof(T) / 8.0, d);
   const T* in = rf;
   for (int j = 0; j < d; ++j) {
@@ -1536,6 +1585,11 @@ void prolong_add(igamg_ctx* c, int l) {
   Level& C = c->lv[l - 1];
   Num<T>& N = num<T>(L);
   const int d = c->pd.dim, K = c->pd.K;
+  if (N.p2) {
+    ProfScope pp(c, CLS_TRANSFER, 2 * L.xfer_flops / 3, 2 * L.xfer_bytes / 3 * sizeof(T) / 8.0, 1);
+    CK(launch_transfer_2d<T>(c->stream, N.p2, K, L.x2_pout0, L.x2_pout1, L.x2_pw1, num<T>(C).U, N.U, 1, nullptr));
+    return;
+  }
   ProfScope pp(c, CLS_TRANSFER, 2 * L.xfer_flops / 3, 2 * L.xfer_bytes / 3 * sizeof(T) / 8.0, d);
   const T* in = num<T>(C).U;
   for (int j = 0; j < d; ++j) {
@@ -2030,6 +2084,17 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     tr_set(A.m0b, B.m0b); tr_set(A.m1b, B.m1b); tr_set(A.m2b, B.m2b);
     tr_set(A.edgeA, B.edgeA); tr_set(A.edgeB, B.edgeB);
     tr_set(A.face0, B.face0); tr_set(A.face1, B.face1); tr_set(A.face2, B.face2); tr_set(A.face3, B.face3);
+    if (!L.r2_h.empty()) {
+      std::vector<Xfer2T<float>> r2, p2;
+      for (const auto& x : L.r2_h)
+        r2.push_back(Xfer2T<float>{x.in_off, x.out_off, x.nin0, x.nin1, x.nout0, x.nout1, tr(x.w0), tr(x.w1), x.st0,
+                                   x.st1, x.width0, x.width1});
+      for (const auto& x : L.p2_h)
+        p2.push_back(Xfer2T<float>{x.in_off, x.out_off, x.nin0, x.nin1, x.nout0, x.nout1, tr(x.w0), tr(x.w1), x.st0,
+                                   x.st1, x.width0, x.width1});
+      B.r2 = c->mem.upload(r2, s);
+      B.p2 = c->mem.upload(p2, s);
+    }
     for (int j = 0; j < 3; ++j) {
       if (L.rp_h[j].empty()) continue;
       std::vector<XferT<float>> rp, pp;

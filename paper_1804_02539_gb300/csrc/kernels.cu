@@ -1215,6 +1215,64 @@ template cudaError_t launch_transfer_1d<double>(cudaStream_t, const XferT<double
 template cudaError_t launch_transfer_1d<float>(cudaStream_t, const XferT<float>*, int, int64_t, const float*, float*,
                                                int, const int64_t*);
 
+// ---------------------------------------------------------------- fused 2D transfer
+
+constexpr int XB1 = 32, XB0 = 8;  // outputs per block: 8 rows x 32 columns
+
+template <class T>
+__global__ void __launch_bounds__(256) k_transfer_2d(const Xfer2T<T>* __restrict__ xs, const T* __restrict__ in,
+                                                     T* __restrict__ out, int add, const int64_t* __restrict__ mask) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* mid = reinterpret_cast<T*>(smraw);  // XB0 x W: the dir-0 pass on the block's input columns
+  const Xfer2T<T> x = xs[blockIdx.z];
+  const int o0b = blockIdx.y * XB0, o1b = blockIdx.x * XB1;
+  if (o0b >= x.nout0 || o1b >= x.nout1) return;
+  const int o1e = min(o1b + XB1, x.nout1) - 1;
+  const int c1lo = x.st1[o1b], c1hi = min(x.st1[o1e] + x.width1, x.nin1);  // input columns used
+  const int W = c1hi - c1lo;
+  const T* src = in + x.in_off;
+  for (int idx = threadIdx.x; idx < XB0 * W; idx += 256) {
+    const int r = idx / W, cc = idx % W, o0 = o0b + r;
+    T acc = 0;
+    if (o0 < x.nout0) {
+      const int s0 = x.st0[o0];
+      const T* w = x.w0 + int64_t(o0) * x.width0;
+      for (int a = 0; a < x.width0; ++a)
+        if (s0 + a < x.nin0) acc = fma(w[a], src[int64_t(s0 + a) * x.nin1 + c1lo + cc], acc);
+    }
+    mid[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < XB0 * XB1; idx += 256) {
+    const int r = idx / XB1, cx = idx % XB1, o0 = o0b + r, o1 = o1b + cx;
+    if (o0 >= x.nout0 || o1 >= x.nout1) continue;
+    const int s1 = x.st1[o1];
+    const T* w = x.w1 + int64_t(o1) * x.width1;
+    T acc = 0;
+    for (int b = 0; b < x.width1; ++b)
+      if (s1 + b < x.nin1) acc = fma(w[b], mid[r * W + s1 - c1lo + b], acc);
+    const int64_t t = x.out_off + int64_t(o0) * x.nout1 + o1;
+    if (mask && mask[t] < 0) acc = 0;
+    out[t] = add ? out[t] + acc : acc;
+  }
+}
+
+template <class T>
+cudaError_t launch_transfer_2d(cudaStream_t s, const Xfer2T<T>* xs, int npatch, int max_out0, int max_out1,
+                               int max_width1, const T* in, T* out, int add, const int64_t* mask) {
+  // the input columns of 32 consecutive outputs: at most 2 per output step plus one width
+  const size_t sm = sizeof(T) * XB0 * size_t(2 * XB1 + max_width1);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_transfer_2d<T>), sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((max_out1 + XB1 - 1) / XB1, (max_out0 + XB0 - 1) / XB0, npatch);
+  k_transfer_2d<T><<<grid, 256, sm, s>>>(xs, in, out, add, mask);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transfer_2d<double>(cudaStream_t, const Xfer2T<double>*, int, int, int, int,
+                                                const double*, double*, int, const int64_t*);
+template cudaError_t launch_transfer_2d<float>(cudaStream_t, const Xfer2T<float>*, int, int, int, int, const float*,
+                                               float*, int, const int64_t*);
+
 // ---------------------------------------------------------------- interior box gather/scatter
 
 // Compact copy of every patch-interior box (3D FD works on compact tensors) and the

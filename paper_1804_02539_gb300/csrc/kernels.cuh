@@ -117,6 +117,21 @@ template <class T>
 cudaError_t launch_transfer_1d(cudaStream_t s, const XferT<T>* xs, int npatch, int64_t max_out, const T* in, T* out,
                                int add, const int64_t* mask);
 
+// Both 1D passes of a 2D transfer in one launch: out = T1 (T0 in) per patch tile, with
+// T_j(o, i) = w_j[o][a] for i = st_j[o] + a (a < width_j); the intermediate rows of a block
+// live in shared memory.  Restriction (mask: zero where mask < 0) and prolongation (add).
+template <class T>
+struct Xfer2T {
+  int64_t in_off, out_off;
+  int nin0, nin1, nout0, nout1;
+  const T *w0, *w1;
+  const int *st0, *st1;
+  int width0, width1;
+};
+template <class T>
+cudaError_t launch_transfer_2d(cudaStream_t s, const Xfer2T<T>* xs, int npatch, int max_out0, int max_out1,
+                               int max_width1, const T* in, T* out, int add, const int64_t* mask);
+
 // Interior box of a tile <-> compact tensor.
 // Whole patch-interior smoother of one small 2D interior in one block (the four FD
 // contractions in shared memory): u (=|+=) tau U0 ((U0^T v U1) .* Dinv) U1^T.
