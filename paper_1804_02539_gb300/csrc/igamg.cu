@@ -206,6 +206,10 @@ struct igamg_ctx {
   int64_t graph_launch[4][8] = {};                        // per-replay launch accounting
   double graph_flops[4][8] = {}, graph_bytes[4][8] = {};
   cudaStream_t cap_stream = nullptr;
+  // the interface pieces of a smoothing step run on a second stream, concurrently with the
+  // patch interiors (disjoint pieces, Eq. additive); forked and joined by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int capturing = -1, pending_graph = -1;
   std::map<const void*, const void*> tc_bf16_twin;         // S=7 slices -> S=1 slices of the same matrix
   double *partials = nullptr, *scal = nullptr;
@@ -1475,6 +1479,41 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
     CK((launch_band_apply_3d<T, T>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r, L.uniform_p)));
 }
 
+// Makes c->stream another stream for the scope (launch helpers use c->stream).
+struct OnStream {
+  igamg_ctx* c;
+  cudaStream_t prev;
+  OnStream(igamg_ctx* c_, cudaStream_t s) : c(c_), prev(c_->stream) { c->stream = s; }
+  ~OnStream() { c->stream = prev; }
+};
+
+// Interface pieces of a smoothing step: edges (1D FD), faces (2D FD) and vertices, with the
+// gather of the copies before and the scatter after (Sigma of Eq. ops6).
+template <class T>
+void smooth_interface(igamg_ctx* c, Level& L, Num<T>& N, const T* v, double tau, bool add) {
+  {
+    ProfScope ps(c, CLS_IFACE, 0.0, 2.0 * sizeof(T) * L.n_if);
+    CK(launch_iface_gather<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, v, N.G));
+  }
+  run_gemm(c, N.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
+  run_gemm(c, N.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  if (N.use_tc && N.tq0.batch) {  // faces follow the interiors' engine
+    run_tc(c, N.tq0, EPI_STORE, 1.0, CLS_IFACE);
+    run_tc(c, N.tq1, EPI_MUL, 1.0, CLS_IFACE);
+    run_tc(c, N.tq2, EPI_STORE, 1.0, CLS_IFACE);
+    run_tc(c, N.tq3, EPI_STORE, 1.0, CLS_IFACE);
+  } else {
+    run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
+    run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
+    run_gemm(c, N.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
+    run_gemm(c, N.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
+  }
+  {
+    ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 3.0 * sizeof(T) * L.n_if);
+    CK(launch_iface_scatter<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, N.Z, N.G, N.vscale, T(tau), add ? 1 : 0, N.U));
+  }
+}
+
 // u (=|+=) tau L^{-1} v for a distributed v (F or R of the level): patch interiors by
 // fast diagonalisation, faces by their 2D and edges by their 1D fast diagonalisation,
 // vertices by scaling (Eq. additive; the pieces are disjoint, so the sum is a set of
@@ -1490,6 +1529,14 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
     ProfScope ps(c, CLS_FD, N.ssmall_flops, 0.0);
     CK(launch_smooth_small<T>(c->stream, N.ssmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
     return;
+  }
+  // the interface pieces on the side stream, concurrently with the interiors below
+  const bool fork = L.n_if > 0 && c->side;
+  if (fork) {
+    CK(cudaEventRecord(c->fork_ev, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    OnStream os(c, c->side);
+    smooth_interface<T>(c, L, N, v, tau, add);
   }
   if (c->pd.dim == 2 && N.use_rows) {
     for (int pass = 1; pass <= 2; ++pass) {
@@ -1533,27 +1580,11 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
     ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
     CK(launch_box_copy<T>(c->stream, L.boxes, L.nbox, L.max_box, N.cX, N.U, 0, T(tau), add ? 1 : 0));
   }
-  if (L.n_if == 0) return;
-  {
-    ProfScope ps(c, CLS_IFACE, 0.0, 2.0 * sizeof(T) * L.n_if);
-    CK(launch_iface_gather<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, v, N.G));
-  }
-  run_gemm(c, N.edgeA, false, false, EPI_COLSCALE, 1.0, CLS_IFACE);
-  run_gemm(c, N.edgeB, false, true, EPI_STORE, 1.0, CLS_IFACE);
-  if (N.use_tc && N.tq0.batch) {  // faces follow the interiors' engine
-    run_tc(c, N.tq0, EPI_STORE, 1.0, CLS_IFACE);
-    run_tc(c, N.tq1, EPI_MUL, 1.0, CLS_IFACE);
-    run_tc(c, N.tq2, EPI_STORE, 1.0, CLS_IFACE);
-    run_tc(c, N.tq3, EPI_STORE, 1.0, CLS_IFACE);
-  } else {
-    run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
-    run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
-    run_gemm(c, N.face2, false, false, EPI_STORE, 1.0, CLS_IFACE);
-    run_gemm(c, N.face3, false, true, EPI_STORE, 1.0, CLS_IFACE);
-  }
-  {
-    ProfScope ps(c, CLS_IFACE, 2.0 * L.n_if, 3.0 * sizeof(T) * L.n_if);
-    CK(launch_iface_scatter<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, N.Z, N.G, N.vscale, T(tau), add ? 1 : 0, N.U));
+  if (fork) {
+    CK(cudaEventRecord(c->join_ev, c->side));
+    CK(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
+  } else if (L.n_if > 0) {
+    smooth_interface<T>(c, L, N, v, tau, add);
   }
 }
 
@@ -2184,6 +2215,13 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
     delete c;
     return e.code;
   }
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    g_setup_error = "cannot create the interface stream";
+    igamg_free(c);
+    return IGAMG_ERR_CUDA;
+  }
   c->t_setup_ms = now_ms() - t0;
   *out = c;
   return IGAMG_OK;
@@ -2460,6 +2498,12 @@ igamg_status igamg_free(igamg_ctx* c) {
     }
   }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   for (auto& t : c->ev_open) {
     cudaEventDestroy(std::get<1>(t));
     cudaEventDestroy(std::get<2>(t));
