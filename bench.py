@@ -287,7 +287,8 @@ def run_ours(args, rank, world, local_rank):
                           "frac": round(tach / pk["bf16_tflops"], 4), "peak_source": src,
                           "note": "includes the interior-FD launches that run on the FMA pipes"}
     roof["timing"] = ("CUDA-event nodes around each launch of the class in the first timed solve "
-                      f"({d['launches']} launches), on the solve's stream")
+                      f"({d['launches']} launches), on the stream each launch runs on; the interface class runs "
+                      "on a second stream concurrently with the interiors, so class times overlap")
     breakdown = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"],
                      "gflop_per_step": round(v["flops"] / 1e9, 4),
                      "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items() if k != "tensor_exec"}

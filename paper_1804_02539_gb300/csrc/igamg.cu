@@ -247,7 +247,7 @@ bool rect_metric(const double* X, double* c0, double* c1) {
 
 // Message returned by igamg_last_error(NULL) on this thread.
 void set_context_free_error(const std::string& msg) { g_setup_error = msg; }
-// Stream a context launches on (the batch driver lends contexts to its worker streams).
+// Stream a context launches on (the batch layer lends contexts to its worker streams).
 cudaStream_t ctx_stream(const igamg_ctx* c) { return c->stream; }
 void ctx_set_stream(igamg_ctx* c, cudaStream_t s) { c->stream = s; }
 // Device memory the context holds (its own allocations).
