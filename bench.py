@@ -233,8 +233,9 @@ def run_ours(args, rank, world, local_rank):
         # end to end: host vectors, H2D + D2H inside the timed region
         e2e_s = float("nan")
         if not args.no_e2e:
-            bh = b.cpu().numpy().copy()
-            xh = np.zeros(N)
+            # pinned host vectors (page-locked, so the copies run at full PCIe/C2C rate)
+            bh = b.cpu().pin_memory().numpy()
+            xh = torch.zeros(N, dtype=torch.float64).pin_memory().numpy()
             ctx.solve_host(bh, xh, TOL)
             t0 = time.perf_counter()
             for _ in range(args.steps):

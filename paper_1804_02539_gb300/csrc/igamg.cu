@@ -1986,6 +1986,74 @@ void autotune(igamg_ctx* c) {
   check_tc(c);
 }
 
+// The FP32 twin of a level picks its own engine: FP32 FMA GEMMs and single BF16 tensor-core
+// products (one slice pair instead of 28) weigh differently than their FP64 counterparts, so
+// the FP64 choice is only the starting point.  Same candidates and timing rule as autotune().
+void apply_choice_low(Level& L, const FdChoice& ch) {
+  Num<float>& N = L.n32;
+  N.use_tc = ch.tc && N.tc1.batch > 0;
+  N.use_fused = ch.R == -1 && L.fused_ok;
+  N.use_rows = ch.R == -2 && N.nfrows > 0;
+  for (GemmSetT<float>* g : {&N.st0F, &N.st0R, &N.st1, &N.st2, &N.st3, &N.m0f, &N.m1f, &N.m2f, &N.m0b, &N.m1b, &N.m2b})
+    g->R = ch.R > 0 ? ch.R : 0;
+}
+
+void autotune_low(igamg_ctx* c) {
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int l = 1; l < int(c->lv.size()); ++l) {
+    Level& L = c->lv[l];
+    Num<float>& N = L.n32;
+    if (!N.st0F.batch && !N.m0f.batch) continue;  // no patch interiors on this level
+    const std::string key = fd_signature(c, L) + (c->low_bf16 ? "|bf16" : "|f32");
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        apply_choice_low(L, it->second);
+        continue;
+      }
+    }
+    std::vector<FdChoice> cand{{false, 1}, {false, 2}, {false, 4}};
+    if (N.tc1.batch) cand.push_back({true, 0});
+    if (L.fused_ok) cand.push_back({false, -1});
+    if (N.nfrows && c->pd.dim == 2) cand.push_back({false, -2});
+    FdChoice best{false, 0};
+    float best_ms = 1e30f;
+    for (const FdChoice& ch : cand) {
+      apply_choice_low(L, ch);
+      smooth<float>(c, l, true, false);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2; ++r) smooth<float>(c, l, true, false);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, 1.5f * t);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ch;
+      }
+    }
+    if (c->verbose)
+      std::fprintf(stderr, "[igamg] autotune level %d (%s): %s R=%d (%.3f ms per smoother)\n", l,
+                   c->low_bf16 ? "bf16" : "fp32",
+                   best.tc ? "tensor" : best.R == -1 ? "one-block" : best.R == -2 ? "row-block" : "fma", best.R,
+                   best_ms / 3);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    apply_choice_low(L, g_tune_cache.emplace(key, best).first->second);
+  }
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  CK(cudaMemsetAsync(c->lv.back().n32.U, 0, c->lv.back().topo.T * sizeof(float), s));
+  check_tc(c);
+}
+
 // Twins of the FP64 numerics in FP32 (bands in FP32 or BF16): every registered FP64 array
 // gets an FP32 copy (constants converted, work buffers allocated) and every FP64
 // descriptor is translated pointer by pointer.
@@ -2207,7 +2275,10 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
     if (!e.empty()) throw Fail{igamg_status(code), e};
     build_levels(c);
     if (c->opt.autotune && c->opt.fd_engine == 0) autotune(c);
-    if (c->opt.precision != IGAMG_FP64) build_low(c, c->opt.precision == IGAMG_BF16);
+    if (c->opt.precision != IGAMG_FP64) {
+      build_low(c, c->opt.precision == IGAMG_BF16);
+      if (c->opt.autotune && c->opt.fd_engine == 0) autotune_low(c);
+    }
   } catch (const Fail& e) {
     g_setup_error = e.msg;
     c->mem.release();
