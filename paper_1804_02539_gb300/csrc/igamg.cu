@@ -2268,6 +2268,10 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
       throw Fail{IGAMG_ERR_ARG, "inner_tol must be in (0, 1)"};
     if (c->opt.nu < 1 || c->opt.mu < 1 || c->opt.mu > 2 || c->opt.max_iter < 0 || !(c->opt.tau > 0))
       throw Fail{IGAMG_ERR_ARG, "bad options"};
+    // the interface stream exists before the autotuner times smoothers
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     int code = 0;
     std::string e = parse_problem(prob->dim, prob->num_patches, prob->degree, prob->num_knots, prob->knots,
                                   prob->geo_degree, prob->geo_num_ctrl, prob->geo_ctrl, prob->side_bc,
@@ -2281,17 +2285,17 @@ igamg_status igamg_setup(const igamg_problem* prob, const igamg_options* opt, vo
     }
   } catch (const Fail& e) {
     g_setup_error = e.msg;
+    if (c->side) {
+      cudaStreamSynchronize(c->side);
+      cudaStreamDestroy(c->side);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
     c->mem.release();
     if (c->h_scal) cudaFreeHost(c->h_scal);
     delete c;
     return e.code;
-  }
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
-    g_setup_error = "cannot create the interface stream";
-    igamg_free(c);
-    return IGAMG_ERR_CUDA;
   }
   c->t_setup_ms = now_ms() - t0;
   *out = c;
