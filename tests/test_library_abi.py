@@ -49,3 +49,44 @@ def test_setup_rejects_bad_problems_without_gpu(built_lib):
     assert h.value is None
     assert b"NULL" in lib.igamg_last_error(None) or b"problem" in lib.igamg_last_error(None)
     assert lib.igamg_free(None) == 0
+
+
+STRUCTS = ("igamg_problem", "igamg_options", "igamg_result", "igamg_request_info", "igamg_server_counters")
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's field names, order, offsets and
+    size: a C program compiled against include/igamg.h prints them (host compiler only)."""
+    import shutil
+    import subprocess
+    from paper_1804_02539_gb300 import igamg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "igamg.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(igamg, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                          text=True).stdout.splitlines())
+    for name in STRUCTS:
+        cls = getattr(igamg, name)
+        assert int(out[f"{name} size"]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(out[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
+    # and no header field is missing from the mirror: the header's member count per struct
+    hdr = open(os.path.join(ROOT, "include", "igamg.h")).read()
+    for name in STRUCTS:
+        end = re.search(r"\}\s*" + name + r"\s*;", hdr).start()
+        body = hdr[hdr.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        decls = [d for d in body.split(";") if d.strip()]
+        count = sum(len(d.split(",")) for d in decls)
+        assert count == len(getattr(igamg, name)._fields_), name
