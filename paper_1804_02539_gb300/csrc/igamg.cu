@@ -1266,8 +1266,6 @@ void build_levels(igamg_ctx* c) {
       int shp[3];
       for (int j = 0; j < 3; ++j) shp[j] = Pf.n[j];
       int64_t in_off = Pf.off;
-      double* bufs[2] = {nullptr, nullptr};
-      (void)bufs;
       for (int j = 0; j < d; ++j) {
         auto& tb = tables(Pc.m[j], Pc.p[j]);
         XferT<double> x{};
