@@ -137,3 +137,38 @@ def test_iteration_counts_band():
             its.append(solver.pcg(H, b, tol=1e-8).iters)
     assert all(10 <= i <= 60 for i in its), its
     assert max(its) - min(its) <= 10, its
+
+
+@pytest.mark.parametrize("mu,nu", [(1, 1), (2, 1), (2, 2)])
+def test_cycle_error_propagation_recursion(mu, nu):
+    """Algorithm 1 as an iteration on A_l u = f has the error propagation
+        E_l = S_l^nu (I - P_l (I - E_{l-1}^mu) A_{l-1}^{-1} P_l^T A_l) S_l^nu,  E_0 = 0,
+    with S_l = I - tau B_l A_l (B_l the additive smoother): mu cycles from zero on the
+    coarse residual equation leave (I - E^mu) A^{-1} r.  The oracle's cycle, applied to the
+    unit vectors with f = 0, must give these dense matrices on every level (V- and W-cycle,
+    one and two smoothing steps)."""
+    from oracle import smoother as osm
+    pr = workloads.perturbed_grid_2d(2, 2, 8, 4, 5)
+    H = solver.build_hierarchy(pr, nu=nu, mu=mu)
+    E_prev = None
+    for l in range(1, len(H.levels)):
+        lv = H.levels[l]
+        A = lv.A.toarray()
+        n = A.shape[0]
+        I = np.eye(n)
+        B = np.stack([osm.apply_smoother(lv.smooth, I[:, i]) for i in range(n)], axis=1)
+        S = np.linalg.matrix_power(I - H.tau * B @ A, nu)
+        Ac = H.levels[l - 1].A.toarray()
+        P = lv.P.toarray()
+        Q = np.eye(Ac.shape[0]) if l == 1 else np.eye(Ac.shape[0]) - np.linalg.matrix_power(E_prev, mu)
+        E = S @ (I - P @ Q @ np.linalg.solve(Ac, P.T @ A)) @ S
+        E_orc = np.stack([solver.multigrid(H, l, I[:, i], np.zeros(n)) for i in range(n)], axis=1)
+        np.testing.assert_allclose(E_orc, E, rtol=0, atol=1e-11 * max(1.0, np.abs(E).max()), err_msg=f"level {l}")
+        E_prev = E
+    # a W-cycle contracts at least as well as a V-cycle here (spectral radius)
+    if mu == 2 and nu == 1:
+        HV = solver.build_hierarchy(pr, nu=1, mu=1)
+        n = HV.levels[-1].A.shape[0]
+        EV = np.stack([solver.multigrid(HV, len(HV.levels) - 1, np.eye(n)[:, i], np.zeros(n)) for i in range(n)],
+                      axis=1)
+        assert np.max(np.abs(np.linalg.eigvals(E_prev))) <= np.max(np.abs(np.linalg.eigvals(EV))) + 1e-12
