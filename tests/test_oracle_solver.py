@@ -172,3 +172,27 @@ def test_cycle_error_propagation_recursion(mu, nu):
         EV = np.stack([solver.multigrid(HV, len(HV.levels) - 1, np.eye(n)[:, i], np.zeros(n)) for i in range(n)],
                       axis=1)
         assert np.max(np.abs(np.linalg.eigvals(E_prev))) <= np.max(np.abs(np.linalg.eigvals(EV))) + 1e-12
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: workloads.perturbed_grid_2d(2, 3, 8, 4, 6),
+    lambda: workloads.perturbed_cube_3d(2, 2, 4, 3, 3),
+])
+def test_pcg_iterates_minimise_energy_error_over_krylov_space(maker):
+    """With an SPD preconditioner B, the k-th PCG iterate from x_0 = 0 is the minimiser of
+    ||x - A^{-1} b||_A over span{B b, (BA) B b, ..., (BA)^{k-1} B b}: the projected system
+    V^T A V y = V^T b on an orthonormal basis V of that space gives it directly."""
+    pr = maker()
+    H = solver.build_hierarchy(pr)
+    A = H.levels[-1].A
+    N = A.shape[0]
+    b = np.random.default_rng(8).uniform(-1, 1, N)
+    K = [solver.precondition(H, b)]
+    for k in range(1, 5):
+        K.append(solver.precondition(H, A @ K[-1]))
+    for k in range(1, 6):
+        V, _ = np.linalg.qr(np.stack(K[:k], axis=1))
+        y = np.linalg.solve(V.T @ (A @ V), V.T @ b)
+        x_opt = V @ y
+        x_k = solver.pcg(H, b, fixed_iters=k).x
+        assert np.linalg.norm(x_k - x_opt) <= 1e-8 * np.linalg.norm(x_opt), k
