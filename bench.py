@@ -37,6 +37,31 @@ TOL = 1e-8
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# FP32 FMA pipes of one GB300: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def combined_roofline(prof, ms_step, precision, pk):
+    """Roofline time of one solve: t_roof = sum over the kernel classes of
+    max(algorithmic bytes / HBM bandwidth, flops / pipe peak).  The interior FD counts its
+    issued tensor-core MMA FLOPs at the BF16 peak (its FMA-run levels are left out), every
+    other class its flops on the FP64 pipe (FP32 pipes in the FP32/BF16 variants), so
+    t_roof is a lower bound and frac = t_roof / measured time an upper bound on the
+    fraction of the combined roofline the solve reaches."""
+    alu = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    tx = prof.get("tensor_exec", {}).get("flops", 0.0)
+    per, t = {}, 0.0
+    for k, v in prof.items():
+        if k == "tensor_exec":
+            continue
+        tb = v["bytes"] / (pk["hbm_gbs"] * 1e9)
+        tf = tx / (pk["bf16_tflops"] * 1e12) if (k == "interior_fd" and tx > 0) else v["flops"] / (alu * 1e12)
+        per[k] = round(max(tb, tf) * 1e3, 4)
+        t += max(tb, tf)
+    return {"t_roof_ms": round(t * 1e3, 3), "frac": round(t * 1e3 / ms_step, 4), "per_class_ms": per,
+            "alu_peak_tflops": round(alu, 2)}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -323,6 +348,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "kernel_breakdown": breakdown,
     }
+    try:  # the combined roofline of the whole solve (per-class bounds of the breakdown above)
+        out["roofline_whole_solve"] = combined_roofline(prof1, ms_step, args.precision, pk)
+    except Exception as e:  # an optional field: never lose the bench line over it
+        out["roofline_whole_solve"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         o = run_oracle(1, 0)
         out["cpu_baseline"] = {"value": round(o["N"] / o["t_solve_s"] / 1e6, 6), "unit": "MDOF/s",
