@@ -90,3 +90,10 @@ def test_binding_structs_match_the_header(tmp_path):
         decls = [d for d in body.split(";") if d.strip()]
         count = sum(len(d.split(",")) for d in decls)
         assert count == len(getattr(igamg, name)._fields_), name
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No silent fallback: without the built library the binding raises."""
+    from paper_1804_02539_gb300 import igamg
+    with pytest.raises(ImportError, match="not built"):
+        igamg.load_library(str(tmp_path / "libigamg.so"))
