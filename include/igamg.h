@@ -112,13 +112,15 @@ typedef struct {
                           of the process                                               */
 } igamg_options;
 
+/* Result of a solve.  The first five fields are the problem statement's result record;
+ * outer_iters, added for the precision variant, comes last so that their layout is kept. */
 typedef struct {
   int iters;           /* PCG iterations performed (inner iterations for mixed)       */
-  int outer_iters;     /* FP64 refinement steps (1 for FP64)                          */
   double relres;       /* ||b - A x||_2 / ||b - A x_0||_2 at exit                      */
   double t_setup_ms;   /* igamg_setup wall time (host + device, synchronised)          */
   double t_assemble_ms;/* part of setup spent assembling the level matrices           */
   double t_solve_ms;   /* this solve, device-synchronised wall time                    */
+  int outer_iters;     /* FP64 refinement steps (1 for FP64)                          */
 } igamg_result;
 
 typedef struct igamg_ctx igamg_ctx;

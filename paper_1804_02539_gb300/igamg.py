@@ -36,8 +36,8 @@ class igamg_options(C.Structure):
 
 
 class igamg_result(C.Structure):
-    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("relres", C.c_double), ("t_setup_ms", C.c_double),
-                ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double)]
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("t_setup_ms", C.c_double),
+                ("t_assemble_ms", C.c_double), ("t_solve_ms", C.c_double), ("outer_iters", C.c_int)]
 
 
 class igamg_request_info(C.Structure):

@@ -42,7 +42,7 @@ def oracle_rows(pr, space, gids):
             if len(where) == 0:
                 continue
             i = where[0]
-            win = [(max(int(i[j]) - p, 0), min(int(i[j]) + 1, int(space.m[k, j]))) for j in range(2)]
+            win = [(max(int(i[j]) - p, 0), min(int(i[j]) + 1, int(space.m[k, j]))) for j in range(space.dim)]
             A = patch.patch_matrices(np.asarray(pr.corners[k]), space.knots[k], space.p[k], elem_window=win)
             li = int(np.ravel_multi_index(tuple(i), tuple(space.n[k])))
             row = A.getrow(li).tocoo()
@@ -54,13 +54,16 @@ def oracle_rows(pr, space, gids):
     return rows
 
 
-def sample_dofs(space, rng, count=40):
+def sample_dofs(space, rng, count=40, neumann_patch=15):
+    """`count` random dofs, the middle dof of every face, edge and vertex piece, and (2D)
+    the last dof of patch `neumann_patch`'s interior (a corner on Neumann sides)."""
     N = space.N
     picks = list(rng.choice(N, count, replace=False))
     for pc in space.pieces:              # at least one dof of every piece kind
-        if pc.kind in ("edge", "vertex"):
+        if pc.kind in ("face", "edge", "vertex"):
             picks.append(int(pc.ids.ravel()[len(pc.ids.ravel()) // 2]))
-    picks.append(int(space.pieces[15].ids[-1, -1]))   # corner of a Neumann patch interior
+    if neumann_patch is not None:
+        picks.append(int(space.pieces[neumann_patch].ids[-1, -1]))
     return sorted(set(int(x) for x in picks))
 
 
