@@ -9,6 +9,11 @@ Default: FP64 on the 2D multi-patch workload grid2d_K16_p4_m256 (1,073,296 dofs)
 modes: --batch (512 independent problems), --serve (Poisson arrivals, p50/p99 latency),
 --fichera (the Table II runs), --micro fd|fp64 (the finest smoother alone, the DGEMM rate).
 
+The default run also reports the FP32 and BF16 variants of the same solve, the cycle of
+each precision as the solve replays it, the tensor-core FD kernel's and the stiffness
+apply's rooflines, and the oracle on the host cores (median of 3 solves with one thread
+and with every logical CPU allowed).
+
 --impl reference times the CPU oracle (FP64 NumPy/SciPy restatement of the method) on
 the host cores, one thread, on a bounded sample of the same workload family."""
 from __future__ import annotations
@@ -33,7 +38,8 @@ WORKLOAD_DESC = ("2D Poisson, K=16 bilinear patches of a 5x5 vertex grid on [0,4
                  "rhs = mass matrix times U(-1,1) spline coefficients (seed 2), FP64 PCG + V(1,1), tol 1e-8")
 ORACLE_SAMPLE = dict(nper=4, p=4, m=64, levels=7, seed=2)
 TOL = 1e-8
-# FP64 FMA pipe of one GB300: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+# FP64 FMA pipe of one GB300, nominal: 152 SMs x 2 FMA/clk/SM x 2 flop x 2.07 GHz (1.26 TFLOP/s);
+# the GPU runs measure it (fp64_peaks) and use the measured rate
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -41,18 +47,22 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def combined_roofline(prof, ms_step, precision, pk):
+# profile entries that are sub-accounts of the kernel classes (never summed with them)
+SUB_ACCOUNTS = ("tensor_exec", "tc_kernel")
+
+
+def combined_roofline(prof, ms_step, precision, pk, fp64_peak=None):
     """Roofline time of one solve: t_roof = sum over the kernel classes of
     max(algorithmic bytes / HBM bandwidth, flops / pipe peak).  The interior FD counts its
     issued tensor-core MMA FLOPs at the BF16 peak (its FMA-run levels are left out), every
     other class its flops on the FP64 pipe (FP32 pipes in the FP32/BF16 variants), so
     t_roof is a lower bound and frac = t_roof / measured time an upper bound on the
     fraction of the combined roofline the solve reaches."""
-    alu = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    alu = (fp64_peak or FP64_PEAK_TFLOPS) if precision == "fp64" else FP32_PEAK_TFLOPS
     tx = prof.get("tensor_exec", {}).get("flops", 0.0)
     per, t = {}, 0.0
     for k, v in prof.items():
-        if k == "tensor_exec":
+        if k in SUB_ACCOUNTS:
             continue
         tb = v["bytes"] / (pk["hbm_gbs"] * 1e9)
         tf = tx / (pk["bf16_tflops"] * 1e12) if (k == "interior_fd" and tx > 0) else v["flops"] / (alu * 1e12)
@@ -134,16 +144,44 @@ def oracle_sample_json():
     warm = int(os.environ.get("IGAMG_ORACLE_WARMUP", "0"))
     for _ in range(warm):
         solver.pcg(H, b, tol=TOL)
-    t0 = time.perf_counter()
-    its = []
+    times, cpu, its = [], [], []
     for _ in range(steps):
+        r0, t0 = os.times(), time.perf_counter()
         its.append(solver.pcg(H, b, tol=TOL).iters)
-    t = (time.perf_counter() - t0) / steps
-    return {"N": sp.N, "t_solve_s": t, "iters": its[-1], "t_setup_s": t_setup, "steps": steps}
+        r1, t1 = os.times(), time.perf_counter()
+        times.append(t1 - t0)
+        cpu.append((r1.user - r0.user) + (r1.system - r0.system))
+    t = statistics.median(times)
+    return {"N": sp.N, "t_solve_s": t, "t_runs_s": [round(x, 4) for x in times], "iters": its[-1],
+            "t_setup_s": t_setup, "steps": steps, "cores_used": round(sum(cpu) / max(sum(times), 1e-9), 2)}
 
 
-def run_oracle(steps=1, warmup=0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+def host_cpu():
+    """(logical CPUs of this host, CPU model name)."""
+    n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return n, model or "unknown"
+
+
+def run_oracle(steps=1, warmup=0, threads=1):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                IGAMG_ORACLE_STEPS=str(steps), IGAMG_ORACLE_WARMUP=str(warmup))
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle"], env=env,
                          stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1800)
@@ -152,10 +190,28 @@ def run_oracle(steps=1, warmup=0):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def sample_desc():
+def sample_desc(runs=1):
     s = ORACLE_SAMPLE
     return (f"same workload family at {s['m']} intervals per patch direction ({s['levels']} levels): "
-            f"one full PCG+V(1,1) solve to 1e-8, setup excluded, 1 thread")
+            f"full PCG+V(1,1) solves to 1e-8, setup excluded, median of {runs}")
+
+
+def cpu_baseline_json(runs=3):
+    """The oracle on the host cores: `runs` solves with one thread and `runs` with every
+    logical CPU allowed (BLAS/OpenMP threads); value = the better median.  `cores` is the
+    CPU time over the wall time of the solves (SciPy's sparse kernels run on one thread, so
+    allowing more threads changes little)."""
+    n, model = host_cpu()
+    one = run_oracle(runs, 0, 1)
+    allc = run_oracle(runs, 0, n)
+    best = one if one["t_solve_s"] <= allc["t_solve_s"] else allc
+    return {"value": round(best["N"] / best["t_solve_s"] / 1e6, 6), "unit": "MDOF/s",
+            "cores": max(1, round(best["cores_used"])), "kind": "oracle", "sample": sample_desc(runs),
+            "sample_dofs": best["N"], "sample_iters": best["iters"], "nproc": n, "cpu_model": model,
+            "one_thread": {"value": round(one["N"] / one["t_solve_s"] / 1e6, 6), "runs_s": one["t_runs_s"],
+                           "cores_used": one["cores_used"]},
+            "all_threads": {"threads": n, "value": round(allc["N"] / allc["t_solve_s"] / 1e6, 6),
+                            "runs_s": allc["t_runs_s"], "cores_used": allc["cores_used"]}}
 
 
 # ---------------------------------------------------------------- replicas over ranks
@@ -175,6 +231,69 @@ def combine_over_ranks(ms_total, dofs, tdist=None, device="cpu"):
 
 # ---------------------------------------------------------------- GPU arm
 
+def fp64_peaks():
+    """Measured FP64 rates of this GPU (the library's FMA-chain and m8n8k4 MMA probes) and
+    its SM count; the FMA rate is the FP64-pipe peak of the roofline fractions."""
+    from paper_1804_02539_gb300 import igamg
+    fma, sms = igamg.igamg_micro_fp64(0, 1 << 16)
+    mma, _ = igamg.igamg_micro_fp64(1, 1 << 14)
+    return {"fma_tflops": round(fma, 4), "mma_tflops": round(mma, 4), "sm_count": sms}
+
+
+def tensor_roofline(prof, pk, src):
+    """Roofline of the tensor-core FD kernel (class 7, all its launches): the BF16 MMA FLOPs
+    its tiles execute (class 6) over its event-timed launches, against the measured BF16
+    peak (sustained: the kernel is timed inside a long solve)."""
+    tc, tx = prof.get("tc_kernel", {}), prof.get("tensor_exec", {})
+    if not tc.get("launches") or not tc.get("ms"):
+        return None
+    ach = tx["flops"] / (tc["ms"] * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    return {"bound": "tensor", "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4), "peak_source": src + " (bf16_tflops_sustained)",
+            "kernel": "k_gemm_tc<7> (tensor-core FD contractions, every level and face it runs)",
+            "launches": tc["launches"], "avg_launch_ms": round(tc["ms"] / tc["launches"], 5),
+            "fp64_equiv_tflops": round(tc["flops"] / (tc["ms"] * 1e-3) / 1e12, 3),
+            "traffic": TC_TRAFFIC_PER_LAUNCH}
+
+
+# DRAM bytes (read + write) per launch of the finest-level tensor-core FD stage, from the ncu
+# capture summarised in profiles/ (None until the current kernel has been captured)
+TC_TRAFFIC_PER_LAUNCH = None
+
+
+def run_precision_variant(pr, prec_name, b, xr, dev, stream, steps, warmup):
+    """The FP32 or BF16 variant of the same solve (FP64 iterative refinement around the
+    low-precision PCG): MDOF/s, iterations, error against the FP64 GPU solution xr, and the
+    graph-replayed low-precision cycle against its algorithmic bytes."""
+    import torch
+    from paper_1804_02539_gb300 import igamg
+    opts = igamg.igamg_default_options()
+    opts.precision = {"fp32": igamg.IGAMG_FP32, "bf16": igamg.IGAMG_BF16}[prec_name]
+    ctx = igamg.Context(pr, opts, stream=stream)
+    N = ctx.num_dofs()
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        x.zero_()
+        ctx.solve(b, x, TOL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        x.zero_()
+        res, st = ctx.solve(b, x, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    err = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
+    ms_v, by_v = ctx.cycle_time(b, 10)
+    out = {"value": round(N / (ms * 1e-3) / 1e6, 4), "ms_per_step": round(ms, 3), "iters": res.iters,
+           "outer_iters": res.outer_iters, "relres": res.relres, "status": st, "rel_err_vs_fp64_solution": err,
+           "vcycle": {"ms": round(ms_v, 4), "algorithmic_gb": round(by_v / 1e9, 4)}}
+    ctx.free()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -188,6 +307,8 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as tdist
         tdist.init_process_group("nccl")
     stream = torch.cuda.Stream(device=dev)
+    pk, src = peaks()
+    f64 = fp64_peaks()
     pr = workloads.CONFIGS[args.workload]()
     prec = {"fp64": igamg.IGAMG_FP64, "fp32": igamg.IGAMG_FP32, "bf16": igamg.IGAMG_BF16}[args.precision]
     opts = igamg.igamg_default_options()
@@ -205,21 +326,23 @@ def run_ours(args, rank, world, local_rank):
             res, st = ctx.solve(b, x, TOL)
         iters = res.iters if args.warmup else None
         # pass 1 (untimed): per-class breakdown of one solve, every class timed with events
-        ctx.profile_enable(0x3F)
+        ctx.profile_enable(0xFF)
         x.zero_()
         ctx.solve(b, x, TOL)
         prof1 = ctx.profile_read()
-        dom = max(prof1, key=lambda k: prof1[k]["ms"])
-        dom_bit = 1 << igamg.Context.PROFILE_CLASSES.index(dom)
+        main = {k: v for k, v in prof1.items() if k not in SUB_ACCOUNTS}
+        dom = max(main, key=lambda k: main[k]["ms"])
+        # the timed solve's first step carries timing nodes around the dominant class and
+        # around the tensor-core kernel's launches
+        tbits = (1 << igamg.Context.PROFILE_CLASSES.index(dom)) | (1 << igamg.Context.TC_KERNEL_CLASS)
         ctx.profile_enable(0)
-        # both graph variants of the PCG iteration (plain, and with timing nodes around the
-        # dominant class) are captured before the timed region
-        ctx.profile_enable(dom_bit)
+        # both graph variants of the PCG iteration (plain, and with timing nodes) are
+        # captured before the timed region
+        ctx.profile_enable(tbits)
         x.zero_()
         ctx.solve(b, x, TOL)
         ctx.profile_enable(0)
-        # timed region: the solves as a user runs them (graph-replayed PCG iterations); the
-        # first timed solve carries CUDA-event nodes around the dominant class's launches
+        # timed region: the solves as a user runs them (graph-replayed PCG iterations)
         sampler = ClockSampler(local_rank)
         if dist:
             tdist.barrier()
@@ -230,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
         prof = None
         for step in range(args.steps):
             if step == 0:
-                ctx.profile_enable(dom_bit)
+                ctx.profile_enable(tbits)
             x.zero_()
             res, st = ctx.solve(b, x, TOL)
             if step == 0:
@@ -245,15 +368,16 @@ def run_ours(args, rank, world, local_rank):
         iters = res.iters
         outer = res.outer_iters
         relres = res.relres
-        err_vs_fp64 = None
-        if prec != igamg.IGAMG_FP64:
-            # error of the mixed-precision solution against the FP64 GPU solution (the FP64
-            # path is the one parity-tested against the FP64 oracle)
+        # the FP64 GPU solution to 1e-12: reference of the precision variants' errors
+        if prec == igamg.IGAMG_FP64:
+            xr = torch.zeros_like(x)
+            ctx.solve(b, xr, 1e-12)
+        else:
             ref = igamg.Context(pr, stream=stream)
             xr = torch.zeros_like(x)
             ref.solve(b, xr, 1e-12)
-            err_vs_fp64 = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
             ref.free()
+        err_vs_fp64 = None if prec == igamg.IGAMG_FP64 else float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
         ms_total, dofs_all = combine_over_ranks(ms_total, N, tdist if dist else None, dev)
         # end to end: host vectors, H2D + D2H inside the timed region
         e2e_s = float("nan")
@@ -270,57 +394,52 @@ def run_ours(args, rank, world, local_rank):
         setup_ms = res.t_setup_ms
         assemble_ms = res.t_assemble_ms
         dev_bytes = ctx.device_bytes()
-        # one FP64 cycle alone (igamg_precondition, launched one by one): its algorithmic
-        # bytes (all classes) against its time, the V-cycle's HBM roofline fraction
-        zc = torch.empty_like(b)
-        ctx.profile_enable(0x3F)
-        ctx.precondition(b, zc)
-        pv = ctx.profile_read()
-        ctx.profile_enable(0)
-        gb_v = sum(v["bytes"] for k, v in pv.items() if k != "tensor_exec") / 1e9
-        for _ in range(2):
-            ctx.precondition(b, zc)
-        torch.cuda.synchronize()
-        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        v0.record(stream)
-        for _ in range(10):
-            ctx.precondition(b, zc)
-        v1.record(stream)
-        torch.cuda.synchronize()
-        ms_v = v0.elapsed_time(v1) / 10
+        # one cycle of the working precision as the solve runs it (graph replay), against its
+        # algorithmic bytes: the V-cycle's HBM roofline fraction
+        ms_v, by_v = ctx.cycle_time(b, 10)
+        gb_v = by_v / 1e9
+        variants = {}
+        if rank == 0 and world == 1 and prec == igamg.IGAMG_FP64 and not args.no_variants:
+            for pn in ("fp32", "bf16"):
+                v = run_precision_variant(pr, pn, b, xr, dev, stream, max(2, min(args.steps, 5)), 2)
+                v["vcycle"]["achieved_gbs"] = round(v["vcycle"]["algorithmic_gb"] / (v["vcycle"]["ms"] * 1e-3), 1)
+                v["vcycle"]["hbm_frac"] = round(v["vcycle"]["achieved_gbs"] / pk["hbm_gbs"], 4)
+                variants[pn] = v
     ms_step = ms_total / args.steps
     value = dofs_all / (ms_step * 1e-3) / 1e6
-    # dominant kernel class (from the breakdown pass) and its roofline, timed in the timed region
-    d = prof[dom]
-    pk, src = peaks()
-    if dom in ("interior_fd", "interface", "coarse") or (dom == "apply" and args.precision == "fp64"):
-        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "kernel": dom, "traffic": None}
+    # rooflines: the tensor-core FD kernel (tensor pipe) and the stiffness apply (FP64 pipe,
+    # or HBM for FP32/BF16 bands); the top-level one is the kernel class with the larger time
+    troof = tensor_roofline(prof, pk, src)
+    ap = prof1["apply"]
+    if args.precision == "fp64":
+        ach = ap["flops"] / (ap["ms"] * 1e-3) / 1e12
+        aroof = {"bound": "alu", "achieved": round(ach, 4), "peak": f64["fma_tflops"], "unit": "TFLOP/s",
+                 "frac": round(ach / f64["fma_tflops"], 4),
+                 "peak_source": "measured in this run: FP64 FMA chains (igamg_micro_fp64 kind 0)",
+                 "kernel": "k_band_apply (stiffness apply / residual, every level)", "traffic": None}
     else:
-        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": src, "kernel": dom, "traffic": None}
-    roof["avg_launch_ms"] = round(d["ms"] / max(d["launches"], 1), 5)
-    tx = prof.get("tensor_exec", {}).get("flops", 0.0)
-    if dom == "interior_fd" and tx > 0:
-        # the same launches seen as tensor-core work: BF16 MMA FLOPs issued (digit-slice pairs
-        # and tile padding included) per second, against the measured dense BF16 peak
-        tach = tx / (d["ms"] * 1e-3) / 1e12
-        roof["tensor"] = {"achieved": round(tach, 2), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                          "frac": round(tach / pk["bf16_tflops"], 4), "peak_source": src,
-                          "note": "includes the interior-FD launches that run on the FMA pipes"}
-    roof["timing"] = ("CUDA-event nodes around each launch of the class in the first timed solve "
-                      f"({d['launches']} launches), on the stream each launch runs on; the interface class runs "
-                      "on a second stream concurrently with the interiors, so class times overlap")
+        ach = ap["bytes"] / (ap["ms"] * 1e-3) / 1e9
+        aroof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": src,
+                 "kernel": "k_band_apply (stiffness apply / residual, every level)", "traffic": None}
+    aroof["launches"] = ap["launches"]
+    aroof["avg_launch_ms"] = round(ap["ms"] / max(ap["launches"], 1), 5)
+    tc_ms = prof1.get("tc_kernel", {}).get("ms", 0.0)
+    if troof is not None and tc_ms >= ap["ms"]:
+        roof, other = troof, aroof
+    else:
+        roof, other = aroof, troof
+    roof["timing"] = ("CUDA-event nodes around each launch in the first timed solve, on the stream each launch "
+                      "runs on; the interface pieces run on a second stream concurrently with the interiors")
     breakdown = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"],
                      "gflop_per_step": round(v["flops"] / 1e9, 4),
-                     "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items() if k != "tensor_exec"}
-    launches = sum(v["launches"] for v in prof.values()) * args.steps
+                     "gbyte_per_step": round(v["bytes"] / 1e9, 4)} for k, v in prof1.items() if k not in SUB_ACCOUNTS}
+    breakdown["tc_kernel (within interior_fd + interface)"] = {
+        "ms_per_step": round(prof1["tc_kernel"]["ms"], 3), "launches_per_step": prof1["tc_kernel"]["launches"],
+        "mma_tflop_per_step": round(prof1["tensor_exec"]["flops"] / 1e12, 4)}
+    launches = sum(v["launches"] for k, v in prof.items() if k not in SUB_ACCOUNTS) * args.steps
     # whole-solve HBM view: algorithmic bytes of every class (bands, vectors, bases) per solve
-    gb = sum(v["bytes"] for k, v in prof1.items() if k != "tensor_exec") / 1e9
+    gb = sum(v["bytes"] for k, v in prof1.items() if k not in SUB_ACCOUNTS) / 1e9
     hbm = {"algorithmic_gb_per_step": round(gb, 3), "achieved_gbs": round(gb / (ms_step * 1e-3), 1),
            "peak": pk["hbm_gbs"], "frac": round(gb / (ms_step * 1e-3) / pk["hbm_gbs"], 4)}
     out = {
@@ -335,28 +454,29 @@ def run_ours(args, rank, world, local_rank):
                    "relres": relres, "tol": TOL, "l2": "inputs larger than L2 (operator bands 0.94 GB)",
                    "parallelism": f"replicas x{world}", "setup_ms": round(setup_ms, 1),
                    "device_gb": round(dev_bytes / 1e9, 3),
-                   "assemble_ms": round(assemble_ms, 1)},
+                   "assemble_ms": round(assemble_ms, 1), "sm_count": f64["sm_count"]},
         "e2e": {"value": None if e2e_s != e2e_s else round(N * world / e2e_s / 1e6, 4), "unit": "MDOF/s",
                 "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "roofline_other_kernel": other,
+        "fp64_peaks_measured": f64,
         "hbm_whole_solve": hbm,
         "vcycle": {"ms": round(ms_v, 4), "algorithmic_gb": round(gb_v, 4),
                    "achieved_gbs": round(gb_v / (ms_v * 1e-3), 1), "peak_gbs": pk["hbm_gbs"],
                    "hbm_frac": round(gb_v / (ms_v * 1e-3) / pk["hbm_gbs"], 4),
-                   "note": "one FP64 cycle via igamg_precondition, launched one by one (no graph)"},
+                   "note": f"one {args.precision} cycle (igamg_cycle_time), graph-replayed as inside the solve"},
         "clocks": clocks,
         "kernel_breakdown": breakdown,
     }
+    if variants:
+        out["precision_variants"] = variants
     try:  # the combined roofline of the whole solve (per-class bounds of the breakdown above)
-        out["roofline_whole_solve"] = combined_roofline(prof1, ms_step, args.precision, pk)
+        out["roofline_whole_solve"] = combined_roofline(prof1, ms_step, args.precision, pk, f64["fma_tflops"])
     except Exception as e:  # an optional field: never lose the bench line over it
         out["roofline_whole_solve"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        o = run_oracle(1, 0)
-        out["cpu_baseline"] = {"value": round(o["N"] / o["t_solve_s"] / 1e6, 6), "unit": "MDOF/s",
-                               "cores": 1, "kind": "oracle", "sample": sample_desc(),
-                               "sample_dofs": o["N"], "sample_iters": o["iters"]}
+        out["cpu_baseline"] = cpu_baseline_json(3)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.free()
@@ -376,8 +496,9 @@ def run_reference(args, rank):
            "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "sample": sample_desc(),
                       "sample_dofs": o["N"], "iters": o["iters"]},
-           "cpu_baseline": {"value": round(value, 6), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
-                            "sample": sample_desc()},
+           "cpu_baseline": {"value": round(value, 6), "unit": "MDOF/s", "cores": max(1, round(o["cores_used"])),
+                            "kind": "oracle", "sample": sample_desc(max(args.steps, 1)) + ", 1 thread",
+                            "nproc": host_cpu()[0], "cpu_model": host_cpu()[1]},
            "e2e": {"value": round(value, 6), "unit": "MDOF/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -549,7 +670,9 @@ def run_batch(args):
     ms_step = ms_total / args.steps
     Ntot = sum(Ns)
     value = Ntot / (ms_step * 1e-3) / 1e6
-    prof.pop("tensor_exec", None)
+    for k in SUB_ACCOUNTS:
+        prof.pop(k, None)
+    f64 = fp64_peaks()
     flops = sum(v["flops"] for v in prof.values())
     byts = sum(v["bytes"] for v in prof.values())
     ach = flops / (ms_step * 1e-3) / 1e12
@@ -568,9 +691,9 @@ def run_batch(args):
         "e2e": {"value": None if e2e is None else round(Ntot / e2e / 1e6, 4), "unit": "MDOF/s",
                 "h2d_bytes_per_step": 8 * Ntot, "d2h_bytes_per_step": 8 * Ntot},
         "gpu_launches": int(sum(v["launches"] for v in prof.values()) * args.steps),
-        "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                     "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+        "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": f64["fma_tflops"],
+                     "unit": "TFLOP/s", "frac": round(ach / f64["fma_tflops"], 4),
+                     "peak_source": "measured in this run: FP64 FMA chains (igamg_micro_fp64 kind 0)",
                      "kernel": "whole batch step (all classes, concurrent streams)",
                      "hbm_gbs": round(byts / (ms_step * 1e-3) / 1e9, 1), "hbm_peak": pk["hbm_gbs"],
                      "traffic": None},
@@ -730,9 +853,12 @@ def run_micro_fp64():
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
-    print(json.dumps({"micro": "fp64 dgemm", "n": n, "ms": round(best, 3),
-                      "tflops": round(2 * n ** 3 / (best * 1e-3) / 1e12, 4),
-                      "derived_fma_peak_tflops": round(FP64_PEAK_TFLOPS, 4)}), flush=True)
+    f64 = fp64_peaks()
+    print(json.dumps({"micro": "fp64", "dgemm_n": n, "dgemm_ms": round(best, 3),
+                      "dgemm_tflops": round(2 * n ** 3 / (best * 1e-3) / 1e12, 4),
+                      "fma_chain_tflops": f64["fma_tflops"], "mma_m8n8k4_tflops": f64["mma_tflops"],
+                      "sm_count": f64["sm_count"],
+                      "nominal_fma_peak_tflops": round(f64["sm_count"] * 2 * 2 * 2.07e9 / 1e12, 4)}), flush=True)
 
 
 def main():
@@ -754,6 +880,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32/BF16 lines of the default run")
     ap.add_argument("--workload", default=WORKLOAD, help="key of workloads.CONFIGS")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--batch", action="store_true", help="the 512-problem batched workload")

@@ -189,6 +189,15 @@ igamg_status igamg_prolong(igamg_ctx* ctx, int level, const double* uc_dev, doub
 igamg_status igamg_coarse_solve(igamg_ctx* ctx, const double* r_dev, double* x_dev);
 igamg_status igamg_precondition(igamg_ctx* ctx, const double* r_dev, double* z_dev);
 
+/* Measurement of the cycle of Algorithm 1 as the solve runs it: z = Multigrid(L, 0, r) in
+ * the context's working precision (FP64, or the FP32/BF16 inner cycle of the precision
+ * variant, fed with r converted to FP32), captured once as a CUDA graph and replayed `reps`
+ * times between CUDA events on the context's stream.  *ms = device time per cycle;
+ * *bytes (may be NULL) = the algorithmic bytes of one cycle (band coefficients, vectors and
+ * smoother bases read and written once, summed over the kernel classes of
+ * igamg_profile_read).  Overwrites the context's cycle work vectors; synchronises. */
+igamg_status igamg_cycle_time(igamg_ctx* ctx, const double* r_dev, int reps, double* ms, double* bytes);
+
 /* Fast-diagonalisation apply of one tensor-product local smoother (Sec. 3: the
  * patch-interior subspace-corrected mass smoother in diagonalised form, L_T^{-1} =
  * (U0 x U1) diag(Dinv) (U0 x U1)^T), the core contraction of every smoothing step:
@@ -236,14 +245,24 @@ igamg_status igamg_fd_apply_noalloc(int n0, int n1, const double* U0, const doub
  * Classes: 0 stiffness apply/residual, 1 patch-interior smoother contractions, 2 interface
  * smoothers (gather, edge contractions, scatter), 3 transfers, 4 coarse solve, 5 vector
  * operations (reductions, PCG updates, conversions); class 6 counts no launches and holds in
- * `flops` the BF16 tensor-core FLOPs the class-1 tensor-core contractions execute (digit
- * pairs and tile padding included).  `enable` is a bit mask of the classes whose launches
- * are bracketed by CUDA events on the context's stream (bit c = class c; 0 disables); the
+ * `flops` the BF16 tensor-core FLOPs the tensor-core contractions execute (digit-slice
+ * pairs and tile padding included; every tile of such a launch runs on the tensor cores);
+ * class 7 is a sub-account of classes 1 and 2: the launches of the tensor-core contraction
+ * kernel alone (their count, time and FP64 GEMM FLOPs).  `enable` is a bit mask of the
+ * classes whose launches are bracketed by CUDA events on the launching stream (bit c =
+ * class c; 0 disables); the
  * PCG iterations then replay a graph variant with event-record nodes (captured once per
  * mask).  Enabling resets the counters.  Reading synchronises the stream. */
 igamg_status igamg_profile_enable(igamg_ctx* ctx, int enable);
 igamg_status igamg_profile_read(igamg_ctx* ctx, int cls, int64_t* launches, double* ms,
                                 double* flops, double* bytes);
+
+/* FP64 throughput of the current device, the denominator of FP64 roofline fractions (not a
+ * step of the method): kind 0 = FP64 FMA pipe (dependent FMA chains, 8 per thread), kind 1 =
+ * FP64 tensor-core MMAs (mma.sync m8n8k4), `iters` iterations per chain over 4 blocks of
+ * 256 threads per SM, timed with CUDA events after a warm-up.  *tflops = the rate;
+ * *sm_count (may be NULL) = the device's multiprocessor count.  Synchronises the device. */
+igamg_status igamg_micro_fp64(int kind, int64_t iters, double* tflops, int* sm_count);
 
 /* Synchronises the context's stream. */
 igamg_status igamg_sync(igamg_ctx* ctx);

@@ -13,7 +13,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libigamg.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["kernels.cu", "igamg.cu", "noalloc.cu", "tc_gemm.cu", "batch.cu", "server.cu"]
+CU_SOURCES = ["kernels.cu", "igamg.cu", "noalloc.cu", "tc_gemm.cu", "batch.cu", "server.cu", "micro.cu"]
 CPP_SOURCES = ["host_math.cpp", "topology.cpp"]
 
 

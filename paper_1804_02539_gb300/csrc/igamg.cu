@@ -193,18 +193,18 @@ struct igamg_ctx {
   std::vector<std::tuple<double*, int64_t, bool>> reg;
   std::vector<int64_t> band_count;                         // band doubles per level
   std::map<std::tuple<int, int>, std::pair<double*, double*>> kron_1d;  // (m, p) -> banded K, M
-  struct SliceSrc { const double* U; int n, tr; };
-  std::map<const void*, SliceSrc> slice_src;  // digit slices -> the FP64 basis they cut
   int* tc_err = nullptr;                                   // device flag: tensor-core wait timed out
   // PCG iteration body replayed as a CUDA graph (index 0 FP64, 1 FP32 inner), captured on a
   // private stream (the legacy stream cannot capture) and launched on `stream`
   // slot 2 * index + (1 while profiling): the plain graph and the one with timing nodes
   // are kept side by side, so switching the profiler between solves costs no capture
-  cudaGraphExec_t iter_graph[4] = {nullptr, nullptr, nullptr, nullptr};
-  unsigned graph_key[4] = {0, 0, 0, 0};                   // profiling mode it was captured in
-  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> graph_ev[4];  // timing nodes inside it
-  int64_t graph_launch[4][8] = {};                        // per-replay launch accounting
-  double graph_flops[4][8] = {}, graph_bytes[4][8] = {};
+  // (index 2 FP64 and 3 low-precision cycle alone, for igamg_cycle_time)
+  static constexpr int kGraphSlots = 8;
+  cudaGraphExec_t iter_graph[kGraphSlots] = {};
+  unsigned graph_key[kGraphSlots] = {};                   // profiling mode it was captured in
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> graph_ev[kGraphSlots];  // timing nodes inside it
+  int64_t graph_launch[kGraphSlots][8] = {};              // per-replay launch accounting
+  double graph_flops[kGraphSlots][8] = {}, graph_bytes[kGraphSlots][8] = {};
   cudaStream_t cap_stream = nullptr;
   // the interface pieces of a smoothing step run on a second stream, concurrently with the
   // patch interiors (disjoint pieces, Eq. additive); forked and joined by events
@@ -270,7 +270,8 @@ double* reg_work(igamg_ctx* c, double* p, int64_t n) {
   return p;
 }
 
-enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5, CLS_TENSOR_EXEC = 6 };
+enum { CLS_APPLY = 0, CLS_FD = 1, CLS_IFACE = 2, CLS_TRANSFER = 3, CLS_COARSE = 4, CLS_VECTOR = 5, CLS_TENSOR_EXEC = 6,
+       CLS_TC_KERNEL = 7 };
 
 cudaEvent_t prof_event(igamg_ctx* c) {
   if (!c->ev_free.empty()) {
@@ -283,17 +284,26 @@ cudaEvent_t prof_event(igamg_ctx* c) {
   return e;
 }
 
-// Brackets one launch of class `cls` with algorithmic work (flops, bytes).
+// Brackets one launch of class `cls` (and of the sub-account `sub`, e.g. the tensor-core
+// kernel inside the FD classes, or -1) with algorithmic work (flops, bytes).  The event pair
+// is recorded when either class is timed; its time goes to the classes that are.
 struct ProfScope {
   igamg_ctx* c;
-  int cls;
+  int code = 0xFF;  // timed main class (low 4 bits) and sub-account (high 4 bits); 15 = none
   cudaEvent_t a = nullptr;
-  ProfScope(igamg_ctx* c_, int cls_, double flops, double bytes, int launches = 1) : c(c_), cls(cls_) {
+  ProfScope(igamg_ctx* c_, int cls, double flops, double bytes, int launches = 1, int sub = -1) : c(c_) {
     if (!c->prof) return;
     c->prof_launch[cls] += launches;
     c->prof_flops[cls] += flops;
     c->prof_bytes[cls] += bytes;
-    if (!((c->prof_mask >> cls) & 1u)) return;
+    if (sub >= 0) {
+      c->prof_launch[sub] += launches;
+      c->prof_flops[sub] += flops;
+      c->prof_bytes[sub] += bytes;
+    }
+    const bool tm = (c->prof_mask >> cls) & 1u, ts = sub >= 0 && ((c->prof_mask >> sub) & 1u);
+    if (!tm && !ts) return;
+    code = (tm ? cls : 15) | ((ts ? sub : 15) << 4);
     a = prof_event(c);
     record(a);
   }
@@ -306,17 +316,22 @@ struct ProfScope {
     if (!a) return;
     cudaEvent_t b = prof_event(c);
     record(b);
-    if (c->capturing >= 0) c->graph_ev[c->capturing].emplace_back(cls, a, b);
-    else c->ev_open.emplace_back(cls, a, b);
+    if (c->capturing >= 0) c->graph_ev[c->capturing].emplace_back(code, a, b);
+    else c->ev_open.emplace_back(code, a, b);
   }
 };
+
+void prof_add_ms(igamg_ctx* c, int code, float ms) {
+  if ((code & 15) != 15) c->prof_ms[code & 15] += ms;
+  if ((code >> 4) != 15) c->prof_ms[code >> 4] += ms;
+}
 
 // Folds completed event pairs into the per-class totals (stream must be synchronised).
 void prof_collect(igamg_ctx* c) {
   for (auto& t : c->ev_open) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
-    c->prof_ms[std::get<0>(t)] += ms;
+    prof_add_ms(c, std::get<0>(t), ms);
     c->ev_free.push_back(std::get<1>(t));
     c->ev_free.push_back(std::get<2>(t));
   }
@@ -325,7 +340,7 @@ void prof_collect(igamg_ctx* c) {
     for (auto& t : c->graph_ev[c->pending_graph]) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t)));
-      c->prof_ms[std::get<0>(t)] += ms;
+      prof_add_ms(c, std::get<0>(t), ms);
     }
     c->pending_graph = -1;
   }
@@ -427,16 +442,7 @@ void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, do
 }
 
 template <class T>
-void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v0) {
-  std::vector<TcDesc<T, T>> v = v0;
-  if constexpr (std::is_same<T, double>::value)
-    for (auto& d : v) {  // the FP64 basis behind the slices, for remainder row tiles
-      auto it = c->slice_src.find(d.Aslices);
-      if (it == c->slice_src.end()) continue;
-      d.Af = it->second.U;
-      d.lda = it->second.n;
-      d.tra = it->second.tr;
-    }
+void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
   ts.h = v;
   ts.batch = int(v.size());
   ts.maxM = ts.maxN = 0;
@@ -454,8 +460,8 @@ void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v0) {
 template <class T>
 void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha, int cls = CLS_FD) {
   if (!ts.batch) return;
-  if (c->prof && cls == CLS_FD) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
-  ProfScope ps(c, cls, ts.flops, 0.0);
+  if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
+  ProfScope ps(c, cls, ts.flops, 0.0, 1, CLS_TC_KERNEL);
   if constexpr (std::is_same<T, double>::value)
     CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err)));
   else
@@ -822,7 +828,6 @@ void build_levels(igamg_ctx* c) {
           c->tc_bf16_twin[da] = c->mem.upload(s1, s);
         }
         sl[key] = Sl{da, c->mem.upload(ev, s), tc_kblocks(n)};
-        c->slice_src[da] = igamg_ctx::SliceSrc{S->dU, n, tr};
       }
       return sl[key];
     };
@@ -2126,8 +2131,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
           auto it = c->tc_bf16_twin.find(d.Aslices);
           if (it == c->tc_bf16_twin.end()) throw Fail{IGAMG_ERR_NUMERIC, "missing BF16 basis slices"};
           v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
-                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K,
-                                            tr(d.Af), d.lda, d.tra});
+                                            d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
         }
         set_tc(c, out, v);
       };
@@ -2444,6 +2448,57 @@ igamg_status igamg_precondition(igamg_ctx* c, const double* r, double* z) {
   });
 }
 
+igamg_status igamg_cycle_time(igamg_ctx* c, const double* r, int reps, double* ms, double* bytes) {
+  return guarded(c, [&]() {
+    if (!r || !ms || reps < 1) throw Fail{IGAMG_ERR_ARG, "bad arguments"};
+    const int Lf = int(c->lv.size()) - 1;
+    Level& L = c->lv[Lf];
+    cudaStream_t s = c->stream;
+    const bool low = c->low;
+    to_dist(c, Lf, r, L.n64.F);
+    if (low) {
+      CK(launch_canonicalize<double>(s, L.n_if, L.if_ptr, L.if_idx, L.n64.F));
+      CK(launch_convert_f64_f32(s, L.topo.T, L.n64.F, 1.0, L.n32.F));
+    }
+    auto cycle = [&]() {
+      if (low) precondition<float>(c);
+      else precondition<double>(c);
+    };
+    // algorithmic bytes of one cycle: one cycle launched one by one with the counters on
+    const bool prof0 = c->prof;
+    const unsigned mask0 = c->prof_mask;
+    double b0[8];
+    std::copy(c->prof_bytes, c->prof_bytes + 8, b0);
+    c->prof = true;
+    c->prof_mask = 0;
+    cycle();
+    double by = 0.0;
+    for (int k = 0; k < 6; ++k) by += c->prof_bytes[k] - b0[k];
+    std::copy(b0, b0 + 8, c->prof_bytes);
+    c->prof = false;
+    // the cycle as the solve runs it: captured once as a graph, replayed
+    graph_run(c, low ? 3 : 2, cycle);
+    graph_run(c, low ? 3 : 2, cycle);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) graph_run(c, low ? 3 : 2, cycle);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = prof0;
+    c->prof_mask = mask0;
+    check_tc(c);
+    *ms = double(t) / reps;
+    if (bytes) *bytes = by;
+    return IGAMG_OK;
+  });
+}
+
 igamg_status igamg_rhs_from_coefs(igamg_ctx* c, const double* coef, double* rhs) {
   return guarded(c, [&]() -> igamg_status {
     if (!coef || !rhs) throw Fail{IGAMG_ERR_ARG, "NULL vector"};
@@ -2563,7 +2618,7 @@ igamg_status igamg_free(igamg_ctx* c) {
   if (!c) return IGAMG_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (int gi = 0; gi < 4; ++gi) {
+  for (int gi = 0; gi < igamg_ctx::kGraphSlots; ++gi) {
     if (c->iter_graph[gi]) cudaGraphExecDestroy(c->iter_graph[gi]);
     for (auto& t : c->graph_ev[gi]) {
       cudaEventDestroy(std::get<1>(t));

@@ -7,25 +7,40 @@
 // S == 7: FP64-accurate product from BF16 digit slices (the error-free splitting scheme of
 //   Ozaki et al.): every row i of A is written as 2^{sigma_i} sum_s A_s 2^{-7s} and every
 //   column j of B as 2^{tau_j} sum_t B_t 2^{-7t}, with integer digits |A_s|, |B_t| <= 127
-//   (exact in BF16).  A digit product summed over K <= 1023 stays below 2^24, so each
-//   tcgen05.mma of one slice pair is exact in FP32; the pairs with s + t = q accumulate
-//   into TMEM accumulator q, and the epilogue forms
+//   (exact in BF16).  Every product A_s B_t is exact in FP32 (|A_s B_t| < 2^14); the pairs
+//   with s + t = q accumulate into TMEM accumulator q, and the epilogue forms
 //       C_ij = 2^{sigma_i + tau_j} sum_{q=2..S+1} D_q(i,j) 2^{-7q}
-//   in FP64 (pairs with s + t > S + 1 are below 2^{-56} relative and are dropped).
+//   (pairs with s + t > S + 1 are below 2^{-49} of the row and column maxima and are
+//   dropped).  An accumulator stays an exact integer while its partial sums are below
+//   2^24, which the worst case guarantees for (q - 1) K 127^2 < 2^24; beyond that FP32
+//   rounds by at most 2^-24 of the partial sum, i.e. by < 2^{-24 - 7(q-2)} relative to the
+//   leading diagonal's scale, which for K <= kTcMaxK stays at or below the 2^-49 digit
+//   truncation for the diagonals where it can occur (q >= 5 at K > 255).
 //
-// The epilogue recombines the diagonals exactly in 64-bit integers (units of 2^-49 of the
-// row and column scales), converts once to FP64 and applies the smoother's epilogue.
+// The epilogue recombines the diagonals in 64-bit integers (units of 2^-49 of the row and
+// column scales), converts once to FP64 and applies the smoother's epilogue.
 //
-// Block: 512 threads (16 warps, 4 per TMEM lane quarter), one 128 x 64 output tile.  A
-// pre-pass finds the column exponents of the tile's 64-column panel.  Then a two-stage
-// pipeline over K blocks of 32: A's slices, pre-arranged on the host in the canonical
-// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes; LBO = 128 B between core
-// matrices along K, SBO = 512 B between 8-row groups), arrive by one bulk TMA copy per
-// stage; B's digits are produced by all threads from register-prefetched operands; one
-// thread issues the MMAs of a block and commits them to the stage's mbarrier while the
-// others stage the next block.  Every mbarrier wait is bounded.  Tiles with at most 32
-// valid rows or columns skip the tensor cores and use FMAs on the FP64 basis; such tiles
-// are scheduled after the full ones.
+// Kernel structure (persistent, warp-specialised).  One CTA per SM walks the product's
+// tiles (128 rows of A x TBN columns of B, over every descriptor of the batch) with a
+// static stride; per tile:
+//   warp 0        bulk TMA copies of A's pre-sliced K blocks ([S][128 x 32] in the
+//                 canonical no-swizzle K-major core-matrix layout) into a ring of stages;
+//   warps 2..9    the B producers: per tile the column exponents tau_j (each warp owns 4
+//                 columns and reduces over K with shuffles), then per K block the digit
+//                 planes of B written into the same ring (register-prefetched loads);
+//   warp 1        one thread issues the MMAs: for digit slice A_s, ONE MMA with the digit
+//                 planes B_1..B_{8-s} stacked along N (N = (8 - s) TBN), whose output
+//                 columns are exactly the accumulators of diagonals s+1 .. 8, which are
+//                 contiguous in TMEM (7 MMAs per 16-wide K step instead of 28; each slice
+//                 of A is read from shared memory once per K step);
+//   warps 10..13  the epilogue, one warp per TMEM lane quarter.
+// Two accumulator sets in TMEM (2 x 7 x 32 of the 512 columns) let the epilogue of one tile
+// run while the MMAs of the next are issued.  Every tile runs on the tensor cores,
+// including the ragged remainders of M, N and K (padded with zero digits).
+// Synchronisation is by mbarriers only (no block barrier inside the tile loop); every wait
+// is bounded and a timeout is decided warp-uniformly, sets a shared abort flag and the
+// device error flag, and every role then leaves its loop; the MMA thread waits (bounded)
+// for its last MMAs and the TMA thread for its last copies before the TMEM is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -33,6 +48,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
@@ -40,36 +56,86 @@
 namespace igamg {
 
 namespace {
-constexpr int TBM = 128, TBN = 64, TBK = 32;  // K block of one pipeline stage
-constexpr int NT = 512;  // threads per CTA: 16 warps, 4 per TMEM lane quarter
+constexpr int TBM = 128, TBK = 32;  // rows of a tile; K block of one pipeline stage
+constexpr int NT = 448;             // 14 warps: TMA, MMA, 8 producers, 4 epilogue
+constexpr int kProdThread0 = 64, kNumProd = 256, kEpiThread0 = 320;
+constexpr int kMaxDescs = 512;      // descriptors of one launch (tile prefix in shared memory)
 constexpr int WAIT_LIMIT = 1 << 24;
-constexpr int kLightRows = 32;  // a tile with this few valid rows or columns skips the tensor cores
+
+template <int S> struct TcCfg;
+template <> struct TcCfg<7> {
+  static constexpr int TBN = 32;       // columns of a tile
+  static constexpr int ACC = 7 * 32;   // TMEM columns of one accumulator set (7 diagonals)
+  static constexpr uint32_t TCOLS = 512;
+  static constexpr int NST = 3;        // pipeline stages
+};
+template <> struct TcCfg<1> {
+  static constexpr int TBN = 128;
+  static constexpr int ACC = 128;
+  static constexpr uint32_t TCOLS = 256;
+  static constexpr int NST = 4;
+};
+
+template <int S>
+constexpr size_t tc_smem_bytes() {
+  using CF = TcCfg<S>;
+  return size_t(CF::NST) * S * (TBM + CF::TBN) * TBK * 2  // A and B stages (BF16)
+         + 2 * CF::TBN * 4                                 // column exponents, two sets
+         + (kMaxDescs + 2) * 4                             // tile prefix
+         + (4 * CF::NST + 8) * 8                           // mbarriers
+         + 16                                              // TMEM slot, abort flag
+         + 1024;                                           // alignment
+}
 
 __device__ __forceinline__ uint32_t sptr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= uint64_t((saddr >> 4) & 0x3FFF);
-  d |= uint64_t(128 >> 4) << 16;   // leading byte offset: next core matrix along K
+  d |= uint64_t(128 >> 4) << 16;              // leading byte offset: next core matrix along K
   d |= uint64_t((TBK / 8 * 128) >> 4) << 32;  // stride byte offset: next 8-row group
-  d |= uint64_t(1) << 46;          // descriptor version
+  d |= uint64_t(1) << 46;                     // descriptor version
   return d;
 }
 
-// element (r, k) of a [rows x 64] K-major no-swizzle tile
+// element (r, k) of a [rows x 32] K-major no-swizzle tile
 __device__ __forceinline__ int core_off(int r, int k) { return ((r >> 3) * (TBK / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
                :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (int it = 0; it < WAIT_LIMIT && !done; ++it)
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(mbar), "r"(phase));
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
   return done != 0;
+}
+// Bounded wait for the completion of phase `phase` of an mbarrier; gives up early when
+// another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, const volatile int* abort) {
+  for (int it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try(mbar, phase)) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
+  }
+  return false;
+}
+
+// Bounded wait for work this thread issued itself (its copies or MMAs), which completes
+// whatever the other roles do: it does not give up on the abort flag.
+__device__ __forceinline__ bool mbar_wait_own(uint32_t mbar, uint32_t phase) {
+  for (int it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try(mbar, phase)) return true;
+  return false;
 }
 
 __device__ __forceinline__ void tmem_ld16_issue(uint32_t ta, uint32_t* r) {
@@ -118,311 +184,413 @@ __device__ __forceinline__ void digits_f64(double x, int tau, float* dig) {
     dig[s - 1] = neg ? -d : d;
   }
 }
+
+// The descriptor q holding tile t (tile prefix `start` of `batch` descriptors): the last q
+// with start[q] <= t (descriptors without tiles are skipped).
+__device__ __forceinline__ int tile_desc(const int* start, int batch, int t) {
+  int lo = 0, hi = batch;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class TB>
+__device__ __forceinline__ TB ld_b(const TB* B, int ldb, int tb, int k, int n) {
+  return __ldg(tb ? B + int64_t(n) * ldb + k : B + int64_t(k) * ldb + n);
+}
 }  // namespace
 
 template <int S, class TB, class TC>
-__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int epi, TC alpha,
-                                                 int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  // two pipeline stages, each [S][128 x TBK] of A and [S][64 x TBK] of B
-  constexpr int ASZ = S * TBM * TBK, BSZ = S * TBN * TBK;
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int batch, int epi,
+                                                 TC alpha, int* __restrict__ err) {
+  using CF = TcCfg<S>;
+  constexpr int TBN = CF::TBN, NST = CF::NST, ACC = CF::ACC;
+  constexpr int ASZ = S * TBM * TBK, BSZ = S * TBN * TBK;  // BF16 elements of one stage
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Bs = As + 2 * ASZ;
-  int* tauS = reinterpret_cast<int*>(Bs + 2 * BSZ);                           // [64]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tauS + TBN);                    // [2] MMAs of a stage done
-  uint64_t* abar = mbar + 2;                                                  // [2] A bulk copy landed
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
-  const TcDesc<TB, TC> d = descs[blockIdx.x];
-  // tile blockIdx.y of this product; the tiles that run on the tensor cores come first, so
-  // that (with the batch as the fastest grid dimension) they fill the first waves and the
-  // light tiles (few valid rows or columns, FMA path) the remainder
-  const int tiles_m = (d.M + TBM - 1) / TBM, tiles_n = (d.N + TBN - 1) / TBN;
-  int t = blockIdx.y;
-  if (t >= tiles_m * tiles_n) return;
-  int Mh = tiles_m, Nh = tiles_n;
-  if (d.Af) {
-    Mh = d.M / TBM + (d.M % TBM > kLightRows ? 1 : 0);
-    Nh = d.N / TBN + (d.N % TBN > kLightRows ? 1 : 0);
-  }
-  int mt, nt;
-  if (t < Mh * Nh) {
-    mt = t / Nh;
-    nt = t % Nh;
-  } else {  // the k-th light tile in row-major order
-    int k = t - Mh * Nh;
-    mt = 0;
-    nt = 0;
-    for (int q = 0; q < tiles_m * tiles_n; ++q) {
-      const int a = q / tiles_n, b = q % tiles_n;
-      if (a < Mh && b < Nh) continue;
-      if (k-- == 0) { mt = a; nt = b; break; }
-    }
-  }
-  const int i0 = mt * TBM, j0 = nt * TBN;
+  __nv_bfloat16* Bs = As + NST * ASZ;
+  int* tauS = reinterpret_cast<int*>(Bs + NST * BSZ);  // [2][TBN]
+  int* tstart = tauS + 2 * TBN;                         // [batch + 1]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tstart + kMaxDescs + 2);
+  uint64_t* abar = bars;             // [NST] A copy landed (expect_tx)
+  uint64_t* bfull = abar + NST;      // [NST] B digits staged (kNumProd arrivals)
+  uint64_t* empty = bfull + NST;     // [NST] MMAs reading the stage done (commit)
+  uint64_t* accf = empty + NST;      // [2] accumulator set complete (commit)
+  uint64_t* acce = accf + 2;         // [2] accumulator set read by the epilogue (128 arrivals)
+  uint64_t* taur = acce + 2;         // [2] column exponents written (kNumProd arrivals)
+  uint64_t* fin = taur + 2;          // [1] every MMA of this CTA done (commit)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rows = min(TBM, d.M - i0), cols = min(TBN, d.N - j0);
-  if (d.Af && (rows <= kLightRows || cols <= kLightRows)) {
-    // a tile of a few remainder rows or columns: plain FMAs over K instead of MMAs on a
-    // mostly empty 128 x 64 tile (this also keeps such tiles out of the waves of full ones)
-    for (int o = tid; o < rows * cols; o += NT) {
-      const int gi = i0 + o / cols, gj = j0 + o % cols;
-      TC acc = TC(0);
-      for (int k = 0; k < d.K; ++k) {
-        const TC a = TC(d.tra ? d.Af[int64_t(k) * d.lda + gi] : d.Af[int64_t(gi) * d.lda + k]);
-        const TC b = TC(d.tb ? d.B[int64_t(gj) * d.ldb + k] : d.B[int64_t(k) * d.ldb + gj]);
-        acc = fma(a, b, acc);
-      }
-      TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
-      switch (epi) {
-        case EPI_MUL: *cp = acc * d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]; break;
-        case EPI_ASSIGN: *cp = alpha * acc; break;
-        case EPI_ADD: *cp = fma(alpha, acc, *cp); break;
-        default: *cp = acc;
-      }
-    }
-    return;
-  }
-  const int quarter = warp & 3, colgrp = warp >> 2;  // TMEM lanes 32*quarter.., columns 16*colgrp..
-  constexpr int NACC = S == 1 ? 1 : S;      // accumulators: diagonals q = 2..S+1
-  constexpr uint32_t TCOLS = S == 1 ? 64 : 512;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sptr(tslot)), "r"(TCOLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sptr(mbar + q)), "r"(1));
+    int acc = 0;
+    for (int q = 0; q < batch; ++q) {
+      tstart[q] = acc;
+      const TcDesc<TB, TC>& d = descs[q];
+      if (d.M > 0 && d.N > 0 && d.K > 0) acc += ((d.M + TBM - 1) / TBM) * ((d.N + TBN - 1) / TBN);
+    }
+    tstart[batch] = acc;
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(sptr(abar + i), 1);
+      mbar_init(sptr(bfull + i), kNumProd);
+      mbar_init(sptr(empty + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(sptr(accf + i), 1);
+      mbar_init(sptr(acce + i), 128);
+      mbar_init(sptr(taur + i), kNumProd);
+    }
+    mbar_init(sptr(fin), 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // column scales of B: tau_j = 1 + the largest exponent in column j of op(B) over all of K
-  // (bit extraction; zero columns give -1022).  Every CTA of a column panel reads the panel
-  // once here (L2-resident for the panel's other CTAs), eight loads in flight per thread.
-  if constexpr (S > 1) {
-    if (tid < TBN) tauS[tid] = 0;  // biased exponent field while reducing
-    __syncthreads();
-    int n, kq;
-    if (d.tb) { n = tid >> 3; kq = tid & 7; }  // 8 lanes along k of one column
-    else { n = tid & 63; kq = tid >> 6; }      // 32 lanes along the columns
-    const int gn = j0 + n;
-    int emax = 0;
-    if (gn < d.N) {
-      for (int k0 = kq; k0 < d.K; k0 += 64) {
-        TB v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = k0 + 8 * u;
-          v[u] = k < d.K ? __ldg(d.tb ? d.B + int64_t(gn) * d.ldb + k : d.B + int64_t(k) * d.ldb + gn) : TB(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          emax = max(emax, int((uint64_t(__double_as_longlong(double(v[u]))) >> 52) & 0x7FF));
-      }
-    }
-    atomicMax(&tauS[n], emax);
-    __syncthreads();
-    if (tid < TBN) tauS[tid] = tauS[tid] ? tauS[tid] - 1023 + 1 : -1022;
+  __syncthreads();
+  const int total = tstart[batch];
+  if (int(blockIdx.x) >= total) return;  // block-uniform, before any TMEM is held
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sptr(tslot)), "r"(CF::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBN >> 3) << 17) | (uint32_t(TBM >> 4) << 24);
-  const int nkb = (d.K + TBK - 1) / TBK;
-  // B staging: thread -> (column bn, 4 consecutive k at bk).  Bits of tid, high to low:
-  // bn / 8 (3), k chunk of 8 (2), bn % 8 (3), half chunk (1).  A half-warp stores 16
-  // distinct 8-byte pieces of one 128-byte core matrix per digit plane (conflict-free), and
-  // the loads are 32-byte sectors fully used for either storage order of B.
-  const int bn = ((tid >> 6) << 3) | ((tid >> 1) & 7);
-  const int bk = ((tid >> 4) & 3) * 8 + (tid & 1) * 4;
-  const int gj = j0 + bn;
-  TB xv[4];
-  auto load_b = [&](int k0) {
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const int gk = k0 + bk + kk;
-      xv[kk] = (gj < d.N && gk < d.K) ? __ldg(d.tb ? d.B + int64_t(gj) * d.ldb + gk : d.B + int64_t(gk) * d.ldb + gj)
-                                      : TB(0);
-    }
+  auto fail = [&](int code) {
+    *abort_flag = 1;
+    atomicExch(err, code);
   };
-  // digit planes of the registers into stage st of B
-  auto stage_b = [&](int st) {
-    uint32_t pk[S][2];
-#pragma unroll
-    for (int kk = 0; kk < 4; kk += 2) {
-      float d0[S], d1[S];
-      if constexpr (S == 1) {
-        d0[0] = float(xv[kk]);
-        d1[0] = float(xv[kk + 1]);
-      } else {
-        digits_f64<S>(double(xv[kk]), tauS[bn], d0);
-        digits_f64<S>(double(xv[kk + 1]), tauS[bn], d1);
+
+  if (warp == 0) {
+    // ---------------- A: one bulk copy of the pre-sliced [S][128 x 32] block per stage
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int q = tile_desc(tstart, batch, t);
+        const TcDesc<TB, TC>& d = descs[q];
+        const int tiles_n = (d.N + TBN - 1) / TBN, mt = (t - tstart[q]) / tiles_n;
+        const int nkb = (d.K + TBK - 1) / TBK;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int st = int(g % NST);
+          if (g >= NST && !mbar_wait(sptr(empty + st), (g / NST - 1) & 1u, abort_flag)) {
+            fail(1);
+            ok = false;
+            break;
+          }
+          const uint32_t bytes = uint32_t(ASZ) * 2u;
+          const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar + st)), "r"(bytes));
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(sptr(As + st * ASZ)), "l"(src), "r"(bytes), "r"(sptr(abar + st)) : "memory");
+        }
       }
-#pragma unroll
-      for (int q = 0; q < S; ++q) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(d0[q], d1[q]);
-        pk[q][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
-      }
+      // the copies of the last stages (the latest use of each) have landed before the CTA
+      // may exit, also after an abort
+      for (uint32_t h = g > NST ? g - NST : 0; h < g; ++h) mbar_wait_own(sptr(abar + h % NST), (h / NST) & 1u);
     }
-    const int off = core_off(bn, bk);
-#pragma unroll
-    for (int q = 0; q < S; ++q)
-      *reinterpret_cast<uint2*>(Bs + st * BSZ + q * TBN * TBK + off) = make_uint2(pk[q][0], pk[q][1]);
-  };
-  // A: the pre-sliced block [S][128 x TBK] is contiguous: one bulk (TMA) copy per stage
-  auto copy_a = [&](int kb, int st) {
-    const uint32_t bytes = uint32_t(ASZ) * sizeof(__nv_bfloat16);
-    const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar + st)), "r"(bytes));
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(sptr(As + st * ASZ)), "l"(src), "r"(bytes), "r"(sptr(abar + st)) : "memory");
-  };
-  bool ok = true;
-  // prologue: stage 0 holds block 0; the registers hold block 1
-  if (tid == 0) copy_a(0, 0);
-  load_b(0);
-  stage_b(0);
-  if (nkb > 1) load_b(TBK);
-  for (int kb = 0; kb < nkb && ok; ++kb) {
-    const int st = kb & 1;
-    const uint32_t par = uint32_t(kb >> 1) & 1u;  // completion count parity of stage st's barriers
-    if (!mbar_wait(sptr(abar + st), par)) {
-      ok = false;
-      if (tid == 0) atomicExch(err, 2);
-      break;
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const bool two = d.K - kb * TBK > 16;  // second 16-wide K step of this block present
-      const uint64_t a0 = smem_desc(sptr(As + st * ASZ)), b0 = smem_desc(sptr(Bs + st * BSZ));
-#pragma unroll
-      for (int s = 1; s <= S; ++s)
-#pragma unroll
-        for (int t = 1; t + s <= (S == 1 ? 2 : S + 1); ++t) {
-          const uint32_t acc_col = S == 1 ? 0 : uint32_t(s + t - 2) * TBN;
+  } else if (warp == 1) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      uint32_t g = 0;
+      int i = 0;
+      bool ok = true, any = false;
+      constexpr uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TBM >> 4) << 24);
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+        const int q = tile_desc(tstart, batch, t);
+        const int K = descs[q].K;
+        const int nkb = (K + TBK - 1) / TBK;
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(sptr(acce + b), ((i >> 1) - 1) & 1u, abort_flag)) {
+          fail(1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t acc0 = tmem + uint32_t(b * ACC);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int st = int(g % NST);
+          const uint32_t par = (g / NST) & 1u;
+          if (!mbar_wait(sptr(abar + st), par, abort_flag) || !mbar_wait(sptr(bfull + st), par, abort_flag)) {
+            fail(2);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const bool two = K - kb * TBK > 16;  // second 16-wide K step of this block present
+          const uint64_t a0 = smem_desc(sptr(As + st * ASZ)), b0 = smem_desc(sptr(Bs + st * BSZ));
 #pragma unroll
           for (int kk = 0; kk < TBK / 16; ++kk) {
             if (kk > 0 && !two) continue;
-            // descriptors differ from the stage's by the operand offsets (address field, 16 B units)
-            const uint64_t da = a0 + uint64_t(((s - 1) * TBM * TBK * 2) >> 4) + uint64_t(kk * 16);
-            const uint64_t db = b0 + uint64_t(((t - 1) * TBN * TBK * 2) >> 4) + uint64_t(kk * 16);
-            // the first contribution to accumulator s + t (pair (1, q-1), first K step)
-            // overwrites it
-            const uint32_t accum = (kb > 0 || kk > 0 || s > 1) ? 1u : 0u;
-            mma_bf16(tmem + acc_col, da, db, idesc, accum);
+            if constexpr (S == 1) {
+              mma_bf16(acc0, a0 + uint64_t(kk * 16), b0 + uint64_t(kk * 16), idesc0 | (uint32_t(TBN >> 3) << 17),
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int sa = 1; sa <= S; ++sa) {
+                // slice A_sa times the planes B_1..B_{8-sa} stacked along N: the outputs are
+                // the accumulators of diagonals sa+1 .. S+1, contiguous from column (sa-1) TBN
+                const uint32_t n = uint32_t(S + 1 - sa) * TBN;
+                const uint64_t da = a0 + uint64_t(((sa - 1) * TBM * TBK * 2) >> 4) + uint64_t(kk * 16);
+                // the first MMA of a tile (slice 1 spans every accumulator) overwrites
+                mma_bf16(acc0 + uint32_t((sa - 1) * TBN), da, b0 + uint64_t(kk * 16), idesc0 | ((n >> 3) << 17),
+                         (kb > 0 || kk > 0 || sa > 1) ? 1u : 0u);
+              }
+            }
           }
+          mma_commit(sptr(empty + st));
+          any = true;
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sptr(mbar + st)));
+        if (!ok) break;
+        mma_commit(sptr(accf + b));
+      }
+      // every MMA this thread issued is complete before the accumulators are released
+      if (any) {
+        mma_commit(sptr(fin));
+        mbar_wait_own(sptr(fin), 0u);
+      }
     }
-    // while these MMAs run: stage the next block into the other buffers, once the MMAs
-    // that read them (block kb - 1) are complete
-    if (kb + 1 < nkb) {
-      if (kb >= 1 && !mbar_wait(sptr(mbar + (st ^ 1)), uint32_t((kb - 1) >> 1) & 1u)) {
-        ok = false;
-        if (tid == 0) atomicExch(err, 1);
+  } else if (tid < kEpiThread0) {
+    // ---------------- B producers: column exponents and digit planes
+    const int p = tid - kProdThread0, pw = p >> 5;
+    const int cl = 4 * pw + (lane >> 3);  // this lane's column within a 32-column group
+    const int kq = lane & 7;              // K quad: k = 4 kq .. 4 kq + 3 of a block
+    constexpr int NG = TBN / 32;          // 32-column groups per tile
+    uint32_t g = 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int q = tile_desc(tstart, batch, t);
+      const TcDesc<TB, TC>& d = descs[q];
+      const int tiles_n = (d.N + TBN - 1) / TBN, nt = (t - tstart[q]) % tiles_n;
+      const int j0 = nt * TBN, K = d.K, nkb = (K + TBK - 1) / TBK;
+      const TB* B = d.B;
+      const int ldb = d.ldb, tb = d.tb;
+      const int b = i & 1;
+      int tau[NG];
+#pragma unroll
+      for (int gq = 0; gq < NG; ++gq) tau[gq] = 0;
+      if constexpr (S > 1) {
+        const bool ok = i < 2 || mbar_wait(sptr(acce + b), ((i >> 1) - 1) & 1u, abort_flag);
+        if (__any_sync(0xffffffffu, !ok)) {
+          fail(1);
+          break;
+        }
+        // tau_j = 1 + the largest exponent in column j of op(B) over all of K (zero
+        // columns give -1022); 8 lanes per column, eight loads in flight per lane
+        const int gn = j0 + cl;
+        int emax = 0;
+        for (int k0 = kq; k0 < K; k0 += 64) {
+          TB v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = k0 + 8 * u;
+            v[u] = (k < K && gn < d.N) ? ld_b(B, ldb, tb, k, gn) : TB(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            emax = max(emax, int((uint64_t(__double_as_longlong(double(v[u]))) >> 52) & 0x7FF));
+        }
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+        tau[0] = emax ? emax - 1023 + 1 : -1022;
+        if (kq == 0) tauS[b * TBN + cl] = tau[0];
+        mbar_arrive(sptr(taur + b));
+      }
+      // register prefetch of one K block: NG groups x 4 consecutive k of one column
+      TB xv[NG][4];
+      auto load_b = [&](int k0) {
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const int gk = k0 + 4 * kq + kk, gj = j0 + gq * 32 + cl;
+            xv[gq][kk] = (gj < d.N && gk < K) ? ld_b(B, ldb, tb, gk, gj) : TB(0);
+          }
+      };
+      load_b(0);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int st = int(g % NST);
+        TB cur[NG][4];
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) cur[gq][kk] = xv[gq][kk];
+        if (kb + 1 < nkb) load_b((kb + 1) * TBK);
+        const bool freed = g < NST || mbar_wait(sptr(empty + st), (g / NST - 1) & 1u, abort_flag);
+        if (__any_sync(0xffffffffu, !freed)) {
+          fail(1);
+          ok = false;
+          break;
+        }
+        __nv_bfloat16* dst = Bs + st * BSZ;
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq) {
+          uint32_t pk[S][2];
+#pragma unroll
+          for (int kk = 0; kk < 4; kk += 2) {
+            float d0[S], d1[S];
+            if constexpr (S == 1) {
+              d0[0] = float(cur[gq][kk]);
+              d1[0] = float(cur[gq][kk + 1]);
+            } else {
+              digits_f64<S>(double(cur[gq][kk]), tau[0], d0);
+              digits_f64<S>(double(cur[gq][kk + 1]), tau[0], d1);
+            }
+#pragma unroll
+            for (int sq = 0; sq < S; ++sq) {
+              __nv_bfloat162 h = __floats2bfloat162_rn(d0[sq], d1[sq]);
+              pk[sq][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
+            }
+          }
+#pragma unroll
+          for (int sq = 0; sq < S; ++sq)
+            *reinterpret_cast<uint2*>(dst + core_off(sq * TBN + gq * 32 + cl, 4 * kq)) = make_uint2(pk[sq][0], pk[sq][1]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(sptr(bfull + st));
+      }
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- epilogue: one warp per TMEM lane quarter, one row per lane
+    const int quarter = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int q = tile_desc(tstart, batch, t);
+      const TcDesc<TB, TC>& d = descs[q];
+      const int tiles_n = (d.N + TBN - 1) / TBN, r = t - tstart[q];
+      const int i0 = (r / tiles_n) * TBM, j0 = (r % tiles_n) * TBN;
+      const int b = i & 1;
+      const uint32_t par = (i >> 1) & 1u;
+      bool ok = mbar_wait(sptr(accf + b), par, abort_flag);
+      if (S > 1 && ok) ok = mbar_wait(sptr(taur + b), par, abort_flag);
+      if (__any_sync(0xffffffffu, !ok)) {
+        fail(1);
         break;
       }
-      if (tid == 0) copy_a(kb + 1, st ^ 1);
-      stage_b(st ^ 1);
-      if (kb + 2 < nkb) load_b((kb + 2) * TBK);
-    }
-  }
-  // the last commit arrives after every MMA of this thread is complete
-  if (ok && !mbar_wait(sptr(mbar + ((nkb - 1) & 1)), uint32_t((nkb - 1) >> 1) & 1u)) {
-    ok = false;
-    if (tid == 0) atomicExch(err, 1);
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
-    const int gi = i0 + quarter * 32 + lane;
-    int sig = 0;
-    if (S > 1 && gi < d.M) sig = d.Aexp[gi];
-    const int c0 = colgrp * 16;
-    const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0);
-    double acc[16];
-    if constexpr (S == 1) {
-      uint32_t r[16];
-      tmem_ld16_issue(trow, r);
-      tmem_ld_wait(r);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int gi = i0 + quarter * 32 + lane;
+      int sig = 0;
+      if (S > 1 && gi < d.M) sig = d.Aexp[gi];
+      const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * ACC);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TBN; c0 += 16) {
+        double acc[16];
+        if constexpr (S == 1) {
+          uint32_t rr[16];
+          tmem_ld16_issue(trow + uint32_t(c0), rr);
+          tmem_ld_wait(rr);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = __uint_as_float(r[q]);
-    } else {
-      // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
-      // units of 2^-49; |sum| < 2^58.  One int64 -> FP64 conversion, then the power-of-two
-      // scale 2^{sigma + tau - 49} is added to the exponent bits.  The TMEM load of the next
-      // diagonal is in flight while one is converted.
-      long long iacc[16];
+          for (int u = 0; u < 16; ++u) acc[u] = __uint_as_float(rr[u]);
+        } else {
+          // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
+          // units of 2^-49; one int64 -> FP64 conversion, then the power-of-two scale
+          // 2^{sigma + tau - 49} added to the exponent bits.  The TMEM load of the next
+          // diagonal is in flight while one is converted.
+          long long iacc[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) iacc[q] = 0;
-      uint32_t r[2][16];
-      tmem_ld16_issue(trow, r[0]);
-      tmem_ld_wait(r[0]);
+          for (int u = 0; u < 16; ++u) iacc[u] = 0;
+          uint32_t rr[2][16];
+          tmem_ld16_issue(trow + uint32_t(c0), rr[0]);
+          tmem_ld_wait(rr[0]);
 #pragma unroll
-      for (int dg = 0; dg < NACC; ++dg) {
-        if (dg + 1 < NACC) tmem_ld16_issue(trow + uint32_t(dg + 1) * TBN, r[(dg + 1) & 1]);
-        const int qd = dg + 2;
+          for (int dg = 0; dg < S; ++dg) {
+            if (dg + 1 < S) tmem_ld16_issue(trow + uint32_t((dg + 1) * TBN + c0), rr[(dg + 1) & 1]);
+            const int qd = dg + 2;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          long long iv = __float2int_rn(__uint_as_float(r[dg & 1][q]));  // exact: |D_q| < 2^24
-          iacc[q] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
+            for (int u = 0; u < 16; ++u) {
+              long long iv = __float2int_rn(__uint_as_float(rr[dg & 1][u]));  // |D_q| < 2^24 in practice
+              iacc[u] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
+            }
+            if (dg + 1 < S) tmem_ld_wait(rr[(dg + 1) & 1]);
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            double x = __ll2double_rn(iacc[u]);
+            const int sh = sig + tauS[b * TBN + c0 + u] - 49;
+            const long long bits = __double_as_longlong(x);
+            if (x != 0.0) {
+              const int eb = int((bits >> 52) & 0x7FF) + sh;
+              x = (eb > 0 && eb < 2047) ? __longlong_as_double(bits + ((long long)sh << 52)) : ldexp(x, sh);
+            }
+            acc[u] = x;
+          }
         }
-        if (dg + 1 < NACC) tmem_ld_wait(r[(dg + 1) & 1]);
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        double x = __ll2double_rn(iacc[q]);
-        int sh = sig + tauS[c0 + q] - 49;
-        long long b = __double_as_longlong(x);
-        if (x != 0.0) {
-          int eb = int((b >> 52) & 0x7FF) + sh;
-          x = (eb > 0 && eb < 2047) ? __longlong_as_double(b + ((long long)sh << 52)) : ldexp(x, sh);
+        if (c0 + 16 >= TBN) {
+          // every TMEM value of this set is in registers: hand the set back to the MMAs
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(sptr(acce + b));
         }
-        acc[q] = x;
-      }
-    }
-    if (gi < d.M) {
-      // epilogue operands first (16 loads in flight), then the stores
-      double e[16];
-      const bool needs = epi == EPI_MUL || epi == EPI_ADD;
+        if (gi < d.M) {
+          // epilogue operands first (16 loads in flight), then the stores
+          double e[16];
+          const bool needs = epi == EPI_MUL || epi == EPI_ADD;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int gj = j0 + c0 + q;
-        e[q] = 0.0;
-        if (needs && gj < d.N) {
-          if (epi == EPI_MUL) e[q] = double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
-          else e[q] = double(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
-        }
-      }
+          for (int u = 0; u < 16; ++u) {
+            const int gj = j0 + c0 + u;
+            e[u] = 0.0;
+            if (needs && gj < d.N) {
+              if (epi == EPI_MUL) e[u] = double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
+              else e[u] = double(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
+            }
+          }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int gj = j0 + c0 + q;
-        if (gj >= d.N) continue;
-        const double v = acc[q];
-        TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
-        switch (epi) {
-          case EPI_MUL: *cp = TC(v * e[q]); break;
-          case EPI_ASSIGN: *cp = TC(double(alpha) * v); break;
-          case EPI_ADD: *cp = TC(fma(double(alpha), v, e[q])); break;
-          default: *cp = TC(v);
+          for (int u = 0; u < 16; ++u) {
+            const int gj = j0 + c0 + u;
+            if (gj >= d.N) continue;
+            const double v = acc[u];
+            TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
+            switch (epi) {
+              case EPI_MUL: *cp = TC(v * e[u]); break;
+              case EPI_ASSIGN: *cp = TC(double(alpha) * v); break;
+              case EPI_ADD: *cp = TC(fma(double(alpha), v, e[u])); break;
+              default: *cp = TC(v);
+            }
+          }
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(CF::TCOLS));
 }
+
+namespace {
+int sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+}  // namespace
 
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err) {
-  if (batch <= 0) return cudaSuccess;
-  size_t smem = 2 * size_t(S) * (TBM + TBN) * TBK * sizeof(__nv_bfloat16) + TBN * sizeof(int) + 64 + 1024;
+  if (batch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  if (batch > kMaxDescs) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes<S>();
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(batch, ((maxN + TBN - 1) / TBN) * ((maxM + TBM - 1) / TBM));
-  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, epi, alpha, err);
+  // persistent CTAs: one per SM, at most one per tile (the exact tile count is known on the
+  // device only; this bound counts every descriptor at the largest shape)
+  const int64_t bound = int64_t(batch) * ((maxM + TBM - 1) / TBM) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
+  const int grid = int(std::min<int64_t>(bound, sm_count()));
+  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, epi, alpha, err);
   return cudaGetLastError();
 }
 template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
@@ -442,11 +610,13 @@ uint16_t bf16_bits_rn(float f) {
 int tc_kblocks(int K) { return (K + TBK - 1) / TBK; }
 
 double tc_exec_flops(int M, int N, int K, int S) {
-  const double tiles = double((M + TBM - 1) / TBM) * ((N + TBN - 1) / TBN);
-  const int pairs = S == 1 ? 1 : S * (S + 1) / 2;
+  if (M <= 0 || N <= 0 || K <= 0) return 0.0;
+  const int tbn = S == 1 ? TcCfg<1>::TBN : TcCfg<7>::TBN;
+  const double tiles = double((M + TBM - 1) / TBM) * ((N + tbn - 1) / tbn);
+  const int pairs = S == 1 ? 1 : S * (S + 1) / 2;  // digit-slice pairs (N-stacked MMAs)
   double ksteps = 0;
   for (int k0 = 0; k0 < K; k0 += TBK) ksteps += std::min(TBK, K - k0 + 15) / 16;
-  return tiles * pairs * ksteps * 2.0 * TBM * TBN * 16;
+  return tiles * pairs * ksteps * 2.0 * TBM * tbn * 16;
 }
 
 void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,

@@ -23,16 +23,13 @@ struct TcDesc {
   const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
   int lde;
   int M, N, K;
-  // the constant operand in the working precision (optional): A(i, k) = tra ? Af[k * lda + i]
-  // : Af[i * lda + k]; a 128 x 64 tile with at most 32 valid rows or columns is then computed
-  // with FMAs
-  const TB* Af = nullptr;
-  int lda = 0, tra = 0;
 };
 
-// S = 7: FP64-accurate digit-slice product (TB = TC = double), exact digit sums for
-// K <= kTcMaxK; S = 1: BF16 product with FP32 accumulation (TB = TC = float).  err: device
-// flag set when an mbarrier wait times out.
+// S = 7: FP64-accurate digit-slice product (TB = TC = double), for K <= kTcMaxK (every single
+// digit product summed over K stays an exact FP32 integer); S = 1: BF16 product with FP32
+// accumulation (TB = TC = float).  Persistent launch over every tile of the `batch`
+// descriptors (at most 512; C must not alias B or E).  err: device flag set when an mbarrier
+// wait times out.
 constexpr int kTcMaxK = 1023;
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,

@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_prolong": ([P, C.c_int, P, P], C.c_int),
         "igamg_coarse_solve": ([P, P, P], C.c_int),
         "igamg_precondition": ([P, P, P], C.c_int),
+        "igamg_cycle_time": ([P, P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
         "igamg_sync": ([P], C.c_int),
         "igamg_profile_enable": ([P, C.c_int], C.c_int),
         "igamg_profile_read": ([P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -79,6 +80,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_fd_apply": ([C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_double, P, C.c_int, P, P], C.c_int),
         "igamg_fd_apply_noalloc": ([C.c_int, C.c_int, P, P, P, P, C.c_int, C.c_double, P, C.c_int, P],
                                    C.c_int),
+        "igamg_micro_fp64": ([C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
         "igamg_free": ([P], C.c_int),
         "igamg_last_error": ([P], C.c_char_p),
         "igamg_setup_batch": ([P, C.c_int, C.POINTER(igamg_options), C.c_int, P, C.POINTER(P)], C.c_int),
@@ -163,6 +165,15 @@ def igamg_fd_apply(U0, U1, Dinv, R, tau, Z, scratch, stream=None):
                               _stream_handle(stream))
     if st != IGAMG_OK:
         raise IgamgError(st, lib().igamg_last_error(None).decode())
+
+
+def igamg_micro_fp64(kind=0, iters=1 << 16):
+    """(TFLOP/s, SM count) of the FP64 FMA pipe (kind 0) or FP64 tensor-core MMAs (kind 1)."""
+    tf, sms = C.c_double(), C.c_int()
+    st = lib().igamg_micro_fp64(int(kind), int(iters), C.byref(tf), C.byref(sms))
+    if st != IGAMG_OK:
+        raise IgamgError(st, "igamg_micro_fp64 failed")
+    return tf.value, sms.value
 
 
 def igamg_default_options() -> igamg_options:
@@ -260,8 +271,16 @@ class Context:
     def precondition(self, r, z):
         self._check(lib().igamg_precondition(self.h, _ptr(r), _ptr(z)))
 
+    def cycle_time(self, r, reps=10):
+        """(ms per cycle, algorithmic bytes of one cycle) of the graph-replayed cycle in the
+        context's working precision."""
+        ms, by = C.c_double(), C.c_double()
+        self._check(lib().igamg_cycle_time(self.h, _ptr(r), int(reps), C.byref(ms), C.byref(by)))
+        return ms.value, by.value
+
     PROFILE_CLASSES = ("apply", "interior_fd", "interface", "transfer", "coarse", "vector")
     TENSOR_EXEC_CLASS = 6  # flops only: BF16 MMA work of the tensor-core FD
+    TC_KERNEL_CLASS = 7    # sub-account of classes 1 and 2: the tensor-core kernel's launches
 
     def profile_enable(self, mask=0x3F):
         """mask: bit c times class c with CUDA events (0 disables profiling)."""
@@ -269,7 +288,8 @@ class Context:
 
     def profile_read(self):
         out = {}
-        for i, name in list(enumerate(self.PROFILE_CLASSES)) + [(self.TENSOR_EXEC_CLASS, "tensor_exec")]:
+        for i, name in list(enumerate(self.PROFILE_CLASSES)) + [(self.TENSOR_EXEC_CLASS, "tensor_exec"),
+                                                                (self.TC_KERNEL_CLASS, "tc_kernel")]:
             n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
             self._check(lib().igamg_profile_read(self.h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
             out[name] = {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
