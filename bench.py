@@ -815,7 +815,7 @@ def run_micro_fd(args):
     z = torch.empty_like(r)
     for _ in range(args.warmup):
         ctx.smooth(L, r, z)
-    ctx.profile_enable(0x3F)
+    ctx.profile_enable(0xFF)
     ctx.smooth(L, r, z)
     prof = ctx.profile_read()
     ctx.profile_enable(0)
@@ -827,10 +827,13 @@ def run_micro_fd(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    fd = prof["interior_fd"]
+    fd, tc = prof["interior_fd"], prof["tc_kernel"]
     print(json.dumps({"micro": "finest smoother", "workload": args.workload, "fd_engine": args.fd_engine,
                       "autotune": o.autotune, "ms_per_smoother": round(ms, 4),
                       "fd_ms_profiled": round(fd["ms"], 4), "fd_launches": fd["launches"],
+                      "tc_gemm_ms_profiled": round(tc["ms"], 4), "tc_gemm_launches": tc["launches"],
+                      "interface_ms_profiled": round(prof["interface"]["ms"], 4),
+                      "tc_mma_tflops": round(prof["tensor_exec"]["flops"] / max(tc["ms"], 1e-9) / 1e9, 1),
                       "fd_fp64_tflops": round(fd["flops"] / (fd["ms"] * 1e-3) / 1e12, 3)}), flush=True)
     ctx.free()
 

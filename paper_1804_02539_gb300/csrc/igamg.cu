@@ -97,6 +97,12 @@ struct TcSet {
   int batch = 0, maxM = 0, maxN = 0;
   double flops = 0;       // algorithmic (the GEMMs' own)
   double exec_flops = 0;  // BF16 MMA work issued
+  double dig_bytes = 0;   // digit pass: B read, digit planes and exponents written
+  // digit scratch of the set: sizes and per-descriptor offsets; the descriptors are uploaded
+  // once the context's scratch is bound (bind_tc)
+  int64_t dig_elems = 0, tau_elems = 0;
+  std::vector<int64_t> dig_off, tau_off;
+  bool side = false;      // launched on the interface stream (its own scratch)
 };
 
 // Numeric data of one level in one precision: the vectors and the descriptor sets the
@@ -442,24 +448,70 @@ void run_gemm(igamg_ctx* c, const GemmSetT<T>& gs, bool ta, bool tb, int epi, do
 }
 
 template <class T>
-void set_tc(igamg_ctx* c, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v) {
+void set_tc(igamg_ctx*, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v, bool side = false) {
+  constexpr int S = sizeof(T) == 8 ? 7 : 1;
   ts.h = v;
   ts.batch = int(v.size());
   ts.maxM = ts.maxN = 0;
-  ts.flops = 0;
-  ts.exec_flops = 0;
+  ts.flops = ts.exec_flops = ts.dig_bytes = 0;
+  ts.dig_elems = ts.tau_elems = 0;
+  ts.dig_off.clear();
+  ts.tau_off.clear();
+  ts.side = side;
   for (auto& d : v) {
     ts.maxM = std::max(ts.maxM, d.M);
     ts.maxN = std::max(ts.maxN, d.N);
     ts.flops += 2.0 * d.M * double(d.N) * d.K;
-    ts.exec_flops += tc_exec_flops(d.M, d.N, d.K, sizeof(T) == 8 ? 7 : 1);
+    ts.exec_flops += tc_exec_flops(d.M, d.N, d.K, S);
+    ts.dig_off.push_back(ts.dig_elems);
+    ts.tau_off.push_back(ts.tau_elems);
+    ts.dig_elems += tc_dig_elems(d.N, d.K, S);
+    ts.tau_elems += tc_tau_elems(d.N, S);
+    ts.dig_bytes += double(d.N) * d.K * (sizeof(T) + 2.0 * S) + 4.0 * tc_tau_elems(d.N, S);
   }
-  ts.d = v.empty() ? nullptr : c->mem.upload(v, c->stream);
+  ts.d = nullptr;  // uploaded by bind_tc
+}
+
+// Every tensor-core set of precision T gets the digit scratch of its stream: the sets
+// launched on the solve's stream run one after another and share one buffer, the interface
+// (face) sets on the side stream share another.  Then the descriptors are uploaded.
+template <class T>
+void bind_tc(igamg_ctx* c) {
+  std::vector<TcSet<T>*> sets;
+  for (Level& L : c->lv) {
+    Num<T>& N = num<T>(L);
+    for (TcSet<T>* p : {&N.tc0F, &N.tc0R, &N.tc1, &N.tc2, &N.tc3, &N.tc4, &N.tc5, &N.tq0, &N.tq1, &N.tq2, &N.tq3})
+      if (p->batch && !p->d) sets.push_back(p);
+  }
+  int64_t dig[2] = {0, 0}, tau[2] = {0, 0};
+  for (TcSet<T>* p : sets) {
+    dig[p->side] = std::max(dig[p->side], p->dig_elems);
+    tau[p->side] = std::max(tau[p->side], p->tau_elems);
+  }
+  __nv_bfloat16* dbase[2] = {nullptr, nullptr};
+  int* tbase[2] = {nullptr, nullptr};
+  for (int k = 0; k < 2; ++k) {
+    if (dig[k]) dbase[k] = c->mem.alloc<__nv_bfloat16>(size_t(dig[k]));
+    if (tau[k]) tbase[k] = c->mem.alloc<int>(size_t(tau[k]));
+  }
+  for (TcSet<T>* p : sets) {
+    for (int i = 0; i < p->batch; ++i) {
+      p->h[i].Bdig = dbase[p->side] + p->dig_off[i];
+      p->h[i].Btau = tbase[p->side] ? tbase[p->side] + p->tau_off[i] : nullptr;
+    }
+    p->d = c->mem.upload(p->h, c->stream);
+  }
 }
 
 template <class T>
 void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha, int cls = CLS_FD) {
   if (!ts.batch) return;
+  if (!ts.d) throw Fail{IGAMG_ERR_NUMERIC, "tensor-core set without scratch"};
+  {
+    ProfScope ps(c, cls, 0.0, ts.dig_bytes);
+    if constexpr (std::is_same<T, double>::value) CK((launch_tc_digits<7, double, double>(c->stream, ts.d, ts.batch, ts.maxN)));
+    else CK((launch_tc_digits<1, float, float>(c->stream, ts.d, ts.batch, ts.maxN)));
+  }
   if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
   ProfScope ps(c, cls, ts.flops, 0.0, 1, CLS_TC_KERNEL);
   if constexpr (std::is_same<T, double>::value)
@@ -1220,10 +1272,10 @@ void build_levels(igamg_ctx* c) {
       for (auto& t : tqd[1]) { t.B = fT + (intptr_t)t.B; t.C = fY + (intptr_t)t.C; }
       for (auto& t : tqd[2]) { t.B = fY + (intptr_t)t.B; t.C = fT + (intptr_t)t.C; }
       for (auto& t : tqd[3]) { t.B = fT + (intptr_t)t.B; t.C = L.n64.Z + (intptr_t)t.C; }
-      set_tc(c, L.n64.tq0, tqd[0]);
-      set_tc(c, L.n64.tq1, tqd[1]);
-      set_tc(c, L.n64.tq2, tqd[2]);
-      set_tc(c, L.n64.tq3, tqd[3]);
+      set_tc(c, L.n64.tq0, tqd[0], true);
+      set_tc(c, L.n64.tq1, tqd[1], true);
+      set_tc(c, L.n64.tq2, tqd[2], true);
+      set_tc(c, L.n64.tq3, tqd[3], true);
     }
 
     // ---------------- transfers from level l-1 (one 1D pass per direction)
@@ -1378,6 +1430,7 @@ void build_levels(igamg_ctx* c) {
       }
     }
   }
+  bind_tc<double>(c);
   // coarse solver: dense A_0 from the level-0 bands, Cholesky, explicit inverse
   Level& L0 = c->lv[0];
   const LevelTopo& T0 = L0.topo;
@@ -2133,7 +2186,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
           v.push_back(TcDesc<float, float>{static_cast<const __nv_bfloat16*>(it->second), nullptr, d.nkb, tr(d.B), d.ldb,
                                             d.tb, tr(d.C), d.ldc, d.tc, tr(d.E), d.lde, d.M, d.N, d.K});
         }
-        set_tc(c, out, v);
+        set_tc(c, out, v, g.side);
       };
       tr_tc(A.tc0F, B.tc0F); tr_tc(A.tc0R, B.tc0R); tr_tc(A.tc1, B.tc1); tr_tc(A.tc2, B.tc2); tr_tc(A.tc3, B.tc3);
       tr_tc(A.tc4, B.tc4); tr_tc(A.tc5, B.tc5);
@@ -2210,6 +2263,7 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
   c->P32 = c->mem.alloc<float>(Tf);
   c->W32 = c->mem.alloc<float>(Tf);
   c->Zold32 = c->mem.alloc<float>(Tf);
+  bind_tc<float>(c);
   c->low = true;
   c->low_bf16 = bf16_bands;
   CK(cudaStreamSynchronize(s));

@@ -20,27 +20,30 @@
 // The epilogue recombines the diagonals in 64-bit integers (units of 2^-49 of the row and
 // column scales), converts once to FP64 and applies the smoother's epilogue.
 //
-// Kernel structure (persistent, warp-specialised).  One CTA per SM walks the product's
-// tiles (128 rows of A x TBN columns of B, over every descriptor of the batch) with a
-// static stride; per tile:
-//   warp 0        bulk TMA copies of A's pre-sliced K blocks ([S][128 x 32] in the
-//                 canonical no-swizzle K-major core-matrix layout) into a ring of stages;
-//   warps 2..9    the B producers: per tile the column exponents tau_j (each warp owns 4
-//                 columns and reduces over K with shuffles), then per K block the digit
-//                 planes of B written into the same ring (register-prefetched loads);
-//   warp 1        one thread issues the MMAs: for digit slice A_s, ONE MMA with the digit
-//                 planes B_1..B_{8-s} stacked along N (N = (8 - s) TBN), whose output
-//                 columns are exactly the accumulators of diagonals s+1 .. 8, which are
-//                 contiguous in TMEM (7 MMAs per 16-wide K step instead of 28; each slice
-//                 of A is read from shared memory once per K step);
-//   warps 10..13  the epilogue, one warp per TMEM lane quarter.
-// Two accumulator sets in TMEM (2 x 7 x 32 of the 512 columns) let the epilogue of one tile
-// run while the MMAs of the next are issued.  Every tile runs on the tensor cores,
-// including the ragged remainders of M, N and K (padded with zero digits).
-// Synchronisation is by mbarriers only (no block barrier inside the tile loop); every wait
-// is bounded and a timeout is decided warp-uniformly, sets a shared abort flag and the
-// device error flag, and every role then leaves its loop; the MMA thread waits (bounded)
-// for its last MMAs and the TMA thread for its last copies before the TMEM is freed.
+// Two kernels per product set.
+//   Digit pass (k_tc_digits): one CTA per 32-column panel of B (per descriptor), one warp
+//   per 4 columns; the warp loads its columns over all of K (up to 288 rows at once, held in
+//   registers), reduces the column exponents tau_j with shuffles and writes, per K block, the
+//   digit planes in the canonical no-swizzle K-major core-matrix layout of an MMA operand.
+//   Every element of B is sliced once per launch, however many row tiles read it.
+//   GEMM (k_gemm_tc, persistent, warp-specialised): one CTA per SM walks the tiles (128 rows
+//   of A x TBN columns of B over every descriptor of the batch) with a static stride;
+//     warp 0       bulk TMA copies of A's pre-sliced K blocks ([S][128 x 32]) and of B's
+//                  digit-plane blocks ([S][TBN x 32]) into a ring of stages (one mbarrier
+//                  with the expected bytes of both);
+//     warp 1       one thread issues the MMAs: for digit slice A_s, ONE MMA with the digit
+//                  planes B_1..B_{8-s} stacked along N (N = (8 - s) TBN), whose output
+//                  columns are exactly the accumulators of diagonals s+1 .. 8, which are
+//                  contiguous in TMEM (7 MMAs per 16-wide K step instead of 28; each slice
+//                  of A is read from shared memory once per K step);
+//     warps 2..5   the epilogue, one warp per TMEM lane quarter.
+//   Two accumulator sets in TMEM (2 x 7 x 32 of the 512 columns) let the epilogue of one
+//   tile run while the MMAs of the next are issued.  Every tile runs on the tensor cores,
+//   including the ragged remainders of M, N and K (padded with zero digits).
+//   Synchronisation is by mbarriers only (no block barrier inside the tile loop); every wait
+//   is bounded and a timeout is decided warp-uniformly, sets a shared abort flag and the
+//   device error flag, and every role then leaves its loop; the MMA thread waits (bounded)
+//   for its last MMAs and the TMA thread for its last copies before the TMEM is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -57,8 +60,9 @@ namespace igamg {
 
 namespace {
 constexpr int TBM = 128, TBK = 32;  // rows of a tile; K block of one pipeline stage
-constexpr int NT = 448;             // 14 warps: TMA, MMA, 8 producers, 4 epilogue
-constexpr int kProdThread0 = 64, kNumProd = 256, kEpiThread0 = 320;
+constexpr int NT = 192;             // 6 warps: TMA, MMA, 4 epilogue
+constexpr int kDigThreads = 256;    // digit pass: 8 warps per 32-column panel
+constexpr int kDigRegBlocks = 9;    // K blocks a digit-pass lane holds in registers (288 rows; S = 7)
 constexpr int kMaxDescs = 512;      // descriptors of one launch (tile prefix in shared memory)
 constexpr int WAIT_LIMIT = 1 << 24;
 
@@ -80,9 +84,8 @@ template <int S>
 constexpr size_t tc_smem_bytes() {
   using CF = TcCfg<S>;
   return size_t(CF::NST) * S * (TBM + CF::TBN) * TBK * 2  // A and B stages (BF16)
-         + 2 * CF::TBN * 4                                 // column exponents, two sets
          + (kMaxDescs + 2) * 4                             // tile prefix
-         + (4 * CF::NST + 8) * 8                           // mbarriers
+         + (2 * CF::NST + 8) * 8                           // mbarriers
          + 16                                              // TMEM slot, abort flag
          + 1024;                                           // alignment
 }
@@ -167,24 +170,6 @@ __device__ __forceinline__ void split_f64(double x, int& e, uint64_t& m, bool& n
   }
 }
 
-template <int S>
-__device__ __forceinline__ void digits_f64(double x, int tau, float* dig) {
-  int e;
-  uint64_t m;
-  bool neg;
-  split_f64(x, e, m, neg);
-  // fixed point F = |x| 2^{7S - tau}, |x| = m 2^{e - 52}
-  int sh = (e - 52) - tau + 7 * S;
-  uint64_t F = 0;
-  if (sh >= 0) F = sh < 11 ? (m << sh) : 0;  // cannot happen when |x| < 2^tau
-  else if (sh > -64) F = m >> (-sh);
-#pragma unroll
-  for (int s = 1; s <= S; ++s) {
-    float d = float(uint32_t(F >> (7 * (S - s))) & 127u);
-    dig[s - 1] = neg ? -d : d;
-  }
-}
-
 // The descriptor q holding tile t (tile prefix `start` of `batch` descriptors): the last q
 // with start[q] <= t (descriptors without tiles are skipped).
 __device__ __forceinline__ int tile_desc(const int* start, int batch, int t) {
@@ -201,7 +186,146 @@ template <class TB>
 __device__ __forceinline__ TB ld_b(const TB* B, int ldb, int tb, int k, int n) {
   return __ldg(tb ? B + int64_t(n) * ldb + k : B + int64_t(k) * ldb + n);
 }
+
+// BF16 bit pattern of an integer 0 <= d < 256 (exact in BF16): 2^23 + d is an FP32 whose
+// low mantissa bits are d, and subtracting 2^23 leaves d exactly; its upper 16 bits are the
+// BF16 encoding.  Full-rate integer and FP32 operations only.
+__device__ __forceinline__ uint32_t bf16_of_small(uint32_t d) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.0f) >> 16;
+}
+
+// Digit planes of two FP64 values (consecutive k) against column scale tau: for plane s the
+// BF16 pair (digit of x1 << 16 | digit of x0), digits of F = |x| 2^{49 - tau} < 2^49.
+__device__ __forceinline__ void digit_pairs7(double x0, double x1, int tau, uint32_t* pk) {
+  uint32_t hi[2], lo[2], sg[2];
+  const double xs[2] = {x0, x1};
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int e;
+    uint64_t m;
+    bool neg;
+    split_f64(xs[u], e, m, neg);
+    const int sh = (e - 52) - tau + 49;
+    uint64_t F = 0;
+    if (sh >= 0) F = sh < 11 ? (m << sh) : 0;  // cannot happen when |x| < 2^tau
+    else if (sh > -64) F = m >> (-sh);
+    hi[u] = uint32_t(F >> 28);                 // bits 28..48: digits 1..3
+    lo[u] = uint32_t(F) & 0x0FFFFFFFu;         // bits 0..27: digits 4..7
+    sg[u] = neg ? 0x8000u : 0u;
+  }
+#pragma unroll
+  for (int sq = 0; sq < 7; ++sq) {
+    uint32_t d0, d1;
+    if (sq < 3) {
+      d0 = (hi[0] >> (7 * (2 - sq))) & 127u;
+      d1 = (hi[1] >> (7 * (2 - sq))) & 127u;
+    } else {
+      d0 = (lo[0] >> (7 * (6 - sq))) & 127u;
+      d1 = (lo[1] >> (7 * (6 - sq))) & 127u;
+    }
+    pk[sq] = (bf16_of_small(d0) | sg[0]) | ((bf16_of_small(d1) | sg[1]) << 16);
+  }
+}
+
+// Panel prefix: number of TBN-column panels of descriptors 0..q-1 in start[q] (start[batch]
+// = total).  Built by one thread into shared memory.
+template <int TBN, class D>
+__device__ void panel_prefix(const D* descs, int batch, int* start) {
+  int acc = 0;
+  for (int q = 0; q < batch; ++q) {
+    start[q] = acc;
+    const D& d = descs[q];
+    if (d.M > 0 && d.N > 0 && d.K > 0) acc += (d.N + TBN - 1) / TBN;
+  }
+  start[batch] = acc;
+}
 }  // namespace
+
+template <int S, class TB, class TC>
+__global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>* __restrict__ descs, int batch) {
+  using CF = TcCfg<S>;
+  constexpr int TBN = CF::TBN, BSZ = S * TBN * TBK, NG = TBN / 32;
+  // K blocks held in registers at once: all of K up to 288 with S = 7 (the exponent pass and
+  // the digits use one load), two blocks with S = 1 (no exponents)
+  constexpr int RB = S > 1 ? kDigRegBlocks : 2;
+  __shared__ int pstart[kMaxDescs + 2];
+  if (threadIdx.x == 0) panel_prefix<TBN>(descs, batch, pstart);
+  __syncthreads();
+  const int total = pstart[batch];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = 4 * warp + (lane >> 3);  // this lane's column within a 32-column group
+  const int kq = lane & 7;                // K quad: k = 4 kq .. 4 kq + 3 of a block
+  for (int pnl = blockIdx.x; pnl < total; pnl += gridDim.x) {
+    const int q = tile_desc(pstart, batch, pnl);
+    const TcDesc<TB, TC>& d = descs[q];
+    const int nt = pnl - pstart[q], j0 = nt * TBN, K = d.K, N = d.N, nkb = (K + TBK - 1) / TBK;
+    const TB* B = d.B;
+    const int ldb = d.ldb, tb = d.tb;
+    __nv_bfloat16* out = d.Bdig + int64_t(nt) * nkb * BSZ;
+    const int nch = (nkb + RB - 1) / RB;  // register chunks of K blocks
+    TB v[RB][NG][4];
+    auto load_chunk = [&](int ch) {
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const int gk = (ch * RB + b) * TBK + 4 * kq + kk, gj = j0 + gq * 32 + cl;
+            v[b][gq][kk] = (gj < N && gk < K) ? ld_b(B, ldb, tb, gk, gj) : TB(0);
+          }
+    };
+    int tau = 0;
+    if constexpr (S > 1) {
+      // tau_j = 1 + the largest exponent in column j over all of K (zero columns: -1022)
+      int emax = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        load_chunk(ch);
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            emax = max(emax, int((uint64_t(__double_as_longlong(double(v[b][0][kk]))) >> 52) & 0x7FF));
+      }
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+      tau = emax ? emax - 1023 + 1 : -1022;
+      if (kq == 0 && j0 + cl < N) d.Btau[j0 + cl] = tau;
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+      if (S == 1 || nch > 1) load_chunk(ch);  // one chunk: still in registers from the tau pass
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int kb = ch * RB + b;
+        if (kb >= nkb) break;
+        __nv_bfloat16* blk = out + int64_t(kb) * BSZ;
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq) {
+          uint32_t pk[S][2];
+          if constexpr (S == 1) {
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(float(v[b][gq][0]), float(v[b][gq][1]));
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(float(v[b][gq][2]), float(v[b][gq][3]));
+            pk[0][0] = *reinterpret_cast<uint32_t*>(&h0);
+            pk[0][1] = *reinterpret_cast<uint32_t*>(&h1);
+          } else {
+            uint32_t a[7], c[7];
+            digit_pairs7(double(v[b][gq][0]), double(v[b][gq][1]), tau, a);
+            digit_pairs7(double(v[b][gq][2]), double(v[b][gq][3]), tau, c);
+#pragma unroll
+            for (int sq = 0; sq < S; ++sq) {
+              pk[sq][0] = a[sq];
+              pk[sq][1] = c[sq];
+            }
+          }
+#pragma unroll
+          for (int sq = 0; sq < S; ++sq)
+            *reinterpret_cast<uint2*>(blk + core_off(sq * TBN + gq * 32 + cl, 4 * kq)) = make_uint2(pk[sq][0], pk[sq][1]);
+        }
+      }
+    }
+  }
+}
 
 template <int S, class TB, class TC>
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int batch, int epi,
@@ -213,16 +337,13 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* Bs = As + NST * ASZ;
-  int* tauS = reinterpret_cast<int*>(Bs + NST * BSZ);  // [2][TBN]
-  int* tstart = tauS + 2 * TBN;                         // [batch + 1]
+  int* tstart = reinterpret_cast<int*>(Bs + NST * BSZ);  // [batch + 1]
   uint64_t* bars = reinterpret_cast<uint64_t*>(tstart + kMaxDescs + 2);
-  uint64_t* abar = bars;             // [NST] A copy landed (expect_tx)
-  uint64_t* bfull = abar + NST;      // [NST] B digits staged (kNumProd arrivals)
-  uint64_t* empty = bfull + NST;     // [NST] MMAs reading the stage done (commit)
+  uint64_t* full = bars;             // [NST] A and B copies landed (expect_tx)
+  uint64_t* empty = full + NST;      // [NST] MMAs reading the stage done (commit)
   uint64_t* accf = empty + NST;      // [2] accumulator set complete (commit)
   uint64_t* acce = accf + 2;         // [2] accumulator set read by the epilogue (128 arrivals)
-  uint64_t* taur = acce + 2;         // [2] column exponents written (kNumProd arrivals)
-  uint64_t* fin = taur + 2;          // [1] every MMA of this CTA done (commit)
+  uint64_t* fin = acce + 2;          // [1] every MMA of this CTA done (commit)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -236,14 +357,12 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     }
     tstart[batch] = acc;
     for (int i = 0; i < NST; ++i) {
-      mbar_init(sptr(abar + i), 1);
-      mbar_init(sptr(bfull + i), kNumProd);
+      mbar_init(sptr(full + i), 1);
       mbar_init(sptr(empty + i), 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(sptr(accf + i), 1);
       mbar_init(sptr(acce + i), 128);
-      mbar_init(sptr(taur + i), kNumProd);
     }
     mbar_init(sptr(fin), 1);
     *abort_flag = 0;
@@ -266,14 +385,15 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   };
 
   if (warp == 0) {
-    // ---------------- A: one bulk copy of the pre-sliced [S][128 x 32] block per stage
+    // ---------------- one bulk copy of A's pre-sliced [S][128 x 32] block and one of B's
+    // digit-plane block [S][TBN x 32] per stage
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const int q = tile_desc(tstart, batch, t);
         const TcDesc<TB, TC>& d = descs[q];
-        const int tiles_n = (d.N + TBN - 1) / TBN, mt = (t - tstart[q]) / tiles_n;
+        const int tiles_n = (d.N + TBN - 1) / TBN, r = t - tstart[q], mt = r / tiles_n, nt = r % tiles_n;
         const int nkb = (d.K + TBK - 1) / TBK;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int st = int(g % NST);
@@ -282,16 +402,20 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
             ok = false;
             break;
           }
-          const uint32_t bytes = uint32_t(ASZ) * 2u;
-          const __nv_bfloat16* src = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(abar + st)), "r"(bytes));
+          const uint32_t abytes = uint32_t(ASZ) * 2u, bbytes = uint32_t(BSZ) * 2u;
+          const __nv_bfloat16* asrc = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
+          const __nv_bfloat16* bsrc = d.Bdig + (int64_t(nt) * nkb + kb) * BSZ;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(full + st)),
+                       "r"(abytes + bbytes));
           asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(sptr(As + st * ASZ)), "l"(src), "r"(bytes), "r"(sptr(abar + st)) : "memory");
+                       :: "r"(sptr(As + st * ASZ)), "l"(asrc), "r"(abytes), "r"(sptr(full + st)) : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(sptr(Bs + st * BSZ)), "l"(bsrc), "r"(bbytes), "r"(sptr(full + st)) : "memory");
         }
       }
       // the copies of the last stages (the latest use of each) have landed before the CTA
       // may exit, also after an abort
-      for (uint32_t h = g > NST ? g - NST : 0; h < g; ++h) mbar_wait_own(sptr(abar + h % NST), (h / NST) & 1u);
+      for (uint32_t h = g > NST ? g - NST : 0; h < g; ++h) mbar_wait_own(sptr(full + h % NST), (h / NST) & 1u);
     }
   } else if (warp == 1) {
     // ---------------- MMA issue (one thread)
@@ -313,8 +437,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
         const uint32_t acc0 = tmem + uint32_t(b * ACC);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int st = int(g % NST);
-          const uint32_t par = (g / NST) & 1u;
-          if (!mbar_wait(sptr(abar + st), par, abort_flag) || !mbar_wait(sptr(bfull + st), par, abort_flag)) {
+          if (!mbar_wait(sptr(full + st), (g / NST) & 1u, abort_flag)) {
             fail(2);
             ok = false;
             break;
@@ -353,109 +476,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
         mbar_wait_own(sptr(fin), 0u);
       }
     }
-  } else if (tid < kEpiThread0) {
-    // ---------------- B producers: column exponents and digit planes
-    const int p = tid - kProdThread0, pw = p >> 5;
-    const int cl = 4 * pw + (lane >> 3);  // this lane's column within a 32-column group
-    const int kq = lane & 7;              // K quad: k = 4 kq .. 4 kq + 3 of a block
-    constexpr int NG = TBN / 32;          // 32-column groups per tile
-    uint32_t g = 0;
-    int i = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-      const int q = tile_desc(tstart, batch, t);
-      const TcDesc<TB, TC>& d = descs[q];
-      const int tiles_n = (d.N + TBN - 1) / TBN, nt = (t - tstart[q]) % tiles_n;
-      const int j0 = nt * TBN, K = d.K, nkb = (K + TBK - 1) / TBK;
-      const TB* B = d.B;
-      const int ldb = d.ldb, tb = d.tb;
-      const int b = i & 1;
-      int tau[NG];
-#pragma unroll
-      for (int gq = 0; gq < NG; ++gq) tau[gq] = 0;
-      if constexpr (S > 1) {
-        const bool ok = i < 2 || mbar_wait(sptr(acce + b), ((i >> 1) - 1) & 1u, abort_flag);
-        if (__any_sync(0xffffffffu, !ok)) {
-          fail(1);
-          break;
-        }
-        // tau_j = 1 + the largest exponent in column j of op(B) over all of K (zero
-        // columns give -1022); 8 lanes per column, eight loads in flight per lane
-        const int gn = j0 + cl;
-        int emax = 0;
-        for (int k0 = kq; k0 < K; k0 += 64) {
-          TB v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int k = k0 + 8 * u;
-            v[u] = (k < K && gn < d.N) ? ld_b(B, ldb, tb, k, gn) : TB(0);
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            emax = max(emax, int((uint64_t(__double_as_longlong(double(v[u]))) >> 52) & 0x7FF));
-        }
-        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
-        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
-        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
-        tau[0] = emax ? emax - 1023 + 1 : -1022;
-        if (kq == 0) tauS[b * TBN + cl] = tau[0];
-        mbar_arrive(sptr(taur + b));
-      }
-      // register prefetch of one K block: NG groups x 4 consecutive k of one column
-      TB xv[NG][4];
-      auto load_b = [&](int k0) {
-#pragma unroll
-        for (int gq = 0; gq < NG; ++gq)
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const int gk = k0 + 4 * kq + kk, gj = j0 + gq * 32 + cl;
-            xv[gq][kk] = (gj < d.N && gk < K) ? ld_b(B, ldb, tb, gk, gj) : TB(0);
-          }
-      };
-      load_b(0);
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb, ++g) {
-        const int st = int(g % NST);
-        TB cur[NG][4];
-#pragma unroll
-        for (int gq = 0; gq < NG; ++gq)
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) cur[gq][kk] = xv[gq][kk];
-        if (kb + 1 < nkb) load_b((kb + 1) * TBK);
-        const bool freed = g < NST || mbar_wait(sptr(empty + st), (g / NST - 1) & 1u, abort_flag);
-        if (__any_sync(0xffffffffu, !freed)) {
-          fail(1);
-          ok = false;
-          break;
-        }
-        __nv_bfloat16* dst = Bs + st * BSZ;
-#pragma unroll
-        for (int gq = 0; gq < NG; ++gq) {
-          uint32_t pk[S][2];
-#pragma unroll
-          for (int kk = 0; kk < 4; kk += 2) {
-            float d0[S], d1[S];
-            if constexpr (S == 1) {
-              d0[0] = float(cur[gq][kk]);
-              d1[0] = float(cur[gq][kk + 1]);
-            } else {
-              digits_f64<S>(double(cur[gq][kk]), tau[0], d0);
-              digits_f64<S>(double(cur[gq][kk + 1]), tau[0], d1);
-            }
-#pragma unroll
-            for (int sq = 0; sq < S; ++sq) {
-              __nv_bfloat162 h = __floats2bfloat162_rn(d0[sq], d1[sq]);
-              pk[sq][kk >> 1] = *reinterpret_cast<uint32_t*>(&h);
-            }
-          }
-#pragma unroll
-          for (int sq = 0; sq < S; ++sq)
-            *reinterpret_cast<uint2*>(dst + core_off(sq * TBN + gq * 32 + cl, 4 * kq)) = make_uint2(pk[sq][0], pk[sq][1]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(sptr(bfull + st));
-      }
-      if (!ok) break;
-    }
   } else {
     // ---------------- epilogue: one warp per TMEM lane quarter, one row per lane
     const int quarter = warp & 3;
@@ -466,9 +486,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       const int tiles_n = (d.N + TBN - 1) / TBN, r = t - tstart[q];
       const int i0 = (r / tiles_n) * TBM, j0 = (r % tiles_n) * TBN;
       const int b = i & 1;
-      const uint32_t par = (i >> 1) & 1u;
-      bool ok = mbar_wait(sptr(accf + b), par, abort_flag);
-      if (S > 1 && ok) ok = mbar_wait(sptr(taur + b), par, abort_flag);
+      const bool ok = mbar_wait(sptr(accf + b), (i >> 1) & 1u, abort_flag);
       if (__any_sync(0xffffffffu, !ok)) {
         fail(1);
         break;
@@ -488,6 +506,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
 #pragma unroll
           for (int u = 0; u < 16; ++u) acc[u] = __uint_as_float(rr[u]);
         } else {
+          // column scales of this chunk (loads in flight during the TMEM reads)
+          int tj[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) tj[u] = j0 + c0 + u < d.N ? __ldg(d.Btau + j0 + c0 + u) : 0;
           // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
           // units of 2^-49; one int64 -> FP64 conversion, then the power-of-two scale
           // 2^{sigma + tau - 49} added to the exponent bits.  The TMEM load of the next
@@ -512,7 +534,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
             double x = __ll2double_rn(iacc[u]);
-            const int sh = sig + tauS[b * TBN + c0 + u] - 49;
+            const int sh = sig + tj[u] - 49;
             const long long bits = __double_as_longlong(x);
             if (x != 0.0) {
               const int eb = int((bits >> 52) & 0x7FF) + sh;
@@ -579,6 +601,16 @@ int sm_count() {
 }  // namespace
 
 template <int S, class TB, class TC>
+cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxN) {
+  if (batch <= 0 || maxN <= 0) return cudaSuccess;
+  if (batch > kMaxDescs) return cudaErrorInvalidValue;
+  const int64_t bound = int64_t(batch) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
+  const int grid = int(std::min<int64_t>(bound, 4 * int64_t(sm_count())));
+  k_tc_digits<S, TB, TC><<<grid, kDigThreads, 0, s>>>(d_desc, batch);
+  return cudaGetLastError();
+}
+
+template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err) {
   if (batch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
@@ -593,6 +625,8 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
   k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, epi, alpha, err);
   return cudaGetLastError();
 }
+template cudaError_t launch_tc_digits<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int);
+template cudaError_t launch_tc_digits<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int);
 template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
                                                        double, int*);
 template cudaError_t launch_gemm_tc<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int, int, int, float,
@@ -608,6 +642,12 @@ uint16_t bf16_bits_rn(float f) {
 }  // namespace
 
 int tc_kblocks(int K) { return (K + TBK - 1) / TBK; }
+
+int64_t tc_dig_elems(int N, int K, int S) {
+  if (N <= 0 || K <= 0) return 0;
+  const int tbn = S == 1 ? TcCfg<1>::TBN : TcCfg<7>::TBN;
+  return int64_t((N + tbn - 1) / tbn) * ((K + TBK - 1) / TBK) * S * tbn * TBK;
+}
 
 double tc_exec_flops(int M, int N, int K, int S) {
   if (M <= 0 || N <= 0 || K <= 0) return 0.0;

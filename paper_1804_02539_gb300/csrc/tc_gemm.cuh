@@ -23,14 +23,26 @@ struct TcDesc {
   const TC* E;                   // EPI_MUL operand, indexed like C with stride lde
   int lde;
   int M, N, K;
+  // scratch written by the digit pass and read by the GEMM: B's digit planes
+  // [N/TBN tiles][K blocks][S][TBN x 32] (core-matrix layout) and its column exponents [N]
+  __nv_bfloat16* Bdig = nullptr;
+  int* Btau = nullptr;
 };
+
+// Scratch sizes of one descriptor (BF16 elements of Bdig, ints of Btau) for S slices.
+int64_t tc_dig_elems(int N, int K, int S);
+inline int64_t tc_tau_elems(int N, int S) { return S > 1 ? N : 0; }
 
 // S = 7: FP64-accurate digit-slice product (TB = TC = double), for K <= kTcMaxK (every single
 // digit product summed over K stays an exact FP32 integer); S = 1: BF16 product with FP32
 // accumulation (TB = TC = float).  Persistent launch over every tile of the `batch`
-// descriptors (at most 512; C must not alias B or E).  err: device flag set when an mbarrier
-// wait times out.
+// descriptors (at most 512; C must not alias B or E; the digit pass must have run on the
+// same stream since B last changed).  err: device flag set when an mbarrier wait times out.
 constexpr int kTcMaxK = 1023;
+// Two launches: the digit pass (B's digit planes and column exponents into Bdig/Btau, every
+// element once) and the GEMM (both operands by bulk copies).
+template <int S, class TB, class TC>
+cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxN);
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
                            TC alpha, int* err);
