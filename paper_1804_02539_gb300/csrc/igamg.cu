@@ -1003,13 +1003,16 @@ void build_levels(igamg_ctx* c) {
           double* Tb = g0.C;   // scratch T (n0 x n1)
           double* Yb = g1.C;   // scratch Y
           Sl a0t = slices(S0, 1), a1t = slices(S1, 1), a0 = slices(S0, 0), a1 = slices(S1, 0);
-          TcDesc<double, double> d0{a0t.a, a0t.e, a0t.nkb, g0.B, P.n[1], 0, Tb, n1, 0, nullptr, 0, n0, n1, n0};
+          // every stage stores its output transposed (lanes of the epilogue write consecutive
+          // addresses): T and S are kept as T^T, S^T ([n1][n0]), which the next stage reads
+          // row by row
+          TcDesc<double, double> d0{a0t.a, a0t.e, a0t.nkb, g0.B, P.n[1], 0, Tb, n0, 1, nullptr, 0, n0, n1, n0};
           t0F.push_back(d0);
           d0.B = s0R[q].B;
           t0R.push_back(d0);
-          t1.push_back(TcDesc<double, double>{a1t.a, a1t.e, a1t.nkb, Tb, n1, 1, Yb, n1, 1, g1.E, n1, n1, n0, n1});
-          t2.push_back(TcDesc<double, double>{a0.a, a0.e, a0.nkb, Yb, n1, 0, Tb, n1, 0, nullptr, 0, n0, n1, n0});
-          t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n1, 1, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
+          t1.push_back(TcDesc<double, double>{a1t.a, a1t.e, a1t.nkb, Tb, n0, 0, Yb, n1, 1, g1.E, n1, n1, n0, n1});
+          t2.push_back(TcDesc<double, double>{a0.a, a0.e, a0.nkb, Yb, n1, 0, Tb, n0, 1, nullptr, 0, n0, n1, n0});
+          t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n0, 0, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
           ++q;
         }
         set_tc(c, L.n64.tc0F, t0F);
@@ -1211,13 +1214,14 @@ void build_levels(igamg_ctx* c) {
           q3.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)off, nullptr, len1, len1, len1, 0, len0, len1, len1});
           if (tcf) {  // the interior formulation on the face block (offsets resolved below)
             using TD = TcDesc<double, double>;
-            tqd[0].push_back(TD{a0t.a, a0t.e, a0t.nkb, (double*)(intptr_t)off, len1, 0, (double*)(intptr_t)tb, len1, 0,
+            // outputs stored transposed, as for the interiors (T^T and S^T in fT)
+            tqd[0].push_back(TD{a0t.a, a0t.e, a0t.nkb, (double*)(intptr_t)off, len1, 0, (double*)(intptr_t)tb, len0, 1,
                                 nullptr, 0, len0, len1, len0});
-            tqd[1].push_back(TD{a1t.a, a1t.e, a1t.nkb, (double*)(intptr_t)tb, len1, 1, (double*)(intptr_t)tb, len1, 1,
+            tqd[1].push_back(TD{a1t.a, a1t.e, a1t.nkb, (double*)(intptr_t)tb, len0, 0, (double*)(intptr_t)tb, len1, 1,
                                 Dinv, len1, len1, len0, len1});
-            tqd[2].push_back(TD{a0.a, a0.e, a0.nkb, (double*)(intptr_t)tb, len1, 0, (double*)(intptr_t)tb, len1, 0,
+            tqd[2].push_back(TD{a0.a, a0.e, a0.nkb, (double*)(intptr_t)tb, len1, 0, (double*)(intptr_t)tb, len0, 1,
                                 nullptr, 0, len0, len1, len0});
-            tqd[3].push_back(TD{a1.a, a1.e, a1.nkb, (double*)(intptr_t)tb, len1, 1, (double*)(intptr_t)off, len1, 1,
+            tqd[3].push_back(TD{a1.a, a1.e, a1.nkb, (double*)(intptr_t)tb, len0, 0, (double*)(intptr_t)off, len1, 1,
                                 nullptr, 0, len1, len0, len1});
           }
         }

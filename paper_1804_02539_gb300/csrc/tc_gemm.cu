@@ -36,7 +36,8 @@
 //                  columns are exactly the accumulators of diagonals s+1 .. 8, which are
 //                  contiguous in TMEM (7 MMAs per 16-wide K step instead of 28; each slice
 //                  of A is read from shared memory once per K step);
-//     warps 2..5   the epilogue, one warp per TMEM lane quarter.
+//     warps 2..17  the epilogue, four warps per TMEM lane quarter (a quarter of the columns
+//                  each; all 7 diagonals of a warp's columns in one round of TMEM loads).
 //   Two accumulator sets in TMEM (2 x 7 x 32 of the 512 columns) let the epilogue of one
 //   tile run while the MMAs of the next are issued.  Every tile runs on the tensor cores,
 //   including the ragged remainders of M, N and K (padded with zero digits).
@@ -52,6 +53,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
@@ -60,7 +62,8 @@ namespace igamg {
 
 namespace {
 constexpr int TBM = 128, TBK = 32;  // rows of a tile; K block of one pipeline stage
-constexpr int NT = 192;             // 6 warps: TMA, MMA, 4 epilogue
+constexpr int NT = 576;             // 18 warps: TMA, MMA, 16 epilogue (4 per TMEM lane quarter)
+constexpr int kEpiThreads = 512;
 constexpr int kDigThreads = 256;    // digit pass: 8 warps per 32-column panel
 constexpr int kDigRegBlocks = 9;    // K blocks a digit-pass lane holds in registers (288 rows; S = 7)
 constexpr int kMaxDescs = 512;      // descriptors of one launch (tile prefix in shared memory)
@@ -141,6 +144,24 @@ __device__ __forceinline__ bool mbar_wait_own(uint32_t mbar, uint32_t phase) {
   return false;
 }
 
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t ta, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+}
+// Waits for all of the thread's outstanding TMEM loads (56 registers of 7 x8 loads).
+__device__ __forceinline__ void tmem_ld_wait56(uint32_t (*r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[0][4]), "+r"(r[0][5]), "+r"(r[0][6]),
+                 "+r"(r[0][7]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[1][4]), "+r"(r[1][5]),
+                 "+r"(r[1][6]), "+r"(r[1][7]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]), "+r"(r[2][4]),
+                 "+r"(r[2][5]), "+r"(r[2][6]), "+r"(r[2][7]), "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]),
+                 "+r"(r[3][4]), "+r"(r[3][5]), "+r"(r[3][6]), "+r"(r[3][7]), "+r"(r[4][0]), "+r"(r[4][1]), "+r"(r[4][2]),
+                 "+r"(r[4][3]), "+r"(r[4][4]), "+r"(r[4][5]), "+r"(r[4][6]), "+r"(r[4][7]), "+r"(r[5][0]), "+r"(r[5][1]),
+                 "+r"(r[5][2]), "+r"(r[5][3]), "+r"(r[5][4]), "+r"(r[5][5]), "+r"(r[5][6]), "+r"(r[5][7]), "+r"(r[6][0]),
+                 "+r"(r[6][1]), "+r"(r[6][2]), "+r"(r[6][3]), "+r"(r[6][4]), "+r"(r[6][5]), "+r"(r[6][6]), "+r"(r[6][7]));
+}
+
 __device__ __forceinline__ void tmem_ld16_issue(uint32_t ta, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -168,6 +189,35 @@ __device__ __forceinline__ void split_f64(double x, int& e, uint64_t& m, bool& n
     e = eb - 1023;
     m = f | (uint64_t(1) << 52);
   }
+}
+
+// v 2^sh for an integer |v| < 2^62, rounded to nearest even like a conversion to FP64
+// followed by an exact power-of-two scaling, with integer operations only (this part's FP64
+// pipe is the slowest unit on the path).
+__device__ __forceinline__ double scaled_i64_to_f64(long long v, int sh) {
+  if (v == 0) return 0.0;
+  const uint64_t sign = v < 0 ? (uint64_t(1) << 63) : 0;
+  const uint64_t a = v < 0 ? uint64_t(-v) : uint64_t(v);
+  int e = 63 - __clzll(a);  // leading bit position
+  uint64_t m;
+  if (e <= 52) {
+    m = a << (52 - e);
+  } else {  // drop e - 52 low bits, round to nearest even
+    const int d = e - 52;
+    const uint64_t rem = a & ((uint64_t(1) << d) - 1), half = uint64_t(1) << (d - 1);
+    m = a >> d;
+    if (rem > half || (rem == half && (m & 1))) {
+      ++m;
+      if (m == (uint64_t(1) << 53)) {
+        m >>= 1;
+        ++e;
+      }
+    }
+  }
+  const uint64_t frac = m & ((uint64_t(1) << 52) - 1);
+  const int eb = e + 1023 + sh;
+  if (eb > 0 && eb < 2047) return __longlong_as_double(static_cast<long long>(sign | (uint64_t(eb) << 52) | frac));
+  return ldexp(__longlong_as_double(static_cast<long long>(sign | (uint64_t(e + 1023) << 52) | frac)), sh);
 }
 
 // The descriptor q holding tile t (tile prefix `start` of `batch` descriptors): the last q
@@ -342,7 +392,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   uint64_t* full = bars;             // [NST] A and B copies landed (expect_tx)
   uint64_t* empty = full + NST;      // [NST] MMAs reading the stage done (commit)
   uint64_t* accf = empty + NST;      // [2] accumulator set complete (commit)
-  uint64_t* acce = accf + 2;         // [2] accumulator set read by the epilogue (128 arrivals)
+  uint64_t* acce = accf + 2;         // [2] accumulator set read by the epilogue (every epilogue thread)
   uint64_t* fin = acce + 2;          // [1] every MMA of this CTA done (commit)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -362,7 +412,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(sptr(accf + i), 1);
-      mbar_init(sptr(acce + i), 128);
+      mbar_init(sptr(acce + i), kEpiThreads);
     }
     mbar_init(sptr(fin), 1);
     *abort_flag = 0;
@@ -477,8 +527,11 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       }
     }
   } else {
-    // ---------------- epilogue: one warp per TMEM lane quarter, one row per lane
-    const int quarter = warp & 3;
+    // ---------------- epilogue: four warps per TMEM lane quarter (a quarter of the tile's
+    // columns each), one row per lane
+    using TA = typename std::conditional<S == 1, float, double>::type;  // epilogue arithmetic
+    const int ew = warp - 2, quarter = warp & 3, part = ew >> 2;
+    constexpr int CW = TBN / 4;  // columns of one epilogue warp
     int i = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
       const int q = tile_desc(tstart, batch, t);
@@ -496,9 +549,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       int sig = 0;
       if (S > 1 && gi < d.M) sig = d.Aexp[gi];
       const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * ACC);
+      constexpr int CC = S == 1 ? 16 : 8;  // columns per chunk
 #pragma unroll 1
-      for (int c0 = 0; c0 < TBN; c0 += 16) {
-        double acc[16];
+      for (int c0 = part * CW; c0 < (part + 1) * CW; c0 += CC) {
+        TA acc[CC];
         if constexpr (S == 1) {
           uint32_t rr[16];
           tmem_ld16_issue(trow + uint32_t(c0), rr);
@@ -507,70 +561,56 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
           for (int u = 0; u < 16; ++u) acc[u] = __uint_as_float(rr[u]);
         } else {
           // column scales of this chunk (loads in flight during the TMEM reads)
-          int tj[16];
+          int tj[8];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) tj[u] = j0 + c0 + u < d.N ? __ldg(d.Btau + j0 + c0 + u) : 0;
-          // exact integer recombination: sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7, in
-          // units of 2^-49; one int64 -> FP64 conversion, then the power-of-two scale
-          // 2^{sigma + tau - 49} added to the exponent bits.  The TMEM load of the next
-          // diagonal is in flight while one is converted.
-          long long iacc[16];
+          for (int u = 0; u < 8; ++u) tj[u] = j0 + c0 + u < d.N ? __ldg(d.Btau + j0 + c0 + u) : 0;
+          // the 7 diagonals of these 8 columns in one round of TMEM loads, then the exact
+          // integer recombination sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7 in units of
+          // 2^-49, and the rounding to FP64 with the power-of-two scale 2^{sigma + tau - 49}
+          uint32_t rr[7][8];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) iacc[u] = 0;
-          uint32_t rr[2][16];
-          tmem_ld16_issue(trow + uint32_t(c0), rr[0]);
-          tmem_ld_wait(rr[0]);
+          for (int dg = 0; dg < 7; ++dg) tmem_ld8_issue(trow + uint32_t(dg * TBN + c0), rr[dg]);
+          tmem_ld_wait56(rr);
 #pragma unroll
-          for (int dg = 0; dg < S; ++dg) {
-            if (dg + 1 < S) tmem_ld16_issue(trow + uint32_t((dg + 1) * TBN + c0), rr[(dg + 1) & 1]);
-            const int qd = dg + 2;
+          for (int u = 0; u < 8; ++u) {
+            long long iacc = 0;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              long long iv = __float2int_rn(__uint_as_float(rr[dg & 1][u]));  // |D_q| < 2^24 in practice
-              iacc[u] += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
+            for (int dg = 0; dg < 7; ++dg) {
+              const int qd = dg + 2;
+              const long long iv = __float2int_rn(__uint_as_float(rr[dg][u]));  // |D_q| < 2^24 in practice
+              iacc += qd <= 7 ? (iv << (7 * (7 - qd))) : (iv >> 7);
             }
-            if (dg + 1 < S) tmem_ld_wait(rr[(dg + 1) & 1]);
-          }
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            double x = __ll2double_rn(iacc[u]);
-            const int sh = sig + tj[u] - 49;
-            const long long bits = __double_as_longlong(x);
-            if (x != 0.0) {
-              const int eb = int((bits >> 52) & 0x7FF) + sh;
-              x = (eb > 0 && eb < 2047) ? __longlong_as_double(bits + ((long long)sh << 52)) : ldexp(x, sh);
-            }
-            acc[u] = x;
+            acc[u] = scaled_i64_to_f64(iacc, sig + tj[u] - 49);
           }
         }
-        if (c0 + 16 >= TBN) {
-          // every TMEM value of this set is in registers: hand the set back to the MMAs
+        if (c0 + CC >= (part + 1) * CW) {
+          // every TMEM value of this warp's columns is in registers: hand them back
           asm volatile("tcgen05.fence::before_thread_sync;");
           mbar_arrive(sptr(acce + b));
         }
         if (gi < d.M) {
-          // epilogue operands first (16 loads in flight), then the stores
-          double e[16];
+          // epilogue operands first (loads in flight), then the stores
+          TA e[CC];
           const bool needs = epi == EPI_MUL || epi == EPI_ADD;
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < CC; ++u) {
             const int gj = j0 + c0 + u;
-            e[u] = 0.0;
+            e[u] = TA(0);
             if (needs && gj < d.N) {
-              if (epi == EPI_MUL) e[u] = double(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
-              else e[u] = double(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
+              if (epi == EPI_MUL) e[u] = TA(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
+              else e[u] = TA(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
             }
           }
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < CC; ++u) {
             const int gj = j0 + c0 + u;
             if (gj >= d.N) continue;
-            const double v = acc[u];
+            const TA v = acc[u];
             TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
             switch (epi) {
               case EPI_MUL: *cp = TC(v * e[u]); break;
-              case EPI_ASSIGN: *cp = TC(double(alpha) * v); break;
-              case EPI_ADD: *cp = TC(fma(double(alpha), v, e[u])); break;
+              case EPI_ASSIGN: *cp = TC(TA(alpha) * v); break;
+              case EPI_ADD: *cp = TC(fma(TA(alpha), v, e[u])); break;
               default: *cp = TC(v);
             }
           }
