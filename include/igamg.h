@@ -226,8 +226,9 @@ igamg_status igamg_fd_apply(int n0, int n1, const double* U0, const double* U1, 
  *   - Arguments and results are those of igamg_fd_apply without `scratch`.
  *   - n0 * n1 must not exceed 262144 (512 x 512); larger tiles are rejected with
  *     IGAMG_ERR_ARG and a message naming the limit, and nothing is launched.
- *   - The first call on a device looks up that device's address of the array (once per
- *     device, with that device current); make that first call before any stream capture.
+ *   - Every call looks up the array's address on the current device (so a device reset
+ *     between calls is harmless); the first call on a device also loads the library's
+ *     device code there: make that first call before any stream capture.
  *   - All calls on a device share the one array, which keeps the last call's contents;
  *     every element is written before it is read, so nothing has to be cleared.  Calls
  *     whose kernels overlap on the GPU (different streams, or threads) race on the array:

@@ -4,8 +4,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <map>
-#include <mutex>
 #include <string>
 
 #include "../../include/igamg.h"
@@ -23,26 +21,15 @@ namespace {
 constexpr int64_t kMaxTile = 512 * 512;
 __device__ __align__(256) double g_fd_scratch[2 * kMaxTile];
 
-std::mutex g_mu;
-std::map<int, double*> g_scratch_addr;  // device ordinal -> device address of g_fd_scratch
-
 // Device address of the scratch array on the current device.  In host code the name
 // g_fd_scratch is only a host-side stand-in, never a device pointer, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up with the device current.  The lookup runs on every call (it is cheap once the
+// library's device code is loaded), so a device reset between calls, which may move the
+// array, never leaves a stale address behind.
 cudaError_t scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(g_mu);
-  auto it = g_scratch_addr.find(dev);
-  if (it != g_scratch_addr.end()) {
-    *out = it->second;
-    return cudaSuccess;
-  }
   void* p = nullptr;
-  e = cudaGetSymbolAddress(&p, g_fd_scratch);
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_fd_scratch);
   if (e != cudaSuccess) return e;
-  g_scratch_addr[dev] = static_cast<double*>(p);
   *out = static_cast<double*>(p);
   return cudaSuccess;
 }
@@ -71,13 +58,18 @@ extern "C" igamg_status igamg_fd_apply_noalloc(int n0, int n1, const double* U0,
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // Every element of T and Y is written before it is read, so the contents left by an
   // earlier call never matter and nothing needs clearing.
-  cudaError_t r[4];
-  r[0] = launch_gemm_one(s, GemmDesc{U0, R, T, nullptr, n0, ldr, n1, 0, n0, n1, n0}, true, false, EPI_STORE, 1.0);
-  r[1] = launch_gemm_one(s, GemmDesc{T, U1, Y, Dinv, n1, n1, n1, n1, n0, n1, n1}, false, false, EPI_MUL, 1.0);
-  r[2] = launch_gemm_one(s, GemmDesc{U0, Y, T, nullptr, n0, n1, n1, 0, n0, n1, n0}, false, false, EPI_STORE, 1.0);
-  r[3] = launch_gemm_one(s, GemmDesc{T, U1, Z, nullptr, n1, n1, ldz, 0, n0, n1, n1}, false, true, EPI_ASSIGN, tau);
-  for (cudaError_t x : r)
+  // the four products in order; a failed launch stops the sequence, so no later product reads
+  // scratch that was not written
+  const GemmDesc g[4] = {GemmDesc{U0, R, T, nullptr, n0, ldr, n1, 0, n0, n1, n0},
+                         GemmDesc{T, U1, Y, Dinv, n1, n1, n1, n1, n0, n1, n1},
+                         GemmDesc{U0, Y, T, nullptr, n0, n1, n1, 0, n0, n1, n0},
+                         GemmDesc{T, U1, Z, nullptr, n1, n1, ldz, 0, n0, n1, n1}};
+  const bool ta[4] = {true, false, false, false}, tb[4] = {false, false, false, true};
+  const int epi[4] = {EPI_STORE, EPI_MUL, EPI_STORE, EPI_ASSIGN};
+  for (int k = 0; k < 4; ++k) {
+    const cudaError_t x = launch_gemm_one(s, g[k], ta[k], tb[k], epi[k], k == 3 ? tau : 1.0);
     if (x != cudaSuccess)
       return fail(IGAMG_ERR_CUDA, std::string("igamg_fd_apply_noalloc: launch: ") + cudaGetErrorString(x));
+  }
   return IGAMG_OK;
 }

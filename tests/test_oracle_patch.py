@@ -111,3 +111,56 @@ def test_elementwise_bands_equal_kronecker_form(dim, p, m):
     M2 = patch.bands_to_csr(patch.patch_bands(C, [t] * dim, [p] * dim, mass=True), [p] * dim)
     assert abs(A1 - A2).max() < 1e-14 * abs(A1).max() * 10
     assert abs(M1 - M2).max() < 1e-14 * abs(M1).max() * 10
+
+
+@pytest.mark.parametrize("dim,p,m", [(2, 2, 3), (2, 4, 2), (3, 2, 2)])
+def test_affine_mass_is_scaled_kronecker_product(dim, p, m):
+    """An affine map G(xi) = x0 + J xi (sheared, not axis-aligned) has constant |det J|, so
+    the geometry mass matrix is |det J| (M x ... x M) with the univariate mass matrix M of
+    the knot vector (whose rows are pinned separately); both the Kronecker-form and the
+    element-by-element (band) assembly must give it."""
+    t = bspline.uniform_knots(m, p)
+    M, _ = bspline.mass_stiffness_1d(t, p)
+    rng = np.random.default_rng(11 + dim)
+    J = np.eye(dim) * 1.3 + rng.uniform(-0.3, 0.3, (dim, dim))
+    x0 = rng.uniform(-2, 2, dim)
+    C = x0 + patch.corner_bits(dim).astype(float) @ J.T
+    expect = abs(np.linalg.det(J)) * M
+    for _ in range(dim - 1):
+        expect = np.kron(expect, M)
+    _, Mg = patch.patch_matrices(C, [t] * dim, [p] * dim, want_mass=True)
+    Mb = patch.bands_to_csr(patch.patch_bands(C, [t] * dim, [p] * dim, mass=True), [p] * dim)
+    np.testing.assert_allclose(Mg.toarray(), expect, atol=1e-14 * abs(expect).max() * 10)
+    np.testing.assert_allclose(Mb.toarray(), expect, atol=1e-14 * abs(expect).max() * 10)
+
+
+@pytest.mark.parametrize("p,m", [(2, 3), (3, 2)])
+def test_bilinear_mass_entries_against_independent_quadrature(p, m):
+    """Non-affine bilinear patch: every entry M_geo[(a,b),(c,d)] = int B_a B_c (xi0)
+    B_b B_d (xi1) |det J(xi)| dxi, evaluated with SciPy's B-splines and a Gauss rule of its
+    own on each element (|det J| is affine for a bilinear map, so the rule is exact) — a
+    mix-up of basis indices in the oracle's element scatter would fail here."""
+    from scipy.interpolate import BSpline
+    t = bspline.uniform_knots(m, p)
+    n = m + p
+    C = quad_corners(QUADS[2])
+    xg, wg = np.polynomial.legendre.leggauss(p + 2)
+    xs, ws = [], []
+    for e in range(m):
+        a, b = e / m, (e + 1) / m
+        xs.append(a + (b - a) * (xg + 1) / 2)
+        ws.append((b - a) / 2 * wg)
+    x1, w1 = np.concatenate(xs), np.concatenate(ws)
+    B = np.stack([BSpline(t, np.eye(n)[i], p, extrapolate=False)(x1) for i in range(n)], axis=1)
+    B = np.nan_to_num(B)
+    X0, X1 = np.meshgrid(x1, x1, indexing="ij")
+    W = np.outer(w1, w1)
+    # Jacobian of the bilinear map written out (corner c = c0 + 2 c1 at xi = (c0, c1))
+    d0 = (1 - X1)[..., None] * (C[1] - C[0]) + X1[..., None] * (C[3] - C[2])
+    d1 = (1 - X0)[..., None] * (C[2] - C[0]) + X0[..., None] * (C[3] - C[1])
+    dj = np.abs(d0[..., 0] * d1[..., 1] - d0[..., 1] * d1[..., 0]) * W
+    expect = np.einsum("qa,qc,rb,rd,qr->abcd", B, B, B, B, dj).reshape(n * n, n * n)
+    Mb = patch.bands_to_csr(patch.patch_bands(C, [t, t], [p, p], mass=True), [p, p]).toarray()
+    _, Mg = patch.patch_matrices(C, [t, t], [p, p], want_mass=True)
+    np.testing.assert_allclose(Mb, expect, atol=1e-13 * abs(expect).max())
+    np.testing.assert_allclose(Mg.toarray(), expect, atol=1e-13 * abs(expect).max())

@@ -73,3 +73,22 @@ def test_no_alloc_rejects_tiles_beyond_its_limit():
                                        C.c_void_p(z.data_ptr()), 512, None)
     assert st == 1
     assert b"262144" in _lib().igamg_last_error(None)
+
+
+def test_no_alloc_in_place_and_on_a_side_stream():
+    """Z may be R itself (ldz == ldr, padded rows), and the call runs on the stream given:
+    both against igamg_fd_apply on the same tile."""
+    n0, n1, pad = 96, 70, 6
+    U0, U1, Dinv, R = _tile(5, n0, n1, pad)
+    ref = _with_scratch(U0, U1, Dinv, R, n1, 0.5)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        RZ = R.clone()
+        st = _lib().igamg_fd_apply_noalloc(n0, n1, C.c_void_p(U0.data_ptr()), C.c_void_p(U1.data_ptr()),
+                                           C.c_void_p(Dinv.data_ptr()), C.c_void_p(RZ.data_ptr()), RZ.stride(0),
+                                           0.5, C.c_void_p(RZ.data_ptr()), RZ.stride(0), C.c_void_p(side.cuda_stream))
+        assert st == 0, _lib().igamg_last_error(None)
+    side.synchronize()
+    assert _rel(RZ[:, :n1], ref) <= TOL
+    assert torch.equal(RZ[:, n1:], R[:, n1:])      # the row padding is left alone
