@@ -287,9 +287,18 @@ def run_precision_variant(pr, prec_name, b, xr, dev, stream, steps, warmup):
     ms = e0.elapsed_time(e1) / steps
     err = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
     ms_v, by_v = ctx.cycle_time(b, 10)
+    # per-class breakdown of one solve (every launch bracketed by events; untimed)
+    ctx.profile_enable(0xFF)
+    x.zero_()
+    ctx.solve(b, x, TOL)
+    prof = ctx.profile_read()
+    ctx.profile_enable(0)
     out = {"value": round(N / (ms * 1e-3) / 1e6, 4), "ms_per_step": round(ms, 3), "iters": res.iters,
            "outer_iters": res.outer_iters, "relres": res.relres, "status": st, "rel_err_vs_fp64_solution": err,
-           "vcycle": {"ms": round(ms_v, 4), "algorithmic_gb": round(by_v / 1e9, 4)}}
+           "vcycle": {"ms": round(ms_v, 4), "algorithmic_gb": round(by_v / 1e9, 4)},
+           "kernel_breakdown": {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"],
+                                    "gbyte_per_step": round(v["bytes"] / 1e9, 4)}
+                                for k, v in prof.items() if k not in SUB_ACCOUNTS}}
     ctx.free()
     return out
 

@@ -100,7 +100,7 @@ struct TcSet {
   double dig_bytes = 0;   // digit pass: B read, digit planes and exponents written
   // digit scratch of the set: sizes and per-descriptor offsets; the descriptors are uploaded
   // once the context's scratch is bound (bind_tc)
-  int64_t dig_elems = 0, tau_elems = 0;
+  int64_t dig_elems = 0, tau_elems = 0, tiles = 0;
   std::vector<int64_t> dig_off, tau_off;
   bool side = false;      // launched on the interface stream (its own scratch)
 };
@@ -454,7 +454,7 @@ void set_tc(igamg_ctx*, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v, bool s
   ts.batch = int(v.size());
   ts.maxM = ts.maxN = 0;
   ts.flops = ts.exec_flops = ts.dig_bytes = 0;
-  ts.dig_elems = ts.tau_elems = 0;
+  ts.dig_elems = ts.tau_elems = ts.tiles = 0;
   ts.dig_off.clear();
   ts.tau_off.clear();
   ts.side = side;
@@ -463,6 +463,7 @@ void set_tc(igamg_ctx*, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v, bool s
     ts.maxN = std::max(ts.maxN, d.N);
     ts.flops += 2.0 * d.M * double(d.N) * d.K;
     ts.exec_flops += tc_exec_flops(d.M, d.N, d.K, S);
+    ts.tiles += d.K > 0 ? tc_tiles(d.M, d.N, S) : 0;
     ts.dig_off.push_back(ts.dig_elems);
     ts.tau_off.push_back(ts.tau_elems);
     ts.dig_elems += tc_dig_elems(d.N, d.K, S);
@@ -515,9 +516,11 @@ void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha, int cls = C
   if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
   ProfScope ps(c, cls, ts.flops, 0.0, 1, CLS_TC_KERNEL);
   if constexpr (std::is_same<T, double>::value)
-    CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err)));
+    CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err,
+                                          ts.tiles)));
   else
-    CK((launch_gemm_tc<1, float, float>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, float(alpha), c->tc_err)));
+    CK((launch_gemm_tc<1, float, float>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, float(alpha), c->tc_err,
+                                        ts.tiles)));
 }
 
 // ---------------------------------------------------------------- setup helpers

@@ -652,25 +652,33 @@ cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int b
 
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
-                           TC alpha, int* err) {
+                           TC alpha, int* err, int64_t tiles) {
   if (batch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
   if (batch > kMaxDescs) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes<S>();
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
-  // persistent CTAs: one per SM, at most one per tile (the exact tile count is known on the
-  // device only; this bound counts every descriptor at the largest shape)
-  const int64_t bound = int64_t(batch) * ((maxM + TBM - 1) / TBM) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
-  const int grid = int(std::min<int64_t>(bound, sm_count()));
+  // persistent CTAs, at most one per SM: the fewest that give every CTA the same largest
+  // number of tiles as one per SM would, so that SMs left over serve the work running
+  // concurrently on the interface stream (tiles <= 0: bound from the largest shape)
+  if (tiles <= 0) tiles = int64_t(batch) * ((maxM + TBM - 1) / TBM) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
+  const int64_t nsm = sm_count(), per = (tiles + nsm - 1) / nsm;
+  const int grid = int(std::min<int64_t>((tiles + per - 1) / per, nsm));
   k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, epi, alpha, err);
   return cudaGetLastError();
 }
 template cudaError_t launch_tc_digits<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int);
 template cudaError_t launch_tc_digits<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int);
 template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
-                                                       double, int*);
+                                                       double, int*, int64_t);
 template cudaError_t launch_gemm_tc<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int, int, int, float,
-                                                     int*);
+                                                     int*, int64_t);
+
+int64_t tc_tiles(int M, int N, int S) {
+  if (M <= 0 || N <= 0) return 0;
+  const int tbn = S == 1 ? TcCfg<1>::TBN : TcCfg<7>::TBN;
+  return int64_t((M + TBM - 1) / TBM) * ((N + tbn - 1) / tbn);
+}
 
 namespace {
 uint16_t bf16_bits_rn(float f) {

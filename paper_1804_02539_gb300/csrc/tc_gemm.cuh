@@ -45,7 +45,9 @@ template <int S, class TB, class TC>
 cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxN);
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
-                           TC alpha, int* err);
+                           TC alpha, int* err, int64_t tiles = 0);
+// Output tiles of one M x N product (the GEMM's work items).
+int64_t tc_tiles(int M, int N, int S);
 
 // K blocks of the slice layout for inner dimension K.
 int tc_kblocks(int K);
