@@ -554,7 +554,8 @@ BATCH_COUNT, BATCH_SEED = 512, 4
 BATCH_DESC = ("512 independent 2D Poisson problems (seed 4): sqrt(K) x sqrt(K) rectangle patches on [0,1]^2, "
               "K in {4,9,16,25,36}, p in {2..6}, m in {16,32,64,128} intervals per patch direction, iid uniform; "
               "all Dirichlet, f = 2 pi^2 sin(pi x) sin(pi y) through its Greville interpolant; FP64 PCG + V(1,1) "
-              "to 1e-8 each, all resident, solved concurrently")
+              "to 1e-8 each, all resident, solved together (lockstep engine: one launch per cycle step over "
+              "all problems)")
 BATCH_ORACLE_SAMPLE = 6   # the oracle solves the first problems of the batch with m <= 32
 
 
@@ -646,19 +647,21 @@ def run_batch(args):
         ms_total = e0.elapsed_time(e1)
         clocks = sampler.stop()
         assert st == 0, sts
-        # profiled pass (untimed): launches and algorithmic work per class over the batch
-        for c in B.contexts:
-            c.profile_enable(0x3F)
-        for x in xs:
-            x.zero_()
-        B.solve(rhs, xs, TOL)
+        # profiled pass (untimed, worker streams: the contexts' own accounting; the lockstep
+        # engine counts its launches and FLOPs itself)
         prof = {}
-        for c in B.contexts:
-            for k, v in c.profile_read().items():
-                acc = prof.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
-                for f in acc:
-                    acc[f] += v[f]
-            c.profile_enable(0)
+        if B.engine() == "streams":
+            for c in B.contexts:
+                c.profile_enable(0x3F)
+            for x in xs:
+                x.zero_()
+            B.solve(rhs, xs, TOL)
+            for c in B.contexts:
+                for k, v in c.profile_read().items():
+                    acc = prof.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                    for f in acc:
+                        acc[f] += v[f]
+                c.profile_enable(0)
         # end to end: pinned host rhs in, solutions out, inside the timed region
         e2e = None
         if not args.no_e2e:
@@ -682,7 +685,9 @@ def run_batch(args):
     for k in SUB_ACCOUNTS:
         prof.pop(k, None)
     f64 = fp64_peaks()
-    flops = sum(v["flops"] for v in prof.values())
+    engine = B.engine()
+    lk = B.stats() if engine == "lockstep" else None
+    flops = lk["flops"] if lk else sum(v["flops"] for v in prof.values())
     byts = sum(v["bytes"] for v in prof.values())
     ach = flops / (ms_step * 1e-3) / 1e12
     pk, src = peaks()
@@ -693,22 +698,27 @@ def run_batch(args):
                                        "bf16": "bf16 bands, f32 (f64 refinement)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "batch512_2d_rect", "description": BATCH_DESC, "problems": len(probs),
+                   "engine": engine, "launches_per_solve": lk["launches"] if lk else None,
                    "dofs_total": Ntot, "dofs_min": min(Ns), "dofs_max": max(Ns), "workers": min(args.workers or 16, len(probs)),
                    "iters_min": min(r.iters for r in res), "iters_max": max(r.iters for r in res),
                    "setup_s": round(t_setup, 1), "l2": "inputs larger than L2 (vectors of 5.3e7 dofs)",
                    "device_gb": round(sum(c.device_bytes() for c in B.contexts) / 1e9, 3)},
         "e2e": {"value": None if e2e is None else round(Ntot / e2e / 1e6, 4), "unit": "MDOF/s",
                 "h2d_bytes_per_step": 8 * Ntot, "d2h_bytes_per_step": 8 * Ntot},
-        "gpu_launches": int(sum(v["launches"] for v in prof.values()) * args.steps),
+        "gpu_launches": int((lk["launches"] if lk else sum(v["launches"] for v in prof.values())) * args.steps),
         "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": f64["fma_tflops"],
                      "unit": "TFLOP/s", "frac": round(ach / f64["fma_tflops"], 4),
                      "peak_source": "measured in this run: FP64 FMA chains (igamg_micro_fp64 kind 0)",
-                     "kernel": "whole batch step (all classes, concurrent streams)",
-                     "hbm_gbs": round(byts / (ms_step * 1e-3) / 1e9, 1), "hbm_peak": pk["hbm_gbs"],
-                     "traffic": None},
+                     "kernel": "whole batch step (all classes, " + ("lockstep launches over all problems"
+                               if lk else "concurrent streams") + ")",
+                     "hbm_gbs": round(byts / (ms_step * 1e-3) / 1e9, 1) if not lk else None,
+                     "hbm_peak": pk["hbm_gbs"], "traffic": None,
+                     "tensor_tflops": round(lk["mma_flops"] / (ms_step * 1e-3) / 1e12, 2) if lk else None},
         "clocks": clocks,
         "kernel_breakdown": {k: {"launches_per_step": v["launches"], "gflop_per_step": round(v["flops"] / 1e9, 3),
-                                 "gbyte_per_step": round(v["bytes"] / 1e9, 3)} for k, v in prof.items()},
+                                 "gbyte_per_step": round(v["bytes"] / 1e9, 3)} for k, v in prof.items()} if not lk
+                            else {"all": {"launches_per_step": lk["launches"], "gflop_per_step": round(lk["flops"] / 1e9, 3),
+                                          "mma_tflop_per_step": round(lk["mma_flops"] / 1e12, 3)}},
     }
     if not args.no_cpu_baseline:
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")

@@ -110,6 +110,11 @@ typedef struct {
                           row-block kernel on 2D interiors) and keep
                           the fastest; choices are cached per interior shape for the life
                           of the process                                               */
+  int batch_engine;    /* igamg_setup_batch: 0 = lockstep when every problem is in its scope
+                          (2D, rectangle patches, FP64, V-cycle): one launch per cycle step
+                          over all problems, one graph replay per PCG iteration of the whole
+                          batch; otherwise, and with 1, worker streams (whole single solves
+                          on concurrent streams).  Results are the same either way.       */
 } igamg_options;
 
 /* Result of a solve.  The first five fields are the problem statement's result record;
@@ -277,11 +282,15 @@ const char* igamg_last_error(const igamg_ctx* ctx);
 
 /* ---------------------------------------------------------------- batched solves
  * Many independent problems (each the model problem of Sec. 2 on its own multi-patch
- * domain) solved concurrently on one device.  Each problem keeps its own context: its
- * hierarchy stays resident between solves.  The solves run on `workers` host threads, each
- * with its own CUDA stream, taking problems in decreasing order of estimated work; a
- * problem's result is bit-identical to igamg_solve on that problem alone.  The paper solves
- * one problem at a time and has no counterpart of this layer. */
+ * domain) solved together on one device.  Each problem keeps its own context: its
+ * hierarchy stays resident between solves.  Two engines (igamg_options.batch_engine): the
+ * lockstep engine runs PCG for all problems at once, each step of Algorithm 1 (apply,
+ * smoother pieces, transfers, coarse solves) one launch over the tiles of every problem at
+ * that depth below its finest level, each PCG iteration of the whole batch one CUDA graph
+ * replay; the worker-stream engine runs whole single solves on `workers` host threads with
+ * a CUDA stream each, in decreasing order of estimated work.  Either way a problem's result
+ * is bit-identical to igamg_solve on that problem alone.  The paper solves one problem at a
+ * time and has no counterpart of this layer. */
 typedef struct igamg_batch igamg_batch;
 
 /* Sets up `count` problems (host array, read during the call) with the same options.
@@ -304,6 +313,14 @@ igamg_status igamg_batch_context(igamg_batch* batch, int i, igamg_ctx** ctx);
  * IGAMG_ERR_NOT_CONVERGED. */
 igamg_status igamg_solve_batch(igamg_batch* batch, const double* const* rhs, double* const* x, double tol,
                                igamg_result* res, igamg_status* status);
+
+/* The engine igamg_solve_batch uses: *engine = 0 lockstep (every step of the cycle one
+ * launch over all problems), 1 worker streams.  For the lockstep engine, the kernel launches
+ * of the last igamg_solve_batch, their algorithmic FLOPs (the FP64 operations of the
+ * method) and the BF16 tensor-core FLOPs of its FD contractions; -1 for worker streams.
+ * launches, flops and mma_flops may be NULL. */
+igamg_status igamg_batch_engine(igamg_batch* batch, int* engine, int64_t* launches, double* flops,
+                                double* mma_flops);
 
 /* Releases every context of the batch and its streams.  NULL is accepted. */
 igamg_status igamg_free_batch(igamg_batch* batch);

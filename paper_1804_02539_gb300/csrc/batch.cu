@@ -22,9 +22,16 @@ void set_context_free_error(const std::string& msg);
 cudaStream_t ctx_stream(const igamg_ctx* c);
 void ctx_set_stream(igamg_ctx* c, cudaStream_t s);
 double ctx_work_estimate(const igamg_ctx* c);
+struct Lockstep;
+Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why);
+igamg_status lockstep_solve(Lockstep* k, cudaStream_t s, const double* const* b, double* const* x, double tol,
+                            igamg_result* res, igamg_status* status);
+void lockstep_free(Lockstep* k);
+void lockstep_stats(const Lockstep* k, int64_t* launches, double* flops, double* mma_flops);
 }  // namespace igamg
 
 struct igamg_batch {
+  igamg::Lockstep* lock = nullptr;  // the lockstep engine, when every problem is in its scope
   std::vector<igamg_ctx*> ctx;
   std::vector<cudaStream_t> streams;  // one per worker
   std::vector<cudaEvent_t> done;      // one per worker
@@ -40,6 +47,7 @@ constexpr int kDefaultWorkers = 16;
 void destroy(igamg_batch* b) {
   if (!b) return;
   if (b->user) cudaStreamSynchronize(b->user);
+  igamg::lockstep_free(b->lock);
   for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
   for (igamg_ctx* c : b->ctx)
     if (c) {
@@ -140,7 +148,23 @@ igamg_status igamg_setup_batch(const igamg_problem* problems, int count, const i
   b->order.resize(count);
   std::iota(b->order.begin(), b->order.end(), 0);
   std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return work[a] > work[c]; });
+  if (!opt || opt->batch_engine == 0) {
+    std::string why;
+    b->lock = igamg::lockstep_build(b->ctx, &why);  // NULL: outside the lockstep scope
+  }
   *out = b;
+  return IGAMG_OK;
+}
+
+igamg_status igamg_batch_engine(igamg_batch* b, int* engine, int64_t* launches, double* flops, double* mma_flops) {
+  if (!b || !engine) return IGAMG_ERR_ARG;
+  *engine = b->lock ? 0 : 1;
+  int64_t l = -1;
+  double f = -1.0, m = -1.0;
+  if (b->lock) igamg::lockstep_stats(b->lock, &l, &f, &m);
+  if (launches) *launches = l;
+  if (flops) *flops = f;
+  if (mma_flops) *mma_flops = m;
   return IGAMG_OK;
 }
 
@@ -156,6 +180,7 @@ igamg_status igamg_solve_batch(igamg_batch* b, const double* const* rhs, double*
   const int n = int(b->ctx.size()), W = int(b->streams.size());
   for (int i = 0; i < n; ++i)
     if (!rhs[i] || !x[i]) return IGAMG_ERR_ARG;
+  if (b->lock) return igamg::lockstep_solve(b->lock, b->user, rhs, x, tol, res, status);
   // the solves start after the work already queued on the caller's stream
   if (cudaEventRecord(b->start, b->user) != cudaSuccess) return IGAMG_ERR_CUDA;
   for (cudaStream_t s : b->streams)

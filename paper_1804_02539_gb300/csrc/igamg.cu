@@ -100,7 +100,8 @@ struct TcSet {
   double dig_bytes = 0;   // digit pass: B read, digit planes and exponents written
   // digit scratch of the set: sizes and per-descriptor offsets; the descriptors are uploaded
   // once the context's scratch is bound (bind_tc)
-  int64_t dig_elems = 0, tau_elems = 0, tiles = 0;
+  int64_t dig_elems = 0, tau_elems = 0, tiles = 0, panels = 0;
+  int *tstart_d = nullptr, *pstart_d = nullptr;  // tile and panel prefixes (device)
   std::vector<int64_t> dig_off, tau_off;
   bool side = false;      // launched on the interface stream (its own scratch)
 };
@@ -463,7 +464,6 @@ void set_tc(igamg_ctx*, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v, bool s
     ts.maxN = std::max(ts.maxN, d.N);
     ts.flops += 2.0 * d.M * double(d.N) * d.K;
     ts.exec_flops += tc_exec_flops(d.M, d.N, d.K, S);
-    ts.tiles += d.K > 0 ? tc_tiles(d.M, d.N, S) : 0;
     ts.dig_off.push_back(ts.dig_elems);
     ts.tau_off.push_back(ts.tau_elems);
     ts.dig_elems += tc_dig_elems(d.N, d.K, S);
@@ -501,6 +501,12 @@ void bind_tc(igamg_ctx* c) {
       p->h[i].Btau = tbase[p->side] ? tbase[p->side] + p->tau_off[i] : nullptr;
     }
     p->d = c->mem.upload(p->h, c->stream);
+    std::vector<int> ts, ps;
+    tc_prefixes(p->h, sizeof(T) == 8 ? 7 : 1, ts, ps);
+    p->tiles = ts.back();
+    p->panels = ps.back();
+    p->tstart_d = c->mem.upload(ts, c->stream);
+    p->pstart_d = c->mem.upload(ps, c->stream);
   }
 }
 
@@ -510,17 +516,18 @@ void run_tc(igamg_ctx* c, const TcSet<T>& ts, int epi, double alpha, int cls = C
   if (!ts.d) throw Fail{IGAMG_ERR_NUMERIC, "tensor-core set without scratch"};
   {
     ProfScope ps(c, cls, 0.0, ts.dig_bytes);
-    if constexpr (std::is_same<T, double>::value) CK((launch_tc_digits<7, double, double>(c->stream, ts.d, ts.batch, ts.maxN)));
-    else CK((launch_tc_digits<1, float, float>(c->stream, ts.d, ts.batch, ts.maxN)));
+    if constexpr (std::is_same<T, double>::value)
+      CK((launch_tc_digits<7, double, double>(c->stream, ts.d, ts.batch, ts.pstart_d, ts.panels)));
+    else
+      CK((launch_tc_digits<1, float, float>(c->stream, ts.d, ts.batch, ts.pstart_d, ts.panels)));
   }
   if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ts.exec_flops;
   ProfScope ps(c, cls, ts.flops, 0.0, 1, CLS_TC_KERNEL);
   if constexpr (std::is_same<T, double>::value)
-    CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, alpha, c->tc_err,
-                                          ts.tiles)));
+    CK((launch_gemm_tc<7, double, double>(c->stream, ts.d, ts.batch, ts.tstart_d, ts.tiles, epi, alpha, c->tc_err)));
   else
-    CK((launch_gemm_tc<1, float, float>(c->stream, ts.d, ts.batch, ts.maxM, ts.maxN, epi, float(alpha), c->tc_err,
-                                        ts.tiles)));
+    CK((launch_gemm_tc<1, float, float>(c->stream, ts.d, ts.batch, ts.tstart_d, ts.tiles, epi, float(alpha),
+                                        c->tc_err)));
 }
 
 // ---------------------------------------------------------------- setup helpers
@@ -2295,6 +2302,650 @@ igamg_status guarded(igamg_ctx* c, F&& f) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- lockstep batches
+//
+// Many independent problems solved by PCG in lockstep, every step of Algorithm 1 one launch
+// over all problems: the stiffness applies, smoother pieces, transfers and coarse solves of
+// every problem at the same depth below its finest level (depth d = level L_q - d of problem
+// q), and the PCG vector operations of all problems.  The launches take job lists built once
+// from the problems' own descriptors, so each problem runs exactly the arithmetic of its
+// single solve (same kernels per entry, same reduction partitions) and its iterates are
+// bit-identical to solving it alone; a problem that has converged keeps its iterate (its
+// updates are masked) while the others continue.  One PCG iteration of the whole batch is
+// one CUDA graph replay.  Scope: 2D problems whose patches are rectangles (Kronecker apply),
+// FP64, V-cycles; other batches use the worker-stream path.
+namespace igamg {
+
+struct LockGemmGroup {  // FMA GEMM stage descriptors of one tile factor R
+  GemmDesc* d = nullptr;
+  int batch = 0, maxM = 0, maxN = 0, R = 0;
+  double flops = 0;
+};
+struct LockTcStage {  // one tensor-core stage over the problems that use the tensor cores
+  TcDesc<double, double>* d = nullptr;
+  int *tstart = nullptr, *pstart = nullptr;
+  int batch = 0;
+  int64_t tiles = 0, panels = 0;
+  double exec_flops = 0, flops = 0;
+};
+struct LockSmooth {  // the smoother of one depth, one direction (from F, assign / from R, add)
+  // one-launch small-level smoothers
+  SmoothSmallT<double>* small = nullptr;
+  int* small_start = nullptr;
+  int nsmall = 0, small_blocks = 0;
+  // interface pieces of the other problems
+  NodeJobT<double>* gather = nullptr;
+  NodeJobT<double>* scatter = nullptr;
+  int niface = 0;
+  int64_t max_if = 0;
+  std::vector<LockGemmGroup> edgeA, edgeB;
+  // interiors by engine
+  FdRowsT<double>* rows = nullptr;
+  int nrows = 0, rows_n0 = 0, rows_n1 = 0;
+  FdSmallT<double>* fsmall = nullptr;
+  int nfsmall = 0;
+  LockTcStage tc[4];
+  std::vector<LockGemmGroup> st[4];
+  double flops = 0;  // algorithmic FLOPs of the kernels outside the GEMM groups and stages
+};
+struct LockDepth {
+  KronJobT<double>* res = nullptr;  // r = f - A u on this depth's levels
+  int nres = 0, res_n0 = 0, res_n1 = 0, res_p = 0;
+  double res_flops = 0, x_flops = 0, coarse_flops = 0;
+  LockSmooth sm[2];                 // [0] from F, assign (zero initial guess); [1] from R, add
+  Xfer2JobT<double>* rst = nullptr;
+  Xfer2JobT<double>* pro = nullptr;
+  int nx = 0, r_out0 = 0, r_out1 = 0, r_w1 = 0, p_out0 = 0, p_out1 = 0, p_w1 = 0;
+  NodeJobT<double>* coarse = nullptr;  // problems whose next level is the coarsest
+  int ncoarse = 0;
+  int64_t coarse_n = 0;
+};
+
+struct Lockstep {
+  std::vector<igamg_ctx*> ctx;
+  DevMem mem;
+  int nprob = 0, depths = 0, nu = 1;
+  double tau = 0.25;
+  std::vector<LockDepth> dep;
+  // finest-level Krylov apply w = A p, and the operands of the PCG vector steps
+  KronJobT<double>* kry = nullptr;
+  int nkry = 0, kry_n0 = 0, kry_n1 = 0, kry_p = 0;
+  double kry_flops = 0, vec_flops = 0;
+  VecJobT<double>* v_fu = nullptr;   // dot(F, U) / copy U -> p (a = F or p, b = U)
+  VecJobT<double>* v_pw = nullptr;   // dot(p, w)
+  VecJobT<double>* v_xr = nullptr;   // x += alpha p, r -= alpha w
+  VecJobT<double>* v_pz = nullptr;   // p = U + beta p
+  VecJobT<double>* v_nrm = nullptr;  // norm of the distributed residual F
+  VecJobT<double>* v_cpu = nullptr;  // p = U
+  int64_t max_T = 0;
+  double* partials = nullptr;        // nprob x RED_BLOCKS
+  double* scal = nullptr;            // nprob x 8 PCG scalars
+  double* h_scal = nullptr;          // pinned mirror
+  int* active = nullptr;
+  int* h_active = nullptr;           // pinned mirror
+  int* err = nullptr;                // tensor-core timeout flag
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t iter = nullptr;
+  // accounting: launches and algorithmic FLOPs of the last solve (per graph replay: the
+  // counts of its capture)
+  int64_t launches = 0, it_launches = 0;
+  double flops = 0, it_flops = 0, mma_flops = 0, it_mma_flops = 0;
+};
+
+namespace {
+
+template <class V>
+V* lk_upload(Lockstep* k, const std::vector<V>& h) {
+  if (h.empty()) return nullptr;
+  V* d = k->mem.alloc<V>(h.size());
+  CK(cudaMemcpy(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return d;
+}
+
+void lk_gemm_groups(Lockstep* k, const std::vector<const GemmSet*>& sets, std::vector<LockGemmGroup>& out) {
+  std::map<int, std::vector<GemmDesc>> byR;
+  for (const GemmSet* g : sets)
+    if (g->batch) byR[g->R].insert(byR[g->R].end(), g->h.begin(), g->h.end());
+  for (auto& kv : byR) {
+    LockGemmGroup gg;
+    gg.R = kv.first;
+    gg.batch = int(kv.second.size());
+    for (auto& d : kv.second) {
+      gg.maxM = std::max(gg.maxM, d.M);
+      gg.maxN = std::max(gg.maxN, d.N);
+    }
+    gg.flops = gemm_flops(kv.second);
+    gg.d = lk_upload(k, kv.second);
+    out.push_back(gg);
+  }
+}
+
+void lk_tc_stage(Lockstep* k, const std::vector<const TcSet<double>*>& sets, LockTcStage& out) {
+  std::vector<TcDesc<double, double>> h;
+  for (const TcSet<double>* t : sets) {
+    h.insert(h.end(), t->h.begin(), t->h.end());
+    out.exec_flops += t->exec_flops;
+    out.flops += t->flops;
+  }
+  if (h.empty()) return;
+  std::vector<int> ts, ps;
+  tc_prefixes(h, 7, ts, ps);
+  out.batch = int(h.size());
+  out.tiles = ts.back();
+  out.panels = ps.back();
+  out.d = lk_upload(k, h);
+  out.tstart = lk_upload(k, ts);
+  out.pstart = lk_upload(k, ps);
+}
+
+}  // namespace
+
+void lockstep_free(Lockstep* k) {
+  if (!k) return;
+  if (k->iter) cudaGraphExecDestroy(k->iter);
+  if (k->cap) cudaStreamDestroy(k->cap);
+  if (k->h_scal) cudaFreeHost(k->h_scal);
+  if (k->h_active) cudaFreeHost(k->h_active);
+  k->mem.release();
+  delete k;
+}
+
+// The lockstep engine of a batch, or NULL (with the reason) when a problem is outside its
+// scope.  Called after every context is set up (their engines chosen and descriptors built).
+Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
+  auto no = [&](const std::string& w) -> Lockstep* {
+    if (why) *why = w;
+    return nullptr;
+  };
+  if (ctx.empty()) return no("empty batch");
+  const igamg_options& o0 = ctx[0]->opt;
+  for (igamg_ctx* c : ctx) {
+    if (c->pd.dim != 2) return no("3D problem");
+    if (c->opt.precision != IGAMG_FP64 || c->low) return no("precision variant");
+    if (c->opt.mu != 1 || c->opt.nu != o0.nu || c->opt.tau != o0.tau) return no("cycle options differ");
+    if (c->lv.size() < 2) return no("single-level hierarchy");
+    for (size_t l = 1; l < c->lv.size(); ++l) {
+      const Level& L = c->lv[l];
+      if (!L.kron || !L.n64.r2 || !L.n64.p2) return no("non-rectangle patch or transfer layout");
+    }
+  }
+  Lockstep* k = new Lockstep();
+  try {
+    k->ctx = ctx;
+    k->nprob = int(ctx.size());
+    k->nu = o0.nu;
+    k->tau = o0.tau;
+    for (igamg_ctx* c : ctx) k->depths = std::max(k->depths, int(c->lv.size()) - 1);
+    k->dep.resize(k->depths);
+    for (int d = 0; d < k->depths; ++d) {
+      LockDepth& D = k->dep[d];
+      std::vector<KronJobT<double>> res;
+      std::vector<Xfer2JobT<double>> rst, pro;
+      std::vector<NodeJobT<double>> coarse;
+      struct Side {
+        std::vector<SmoothSmallT<double>> small;
+        std::vector<int> small_start{0};
+        std::vector<NodeJobT<double>> gather, scatter;
+        std::vector<const GemmSet*> eA, eB, st[4];
+        std::vector<const TcSet<double>*> tc[4];
+        std::vector<FdRowsT<double>> rows;
+        std::vector<FdSmallT<double>> fsmall;
+      } sd[2];
+      for (igamg_ctx* c : ctx) {
+        const int l = int(c->lv.size()) - 1 - d;
+        if (l < 1) continue;
+        Level& L = c->lv[l];
+        Level& C = c->lv[l - 1];
+        Num<double>& N = L.n64;
+        for (const auto& kd : L.kd_h) res.push_back(KronJobT<double>{kd, L.active, N.U, N.F, N.R});
+        D.res_flops += L.apply_flops;
+        D.x_flops += L.xfer_flops / 3;  // restriction; the prolongation is 2/3 of xfer_flops
+        D.res_n0 = std::max(D.res_n0, L.max_n[0]);
+        D.res_n1 = std::max(D.res_n1, L.max_n[1]);
+        D.res_p = std::max(D.res_p, L.max_p);
+        for (const auto& x : L.r2_h) rst.push_back(Xfer2JobT<double>{x, N.R, C.n64.F, C.l2g});
+        for (const auto& x : L.p2_h) pro.push_back(Xfer2JobT<double>{x, C.n64.U, N.U, nullptr});
+        D.r_out0 = std::max(D.r_out0, L.x2_rout0);
+        D.r_out1 = std::max(D.r_out1, L.x2_rout1);
+        D.r_w1 = std::max(D.r_w1, L.x2_rw1);
+        D.p_out0 = std::max(D.p_out0, L.x2_pout0);
+        D.p_out1 = std::max(D.p_out1, L.x2_pout1);
+        D.p_w1 = std::max(D.p_w1, L.x2_pw1);
+        if (l == 1) {
+          Level& L0 = c->lv[0];
+          NodeJobT<double> j{};
+          j.n = c->N0;
+          j.ptr = L0.g2t_ptr;
+          j.idx = L0.g2t;
+          j.v = L0.n64.F;
+          j.u = L0.n64.U;
+          j.Ainv = c->A0inv;
+          coarse.push_back(j);
+          D.coarse_n = std::max(D.coarse_n, c->N0);
+          D.coarse_flops += 2.0 * double(c->N0) * c->N0;
+        }
+        for (int dir = 0; dir < 2; ++dir) {  // 0: from F (assign), 1: from R (add)
+          Side& S = sd[dir];
+          const double* v = dir == 0 ? N.F : N.R;
+          if (N.use_fused && L.small_ok) {
+            D.sm[dir].flops += N.ssmall_flops;
+            S.small.push_back(N.ssmall);
+            const SmoothSmallT<double>& q = N.ssmall;
+            S.small_start.push_back(S.small_start.back() + q.nfd + q.nedges + (q.vend > q.vbeg ? 1 : 0));
+            continue;
+          }
+          if (L.n_if > 0) {
+            NodeJobT<double> g{};
+            g.n = L.n_if;
+            g.ptr = L.if_ptr;
+            g.idx = L.if_idx;
+            g.v = v;
+            g.G = N.G;
+            S.gather.push_back(g);
+            NodeJobT<double> t{};
+            t.n = L.n_if;
+            t.ptr = L.if_ptr;
+            t.idx = L.if_idx;
+            t.Z = N.Z;
+            t.G = N.G;
+            t.vscale = N.vscale;
+            t.u = N.U;
+            S.scatter.push_back(t);
+            S.eA.push_back(&N.edgeA);
+            S.eB.push_back(&N.edgeB);
+            LockSmooth& LS = D.sm[dir];
+            LS.max_if = std::max(LS.max_if, L.n_if);
+          }
+          // The tensor cores wherever their stage sets were built and the interiors exceed
+          // the one-block size: a problem timed alone may lose with few tiles, but the
+          // lockstep launches hold the tiles of every problem at this depth.
+          const bool tc = N.tc0F.batch && (N.use_tc || (c->opt.fd_engine == 0 && L.tc_ok && !L.fused_ok));
+          if (tc) {
+            S.tc[0].push_back(dir == 0 ? &N.tc0F : &N.tc0R);
+            S.tc[1].push_back(&N.tc1);
+            S.tc[2].push_back(&N.tc2);
+            S.tc[3].push_back(&N.tc3);
+          } else if (N.use_rows) {
+            D.sm[dir].flops += 4.0 * N.st1.flops;
+            S.rows.insert(S.rows.end(), L.fr_h.begin(), L.fr_h.end());
+            D.sm[dir].rows_n0 = std::max(D.sm[dir].rows_n0, N.frows_n0);
+            D.sm[dir].rows_n1 = std::max(D.sm[dir].rows_n1, N.frows_n1);
+          } else if (N.use_fused) {
+            D.sm[dir].flops += N.fsmall_flops;
+            S.fsmall.insert(S.fsmall.end(), L.fs_h.begin(), L.fs_h.end());
+          } else {
+            S.st[0].push_back(dir == 0 ? &N.st0F : &N.st0R);
+            S.st[1].push_back(&N.st1);
+            S.st[2].push_back(&N.st2);
+            S.st[3].push_back(&N.st3);
+          }
+        }
+      }
+      D.res = lk_upload(k, res);
+      D.nres = int(res.size());
+      D.rst = lk_upload(k, rst);
+      D.pro = lk_upload(k, pro);
+      D.nx = int(rst.size());
+      if (pro.size() != rst.size()) throw Fail{IGAMG_ERR_NUMERIC, "lockstep: transfer job lists differ"};
+      D.coarse = lk_upload(k, coarse);
+      D.ncoarse = int(coarse.size());
+      for (int dir = 0; dir < 2; ++dir) {
+        Side& S = sd[dir];
+        LockSmooth& LS = D.sm[dir];
+        LS.small = lk_upload(k, S.small);
+        LS.nsmall = int(S.small.size());
+        LS.small_start = LS.nsmall ? lk_upload(k, S.small_start) : nullptr;
+        LS.small_blocks = S.small_start.back();
+        LS.gather = lk_upload(k, S.gather);
+        LS.scatter = lk_upload(k, S.scatter);
+        LS.niface = int(S.gather.size());
+        lk_gemm_groups(k, S.eA, LS.edgeA);
+        lk_gemm_groups(k, S.eB, LS.edgeB);
+        LS.rows = lk_upload(k, S.rows);
+        LS.nrows = int(S.rows.size());
+        LS.fsmall = lk_upload(k, S.fsmall);
+        LS.nfsmall = int(S.fsmall.size());
+        for (int st = 0; st < 4; ++st) {
+          lk_tc_stage(k, S.tc[st], LS.tc[st]);
+          lk_gemm_groups(k, S.st[st], LS.st[st]);
+        }
+      }
+    }
+    // finest level: Krylov apply and PCG vectors (scalars of problem q at scal[8 q ..])
+    k->scal = k->mem.alloc<double>(size_t(8) * k->nprob);
+    CK(cudaMemset(k->scal, 0, sizeof(double) * 8 * k->nprob));
+    k->partials = k->mem.alloc<double>(size_t(RED_BLOCKS) * k->nprob);
+    k->active = k->mem.alloc<int>(size_t(k->nprob));
+    k->err = k->mem.alloc<int>(1);
+    CK(cudaMemset(k->err, 0, sizeof(int)));
+    CK(cudaMallocHost(&k->h_scal, sizeof(double) * 8 * k->nprob));
+    CK(cudaMallocHost(&k->h_active, sizeof(int) * k->nprob));
+    std::vector<KronJobT<double>> kry;
+    std::vector<VecJobT<double>> fu, pw, xr, pz, nrm, cpu;
+    for (int q = 0; q < k->nprob; ++q) {
+      igamg_ctx* c = ctx[q];
+      Level& L = c->lv.back();
+      Num<double>& N = L.n64;
+      for (const auto& kd : L.kd_h) kry.push_back(KronJobT<double>{kd, L.active, c->Pv, nullptr, c->W});
+      k->kry_flops += L.apply_flops;
+      k->vec_flops += 12.0 * double(L.topo.T);  // two dots, the x, r and p updates, the norm
+      k->kry_n0 = std::max(k->kry_n0, L.max_n[0]);
+      k->kry_n1 = std::max(k->kry_n1, L.max_n[1]);
+      k->kry_p = std::max(k->kry_p, L.max_p);
+      const int64_t T = L.topo.T;
+      k->max_T = std::max(k->max_T, T);
+      double* sc = k->scal + 8 * q;
+      fu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, N.F, N.U, nullptr, nullptr});
+      pw.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, c->W, nullptr, nullptr});
+      xr.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->X, N.F, c->Pv, c->W});
+      pz.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, nullptr, N.U, nullptr});
+      nrm.push_back(VecJobT<double>{L.topo.N, sc, L.g2t_ptr, L.g2t, N.F, nullptr, nullptr, nullptr});
+      cpu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, N.U, nullptr, nullptr});
+    }
+    k->kry = lk_upload(k, kry);
+    k->nkry = int(kry.size());
+    k->v_fu = lk_upload(k, fu);
+    k->v_pw = lk_upload(k, pw);
+    k->v_xr = lk_upload(k, xr);
+    k->v_pz = lk_upload(k, pz);
+    k->v_nrm = lk_upload(k, nrm);
+    k->v_cpu = lk_upload(k, cpu);
+    CK(cudaStreamCreateWithFlags(&k->cap, cudaStreamNonBlocking));
+  } catch (const Fail& f) {
+    lockstep_free(k);
+    return no(f.msg);
+  }
+  return k;
+}
+
+namespace {
+
+void lk_count(Lockstep* k, int launches, double flops, double mma = 0.0) {
+  k->launches += launches;
+  k->flops += flops;
+  k->mma_flops += mma;
+}
+
+void lk_res(Lockstep* k, cudaStream_t s, const LockDepth& D) {
+  if (!D.nres) return;
+  CK(launch_kron_apply_2d_b<double>(s, D.res, D.nres, D.res_n0, D.res_n1, D.res_p));
+  lk_count(k, 1, D.res_flops);
+}
+
+// One smoothing step of every problem at one depth: the small-level one-launch smoothers,
+// then the interface pieces and the interiors of the others, each by the engine its own
+// solve uses (the pieces are disjoint, so their order does not change any result).
+void lk_smooth(Lockstep* k, cudaStream_t s, const LockSmooth& S, bool from_F, bool add) {
+  const double tau = k->tau;
+  const int fF = from_F ? 1 : 0, ad = add ? 1 : 0;
+  lk_count(k, (S.nsmall ? 1 : 0) + (S.niface ? 2 : 0) + (S.nrows ? 2 : 0) + (S.nfsmall ? 1 : 0), S.flops);
+  CK(launch_smooth_small_b<double>(s, S.small, S.small_start, S.nsmall, S.small_blocks, fF, tau, ad));
+  if (S.niface) {
+    CK(launch_iface_gather_b<double>(s, S.gather, S.niface, S.max_if));
+    for (const auto& g : S.edgeA) {
+      CK(launch_gemm<double>(s, g.d, g.batch, g.maxM, g.maxN, false, false, EPI_COLSCALE, 1.0, g.R));
+      lk_count(k, 1, g.flops);
+    }
+    for (const auto& g : S.edgeB) {
+      CK(launch_gemm<double>(s, g.d, g.batch, g.maxM, g.maxN, false, true, EPI_STORE, 1.0, g.R));
+      lk_count(k, 1, g.flops);
+    }
+    CK(launch_iface_scatter_b<double>(s, S.scatter, S.niface, S.max_if, tau, ad));
+  }
+  for (int pass = 1; pass <= 2 && S.nrows; ++pass)
+    CK(launch_fd_rows<double>(s, S.rows, S.nrows, S.rows_n0, S.rows_n1, pass, fF, tau, ad));
+  if (S.nfsmall) CK(launch_fd_small<double>(s, S.fsmall, S.nfsmall, fF, tau, ad));
+  const int epi3 = add ? EPI_ADD : EPI_ASSIGN;
+  const int tepi[4] = {EPI_STORE, EPI_MUL, EPI_STORE, epi3};
+  for (int st = 0; st < 4; ++st) {
+    const LockTcStage& t = S.tc[st];
+    if (!t.batch) continue;
+    CK((launch_tc_digits<7, double, double>(s, t.d, t.batch, t.pstart, t.panels)));
+    CK((launch_gemm_tc<7, double, double>(s, t.d, t.batch, t.tstart, t.tiles, tepi[st], st == 3 ? tau : 1.0, k->err)));
+    lk_count(k, 2, t.flops, t.exec_flops);
+  }
+  const bool ta[4] = {true, false, false, false}, tb[4] = {false, false, false, true};
+  for (int st = 0; st < 4; ++st)
+    for (const auto& g : S.st[st]) {
+      CK(launch_gemm<double>(s, g.d, g.batch, g.maxM, g.maxN, ta[st], tb[st], tepi[st], st == 3 ? tau : 1.0, g.R));
+      lk_count(k, 1, g.flops);
+    }
+}
+
+// z = Multigrid(L_q, 0, r) for every problem (Algorithm 1, V-cycle), depth by depth.
+void lk_cycle(Lockstep* k, cudaStream_t s) {
+  for (int d = 0; d < k->depths; ++d) {
+    const LockDepth& D = k->dep[d];
+    for (int i = 0; i < k->nu; ++i) {
+      if (i == 0) {
+        lk_smooth(k, s, D.sm[0], true, false);  // u = 0: the residual is f itself
+      } else {
+        lk_res(k, s, D);
+        lk_smooth(k, s, D.sm[1], false, true);
+      }
+    }
+    lk_res(k, s, D);
+    CK(launch_transfer_2d_b<double>(s, D.rst, D.nx, D.r_out0, D.r_out1, D.r_w1, 0));
+    CK(launch_coarse_solve_b<double>(s, D.coarse, D.ncoarse, D.coarse_n));
+    lk_count(k, 1 + (D.ncoarse ? 1 : 0), D.x_flops + D.coarse_flops);
+  }
+  for (int d = k->depths - 1; d >= 0; --d) {
+    const LockDepth& D = k->dep[d];
+    CK(launch_transfer_2d_b<double>(s, D.pro, D.nx, D.p_out0, D.p_out1, D.p_w1, 1));
+    lk_count(k, 1, 2.0 * D.x_flops);
+    for (int i = 0; i < k->nu; ++i) {
+      lk_res(k, s, D);
+      lk_smooth(k, s, D.sm[1], false, true);
+    }
+  }
+}
+
+// One PCG step of every problem (updates masked for the problems that have stopped): z = B r,
+// beta, p, w = A p, alpha, x, r, ||r||.
+void lk_body(Lockstep* k, cudaStream_t s, bool with_precondition) {
+  if (with_precondition) {
+    lk_cycle(k, s);
+    CK(launch_dot_b<double>(s, k->v_fu, k->nprob, 2, k->partials));
+    CK(launch_pcg_p_b<double>(s, k->v_pz, k->nprob, k->max_T, k->active));
+    lk_count(k, 4, 0.0);
+  }
+  CK(launch_kron_apply_2d_b<double>(s, k->kry, k->nkry, k->kry_n0, k->kry_n1, k->kry_p));
+  CK(launch_dot_b<double>(s, k->v_pw, k->nprob, 1, k->partials));
+  CK(launch_pcg_xr_b<double>(s, k->v_xr, k->nprob, k->max_T, k->active));
+  CK(launch_norm2_dist_b<double>(s, k->v_nrm, k->nprob, 3, k->partials));
+  lk_count(k, 6, k->kry_flops + k->vec_flops);
+}
+
+}  // namespace
+
+// Solves every problem of the batch from x[q] (in: x_0, out: x) for rhs b[q] to the relative
+// tolerance tol, in lockstep on stream s; res and status (may be NULL) per problem.
+igamg_status lockstep_solve(Lockstep* k, cudaStream_t s, const double* const* b, double* const* x, double tol,
+                            igamg_result* res, igamg_status* status) {
+  const double t0 = now_ms();
+  const int n = k->nprob;
+  std::vector<igamg_status> st(n, IGAMG_OK);
+  std::vector<int> its(n, 0);
+  std::vector<double> rr0(n, 0.0), rel(n, 1.0);
+  k->launches = 0;
+  k->flops = k->mma_flops = 0.0;
+  try {
+    // per-solve jobs: the caller's global vectors into the tile layout, and back
+    std::vector<NodeJobT<double>> gd, ga, back;
+    std::vector<VecJobT<double>> zero, keep, fin;
+    std::vector<KronJobT<double>> r0;
+    int64_t maxN = 0;
+    int n0 = 0, n1 = 0, pm = 0;
+    for (int q = 0; q < n; ++q) {
+      igamg_ctx* c = k->ctx[q];
+      Level& L = c->lv.back();
+      const int64_t T = L.topo.T, N = L.topo.N;
+      maxN = std::max(maxN, N);
+      NodeJobT<double> j{};
+      j.n = N;
+      j.ptr = L.g2t_ptr;
+      j.idx = L.g2t;
+      j.G = const_cast<double*>(b[q]);
+      j.u = c->Bt;
+      gd.push_back(j);
+      j.G = x[q];
+      j.u = c->X;
+      ga.push_back(j);
+      NodeJobT<double> bk{};
+      bk.n = N;
+      bk.ptr = L.g2t_ptr;
+      bk.idx = L.g2t;
+      bk.v = c->X;
+      bk.G = x[q];
+      back.push_back(bk);
+      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->Bt, nullptr, nullptr, nullptr});
+      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->X, nullptr, nullptr, nullptr});
+      keep.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->Rr, c->X, nullptr, nullptr});
+      fin.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->X, c->Rr, nullptr, nullptr});
+      for (const auto& kd : L.kd_h) r0.push_back(KronJobT<double>{kd, L.active, c->X, c->Bt, L.n64.F});
+      n0 = std::max(n0, L.max_n[0]);
+      n1 = std::max(n1, L.max_n[1]);
+      pm = std::max(pm, L.max_p);
+    }
+    DevMem tmp;
+    auto up = [&](auto& h) {
+      using V = typename std::decay<decltype(h)>::type::value_type;
+      V* d = tmp.alloc<V>(h.size());
+      CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, s));
+      return d;
+    };
+    struct Guard {
+      DevMem& m;
+      cudaStream_t s;
+      ~Guard() {
+        cudaStreamSynchronize(s);
+        m.release();
+      }
+    } guard{tmp, s};
+    auto* d_gd = up(gd);
+    auto* d_ga = up(ga);
+    auto* d_back = up(back);
+    auto* d_zero = up(zero);
+    auto* d_keep = up(keep);
+    auto* d_fin = up(fin);
+    auto* d_r0 = up(r0);
+    // d = solution of A d = b - A x0 from d = 0; x = x0 + d (Rr holds x0)
+    CK(launch_copy_b<double>(s, d_zero, 2 * n, k->max_T, 1));
+    CK(launch_global_to_tile_b<double>(s, d_gd, n, maxN, 1));
+    CK(launch_global_to_tile_b<double>(s, d_ga, n, maxN, 0));
+    CK(launch_kron_apply_2d_b<double>(s, d_r0, int(r0.size()), n0, n1, pm));
+    CK(launch_copy_b<double>(s, d_keep, n, k->max_T, 0));
+    CK(launch_copy_b<double>(s, d_zero + 0, 2 * n, k->max_T, 1));  // Bt and X: X = 0 (Bt no longer needed)
+    CK(launch_norm2_dist_b<double>(s, k->v_nrm, n, 3, k->partials));
+    CK(cudaMemcpyAsync(k->h_scal, k->scal, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int live = 0;
+    for (int q = 0; q < n; ++q) {
+      rr0[q] = k->h_scal[8 * q + 3];
+      if (!std::isfinite(rr0[q])) st[q] = IGAMG_ERR_NUMERIC;
+      const bool go = st[q] == IGAMG_OK && rr0[q] != 0.0 && k->ctx[q]->opt.max_iter > 0 && !(tol > 0 && 1.0 <= tol);
+      k->h_active[q] = go ? 1 : 0;
+      live += go;
+      if (rr0[q] == 0.0) rel[q] = 0.0;
+    }
+    if (live) {
+      CK(cudaMemcpyAsync(k->active, k->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+      lk_cycle(k, s);
+      CK(launch_copy_b<double>(s, k->v_cpu, n, k->max_T, 0));
+      CK(launch_dot_b<double>(s, k->v_fu, n, 0, k->partials));
+    }
+    bool first = true;
+    while (live) {
+      if (first) {
+        lk_body(k, s, false);
+        first = false;
+      } else {
+        if (!k->iter) {  // the step touches fixed buffers only: captured once, replayed
+          const int64_t l0 = k->launches;
+          const double f0 = k->flops, m0 = k->mma_flops;
+          cudaGraph_t g = nullptr;
+          CK(cudaStreamBeginCapture(k->cap, cudaStreamCaptureModeRelaxed));
+          try {
+            lk_body(k, k->cap, true);
+          } catch (...) {
+            cudaGraph_t dead = nullptr;
+            cudaStreamEndCapture(k->cap, &dead);
+            if (dead) cudaGraphDestroy(dead);
+            throw;
+          }
+          CK(cudaStreamEndCapture(k->cap, &g));
+          CK(cudaGraphInstantiate(&k->iter, g, 0));
+          CK(cudaGraphDestroy(g));
+          k->it_launches = k->launches - l0;  // the capture launched nothing: count per replay
+          k->it_flops = k->flops - f0;
+          k->it_mma_flops = k->mma_flops - m0;
+          k->launches = l0;
+          k->flops = f0;
+          k->mma_flops = m0;
+        }
+        CK(cudaGraphLaunch(k->iter, s));
+        lk_count(k, int(k->it_launches), k->it_flops, k->it_mma_flops);
+      }
+      CK(cudaMemcpyAsync(k->h_scal, k->scal, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool changed = false;
+      for (int q = 0; q < n; ++q) {
+        if (!k->h_active[q]) continue;
+        ++its[q];
+        const double rr = k->h_scal[8 * q + 3];
+        if (!std::isfinite(rr)) {
+          st[q] = IGAMG_ERR_NUMERIC;
+        } else {
+          rel[q] = std::sqrt(rr / rr0[q]);
+          if (!((tol > 0 && rel[q] <= tol) || its[q] >= k->ctx[q]->opt.max_iter)) continue;
+        }
+        k->h_active[q] = 0;
+        --live;
+        changed = true;
+      }
+      if (changed && live) CK(cudaMemcpyAsync(k->active, k->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    }
+    CK(launch_copy_b<double>(s, d_fin, n, k->max_T, 2));
+    CK(launch_tile_to_global_b<double>(s, d_back, n, maxN, 0));
+    CK(cudaStreamSynchronize(s));
+    int e = 0;
+    CK(cudaMemcpy(&e, k->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) throw Fail{IGAMG_ERR_TIMEOUT, "a tensor-core contraction timed out waiting for its MMAs"};
+  } catch (const Fail& f) {
+    set_context_free_error("lockstep batch: " + f.msg);
+    for (int q = 0; q < n; ++q) {
+      if (status) status[q] = f.code;
+      if (res) res[q] = igamg_result{};
+    }
+    return f.code;
+  }
+  const double t = now_ms() - t0;
+  igamg_status worst = IGAMG_OK;
+  for (int q = 0; q < n; ++q) {
+    if (st[q] == IGAMG_OK && tol > 0 && rel[q] > tol) st[q] = IGAMG_ERR_NOT_CONVERGED;
+    if (status) status[q] = st[q];
+    if (res) {
+      igamg_result& r = res[q];
+      r.iters = its[q];
+      r.outer_iters = 1;
+      r.relres = rel[q];
+      r.t_setup_ms = k->ctx[q]->t_setup_ms;
+      r.t_assemble_ms = k->ctx[q]->t_assemble_ms;
+      r.t_solve_ms = t;
+    }
+    if (st[q] != IGAMG_OK && (worst == IGAMG_OK || worst == IGAMG_ERR_NOT_CONVERGED)) worst = st[q];
+  }
+  return worst;
+}
+
+void lockstep_stats(const Lockstep* k, int64_t* launches, double* flops, double* mma_flops) {
+  *launches = k->launches;
+  *flops = k->flops;
+  *mma_flops = k->mma_flops;
+}
+
+}  // namespace igamg
+
 extern "C" {
 
 igamg_status igamg_default_options(igamg_options* opt) {
@@ -2307,6 +2958,7 @@ igamg_status igamg_default_options(igamg_options* opt) {
   opt->precision = IGAMG_FP64;
   opt->inner_tol = 1e-4;
   opt->fd_engine = 0;
+  opt->batch_engine = 0;
   opt->graphs = 1;
   opt->apply_engine = 0;
   opt->autotune = 1;

@@ -164,12 +164,9 @@ size_t kron_apply_smem(int elem_size, int max_p) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(AX * AY) k_kron_apply_2d(const KronDevT<T>* __restrict__ kds,
-                                                           const unsigned char* __restrict__ active,
-                                                           const T* __restrict__ u, const T* __restrict__ f,
-                                                           T* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const KronDevT<T> kd = kds[blockIdx.z];
+__device__ __forceinline__ void kron_apply_block(const KronDevT<T>& kd, const unsigned char* __restrict__ active,
+                                                 const T* __restrict__ u, const T* __restrict__ f,
+                                                 T* __restrict__ y, unsigned char* smraw) {
   const int n0 = kd.n0, n1 = kd.n1, p0 = kd.p0, p1 = kd.p1;
   const int i0b = blockIdx.y * KY, i1b = blockIdx.x * AX;
   if (i0b >= n0 || i1b >= n1) return;
@@ -226,6 +223,36 @@ __global__ void __launch_bounds__(AX * AY) k_kron_apply_2d(const KronDevT<T>* __
     y[node] = f ? f[node] - acc : acc;
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(AX * AY) k_kron_apply_2d(const KronDevT<T>* __restrict__ kds,
+                                                           const unsigned char* __restrict__ active,
+                                                           const T* __restrict__ u, const T* __restrict__ f,
+                                                           T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  kron_apply_block<T>(kds[blockIdx.z], active, u, f, y, smraw);
+}
+
+// The same apply over patch jobs of many levels or problems (each with its own vectors).
+template <class T>
+__global__ void __launch_bounds__(AX * AY) k_kron_apply_2d_b(const KronJobT<T>* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const KronJobT<T> j = jobs[blockIdx.z];
+  kron_apply_block<T>(j.kd, j.active, j.u, j.f, j.y, smraw);
+}
+
+template <class T>
+cudaError_t launch_kron_apply_2d_b(cudaStream_t s, const KronJobT<T>* jobs, int njobs, int max_n0, int max_n1,
+                                   int max_p) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 grid((max_n1 + AX - 1) / AX, (max_n0 + KY - 1) / KY, njobs);
+  size_t sm = kron_apply_smem(sizeof(T), max_p);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_kron_apply_2d_b<T>), sm);
+  if (e != cudaSuccess) return e;
+  k_kron_apply_2d_b<T><<<grid, dim3(AX, AY), sm, s>>>(jobs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_kron_apply_2d_b<double>(cudaStream_t, const KronJobT<double>*, int, int, int, int);
 
 template <class T>
 cudaError_t launch_kron_apply_2d(cudaStream_t s, const KronDevT<T>* kd, int K, int max_n0, int max_n1, int max_p,
@@ -289,11 +316,11 @@ __global__ void __launch_bounds__(256) k_fd_small(const FdSmallT<T>* __restrict_
   fd_small_block<T>(ds[blockIdx.x], from_F, tau, add, U0, U1, X, Tm);
 }
 
+// Block b of the one-launch small-level smoother of one level (interiors, edges, vertices).
 template <class T>
-__global__ void __launch_bounds__(256) k_smooth_small(const SmoothSmallT<T> p, int from_F, T tau, int add) {
-  constexpr int M = kFdSmallMax;
-  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
-  const int b = blockIdx.x, tid = threadIdx.x;
+__device__ void smooth_small_block(const SmoothSmallT<T>& p, int b, int from_F, T tau, int add, T* U0, T* U1, T* X,
+                                   T* Tm) {
+  const int tid = threadIdx.x;
   const T* v = from_F ? p.vF : p.vR;
   if (b < p.nfd) {
     fd_small_block<T>(p.fd[b], from_F, tau, add, U0, U1, X, Tm);
@@ -338,6 +365,42 @@ __global__ void __launch_bounds__(256) k_smooth_small(const SmoothSmallT<T> p, i
     }
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_small(const SmoothSmallT<T> p, int from_F, T tau, int add) {
+  constexpr int M = kFdSmallMax;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  smooth_small_block<T>(p, blockIdx.x, from_F, tau, add, U0, U1, X, Tm);
+}
+
+// The small-level smoothers of many levels (of different problems) in one launch: block b
+// belongs to job j with bstart[j] <= b < bstart[j + 1].
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_small_b(const SmoothSmallT<T>* __restrict__ jobs,
+                                                        const int* __restrict__ bstart, int njobs, int from_F, T tau,
+                                                        int add) {
+  constexpr int M = kFdSmallMax;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  int lo = 0, hi = njobs;
+  const int b = blockIdx.x;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (bstart[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const SmoothSmallT<T> p = jobs[lo];
+  smooth_small_block<T>(p, b - bstart[lo], from_F, tau, add, U0, U1, X, Tm);
+}
+
+template <class T>
+cudaError_t launch_smooth_small_b(cudaStream_t s, const SmoothSmallT<T>* jobs, const int* bstart, int njobs,
+                                  int total_blocks, int from_F, T tau, int add) {
+  if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+  k_smooth_small_b<T><<<total_blocks, 256, 0, s>>>(jobs, bstart, njobs, from_F, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_smooth_small_b<double>(cudaStream_t, const SmoothSmallT<double>*, const int*, int, int, int,
+                                                   double, int);
 
 template <class T>
 cudaError_t launch_smooth_small(cudaStream_t s, const SmoothSmallT<T>& p, int from_F, T tau, int add) {
@@ -811,6 +874,247 @@ template cudaError_t launch_pcg_xr<float>(cudaStream_t, int64_t, const double*, 
 template cudaError_t launch_pcg_p<double>(cudaStream_t, int64_t, double*, double*, const double*);
 template cudaError_t launch_pcg_p<float>(cudaStream_t, int64_t, double*, float*, const float*);
 
+// ---------------------------------------------------------------- cross-problem batches
+// Node-list and vector kernels over job lists: blockIdx.y is the job, blockIdx.x and the
+// threads stride over the job's nodes exactly as the single-problem kernels stride over
+// theirs, so every entry is computed with the same arithmetic.
+
+template <class T>
+__global__ void k_iface_gather_b(const NodeJobT<T>* __restrict__ jobs) {
+  const NodeJobT<T> j = jobs[blockIdx.y];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * blockDim.x) {
+    T s = 0;
+    for (int64_t c = j.ptr[i]; c < j.ptr[i + 1]; ++c) s += j.v[j.idx[c]];
+    j.G[i] = s;
+  }
+}
+
+template <class T>
+__global__ void k_iface_scatter_b(const NodeJobT<T>* __restrict__ jobs, T tau, int add) {
+  const NodeJobT<T> j = jobs[blockIdx.y];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * blockDim.x) {
+    T val = tau * fma(j.vscale[i], j.G[i], j.Z[i]);
+    for (int64_t c = j.ptr[i]; c < j.ptr[i + 1]; ++c) {
+      int64_t t = j.idx[c];
+      j.u[t] = add ? j.u[t] + val : val;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_iface_gather_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_iface_gather_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_iface_scatter_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, T tau,
+                                   int add) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_iface_scatter_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, tau, add);
+  return cudaGetLastError();
+}
+
+// One block per job: x_copies = Ainv (sum of copies of v), warp per row as k_coarse_solve.
+template <class T>
+__global__ void k_coarse_solve_b(const NodeJobT<T>* __restrict__ jobs) {
+  extern __shared__ double g[];
+  const NodeJobT<T> j = jobs[blockIdx.y];
+  const int64_t N0 = j.n;
+  for (int64_t i = threadIdx.x; i < N0; i += blockDim.x) {
+    double s = 0.0;
+    for (int64_t c = j.ptr[i]; c < j.ptr[i + 1]; ++c) s += double(j.v[j.idx[c]]);
+    g[i] = s;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t r = int64_t(blockIdx.x) * nw + warp; r < N0; r += int64_t(gridDim.x) * nw) {
+    double acc = 0.0;
+    for (int64_t c = lane; c < N0; c += 32) acc = fma(j.Ainv[r * N0 + c], g[c], acc);
+    acc = warp_sum(acc);
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    for (int64_t c = j.ptr[r] + lane; c < j.ptr[r + 1]; c += 32) j.u[j.idx[c]] = T(acc);
+  }
+}
+
+template <class T>
+cudaError_t launch_coarse_solve_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  int blocks = int((max_n + 7) / 8);
+  if (blocks > 16) blocks = 16;
+  const size_t sm = sizeof(double) * size_t(max_n);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_coarse_solve_b<T>), sm);
+  if (e != cudaSuccess) return e;
+  k_coarse_solve_b<T><<<dim3(blocks, njobs), 256, sm, s>>>(jobs);
+  return cudaGetLastError();
+}
+
+template <class T>
+__global__ void k_global_to_tile_b(const NodeJobT<T>* __restrict__ jobs, int first_only) {
+  const NodeJobT<T> j = jobs[blockIdx.y];
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < j.n; g += int64_t(gridDim.x) * blockDim.x) {
+    T v = j.G[g];
+    for (int64_t c = j.ptr[g]; c < j.ptr[g + 1]; ++c) j.u[j.idx[c]] = (first_only && c > j.ptr[g]) ? T(0) : v;
+  }
+}
+
+template <class T>
+__global__ void k_tile_to_global_b(const NodeJobT<T>* __restrict__ jobs, int sum_copies) {
+  const NodeJobT<T> j = jobs[blockIdx.y];
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < j.n; g += int64_t(gridDim.x) * blockDim.x) {
+    T v = j.v[j.idx[j.ptr[g]]];
+    if (sum_copies)
+      for (int64_t c = j.ptr[g] + 1; c < j.ptr[g + 1]; ++c) v += j.v[j.idx[c]];
+    j.G[g] = v;
+  }
+}
+
+template <class T>
+cudaError_t launch_global_to_tile_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, int first_only) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_global_to_tile_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, first_only);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_tile_to_global_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, int sum_copies) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_tile_to_global_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, sum_copies);
+  return cudaGetLastError();
+}
+
+// Reductions: the single-problem grid of RED_BLOCKS blocks per job (blockIdx.x), partials in
+// partials[j * RED_BLOCKS + b], then one block per job in the same order as k_reduce_final.
+template <class T>
+__global__ void __launch_bounds__(256) k_dot_partial_b(const VecJobT<T>* __restrict__ jobs, double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const VecJobT<T> j = jobs[blockIdx.y];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * 256)
+    s = fma(double(j.a[i]), double(j.b[i]), s);
+  s = block_sum_256(s, sh);
+  if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * RED_BLOCKS + blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_norm2_dist_partial_b(const VecJobT<T>* __restrict__ jobs,
+                                                              double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const VecJobT<T> j = jobs[blockIdx.y];
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(256) + threadIdx.x; g < j.n; g += int64_t(gridDim.x) * 256) {
+    double c = 0.0;
+    for (int64_t k = j.ptr[g]; k < j.ptr[g + 1]; ++k) c += double(j.a[j.idx[k]]);
+    s = fma(c, c, s);
+  }
+  s = block_sum_256(s, sh);
+  if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * RED_BLOCKS + blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_reduce_final_b(const VecJobT<T>* __restrict__ jobs,
+                                                        const double* __restrict__ partials, int out) {
+  __shared__ double sh[256];
+  const double* pj = partials + int64_t(blockIdx.x) * RED_BLOCKS;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < RED_BLOCKS; i += 256) s += pj[i];
+  s = block_sum_256(s, sh);
+  if (threadIdx.x == 0) jobs[blockIdx.x].scal[out] = s;
+}
+
+template <class T>
+cudaError_t launch_dot_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int out, double* partials) {
+  if (njobs <= 0) return cudaSuccess;
+  k_dot_partial_b<T><<<dim3(RED_BLOCKS, njobs), 256, 0, s>>>(jobs, partials);
+  k_reduce_final_b<T><<<njobs, 256, 0, s>>>(jobs, partials, out);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_norm2_dist_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int out, double* partials) {
+  if (njobs <= 0) return cudaSuccess;
+  k_norm2_dist_partial_b<T><<<dim3(RED_BLOCKS, njobs), 256, 0, s>>>(jobs, partials);
+  k_reduce_final_b<T><<<njobs, 256, 0, s>>>(jobs, partials, out);
+  return cudaGetLastError();
+}
+
+template <class T>
+__global__ void k_pcg_xr_b(const VecJobT<T>* __restrict__ jobs, const int* __restrict__ active) {
+  if (!active[blockIdx.y]) return;
+  const VecJobT<T> j = jobs[blockIdx.y];
+  __shared__ T alpha_s;
+  if (threadIdx.x == 0) alpha_s = T(j.scal[0] / j.scal[1]);
+  __syncthreads();
+  const T alpha = alpha_s;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * blockDim.x) {
+    j.a[i] = fma(alpha, j.c[i], j.a[i]);
+    j.b[i] = fma(-alpha, j.d[i], j.b[i]);
+  }
+}
+
+template <class T>
+__global__ void k_pcg_p_b(const VecJobT<T>* __restrict__ jobs, const int* __restrict__ active) {
+  if (!active[blockIdx.y]) return;
+  const VecJobT<T> j = jobs[blockIdx.y];
+  __shared__ T beta_s;
+  if (threadIdx.x == 0) beta_s = T(j.scal[2] / j.scal[0]);
+  __syncthreads();
+  const T beta = beta_s;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * blockDim.x)
+    j.a[i] = fma(beta, j.a[i], j.c[i]);
+}
+
+template <class T>
+__global__ void k_scalar_shift_b(const VecJobT<T>* __restrict__ jobs, const int* __restrict__ active, int njobs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < njobs && active[q]) jobs[q].scal[0] = jobs[q].scal[2];
+}
+
+template <class T>
+cudaError_t launch_pcg_xr_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, const int* active) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_pcg_xr_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, active);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pcg_p_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, const int* active) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_pcg_p_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, active);
+  k_scalar_shift_b<T><<<(njobs + 255) / 256, 256, 0, s>>>(jobs, active, njobs);
+  return cudaGetLastError();
+}
+
+// mode 0: a = b; mode 1: a = 0; mode 2: a = 1 * b + 1 * a (the axpby of the solve's end)
+template <class T>
+__global__ void k_copy_b(const VecJobT<T>* __restrict__ jobs, int mode) {
+  const VecJobT<T> j = jobs[blockIdx.y];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < j.n; i += int64_t(gridDim.x) * blockDim.x) {
+    if (mode == 0) j.a[i] = j.b[i];
+    else if (mode == 1) j.a[i] = T(0);
+    else j.a[i] = 1.0 * j.b[i] + 1.0 * j.a[i];
+  }
+}
+
+template <class T>
+cudaError_t launch_copy_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, int mode) {
+  if (njobs <= 0 || max_n <= 0) return cudaSuccess;
+  k_copy_b<T><<<dim3(grid_for(max_n, 256), njobs), 256, 0, s>>>(jobs, mode);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_iface_gather_b<double>(cudaStream_t, const NodeJobT<double>*, int, int64_t);
+template cudaError_t launch_iface_scatter_b<double>(cudaStream_t, const NodeJobT<double>*, int, int64_t, double, int);
+template cudaError_t launch_coarse_solve_b<double>(cudaStream_t, const NodeJobT<double>*, int, int64_t);
+template cudaError_t launch_global_to_tile_b<double>(cudaStream_t, const NodeJobT<double>*, int, int64_t, int);
+template cudaError_t launch_tile_to_global_b<double>(cudaStream_t, const NodeJobT<double>*, int, int64_t, int);
+template cudaError_t launch_dot_b<double>(cudaStream_t, const VecJobT<double>*, int, int, double*);
+template cudaError_t launch_norm2_dist_b<double>(cudaStream_t, const VecJobT<double>*, int, int, double*);
+template cudaError_t launch_pcg_xr_b<double>(cudaStream_t, const VecJobT<double>*, int, int64_t, const int*);
+template cudaError_t launch_pcg_p_b<double>(cudaStream_t, const VecJobT<double>*, int, int64_t, const int*);
+template cudaError_t launch_copy_b<double>(cudaStream_t, const VecJobT<double>*, int, int64_t, int);
+
 // Flexible CG (Polak-Ribiere): beta = (rz_new - (r_new, z_old)) / rz_old; scal[5] = beta,
 // scal[0] = rz_new.
 __global__ void k_fcg_beta(double* scal) {
@@ -1220,11 +1524,9 @@ template cudaError_t launch_transfer_1d<float>(cudaStream_t, const XferT<float>*
 constexpr int XB1 = 32, XB0 = 8;  // outputs per block: 8 rows x 32 columns
 
 template <class T>
-__global__ void __launch_bounds__(256) k_transfer_2d(const Xfer2T<T>* __restrict__ xs, const T* __restrict__ in,
-                                                     T* __restrict__ out, int add, const int64_t* __restrict__ mask) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void transfer2d_block(const Xfer2T<T>& x, const T* __restrict__ in, T* __restrict__ out,
+                                                 int add, const int64_t* __restrict__ mask, unsigned char* smraw) {
   T* mid = reinterpret_cast<T*>(smraw);  // XB0 x W: the dir-0 pass on the block's input columns
-  const Xfer2T<T> x = xs[blockIdx.z];
   const int o0b = blockIdx.y * XB0, o1b = blockIdx.x * XB1;
   if (o0b >= x.nout0 || o1b >= x.nout1) return;
   const int o1e = min(o1b + XB1, x.nout1) - 1;
@@ -1256,6 +1558,33 @@ __global__ void __launch_bounds__(256) k_transfer_2d(const Xfer2T<T>* __restrict
     out[t] = add ? out[t] + acc : acc;
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_transfer_2d(const Xfer2T<T>* __restrict__ xs, const T* __restrict__ in,
+                                                     T* __restrict__ out, int add, const int64_t* __restrict__ mask) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  transfer2d_block<T>(xs[blockIdx.z], in, out, add, mask, smraw);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_transfer_2d_b(const Xfer2JobT<T>* __restrict__ jobs, int add) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Xfer2JobT<T> j = jobs[blockIdx.z];
+  transfer2d_block<T>(j.x, j.in, j.out, add, j.mask, smraw);
+}
+
+template <class T>
+cudaError_t launch_transfer_2d_b(cudaStream_t s, const Xfer2JobT<T>* jobs, int njobs, int max_out0, int max_out1,
+                                 int max_width1, int add) {
+  if (njobs <= 0) return cudaSuccess;
+  const size_t sm = sizeof(T) * XB0 * size_t(2 * XB1 + max_width1);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_transfer_2d_b<T>), sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((max_out1 + XB1 - 1) / XB1, (max_out0 + XB0 - 1) / XB0, njobs);
+  k_transfer_2d_b<T><<<grid, 256, sm, s>>>(jobs, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transfer_2d_b<double>(cudaStream_t, const Xfer2JobT<double>*, int, int, int, int, int);
 
 template <class T>
 cudaError_t launch_transfer_2d(cudaStream_t s, const Xfer2T<T>* xs, int npatch, int max_out0, int max_out1,

@@ -232,4 +232,82 @@ cudaError_t launch_convert_f64_f32(cudaStream_t s, int64_t n, const double* src,
 cudaError_t launch_convert_f64_bf16(cudaStream_t s, int64_t n, const double* src, __nv_bfloat16* dst);
 cudaError_t launch_add_scaled_f32(cudaStream_t s, int64_t n, const float* d, double scale, double* x);
 
+// ---------------------------------------------------------------- cross-problem batches
+// The kernels above over job lists whose entries carry their own vectors, so that one
+// launch covers the patches, levels or vectors of many independent problems.  Every job is
+// computed with exactly the arithmetic of the single-problem kernel (the results do not
+// depend on what else the launch holds).
+template <class T>
+struct KronJobT {  // one rectangle patch of one level
+  KronDevT<T> kd;
+  const unsigned char* active;
+  const T* u;
+  const T* f;  // NULL: y = A u
+  T* y;
+};
+template <class T>
+cudaError_t launch_kron_apply_2d_b(cudaStream_t s, const KronJobT<T>* jobs, int njobs, int max_n0, int max_n1,
+                                   int max_p);
+// Small-level smoothers of many levels: job j owns blocks [bstart[j], bstart[j+1]).
+template <class T>
+cudaError_t launch_smooth_small_b(cudaStream_t s, const SmoothSmallT<T>* jobs, const int* bstart, int njobs,
+                                  int total_blocks, int from_F, T tau, int add);
+template <class T>
+struct Xfer2JobT {  // one patch tile of a 2D transfer
+  Xfer2T<T> x;
+  const T* in;
+  T* out;
+  const int64_t* mask;
+};
+template <class T>
+cudaError_t launch_transfer_2d_b(cudaStream_t s, const Xfer2JobT<T>* jobs, int njobs, int max_out0, int max_out1,
+                                 int max_width1, int add);
+// Node lists of one level: interface gather (G = sums of copies of v), scatter (u (=|+=)
+// tau (Z + vscale G) to every copy), coarse solves and global <-> tile conversions.
+template <class T>
+struct NodeJobT {
+  int64_t n;
+  const int64_t *ptr, *idx;
+  const T* v;          // gather / coarse: the distributed input
+  T* G;                // gathered sums (interface) / global vector (conversions)
+  const T* Z;
+  const T* vscale;
+  T* u;                // scatter / coarse: the accumulated output
+  const double* Ainv;  // coarse solve: the explicit inverse (n x n)
+};
+template <class T>
+cudaError_t launch_iface_gather_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n);
+template <class T>
+cudaError_t launch_iface_scatter_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, T tau,
+                                   int add);
+template <class T>
+cudaError_t launch_coarse_solve_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n);
+// global -> tile (G -> u, first_only) and tile -> global (v -> G, sum_copies)
+template <class T>
+cudaError_t launch_global_to_tile_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, int first_only);
+template <class T>
+cudaError_t launch_tile_to_global_b(cudaStream_t s, const NodeJobT<T>* jobs, int njobs, int64_t max_n, int sum_copies);
+// Vectors of many problems.  Reductions keep the single-problem partition (RED_BLOCKS
+// partials per job in `partials` + j * RED_BLOCKS, then one block per job).
+template <class T>
+struct VecJobT {
+  int64_t n;
+  double* scal;      // the job's PCG scalars (also the reduction output base)
+  const int64_t *ptr, *idx;  // norm of a distributed vector: copies per active dof (n dofs)
+  T *a, *b, *c, *d;  // operands (meaning per kernel)
+};
+template <class T>
+cudaError_t launch_dot_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int out, double* partials);
+template <class T>
+cudaError_t launch_norm2_dist_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int out, double* partials);
+// x += alpha p, r -= alpha w (a = x, b = r, c = p, d = w) for the jobs with active[j] != 0
+template <class T>
+cudaError_t launch_pcg_xr_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, const int* active);
+// p = z + beta p, then scal[0] = scal[2] (a = p, c = z) for the active jobs
+template <class T>
+cudaError_t launch_pcg_p_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, const int* active);
+// a = b (copy), a = 0 (b == NULL), or b += a (axpy_into: b = 1 * a + 1 * b)
+template <class T>
+cudaError_t launch_copy_b(cudaStream_t s, const VecJobT<T>* jobs, int njobs, int64_t max_n, int mode);
+
 }  // namespace igamg

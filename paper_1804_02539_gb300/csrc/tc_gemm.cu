@@ -66,7 +66,6 @@ constexpr int NT = 576;             // 18 warps: TMA, MMA, 16 epilogue (4 per TM
 constexpr int kEpiThreads = 512;
 constexpr int kDigThreads = 256;    // digit pass: 8 warps per 32-column panel
 constexpr int kDigRegBlocks = 9;    // K blocks a digit-pass lane holds in registers (288 rows; S = 7)
-constexpr int kMaxDescs = 512;      // descriptors of one launch (tile prefix in shared memory)
 constexpr int WAIT_LIMIT = 1 << 24;
 
 template <int S> struct TcCfg;
@@ -87,7 +86,6 @@ template <int S>
 constexpr size_t tc_smem_bytes() {
   using CF = TcCfg<S>;
   return size_t(CF::NST) * S * (TBM + CF::TBN) * TBK * 2  // A and B stages (BF16)
-         + (kMaxDescs + 2) * 4                             // tile prefix
          + (2 * CF::NST + 8) * 8                           // mbarriers
          + 16                                              // TMEM slot, abort flag
          + 1024;                                           // alignment
@@ -277,31 +275,17 @@ __device__ __forceinline__ void digit_pairs7(double x0, double x1, int tau, uint
   }
 }
 
-// Panel prefix: number of TBN-column panels of descriptors 0..q-1 in start[q] (start[batch]
-// = total).  Built by one thread into shared memory.
-template <int TBN, class D>
-__device__ void panel_prefix(const D* descs, int batch, int* start) {
-  int acc = 0;
-  for (int q = 0; q < batch; ++q) {
-    start[q] = acc;
-    const D& d = descs[q];
-    if (d.M > 0 && d.N > 0 && d.K > 0) acc += (d.N + TBN - 1) / TBN;
-  }
-  start[batch] = acc;
-}
 }  // namespace
 
 template <int S, class TB, class TC>
-__global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>* __restrict__ descs, int batch) {
+__global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>* __restrict__ descs, int batch,
+                                                           const int* __restrict__ pstart) {
   using CF = TcCfg<S>;
   constexpr int TBN = CF::TBN, BSZ = S * TBN * TBK, NG = TBN / 32;
   // K blocks held in registers at once: all of K up to 288 with S = 7 (the exponent pass and
   // the digits use one load), two blocks with S = 1 (no exponents)
   constexpr int RB = S > 1 ? kDigRegBlocks : 2;
-  __shared__ int pstart[kMaxDescs + 2];
-  if (threadIdx.x == 0) panel_prefix<TBN>(descs, batch, pstart);
-  __syncthreads();
-  const int total = pstart[batch];
+  const int total = pstart[batch];  // panel prefix over the descriptors (tc_prefixes)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cl = 4 * warp + (lane >> 3);  // this lane's column within a 32-column group
   const int kq = lane & 7;                // K quad: k = 4 kq .. 4 kq + 3 of a block
@@ -378,8 +362,9 @@ __global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>*
 }
 
 template <int S, class TB, class TC>
-__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int batch, int epi,
-                                                 TC alpha, int* __restrict__ err) {
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int batch,
+                                                 const int* __restrict__ tstart, int epi, TC alpha,
+                                                 int* __restrict__ err) {
   using CF = TcCfg<S>;
   constexpr int TBN = CF::TBN, NST = CF::NST, ACC = CF::ACC;
   constexpr int ASZ = S * TBM * TBK, BSZ = S * TBN * TBK;  // BF16 elements of one stage
@@ -387,8 +372,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* Bs = As + NST * ASZ;
-  int* tstart = reinterpret_cast<int*>(Bs + NST * BSZ);  // [batch + 1]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tstart + kMaxDescs + 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + NST * BSZ);
   uint64_t* full = bars;             // [NST] A and B copies landed (expect_tx)
   uint64_t* empty = full + NST;      // [NST] MMAs reading the stage done (commit)
   uint64_t* accf = empty + NST;      // [2] accumulator set complete (commit)
@@ -399,13 +383,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    int acc = 0;
-    for (int q = 0; q < batch; ++q) {
-      tstart[q] = acc;
-      const TcDesc<TB, TC>& d = descs[q];
-      if (d.M > 0 && d.N > 0 && d.K > 0) acc += ((d.M + TBM - 1) / TBM) * ((d.N + TBN - 1) / TBN);
-    }
-    tstart[batch] = acc;
     for (int i = 0; i < NST; ++i) {
       mbar_init(sptr(full + i), 1);
       mbar_init(sptr(empty + i), 1);
@@ -419,7 +396,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  const int total = tstart[batch];
+  const int total = tstart[batch];  // tile prefix over the descriptors (tc_prefixes)
   if (int(blockIdx.x) >= total) return;  // block-uniform, before any TMEM is held
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sptr(tslot)), "r"(CF::TCOLS));
@@ -641,38 +618,54 @@ int sm_count() {
 }  // namespace
 
 template <int S, class TB, class TC>
-cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxN) {
-  if (batch <= 0 || maxN <= 0) return cudaSuccess;
-  if (batch > kMaxDescs) return cudaErrorInvalidValue;
-  const int64_t bound = int64_t(batch) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
-  const int grid = int(std::min<int64_t>(bound, 4 * int64_t(sm_count())));
-  k_tc_digits<S, TB, TC><<<grid, kDigThreads, 0, s>>>(d_desc, batch);
+cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, const int* panel_start,
+                             int64_t panels) {
+  if (batch <= 0 || panels <= 0) return cudaSuccess;
+  const int grid = int(std::min<int64_t>(panels, 4 * int64_t(sm_count())));
+  k_tc_digits<S, TB, TC><<<grid, kDigThreads, 0, s>>>(d_desc, batch, panel_start);
   return cudaGetLastError();
 }
 
 template <int S, class TB, class TC>
-cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
-                           TC alpha, int* err, int64_t tiles) {
-  if (batch <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
-  if (batch > kMaxDescs) return cudaErrorInvalidValue;
+cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, const int* tile_start,
+                           int64_t tiles, int epi, TC alpha, int* err) {
+  if (batch <= 0 || tiles <= 0) return cudaSuccess;
   const size_t smem = tc_smem_bytes<S>();
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
   if (e != cudaSuccess) return e;
   // persistent CTAs, at most one per SM: the fewest that give every CTA the same largest
   // number of tiles as one per SM would, so that SMs left over serve the work running
-  // concurrently on the interface stream (tiles <= 0: bound from the largest shape)
-  if (tiles <= 0) tiles = int64_t(batch) * ((maxM + TBM - 1) / TBM) * ((maxN + TcCfg<S>::TBN - 1) / TcCfg<S>::TBN);
+  // concurrently on the interface stream
   const int64_t nsm = sm_count(), per = (tiles + nsm - 1) / nsm;
   const int grid = int(std::min<int64_t>((tiles + per - 1) / per, nsm));
-  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, epi, alpha, err);
+  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, tile_start, epi, alpha, err);
   return cudaGetLastError();
 }
-template cudaError_t launch_tc_digits<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int);
-template cudaError_t launch_tc_digits<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int);
-template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, int, int, int,
-                                                       double, int*, int64_t);
-template cudaError_t launch_gemm_tc<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, int, int, int, float,
-                                                     int*, int64_t);
+template cudaError_t launch_tc_digits<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, const int*,
+                                                         int64_t);
+template cudaError_t launch_tc_digits<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, const int*,
+                                                       int64_t);
+template cudaError_t launch_gemm_tc<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, const int*,
+                                                       int64_t, int, double, int*);
+template cudaError_t launch_gemm_tc<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, const int*, int64_t,
+                                                     int, float, int*);
+
+template <class TB, class TC>
+void tc_prefixes(const std::vector<TcDesc<TB, TC>>& h, int S, std::vector<int>& tile_start,
+                 std::vector<int>& panel_start) {
+  const int tbn = S == 1 ? TcCfg<1>::TBN : TcCfg<7>::TBN;
+  tile_start.assign(h.size() + 1, 0);
+  panel_start.assign(h.size() + 1, 0);
+  for (size_t q = 0; q < h.size(); ++q) {
+    const bool any = h[q].M > 0 && h[q].N > 0 && h[q].K > 0;
+    tile_start[q + 1] = tile_start[q] + (any ? int(tc_tiles(h[q].M, h[q].N, S)) : 0);
+    panel_start[q + 1] = panel_start[q] + (any ? (h[q].N + tbn - 1) / tbn : 0);
+  }
+}
+template void tc_prefixes<double, double>(const std::vector<TcDesc<double, double>>&, int, std::vector<int>&,
+                                          std::vector<int>&);
+template void tc_prefixes<float, float>(const std::vector<TcDesc<float, float>>&, int, std::vector<int>&,
+                                        std::vector<int>&);
 
 int64_t tc_tiles(int M, int N, int S) {
   if (M <= 0 || N <= 0) return 0;

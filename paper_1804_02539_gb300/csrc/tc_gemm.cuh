@@ -35,17 +35,25 @@ inline int64_t tc_tau_elems(int N, int S) { return S > 1 ? N : 0; }
 
 // S = 7: FP64-accurate digit-slice product (TB = TC = double), for K <= kTcMaxK (every single
 // digit product summed over K stays an exact FP32 integer); S = 1: BF16 product with FP32
-// accumulation (TB = TC = float).  Persistent launch over every tile of the `batch`
-// descriptors (at most 512; C must not alias B or E; the digit pass must have run on the
-// same stream since B last changed).  err: device flag set when an mbarrier wait times out.
+// accumulation (TB = TC = float).
 constexpr int kTcMaxK = 1023;
 // Two launches: the digit pass (B's digit planes and column exponents into Bdig/Btau, every
-// element once) and the GEMM (both operands by bulk copies).
+// element once) and the GEMM (both operands by bulk copies).  tile_start / panel_start are
+// device copies of the prefixes tc_prefixes computes (batch + 1 entries), tiles / panels
+// their totals.  Any number of descriptors; C must not alias B or E; the digit pass must
+// have run on the same stream since B last changed.  err: device flag set when an mbarrier
+// wait times out.
 template <int S, class TB, class TC>
-cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxN);
+cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, const int* panel_start,
+                             int64_t panels);
 template <int S, class TB, class TC>
-cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, int maxM, int maxN, int epi,
-                           TC alpha, int* err, int64_t tiles = 0);
+cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, const int* tile_start,
+                           int64_t tiles, int epi, TC alpha, int* err);
+// Prefix sums over descriptors of their output tiles (GEMM work items) and of their
+// 32-column (S = 7) or 128-column (S = 1) panels of B (digit-pass work items).
+template <class TB, class TC>
+void tc_prefixes(const std::vector<TcDesc<TB, TC>>& h, int S, std::vector<int>& tile_start,
+                 std::vector<int>& panel_start);
 // Output tiles of one M x N product (the GEMM's work items).
 int64_t tc_tiles(int M, int N, int S);
 

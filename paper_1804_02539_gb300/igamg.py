@@ -32,7 +32,8 @@ class igamg_options(C.Structure):
                 ("fd_engine", C.c_int),
                 ("graphs", C.c_int),
                 ("apply_engine", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int),
+                ("batch_engine", C.c_int)]
 
 
 class igamg_result(C.Structure):
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_solve_batch": ([P, C.POINTER(P), C.POINTER(P), C.c_double, C.POINTER(igamg_result),
                                C.POINTER(C.c_int)], C.c_int),
         "igamg_free_batch": ([P], C.c_int),
+        "igamg_batch_engine": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)], C.c_int),
         "igamg_server_create": ([C.POINTER(igamg_options), C.c_int, C.c_int64, C.POINTER(P)], C.c_int),
         "igamg_server_add_model": ([P, C.POINTER(igamg_problem), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64)], C.c_int),
@@ -338,6 +341,21 @@ class Batch:
 
     def __len__(self):
         return len(self.contexts)
+
+    def engine(self) -> str:
+        """'lockstep' or 'streams': the engine igamg_solve_batch uses for this batch."""
+        e = C.c_int()
+        lib().igamg_batch_engine(self.h, C.byref(e), None, None, None)
+        return "lockstep" if e.value == 0 else "streams"
+
+    def stats(self):
+        """Lockstep engine: kernel launches, algorithmic FLOPs and tensor-core MMA FLOPs of
+        the last solve (None for worker streams)."""
+        e, n, f, m = C.c_int(), C.c_int64(), C.c_double(), C.c_double()
+        lib().igamg_batch_engine(self.h, C.byref(e), C.byref(n), C.byref(f), C.byref(m))
+        if e.value != 0:
+            return None
+        return {"launches": n.value, "flops": f.value, "mma_flops": m.value}
 
     def solve(self, rhs, xs, tol=1e-8):
         """rhs, xs: sequences of contiguous CUDA float64 tensors (xs hold the initial guesses).
