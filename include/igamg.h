@@ -114,7 +114,7 @@ typedef struct {
                           (2D, rectangle patches, FP64, V-cycle): one launch per cycle step
                           over all problems, one graph replay per PCG iteration of the whole
                           batch; otherwise, and with 1, worker streams (whole single solves
-                          on concurrent streams).  Results are the same either way.       */
+                          on concurrent streams)                                        */
 } igamg_options;
 
 /* Result of a solve.  The first five fields are the problem statement's result record;
@@ -288,9 +288,12 @@ const char* igamg_last_error(const igamg_ctx* ctx);
  * smoother pieces, transfers, coarse solves) one launch over the tiles of every problem at
  * that depth below its finest level, each PCG iteration of the whole batch one CUDA graph
  * replay; the worker-stream engine runs whole single solves on `workers` host threads with
- * a CUDA stream each, in decreasing order of estimated work.  Either way a problem's result
- * is bit-identical to igamg_solve on that problem alone.  The paper solves one problem at a
- * time and has no counterpart of this layer. */
+ * a CUDA stream each, in decreasing order of estimated work.  With worker streams, or with a
+ * forced FD engine (fd_engine 1..4), a problem's result is bit-identical to igamg_solve on
+ * that problem alone; with the autotuned default the lockstep engine runs every level whose
+ * tensor-core stages exist on the tensor cores (its launches hold the tiles of all problems),
+ * which can differ from a problem's own choice by FP64 rounding.  The paper solves one
+ * problem at a time and has no counterpart of this layer. */
 typedef struct igamg_batch igamg_batch;
 
 /* Sets up `count` problems (host array, read during the call) with the same options.

@@ -1,9 +1,10 @@
 // Batched solves of independent problems: one context per problem (its own hierarchy, kept
-// resident), solved concurrently by a pool of host worker threads that each own a CUDA
-// stream.  Each worker takes the next problem in largest-first order (longest-processing-
-// time list scheduling), lends the context its stream for the solve and returns it.  The
-// solves themselves are the single-problem path (PCG iterations replayed as CUDA graphs),
-// so a batch result is bit-identical to solving that problem alone.
+// resident).  When every problem is in its scope the lockstep engine (igamg.cu) solves them
+// all at once, each step of the cycle one launch over every problem.  Otherwise a pool of
+// host worker threads that each own a CUDA stream takes the problems in largest-first order
+// (longest-processing-time list scheduling), lends each context its stream for the solve and
+// returns it; those solves are the single-problem path (PCG iterations replayed as CUDA
+// graphs), so their results are bit-identical to solving each problem alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
