@@ -91,6 +91,14 @@ struct GemmSetT {
 using GemmSet = GemmSetT<double>;
 
 template <class T>
+struct ModeSetT {  // one mode-product stage of the 3D interiors (all interiors of a level)
+  ModeDescT<T>* d = nullptr;
+  std::vector<ModeDescT<T>> h;
+  int batch = 0, max_n = 0;
+  int64_t max_fibres = 0;
+};
+
+template <class T>
 struct TcSet {
   TcDesc<T, T>* d = nullptr;
   std::vector<TcDesc<T, T>> h;
@@ -119,6 +127,7 @@ struct Num {
   TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // interiors on the tensor cores (2D: 4
   TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
   TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
+  ModeSetT<T> fm[4];                                // 3D faces as mode products (FMA engine)
   FdSmallT<T>* fsmall = nullptr;                    // small 2D interiors, one block each
   SmoothSmallT<T> ssmall{};                         // + edges and vertices in the same launch
   FdRowsT<T>* frows = nullptr;                      // 2D interiors by row blocks (two launches)
@@ -130,6 +139,7 @@ struct Num {
   double fsmall_flops = 0;
   bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
+  ModeSetT<T> md[6];                                // the same six products as mode products
   T* cX = nullptr;                                  // compact 3D interior tensor
   T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
   GemmSetT<T> edgeA, edgeB, face0, face1, face2, face3;
@@ -439,6 +449,23 @@ void set_gemm(igamg_ctx* c, GemmSetT<T>& gs, const std::vector<GemmDescT<T>>& v)
   gs.flops = gemm_flops(v);
   gs.bytes = 0;
   for (auto& d : v) gs.bytes += 8.0 * (double(d.M) * d.K + double(d.K) * d.N + 2.0 * d.M * d.N);
+}
+
+template <class T>
+void set_mode(igamg_ctx* c, ModeSetT<T>& ms, const std::vector<ModeDescT<T>>& v) {
+  ms.h = v;
+  ms.batch = int(v.size());
+  ms.max_fibres = 0;
+  ms.max_n = 0;
+  for (auto& d : v) ms.max_fibres = std::max(ms.max_fibres, d.fibres), ms.max_n = std::max(ms.max_n, d.n);
+  ms.d = v.empty() ? nullptr : c->mem.upload(v, c->stream);
+}
+
+// One mode-product stage with the work accounting of the GEMM stage it replaces.
+template <class T>
+void run_mode(igamg_ctx* c, const ModeSetT<T>& ms, const GemmSetT<T>& gs, int epi, int cls = CLS_FD) {
+  ProfScope ps(c, cls, gs.flops, gs.bytes * sizeof(T) / 8.0);
+  CK(launch_mode_product<T>(c->stream, ms.d, ms.batch, ms.max_fibres, ms.max_n, epi));
 }
 
 template <class T>
@@ -1096,6 +1123,27 @@ void build_levels(igamg_ctx* c) {
           b1.push_back(GemmDesc{U1, B2 + int64_t(a) * n12, B1 + int64_t(a) * n12, nullptr, n1, n2, n2, 0, n1, n2, n1});
         b2.push_back(GemmDesc{B1, U2, X, nullptr, n2, n2, n2, 0, n0 * n1, n2, n2});
       }
+      // the same products as one mode-product launch per stage (matrices of at most
+      // kModeMaxN rows), used instead of the GEMM stages by the FMA engine
+      {
+        bool ok = !pend.empty();
+        std::vector<ModeDescT<double>> md[6];
+        for (const Pend& pe : pend) {
+          int n0 = pe.n0, n1 = pe.n1, n2 = pe.n2;
+          ok = ok && std::max(n0, std::max(n1, n2)) <= kModeMaxN;
+          const int64_t n12 = int64_t(n1) * n2;
+          double *X = L.n64.cX + pe.base, *B1 = cB1 + pe.base, *B2 = cB2 + pe.base;
+          const double *U0 = pe.S[0]->dU, *U1 = pe.S[1]->dU, *U2 = pe.S[2]->dU;
+          md[0].push_back(ModeDescT<double>{U0, X, B1, nullptr, n0, 1, n12, n12});
+          md[1].push_back(ModeDescT<double>{U1, B1, B2, nullptr, n1, 1, n2, int64_t(n0) * n2});
+          md[2].push_back(ModeDescT<double>{U2, B2, B1, pe.Dinv, n2, 1, 1, int64_t(n0) * n1});
+          md[3].push_back(ModeDescT<double>{U0, B1, B2, nullptr, n0, 0, n12, n12});
+          md[4].push_back(ModeDescT<double>{U1, B2, B1, nullptr, n1, 0, n2, int64_t(n0) * n2});
+          md[5].push_back(ModeDescT<double>{U2, B1, X, nullptr, n2, 0, 1, int64_t(n0) * n1});
+        }
+        if (ok)
+          for (int j = 0; j < 6; ++j) set_mode(c, L.n64.md[j], md[j]);
+      }
       set_gemm(c, L.n64.m0f, f0);
       set_gemm(c, L.n64.m1f, f1);
       set_gemm(c, L.n64.m2f, f2);
@@ -1280,6 +1328,20 @@ void build_levels(igamg_ctx* c) {
     set_gemm(c, L.n64.face1, q1);
     set_gemm(c, L.n64.face2, q2);
     set_gemm(c, L.n64.face3, q3);
+    if (!q0.empty()) {  // the same four products as mode products (faces of <= kModeMaxN)
+      bool ok = true;
+      std::vector<ModeDescT<double>> fm[4];
+      for (size_t f = 0; f < q0.size(); ++f) {
+        const int len0 = q0[f].M, len1 = q0[f].N;
+        ok = ok && std::max(len0, len1) <= kModeMaxN;
+        fm[0].push_back(ModeDescT<double>{q0[f].A, q0[f].B, q0[f].C, nullptr, len0, 1, len1, len1});
+        fm[1].push_back(ModeDescT<double>{q1[f].B, q1[f].A, q1[f].C, q1[f].E, len1, 1, 1, len0});
+        fm[2].push_back(ModeDescT<double>{q2[f].A, q2[f].B, q2[f].C, nullptr, len0, 0, len1, len1});
+        fm[3].push_back(ModeDescT<double>{q3[f].B, q3[f].A, q3[f].C, nullptr, len1, 0, 1, len0});
+      }
+      if (ok)
+        for (int j = 0; j < 4; ++j) set_mode(c, L.n64.fm[j], fm[j]);
+    }
     if (face_tc && !q0.empty()) {
       // stage 0 reads G, 1 reads T writes Y, 2 reads Y writes T, 3 reads T writes Z
       for (auto& t : tqd[0]) { t.B = L.n64.G + (intptr_t)t.B; t.C = fT + (intptr_t)t.C; }
@@ -1572,6 +1634,11 @@ void smooth_interface(igamg_ctx* c, Level& L, Num<T>& N, const T* v, double tau,
     run_tc(c, N.tq1, EPI_MUL, 1.0, CLS_IFACE);
     run_tc(c, N.tq2, EPI_STORE, 1.0, CLS_IFACE);
     run_tc(c, N.tq3, EPI_STORE, 1.0, CLS_IFACE);
+  } else if (N.fm[0].batch) {
+    run_mode(c, N.fm[0], N.face0, EPI_STORE, CLS_IFACE);
+    run_mode(c, N.fm[1], N.face1, EPI_MUL, CLS_IFACE);
+    run_mode(c, N.fm[2], N.face2, EPI_STORE, CLS_IFACE);
+    run_mode(c, N.fm[3], N.face3, EPI_STORE, CLS_IFACE);
   } else {
     run_gemm(c, N.face0, true, false, EPI_STORE, 1.0, CLS_IFACE);
     run_gemm(c, N.face1, false, false, EPI_MUL, 1.0, CLS_IFACE);
@@ -1639,6 +1706,13 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
       run_tc(c, N.tc3, EPI_STORE, 1.0);
       run_tc(c, N.tc4, EPI_STORE, 1.0);
       run_tc(c, N.tc5, EPI_STORE, 1.0);
+    } else if (N.md[0].batch) {
+      run_mode(c, N.md[0], N.m0f, EPI_STORE);
+      run_mode(c, N.md[1], N.m1f, EPI_STORE);
+      run_mode(c, N.md[2], N.m2f, EPI_MUL);
+      run_mode(c, N.md[3], N.m0b, EPI_STORE);
+      run_mode(c, N.md[4], N.m1b, EPI_STORE);
+      run_mode(c, N.md[5], N.m2b, EPI_STORE);
     } else {
       run_gemm(c, N.m0f, true, false, EPI_STORE, 1.0, CLS_FD);
       run_gemm(c, N.m1f, true, false, EPI_STORE, 1.0, CLS_FD);
@@ -2250,6 +2324,15 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
     tr_set(A.st3, B.st3);
     tr_set(A.m0f, B.m0f); tr_set(A.m1f, B.m1f); tr_set(A.m2f, B.m2f);
     tr_set(A.m0b, B.m0b); tr_set(A.m1b, B.m1b); tr_set(A.m2b, B.m2b);
+    auto tr_mode = [&](const ModeSetT<double>& a, ModeSetT<float>& b) {
+      if (!a.batch) return;
+      std::vector<ModeDescT<float>> v;
+      for (const auto& d : a.h)
+        v.push_back(ModeDescT<float>{tr(d.Mat), tr(d.X), tr(d.Y), tr(d.E), d.n, d.mtr, d.inner, d.fibres});
+      set_mode(c, b, v);
+    };
+    for (int j = 0; j < 6; ++j) tr_mode(A.md[j], B.md[j]);
+    for (int j = 0; j < 4; ++j) tr_mode(A.fm[j], B.fm[j]);
     tr_set(A.edgeA, B.edgeA); tr_set(A.edgeB, B.edgeB);
     tr_set(A.face0, B.face0); tr_set(A.face1, B.face1); tr_set(A.face2, B.face2); tr_set(A.face3, B.face3);
     if (!L.r2_h.empty()) {

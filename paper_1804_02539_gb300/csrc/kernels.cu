@@ -1602,6 +1602,175 @@ template cudaError_t launch_transfer_2d<double>(cudaStream_t, const Xfer2T<doubl
 template cudaError_t launch_transfer_2d<float>(cudaStream_t, const Xfer2T<float>*, int, int, int, int, const float*,
                                                float*, int, const int64_t*);
 
+// ---------------------------------------------------------------- mode products
+
+// Shared-memory layout of one block: the n x n matrix as rows of odd stride (the two row
+// groups a warp reads fall in different banks), then n rows of kModeCH fibres with stride
+// kModeLDX (16-byte rows: each thread reads its four fibres as one vector).
+constexpr int kModeCH = 64, kModeLDX = kModeCH + 4;
+__host__ __device__ inline int mode_ldm(int n) { return (n & 1) ? n + 2 : n + 1; }
+template <class T>
+__host__ __device__ inline int mode_xoff(int n) {  // element offset of the fibre tile
+  constexpr int al = 16 / int(sizeof(T));
+  return (n * mode_ldm(n) + al - 1) / al * al;
+}
+
+__device__ __forceinline__ void cp_async_elem(float* s, const float* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(unsigned(__cvta_generic_to_shared(s))), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* s, const double* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(unsigned(__cvta_generic_to_shared(s))), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void ld4(const float* p, float (&b)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  b[0] = v.x, b[1] = v.y, b[2] = v.z, b[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&b)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+  b[0] = v0.x, b[1] = v0.y, b[2] = v1.x, b[3] = v1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&b)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(b[0], b[1], b[2], b[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&b)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(b[0], b[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(b[2], b[3]);
+}
+
+// One block: the matrix and kModeCH fibres copied to shared memory with asynchronous
+// element copies (all of a thread's copies in flight at once), each thread then RPT rows
+// (i = rg + 16 t) x 4 adjacent fibres in registers, one FMA chain per output over
+// k = 0..n-1.  The output tile goes back through shared memory.  Fibres that run along
+// memory (inner > 1) are moved with lanes along the fibres; fibres contiguous in memory
+// (inner == 1) with each warp on an 8 (k) x 4 (fibre) patch, which keeps both the global
+// accesses (32-byte pieces) and the shared-memory accesses (32 distinct banks) whole.
+template <class T, int RPT>
+__global__ void __launch_bounds__(256) k_mode_product(const ModeDescT<T>* __restrict__ ds, int epi) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ModeDescT<T> d = ds[blockIdx.y];
+  const int64_t c0 = int64_t(blockIdx.x) * kModeCH;
+  if (c0 >= d.fibres) return;
+  const int n = d.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cw = int(d.fibres - c0 < kModeCH ? d.fibres - c0 : int64_t(kModeCH));
+  const int ldm = mode_ldm(n);
+  T* Ms = reinterpret_cast<T*>(smraw);
+  T* Xs = Ms + mode_xoff<T>(n);
+  const T* __restrict__ X = d.X;
+  const T* __restrict__ Mat = d.Mat;
+  T* __restrict__ Y = d.Y;
+  const T* __restrict__ E = d.E;
+  if (d.mtr) {
+    for (int idx = tid; idx < n * n; idx += 256) {
+      const int k = idx / n, i = idx - k * n;
+      cp_async_elem(Ms + i * ldm + k, Mat + idx);
+    }
+  } else {
+    for (int idx = tid; idx < n * n; idx += 256) {
+      const int i = idx / n, k = idx - i * n;
+      cp_async_elem(Ms + i * ldm + k, Mat + idx);
+    }
+  }
+  const int64_t inner = d.inner, slab = int64_t(n) * inner;
+  const int nkb = (n + 7) >> 3;
+  int64_t off = 0;  // inner > 1: this thread's fibre c0 + tid % kModeCH stays fixed
+  if (inner > 1) {
+    const int cl = tid % kModeCH;
+    const int64_t c = c0 + cl;
+    off = (c / inner) * slab + c % inner;
+    for (int k = tid / kModeCH; k < n; k += 256 / kModeCH) {
+      if (cl < cw) cp_async_elem(Xs + k * kModeLDX + cl, X + off + int64_t(k) * inner);
+      else Xs[k * kModeLDX + cl] = T(0);
+    }
+  } else {
+    const int kk = lane & 7, cc = lane >> 3;
+    for (int tile = warp; tile < nkb * (kModeCH / 4); tile += 8) {
+      const int k = (tile % nkb) * 8 + kk, cl = (tile / nkb) * 4 + cc;
+      if (k >= n) continue;
+      if (cl < cw) cp_async_elem(Xs + k * kModeLDX + cl, X + (c0 + cl) * n + k);
+      else Xs[k * kModeLDX + cl] = T(0);
+    }
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  const int cg = tid & 15, rg = tid >> 4;
+  T acc[RPT][4];
+  int rowoff[RPT];
+#pragma unroll
+  for (int t = 0; t < RPT; ++t) {
+    const int i = rg + 16 * t;
+    rowoff[t] = (i < n ? i : 0) * ldm;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[t][u] = T(0);
+  }
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    T b[4];
+    ld4(Xs + k * kModeLDX + cg * 4, b);
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+      const T a = Ms[rowoff[t] + k];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[t][u] = fma(a, b[u], acc[t][u]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < RPT; ++t) {
+    const int i = rg + 16 * t;
+    if (i < n) st4(Xs + i * kModeLDX + cg * 4, acc[t]);
+  }
+  __syncthreads();
+  const bool mul = epi == EPI_MUL;
+  if (inner > 1) {
+    const int cl = tid % kModeCH;
+    if (cl < cw) {
+#pragma unroll 4
+      for (int i = tid / kModeCH; i < n; i += 256 / kModeCH) {
+        const int64_t a = off + int64_t(i) * inner;
+        const T v = Xs[i * kModeLDX + cl];
+        Y[a] = mul ? v * E[a] : v;
+      }
+    }
+  } else {
+    const int kk = lane & 7, cc = lane >> 3;
+#pragma unroll 2
+    for (int tile = warp; tile < nkb * (kModeCH / 4); tile += 8) {
+      const int i = (tile % nkb) * 8 + kk, cl = (tile / nkb) * 4 + cc;
+      if (i >= n || cl >= cw) continue;
+      const int64_t a = (c0 + cl) * n + i;
+      const T v = Xs[i * kModeLDX + cl];
+      Y[a] = mul ? v * E[a] : v;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_mode_product(cudaStream_t s, const ModeDescT<T>* d, int batch, int64_t max_fibres, int max_n,
+                                int epi) {
+  if (batch <= 0 || max_fibres <= 0) return cudaSuccess;
+  if (max_n < 1 || max_n > kModeMaxN) return cudaErrorInvalidValue;
+  const size_t sm = sizeof(T) * (size_t(mode_xoff<T>(max_n)) + size_t(max_n) * kModeLDX);
+  const dim3 grid(unsigned((max_fibres + kModeCH - 1) / kModeCH), unsigned(batch));
+  const int rpt = (max_n + 15) / 16;
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, sm, s>>>(d, epi);
+    return cudaGetLastError();
+  };
+  switch (rpt) {
+    case 1: return go(k_mode_product<T, 1>);
+    case 2: return go(k_mode_product<T, 2>);
+    case 3: return go(k_mode_product<T, 3>);
+    case 4: return go(k_mode_product<T, 4>);
+    default: return go(k_mode_product<T, 5>);
+  }
+}
+template cudaError_t launch_mode_product<double>(cudaStream_t, const ModeDescT<double>*, int, int64_t, int, int);
+template cudaError_t launch_mode_product<float>(cudaStream_t, const ModeDescT<float>*, int, int64_t, int, int);
+
 // ---------------------------------------------------------------- interior box gather/scatter
 
 // Compact copy of every patch-interior box (3D FD works on compact tensors) and the

@@ -195,6 +195,27 @@ template <class T>
 cudaError_t launch_box_copy(cudaStream_t s, const BoxDev* boxes, int nbox, int64_t max_box, const T* src, T* dst,
                             int to_compact, T tau, int add);
 
+// Product of a small dense n x n matrix along one mode of a tensor (the FD contractions of
+// the 3D interiors): for every fibre c and row i,
+//   Y(i, c) = sum_k M(i, k) X(k, c),   M(i, k) = mtr ? Mat[k * n + i] : Mat[i * n + k],
+// with X(k, c) at X[off(c) + k * inner], off(c) = (c / inner) * n * inner + c % inner (the
+// tensor viewed as outer x n x inner; `fibres` = outer * inner), Y laid out like X, and
+// E (EPI_MUL) like Y.  Every output is one FMA chain over k = 0..n-1 in order, as in
+// launch_gemm.  n <= kModeMaxN.
+template <class T>
+struct ModeDescT {
+  const T* Mat;
+  const T* X;
+  T* Y;
+  const T* E;
+  int n, mtr;
+  int64_t inner, fibres;
+};
+constexpr int kModeMaxN = 80;
+template <class T>
+cudaError_t launch_mode_product(cudaStream_t s, const ModeDescT<T>* d, int batch, int64_t max_fibres, int max_n,
+                                int epi);
+
 // Coarse solve in FP64: x_copies = A0inv * (sum of copies of f) for the N0 level-0 dofs.
 template <class T>
 cudaError_t launch_coarse_solve(cudaStream_t s, int64_t N0, const int64_t* ptr, const int64_t* idx,
