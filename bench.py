@@ -741,7 +741,8 @@ SERVE_DESC = ("Poisson arrivals of single-rhs requests over a catalog of 110 mod
               "and 10 perturbed 2x2x2 cubes (p in {2,3}, m in {16,24,32,40,48}) with 20%; rhs = U(-1,1) load "
               "vectors; PCG + V(1,1) to relative residual 1e-8 (mixed precision: FP64 iterative refinement); "
               "hierarchies resident under the device-memory budget (one untimed warm-up request per model "
-              "builds them)")
+              "builds them); waiting requests of one 2D model taken together (up to 16) and solved as "
+              "several right-hand sides in lockstep (FP64 numerics)")
 
 
 def run_serve(args):
@@ -794,6 +795,8 @@ def run_serve(args):
                       "p99_ms": round(float(np.percentile(lat, 99)), 2),
                       "mean_service_ms": round(float(svc.mean()), 2),
                       "mdof_per_s": round(dofs / (span * 1e-3) / 1e6, 3),
+                      "mean_group": round(float(np.mean([i["group"] for i in infos])), 2),
+                      "max_group": int(max(i["group"] for i in infos)),
                       "served_per_s": round(len(reqs) / (span * 1e-3), 1), "clocks": clocks})
     st = srv.stats()
     srv.free()
@@ -807,6 +810,7 @@ def run_serve(args):
                       "precision": args.precision,
                       "budget_gb": args.budget_gb, "warmup_s": round(t_warm, 1), "models": len(probs),
                       "resident": st["resident"], "setups": st["setups"], "evictions": st["evictions"],
+                      "groups": st["groups"], "grouped_requests": st["grouped"],
                       "device_gb": round(st["device_bytes"] / 1e9, 3),
                       "l2": "inputs larger than L2 (resident hierarchies of GBs)"},
            "serving": lines}
@@ -909,8 +913,8 @@ def main():
     ap.add_argument("--workers", type=int, default=16, help="host worker threads of the batch")
     ap.add_argument("--micro", choices=["fd", "fp64"], help="micro-benchmark instead of the solve")
     ap.add_argument("--serve", action="store_true", help="the served workload (Poisson arrivals)")
-    ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 200.0, 500.0, 2000.0])
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--rates", type=float, nargs="+", default=[200.0, 500.0, 2000.0])
+    ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--budget-gb", type=float, default=96.0)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fd-engine", type=int, default=0)

@@ -174,6 +174,25 @@ igamg_status igamg_rhs_from_coefs(igamg_ctx* ctx, const double* coef_dev, double
 igamg_status igamg_solve(igamg_ctx* ctx, const double* rhs_dev, double* x_dev, double tol,
                          igamg_result* res);
 
+/* Several right-hand sides of one problem solved together: igamg_solve for the nrhs device
+ * vectors rhs_dev[q] (x_dev[q]: in x_0, out x; host arrays of nrhs device pointers, each
+ * vector of length N_L, all distinct), each stopped by its own residual test.  Where the
+ * problem qualifies (2D, every level above the coarsest of rectangle patches, V-cycle) the
+ * lockstep engine of igamg_solve_batch runs them: each step of Algorithm 1 is one launch
+ * over all right-hand sides, which share the hierarchy's constant arrays (1D factors,
+ * smoother bases, transfer weights) and read them once per launch; the work arrays are
+ * copied once per extra right-hand side on first use (kept until igamg_free, counted by the
+ * context's device bytes).  This path runs the FP64 numerics whatever the precision option
+ * (each answer meets the same tolerance); with a forced FD engine (fd_engine 1..4) and FP64
+ * each answer is bit-identical to igamg_solve of that right-hand side alone.  Otherwise the
+ * right-hand sides are solved one after the other by igamg_solve.  `res` and `status` (may
+ * be NULL) receive nrhs entries.  Returns the worst status (IGAMG_ERR_NOT_CONVERGED only if
+ * nothing worse); IGAMG_ERR_ARG for nrhs < 1, null arrays or vectors, tol < 0.
+ * Synchronises the stream. */
+igamg_status igamg_solve_multi(igamg_ctx* ctx, int nrhs, const double* const* rhs_dev,
+                               double* const* x_dev, double tol, igamg_result* res,
+                               igamg_status* status);
+
 /* igamg_solve with HOST vectors: copies rhs and x_0 to the device, solves, copies x back
  * (the end-to-end call).  Synchronises. */
 igamg_status igamg_solve_host(igamg_ctx* ctx, const double* rhs_host, double* x_host,
@@ -332,6 +351,11 @@ igamg_status igamg_free_batch(igamg_batch* batch);
  * A request is one right-hand side of a registered model (a problem as in igamg_setup).
  * Requests are answered by `workers` host threads with a CUDA stream each, in arrival
  * order, except that a request waits while another worker uses its model's hierarchy.
+ * A worker that takes a request of a model igamg_solve_multi runs in lockstep also takes
+ * the model's other waiting requests of the same tolerance (oldest first, up to 16 in all)
+ * and solves them together with igamg_solve_multi (one launch per step for the group, the
+ * hierarchy's constant arrays shared; FP64 numerics); other models' requests are solved
+ * one at a time with igamg_solve.
  * Hierarchies stay resident between requests; a model's hierarchy is built on its first
  * request when its estimated size fits the device-memory budget, after freeing the least
  * recently used idle hierarchies.  Times are milliseconds since igamg_server_create.  The
@@ -346,12 +370,15 @@ typedef struct {
   double t_start_ms;    /* a worker took the request                                 */
   double t_done_ms;     /* solution copied to x                                      */
   double setup_ms;      /* hierarchy built for this request (0 if it was resident)    */
+  int group;            /* requests solved together with this one, itself included   */
 } igamg_request_info;
 
 typedef struct {
   int models, resident;
   int64_t device_bytes;  /* hierarchies (measured; estimates while being built)        */
   int64_t setups, evictions, completed, waiting;
+  int64_t groups;        /* igamg_solve_multi calls of more than one request          */
+  int64_t grouped;       /* requests answered by those calls                          */
 } igamg_server_counters;
 
 /* Starts the workers.  opt (NULL = defaults) applies to every model; hbm_budget_bytes

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -192,6 +193,20 @@ template <> Num<float>& num<float>(Level& L) { return L.n32; }
 
 }  // namespace
 
+namespace igamg {
+struct Lockstep;
+void lockstep_free(Lockstep* k);
+// One more set of a context's work arrays, for solving several right-hand sides of one
+// problem together: every array the cycle and the PCG write (the registered work arrays, the
+// Krylov vectors, the tensor-core digit scratch) once more; the constant arrays are shared.
+struct WorkCopy {
+  std::vector<std::tuple<const double*, int64_t, double*>> tw;  // (context's array, count, this copy's), by base
+  double *X = nullptr, *Pv = nullptr, *W = nullptr, *Bt = nullptr, *Rr = nullptr;
+  __nv_bfloat16* dig[2] = {nullptr, nullptr};
+  int* tau[2] = {nullptr, nullptr};
+};
+}  // namespace igamg
+
 struct igamg_ctx {
   cudaStream_t stream = nullptr;
   igamg_options opt{};
@@ -242,6 +257,11 @@ struct igamg_ctx {
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_open;
   int cur_cls = -1;
   cudaEvent_t cur_start = nullptr;
+  // several right-hand sides solved together (igamg_solve_multi): the FP64 digit scratch
+  // sizes, the work-array copies 1.., and the lockstep engines by number of right-hand sides
+  int64_t dig64[2] = {0, 0}, tau64[2] = {0, 0};
+  std::deque<igamg::WorkCopy> copies;  // stable addresses: the engines point into it
+  std::map<int, igamg::Lockstep*> multi;
 };
 
 static thread_local std::string g_setup_error = "no error";
@@ -521,6 +541,7 @@ void bind_tc(igamg_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     if (dig[k]) dbase[k] = c->mem.alloc<__nv_bfloat16>(size_t(dig[k]));
     if (tau[k]) tbase[k] = c->mem.alloc<int>(size_t(tau[k]));
+    if (sizeof(T) == 8) c->dig64[k] = dig[k], c->tau64[k] = tau[k];
   }
   for (TcSet<T>* p : sets) {
     for (int i = 0; i < p->batch; ++i) {
@@ -2444,8 +2465,32 @@ struct LockDepth {
   int64_t coarse_n = 0;
 };
 
+// One right-hand side of a lockstep solve: a context and the work arrays it runs on (its
+// own, or one of its copies when several right-hand sides of one problem run together).
+struct LockMember {
+  igamg_ctx* c = nullptr;
+  const WorkCopy* w = nullptr;  // nullptr: the context's own arrays
+  // this member's array for an array of the context (constant arrays map to themselves)
+  double* tr(const double* p) const {
+    if (!w || !p) return const_cast<double*>(p);
+    auto it = std::upper_bound(w->tw.begin(), w->tw.end(), p,
+                               [](const double* q, const auto& e) { return q < std::get<0>(e); });
+    if (it == w->tw.begin()) throw Fail{IGAMG_ERR_NUMERIC, "untracked array in a descriptor"};
+    --it;
+    const int64_t off = p - std::get<0>(*it);
+    if (off < 0 || off > std::get<1>(*it)) throw Fail{IGAMG_ERR_NUMERIC, "untracked array in a descriptor"};
+    return std::get<2>(*it) + off;
+  }
+  double* X() const { return w ? w->X : c->X; }
+  double* Pv() const { return w ? w->Pv : c->Pv; }
+  double* W() const { return w ? w->W : c->W; }
+  double* Bt() const { return w ? w->Bt : c->Bt; }
+  double* Rr() const { return w ? w->Rr : c->Rr; }
+};
+
 struct Lockstep {
   std::vector<igamg_ctx*> ctx;
+  std::vector<LockMember> mb;
   DevMem mem;
   int nprob = 0, depths = 0, nu = 1;
   double tau = 0.25;
@@ -2485,10 +2530,23 @@ V* lk_upload(Lockstep* k, const std::vector<V>& h) {
   return d;
 }
 
-void lk_gemm_groups(Lockstep* k, const std::vector<const GemmSet*>& sets, std::vector<LockGemmGroup>& out) {
+using MemberGemm = std::pair<const GemmSet*, const LockMember*>;
+using MemberTc = std::pair<const TcSet<double>*, const LockMember*>;
+
+void lk_gemm_groups(Lockstep* k, const std::vector<MemberGemm>& sets, std::vector<LockGemmGroup>& out) {
   std::map<int, std::vector<GemmDesc>> byR;
-  for (const GemmSet* g : sets)
-    if (g->batch) byR[g->R].insert(byR[g->R].end(), g->h.begin(), g->h.end());
+  for (const auto& gm : sets) {
+    const GemmSet* g = gm.first;
+    const LockMember& m = *gm.second;
+    if (!g->batch) continue;
+    for (GemmDesc d : g->h) {
+      d.A = m.tr(d.A);
+      d.B = m.tr(d.B);
+      d.C = m.tr(d.C);
+      d.E = m.tr(d.E);
+      byR[g->R].push_back(d);
+    }
+  }
   for (auto& kv : byR) {
     LockGemmGroup gg;
     gg.R = kv.first;
@@ -2503,10 +2561,22 @@ void lk_gemm_groups(Lockstep* k, const std::vector<const GemmSet*>& sets, std::v
   }
 }
 
-void lk_tc_stage(Lockstep* k, const std::vector<const TcSet<double>*>& sets, LockTcStage& out) {
+void lk_tc_stage(Lockstep* k, const std::vector<MemberTc>& sets, LockTcStage& out) {
   std::vector<TcDesc<double, double>> h;
-  for (const TcSet<double>* t : sets) {
-    h.insert(h.end(), t->h.begin(), t->h.end());
+  for (const auto& tm : sets) {
+    const TcSet<double>* t = tm.first;
+    const LockMember& m = *tm.second;
+    for (int i = 0; i < t->batch; ++i) {
+      TcDesc<double, double> d = t->h[i];
+      if (m.w) {  // the copy's inputs, outputs and digit scratch
+        d.B = m.tr(d.B);
+        d.C = m.tr(d.C);
+        d.E = m.tr(d.E);
+        d.Bdig = m.w->dig[t->side] + t->dig_off[i];
+        d.Btau = m.w->tau[t->side] ? m.w->tau[t->side] + t->tau_off[i] : nullptr;
+      }
+      h.push_back(d);
+    }
     out.exec_flops += t->exec_flops;
     out.flops += t->flops;
   }
@@ -2533,18 +2603,37 @@ void lockstep_free(Lockstep* k) {
   delete k;
 }
 
+// The one-launch small-level smoother of member m (the copy's arrays for a copy).
+SmoothSmallT<double> lk_small(Lockstep* k, const LockMember& m, const Level& L) {
+  const SmoothSmallT<double>& a = L.n64.ssmall;
+  if (!m.w) return a;
+  SmoothSmallT<double> q = a;
+  std::vector<FdSmallT<double>> fs;
+  for (const auto& f : L.fs_h)
+    fs.push_back(FdSmallT<double>{f.U0, f.U1, f.Dinv, m.tr(f.vF), m.tr(f.vR), m.tr(f.u), f.n0, f.n1, f.ld});
+  q.fd = lk_upload(k, fs);
+  q.vF = m.tr(a.vF);
+  q.vR = m.tr(a.vR);
+  q.u = m.tr(a.u);
+  return q;  // the edge pieces read and write only through vF, vR and u
+}
+
 // The lockstep engine of a batch, or NULL (with the reason) when a problem is outside its
 // scope.  Called after every context is set up (their engines chosen and descriptors built).
-Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
+// `mb` lists the right-hand sides: distinct problems, or one problem and its work copies;
+// with fp64_of_low a precision-variant context runs its FP64 numerics.
+Lockstep* lockstep_build(const std::vector<LockMember>& mb, std::string* why, bool fp64_of_low) {
   auto no = [&](const std::string& w) -> Lockstep* {
     if (why) *why = w;
     return nullptr;
   };
-  if (ctx.empty()) return no("empty batch");
+  if (mb.empty()) return no("empty batch");
+  std::vector<igamg_ctx*> ctx;
+  for (const auto& m : mb) ctx.push_back(m.c);
   const igamg_options& o0 = ctx[0]->opt;
   for (igamg_ctx* c : ctx) {
     if (c->pd.dim != 2) return no("3D problem");
-    if (c->opt.precision != IGAMG_FP64 || c->low) return no("precision variant");
+    if (!fp64_of_low && (c->opt.precision != IGAMG_FP64 || c->low)) return no("precision variant");
     if (c->opt.mu != 1 || c->opt.nu != o0.nu || c->opt.tau != o0.tau) return no("cycle options differ");
     if (c->lv.size() < 2) return no("single-level hierarchy");
     for (size_t l = 1; l < c->lv.size(); ++l) {
@@ -2555,6 +2644,7 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
   Lockstep* k = new Lockstep();
   try {
     k->ctx = ctx;
+    k->mb = mb;
     k->nprob = int(ctx.size());
     k->nu = o0.nu;
     k->tau = o0.tau;
@@ -2569,25 +2659,26 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
         std::vector<SmoothSmallT<double>> small;
         std::vector<int> small_start{0};
         std::vector<NodeJobT<double>> gather, scatter;
-        std::vector<const GemmSet*> eA, eB, st[4];
-        std::vector<const TcSet<double>*> tc[4];
+        std::vector<MemberGemm> eA, eB, st[4];
+        std::vector<MemberTc> tc[4];
         std::vector<FdRowsT<double>> rows;
         std::vector<FdSmallT<double>> fsmall;
       } sd[2];
-      for (igamg_ctx* c : ctx) {
+      for (const LockMember& m : k->mb) {
+        igamg_ctx* c = m.c;
         const int l = int(c->lv.size()) - 1 - d;
         if (l < 1) continue;
         Level& L = c->lv[l];
         Level& C = c->lv[l - 1];
         Num<double>& N = L.n64;
-        for (const auto& kd : L.kd_h) res.push_back(KronJobT<double>{kd, L.active, N.U, N.F, N.R});
+        for (const auto& kd : L.kd_h) res.push_back(KronJobT<double>{kd, L.active, m.tr(N.U), m.tr(N.F), m.tr(N.R)});
         D.res_flops += L.apply_flops;
         D.x_flops += L.xfer_flops / 3;  // restriction; the prolongation is 2/3 of xfer_flops
         D.res_n0 = std::max(D.res_n0, L.max_n[0]);
         D.res_n1 = std::max(D.res_n1, L.max_n[1]);
         D.res_p = std::max(D.res_p, L.max_p);
-        for (const auto& x : L.r2_h) rst.push_back(Xfer2JobT<double>{x, N.R, C.n64.F, C.l2g});
-        for (const auto& x : L.p2_h) pro.push_back(Xfer2JobT<double>{x, C.n64.U, N.U, nullptr});
+        for (const auto& x : L.r2_h) rst.push_back(Xfer2JobT<double>{x, m.tr(N.R), m.tr(C.n64.F), C.l2g});
+        for (const auto& x : L.p2_h) pro.push_back(Xfer2JobT<double>{x, m.tr(C.n64.U), m.tr(N.U), nullptr});
         D.r_out0 = std::max(D.r_out0, L.x2_rout0);
         D.r_out1 = std::max(D.r_out1, L.x2_rout1);
         D.r_w1 = std::max(D.r_w1, L.x2_rw1);
@@ -2600,8 +2691,8 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
           j.n = c->N0;
           j.ptr = L0.g2t_ptr;
           j.idx = L0.g2t;
-          j.v = L0.n64.F;
-          j.u = L0.n64.U;
+          j.v = m.tr(L0.n64.F);
+          j.u = m.tr(L0.n64.U);
           j.Ainv = c->A0inv;
           coarse.push_back(j);
           D.coarse_n = std::max(D.coarse_n, c->N0);
@@ -2609,10 +2700,10 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
         }
         for (int dir = 0; dir < 2; ++dir) {  // 0: from F (assign), 1: from R (add)
           Side& S = sd[dir];
-          const double* v = dir == 0 ? N.F : N.R;
+          const double* v = m.tr(dir == 0 ? N.F : N.R);
           if (N.use_fused && L.small_ok) {
             D.sm[dir].flops += N.ssmall_flops;
-            S.small.push_back(N.ssmall);
+            S.small.push_back(lk_small(k, m, L));
             const SmoothSmallT<double>& q = N.ssmall;
             S.small_start.push_back(S.small_start.back() + q.nfd + q.nedges + (q.vend > q.vbeg ? 1 : 0));
             continue;
@@ -2623,19 +2714,19 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
             g.ptr = L.if_ptr;
             g.idx = L.if_idx;
             g.v = v;
-            g.G = N.G;
+            g.G = m.tr(N.G);
             S.gather.push_back(g);
             NodeJobT<double> t{};
             t.n = L.n_if;
             t.ptr = L.if_ptr;
             t.idx = L.if_idx;
-            t.Z = N.Z;
-            t.G = N.G;
+            t.Z = m.tr(N.Z);
+            t.G = m.tr(N.G);
             t.vscale = N.vscale;
-            t.u = N.U;
+            t.u = m.tr(N.U);
             S.scatter.push_back(t);
-            S.eA.push_back(&N.edgeA);
-            S.eB.push_back(&N.edgeB);
+            S.eA.push_back({&N.edgeA, &m});
+            S.eB.push_back({&N.edgeB, &m});
             LockSmooth& LS = D.sm[dir];
             LS.max_if = std::max(LS.max_if, L.n_if);
           }
@@ -2644,23 +2735,27 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
           // lockstep launches hold the tiles of every problem at this depth.
           const bool tc = N.tc0F.batch && (N.use_tc || (c->opt.fd_engine == 0 && L.tc_ok && !L.fused_ok));
           if (tc) {
-            S.tc[0].push_back(dir == 0 ? &N.tc0F : &N.tc0R);
-            S.tc[1].push_back(&N.tc1);
-            S.tc[2].push_back(&N.tc2);
-            S.tc[3].push_back(&N.tc3);
+            S.tc[0].push_back({dir == 0 ? &N.tc0F : &N.tc0R, &m});
+            S.tc[1].push_back({&N.tc1, &m});
+            S.tc[2].push_back({&N.tc2, &m});
+            S.tc[3].push_back({&N.tc3, &m});
           } else if (N.use_rows) {
             D.sm[dir].flops += 4.0 * N.st1.flops;
-            S.rows.insert(S.rows.end(), L.fr_h.begin(), L.fr_h.end());
+            for (const auto& f : L.fr_h)
+              S.rows.push_back(FdRowsT<double>{f.U0, f.U1, f.Dinv, m.tr(f.vF), m.tr(f.vR), m.tr(f.u), m.tr(f.Y),
+                                               f.n0, f.n1, f.ld});
             D.sm[dir].rows_n0 = std::max(D.sm[dir].rows_n0, N.frows_n0);
             D.sm[dir].rows_n1 = std::max(D.sm[dir].rows_n1, N.frows_n1);
           } else if (N.use_fused) {
             D.sm[dir].flops += N.fsmall_flops;
-            S.fsmall.insert(S.fsmall.end(), L.fs_h.begin(), L.fs_h.end());
+            for (const auto& f : L.fs_h)
+              S.fsmall.push_back(FdSmallT<double>{f.U0, f.U1, f.Dinv, m.tr(f.vF), m.tr(f.vR), m.tr(f.u), f.n0, f.n1,
+                                                  f.ld});
           } else {
-            S.st[0].push_back(dir == 0 ? &N.st0F : &N.st0R);
-            S.st[1].push_back(&N.st1);
-            S.st[2].push_back(&N.st2);
-            S.st[3].push_back(&N.st3);
+            S.st[0].push_back({dir == 0 ? &N.st0F : &N.st0R, &m});
+            S.st[1].push_back({&N.st1, &m});
+            S.st[2].push_back({&N.st2, &m});
+            S.st[3].push_back({&N.st3, &m});
           }
         }
       }
@@ -2706,10 +2801,11 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
     std::vector<KronJobT<double>> kry;
     std::vector<VecJobT<double>> fu, pw, xr, pz, nrm, cpu;
     for (int q = 0; q < k->nprob; ++q) {
-      igamg_ctx* c = ctx[q];
+      const LockMember& m = k->mb[q];
+      igamg_ctx* c = m.c;
       Level& L = c->lv.back();
       Num<double>& N = L.n64;
-      for (const auto& kd : L.kd_h) kry.push_back(KronJobT<double>{kd, L.active, c->Pv, nullptr, c->W});
+      for (const auto& kd : L.kd_h) kry.push_back(KronJobT<double>{kd, L.active, m.Pv(), nullptr, m.W()});
       k->kry_flops += L.apply_flops;
       k->vec_flops += 12.0 * double(L.topo.T);  // two dots, the x, r and p updates, the norm
       k->kry_n0 = std::max(k->kry_n0, L.max_n[0]);
@@ -2718,12 +2814,13 @@ Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
       const int64_t T = L.topo.T;
       k->max_T = std::max(k->max_T, T);
       double* sc = k->scal + 8 * q;
-      fu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, N.F, N.U, nullptr, nullptr});
-      pw.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, c->W, nullptr, nullptr});
-      xr.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->X, N.F, c->Pv, c->W});
-      pz.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, nullptr, N.U, nullptr});
-      nrm.push_back(VecJobT<double>{L.topo.N, sc, L.g2t_ptr, L.g2t, N.F, nullptr, nullptr, nullptr});
-      cpu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, c->Pv, N.U, nullptr, nullptr});
+      double *F = m.tr(N.F), *U = m.tr(N.U);
+      fu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, F, U, nullptr, nullptr});
+      pw.push_back(VecJobT<double>{T, sc, nullptr, nullptr, m.Pv(), m.W(), nullptr, nullptr});
+      xr.push_back(VecJobT<double>{T, sc, nullptr, nullptr, m.X(), F, m.Pv(), m.W()});
+      pz.push_back(VecJobT<double>{T, sc, nullptr, nullptr, m.Pv(), nullptr, U, nullptr});
+      nrm.push_back(VecJobT<double>{L.topo.N, sc, L.g2t_ptr, L.g2t, F, nullptr, nullptr, nullptr});
+      cpu.push_back(VecJobT<double>{T, sc, nullptr, nullptr, m.Pv(), U, nullptr, nullptr});
     }
     k->kry = lk_upload(k, kry);
     k->nkry = int(kry.size());
@@ -2860,7 +2957,8 @@ igamg_status lockstep_solve(Lockstep* k, cudaStream_t s, const double* const* b,
     int64_t maxN = 0;
     int n0 = 0, n1 = 0, pm = 0;
     for (int q = 0; q < n; ++q) {
-      igamg_ctx* c = k->ctx[q];
+      const LockMember& m = k->mb[q];
+      igamg_ctx* c = m.c;
       Level& L = c->lv.back();
       const int64_t T = L.topo.T, N = L.topo.N;
       maxN = std::max(maxN, N);
@@ -2869,23 +2967,23 @@ igamg_status lockstep_solve(Lockstep* k, cudaStream_t s, const double* const* b,
       j.ptr = L.g2t_ptr;
       j.idx = L.g2t;
       j.G = const_cast<double*>(b[q]);
-      j.u = c->Bt;
+      j.u = m.Bt();
       gd.push_back(j);
       j.G = x[q];
-      j.u = c->X;
+      j.u = m.X();
       ga.push_back(j);
       NodeJobT<double> bk{};
       bk.n = N;
       bk.ptr = L.g2t_ptr;
       bk.idx = L.g2t;
-      bk.v = c->X;
+      bk.v = m.X();
       bk.G = x[q];
       back.push_back(bk);
-      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->Bt, nullptr, nullptr, nullptr});
-      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->X, nullptr, nullptr, nullptr});
-      keep.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->Rr, c->X, nullptr, nullptr});
-      fin.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, c->X, c->Rr, nullptr, nullptr});
-      for (const auto& kd : L.kd_h) r0.push_back(KronJobT<double>{kd, L.active, c->X, c->Bt, L.n64.F});
+      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, m.Bt(), nullptr, nullptr, nullptr});
+      zero.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, m.X(), nullptr, nullptr, nullptr});
+      keep.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, m.Rr(), m.X(), nullptr, nullptr});
+      fin.push_back(VecJobT<double>{T, nullptr, nullptr, nullptr, m.X(), m.Rr(), nullptr, nullptr});
+      for (const auto& kd : L.kd_h) r0.push_back(KronJobT<double>{kd, L.active, m.X(), m.Bt(), m.tr(L.n64.F)});
       n0 = std::max(n0, L.max_n[0]);
       n1 = std::max(n1, L.max_n[1]);
       pm = std::max(pm, L.max_p);
@@ -3025,6 +3123,80 @@ void lockstep_stats(const Lockstep* k, int64_t* launches, double* flops, double*
   *launches = k->launches;
   *flops = k->flops;
   *mma_flops = k->mma_flops;
+}
+
+Lockstep* lockstep_build(const std::vector<igamg_ctx*>& ctx, std::string* why) {
+  std::vector<LockMember> mb;
+  for (igamg_ctx* c : ctx) mb.push_back(LockMember{c, nullptr});
+  return lockstep_build(mb, why, false);
+}
+
+// Whether the lockstep engine can run several right-hand sides of this context together
+// (2D, every level above the coarsest made of rectangle patches with fused transfers,
+// V-cycle); a precision-variant context qualifies and runs its FP64 numerics.
+bool ctx_multi_ok(const igamg_ctx* c) {
+  if (c->pd.dim != 2 || c->opt.mu != 1 || c->lv.size() < 2) return false;
+  for (size_t l = 1; l < c->lv.size(); ++l) {
+    const Level& L = c->lv[l];
+    if (!L.kron || !L.n64.r2 || !L.n64.p2) return false;
+  }
+  return true;
+}
+
+namespace {
+
+// Work copies 1 .. n-1 of a context: every registered work array with its current content
+// (so that a copy starts in the state of the context), the Krylov vectors and the FP64
+// digit scratch; allocated once and kept until the context is freed.
+void ensure_copies(igamg_ctx* c, int n) {
+  const cudaStream_t s = c->stream;
+  const int64_t Tf = c->lv.back().topo.T;
+  while (int(c->copies.size()) < n - 1) {
+    WorkCopy w;
+    for (const auto& r : c->reg) {
+      double* base = std::get<0>(r);
+      const int64_t cnt = std::get<1>(r);
+      double* p = base;
+      if (!std::get<2>(r)) {
+        p = c->mem.alloc<double>(size_t(std::max<int64_t>(cnt, 1)));
+        if (cnt > 0) CK(cudaMemcpyAsync(p, base, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      w.tw.emplace_back(base, cnt, p);
+    }
+    std::sort(w.tw.begin(), w.tw.end(), [](const auto& a, const auto& b) { return std::get<0>(a) < std::get<0>(b); });
+    w.X = c->mem.alloc<double>(size_t(Tf));
+    w.Pv = c->mem.alloc<double>(size_t(Tf));
+    w.W = c->mem.alloc<double>(size_t(Tf));
+    w.Bt = c->mem.alloc<double>(size_t(Tf));
+    w.Rr = c->mem.alloc<double>(size_t(Tf));
+    for (int k = 0; k < 2; ++k) {
+      if (c->dig64[k]) w.dig[k] = c->mem.alloc<__nv_bfloat16>(size_t(c->dig64[k]));
+      if (c->tau64[k]) w.tau[k] = c->mem.alloc<int>(size_t(c->tau64[k]));
+    }
+    c->copies.push_back(std::move(w));
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+// nrhs right-hand sides of one context solved together by the lockstep engine over the
+// context and nrhs - 1 work copies (one launch per step for all of them, the operator's
+// constant arrays shared); NULL when the context is outside the engine's scope.  Engines are
+// kept per nrhs.
+Lockstep* multi_engine(igamg_ctx* c, int nrhs) {
+  auto it = c->multi.find(nrhs);
+  if (it != c->multi.end()) return it->second;
+  Lockstep* k = nullptr;
+  if (ctx_multi_ok(c)) {
+    ensure_copies(c, nrhs);
+    std::vector<LockMember> mb{LockMember{c, nullptr}};
+    for (int q = 1; q < nrhs; ++q) mb.push_back(LockMember{c, &c->copies[size_t(q - 1)]});
+    std::string why;
+    k = lockstep_build(mb, &why, true);
+  }
+  c->multi[nrhs] = k;
+  return k;
 }
 
 }  // namespace igamg
@@ -3383,6 +3555,42 @@ igamg_status igamg_solve(igamg_ctx* c, const double* b, double* x, double tol, i
   });
 }
 
+igamg_status igamg_solve_multi(igamg_ctx* c, int nrhs, const double* const* b, double* const* x, double tol,
+                               igamg_result* res, igamg_status* status) {
+  if (!c) return IGAMG_ERR_ARG;
+  if (nrhs < 1 || !b || !x || !(tol >= 0)) {
+    c->err = "igamg_solve_multi: need nrhs >= 1, b and x arrays, tol >= 0";
+    return IGAMG_ERR_ARG;
+  }
+  for (int q = 0; q < nrhs; ++q)
+    if (!b[q] || !x[q]) {
+      c->err = "igamg_solve_multi: null right-hand side or solution pointer";
+      return IGAMG_ERR_ARG;
+    }
+  igamg::Lockstep* k = nullptr;
+  if (nrhs > 1) {
+    igamg_status st = guarded(c, [&]() {
+      k = igamg::multi_engine(c, nrhs);
+      return IGAMG_OK;
+    });
+    if (st != IGAMG_OK) return st;
+  }
+  if (!k) {  // one at a time
+    igamg_status worst = IGAMG_OK;
+    for (int q = 0; q < nrhs; ++q) {
+      igamg_result r{};
+      igamg_status st = igamg_solve(c, b[q], x[q], tol, &r);
+      if (res) res[q] = r;
+      if (status) status[q] = st;
+      if (st != IGAMG_OK && (worst == IGAMG_OK || worst == IGAMG_ERR_NOT_CONVERGED)) worst = st;
+    }
+    return worst;
+  }
+  igamg_status st = igamg::lockstep_solve(k, c->stream, b, x, tol, res, status);
+  if (st != IGAMG_OK && st != IGAMG_ERR_NOT_CONVERGED) c->err = igamg_last_error(nullptr);
+  return st;
+}
+
 igamg_status igamg_solve_host(igamg_ctx* c, const double* bh, double* xh, double tol, igamg_result* res) {
   return guarded(c, [&]() {
     if (!bh || !xh || !(tol >= 0)) throw Fail{IGAMG_ERR_ARG, "bad arguments"};
@@ -3433,6 +3641,7 @@ igamg_status igamg_free(igamg_ctx* c) {
     cudaEventDestroy(std::get<2>(t));
   }
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  for (auto& kv : c->multi) igamg::lockstep_free(kv.second);
   c->mem.release();
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;

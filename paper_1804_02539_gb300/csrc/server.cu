@@ -5,7 +5,10 @@
 // estimated footprint fits, after evicting least-recently-used idle hierarchies; requests
 // wait in arrival order, and a worker takes the oldest request whose model is not in use by
 // another worker (continuous batching: a freed worker starts the next request at once, so
-// requests of different models run concurrently on the device).
+// requests of different models run concurrently on the device).  For a model the lockstep
+// engine covers, the worker also takes that model's other waiting requests of the same
+// tolerance (up to kMaxGroup in all) and solves them together with igamg_solve_multi: one
+// launch per step of the cycle for the whole group, the hierarchy's constant arrays shared.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,10 +32,13 @@ namespace igamg {
 void set_context_free_error(const std::string& msg);
 void ctx_set_stream(igamg_ctx* c, cudaStream_t s);
 size_t ctx_device_bytes(const igamg_ctx* c);
+bool ctx_multi_ok(const igamg_ctx* c);
 bool rect_metric(const double* X, double* c0, double* c1);
 }  // namespace igamg
 
 namespace {
+
+constexpr size_t kMaxGroup = 16;  // requests of one model solved together at most
 
 struct ProblemCopy {  // owns the arrays an igamg_problem points to
   std::vector<int> degree, num_knots, geo_degree, geo_num_ctrl, side_bc;
@@ -73,6 +79,7 @@ struct Model {
   size_t est_bytes = 0;  // admission estimate before the first setup, then the measured size
   igamg_ctx* ctx = nullptr;
   bool busy = false, building = false;
+  bool multi = false;  // igamg_solve_multi runs its requests in lockstep
   uint64_t last_use = 0;
 };
 
@@ -101,7 +108,7 @@ struct igamg_server {
   std::deque<int64_t> queue;  // waiting requests, arrival order
   int64_t next_id = 0;
   uint64_t tick = 0;
-  int64_t setups = 0, evictions = 0, completed = 0;
+  int64_t setups = 0, evictions = 0, completed = 0, groups = 0, grouped = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
@@ -169,25 +176,39 @@ void ensure_staging(Worker& w, int64_t n) {
   w.cap = n;
 }
 
-// Solve of one request on worker w (model hierarchy resident and reserved for it).
-void run_request(igamg_server* S, Worker& w, Model& m, Request& r) {
+// Solve of a group of requests of one model (one request: igamg_solve; more: together by
+// igamg_solve_multi) on worker w (model hierarchy resident and reserved for it).
+void run_group(Worker& w, Model& m, const std::vector<Request*>& rs) {
   const int64_t n = m.ndofs;
-  ensure_staging(w, n);
-  igamg_status st = IGAMG_ERR_OOM;
-  igamg_result res{};
-  if (w.cap >= n) {
-    std::memcpy(w.hb, r.b, n * sizeof(double));
-    cudaMemcpyAsync(w.db, w.hb, n * sizeof(double), cudaMemcpyHostToDevice, w.stream);
-    cudaMemsetAsync(w.dx, 0, n * sizeof(double), w.stream);
+  const int g = int(rs.size());
+  ensure_staging(w, n * g);
+  std::vector<igamg_result> res(static_cast<size_t>(g), igamg_result{});
+  std::vector<igamg_status> sts(static_cast<size_t>(g), IGAMG_ERR_OOM);
+  if (w.cap >= n * g) {
+    std::vector<const double*> bp(static_cast<size_t>(g), nullptr);
+    std::vector<double*> xp(static_cast<size_t>(g), nullptr);
+    for (int i = 0; i < g; ++i) {
+      std::memcpy(w.hb + i * n, rs[i]->b, n * sizeof(double));
+      bp[i] = w.db + i * n;
+      xp[i] = w.dx + i * n;
+    }
+    cudaMemcpyAsync(w.db, w.hb, g * n * sizeof(double), cudaMemcpyHostToDevice, w.stream);
+    cudaMemsetAsync(w.dx, 0, g * n * sizeof(double), w.stream);
     igamg::ctx_set_stream(m.ctx, w.stream);
-    st = igamg_solve(m.ctx, w.db, w.dx, r.tol, &res);
-    cudaMemcpyAsync(w.hx, w.dx, n * sizeof(double), cudaMemcpyDeviceToHost, w.stream);
-    if (cudaStreamSynchronize(w.stream) != cudaSuccess && st == IGAMG_OK) st = IGAMG_ERR_CUDA;
-    std::memcpy(r.x, w.hx, n * sizeof(double));
+    igamg_status st;
+    if (g == 1) st = sts[0] = igamg_solve(m.ctx, bp[0], xp[0], rs[0]->tol, &res[0]);
+    else st = igamg_solve_multi(m.ctx, g, bp.data(), xp.data(), rs[0]->tol, res.data(), sts.data());
+    cudaMemcpyAsync(w.hx, w.dx, g * n * sizeof(double), cudaMemcpyDeviceToHost, w.stream);
+    if (cudaStreamSynchronize(w.stream) != cudaSuccess && st == IGAMG_OK)
+      for (auto& x : sts) x = IGAMG_ERR_CUDA;
+    for (int i = 0; i < g; ++i) std::memcpy(rs[i]->x, w.hx + i * n, n * sizeof(double));
   }
-  r.info.status = st;
-  r.info.iters = res.iters;
-  r.info.relres = res.relres;
+  for (int i = 0; i < g; ++i) {
+    rs[i]->info.status = sts[i];
+    rs[i]->info.iters = res[i].iters;
+    rs[i]->info.relres = res[i].relres;
+    rs[i]->info.group = g;
+  }
 }
 
 // Frees least-recently-used idle hierarchies until `need` more bytes fit the budget.
@@ -272,16 +293,41 @@ void worker_main(igamg_server* S, int wi) {
       S->used += actual - int64_t(m.est_bytes);
       m.est_bytes = size_t(actual);
       m.ctx = ctx;
+      m.multi = igamg::ctx_multi_ok(ctx);
+    }
+    std::vector<Request*> grp{&r};
+    if (m.multi) {  // the model's other waiting requests of the same tolerance, oldest first
+      const double t_take = S->now();
+      for (auto it = S->queue.begin(); it != S->queue.end() && grp.size() < kMaxGroup;) {
+        Request& q = S->reqs[*it];
+        if (q.model == r.model && q.tol == r.tol) {
+          q.info.t_start_ms = t_take;
+          grp.push_back(&q);
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
     }
     m.busy = true;
     lk.unlock();
-    run_request(S, w, m, r);
+    run_group(w, m, grp);
     lk.lock();
     m.busy = false;
     m.last_use = ++S->tick;
-    r.info.t_done_ms = S->now();
-    r.done = true;
-    ++S->completed;
+    const int64_t now_bytes = int64_t(igamg::ctx_device_bytes(m.ctx));  // work copies made for the group
+    S->used += now_bytes - int64_t(m.est_bytes);
+    m.est_bytes = size_t(now_bytes);
+    const double t_done = S->now();
+    for (Request* q : grp) {
+      q->info.t_done_ms = t_done;
+      q->done = true;
+      ++S->completed;
+    }
+    if (grp.size() > 1) {
+      ++S->groups;
+      S->grouped += int64_t(grp.size());
+    }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
@@ -349,6 +395,7 @@ igamg_status igamg_server_submit(igamg_server* S, int model, const double* rhs, 
   r.x = x;
   r.tol = tol;
   r.info.t_submit_ms = S->now();
+  r.info.group = 1;
   S->queue.push_back(id);
   S->cv_work.notify_one();
   *request = id;
@@ -377,6 +424,8 @@ igamg_status igamg_server_stats(igamg_server* S, igamg_server_counters* st) {
   st->evictions = S->evictions;
   st->completed = S->completed;
   st->waiting = int64_t(S->queue.size());
+  st->groups = S->groups;
+  st->grouped = S->grouped;
   return IGAMG_OK;
 }
 

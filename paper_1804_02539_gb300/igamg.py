@@ -43,12 +43,13 @@ class igamg_result(C.Structure):
 
 class igamg_request_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("relres", C.c_double), ("t_submit_ms", C.c_double),
-                ("t_start_ms", C.c_double), ("t_done_ms", C.c_double), ("setup_ms", C.c_double)]
+                ("t_start_ms", C.c_double), ("t_done_ms", C.c_double), ("setup_ms", C.c_double), ("group", C.c_int)]
 
 
 class igamg_server_counters(C.Structure):
     _fields_ = [("models", C.c_int), ("resident", C.c_int), ("device_bytes", C.c_int64), ("setups", C.c_int64),
-                ("evictions", C.c_int64), ("completed", C.c_int64), ("waiting", C.c_int64)]
+                ("evictions", C.c_int64), ("completed", C.c_int64), ("waiting", C.c_int64), ("groups", C.c_int64),
+                ("grouped", C.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -67,6 +68,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "igamg_greville_points": ([P, C.c_int, P], C.c_int),
         "igamg_solve": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
         "igamg_solve_host": ([P, P, P, C.c_double, C.POINTER(igamg_result)], C.c_int),
+        "igamg_solve_multi": ([P, C.c_int, C.POINTER(P), C.POINTER(P), C.c_double, C.POINTER(igamg_result),
+                               C.POINTER(C.c_int)], C.c_int),
         "igamg_apply": ([P, C.c_int, P, P], C.c_int),
         "igamg_smooth": ([P, C.c_int, P, P], C.c_int),
         "igamg_restrict": ([P, C.c_int, P, P], C.c_int),
@@ -249,6 +252,19 @@ class Context:
         res = igamg_result()
         st = self._check(lib().igamg_solve(self.h, _ptr(rhs), _ptr(x), tol, C.byref(res)), allow_nc=True)
         return res, st
+
+    def solve_multi(self, rhs, xs, tol=1e-8):
+        """Several right-hand sides of this problem together (igamg_solve_multi); rhs, xs:
+        equal-length sequences of contiguous CUDA float64 tensors (xs: initial guesses in,
+        solutions out).  Returns (overall status, [igamg_result], [status])."""
+        n = len(rhs)
+        assert len(xs) == n and n >= 1
+        bp = (C.c_void_p * n)(*[_ptr(t) for t in rhs])
+        xp = (C.c_void_p * n)(*[_ptr(t) for t in xs])
+        res = (igamg_result * n)()
+        sts = (C.c_int * n)()
+        st = self._check(lib().igamg_solve_multi(self.h, n, bp, xp, tol, res, sts), allow_nc=True)
+        return st, list(res), list(sts)
 
     def solve_host(self, rhs: np.ndarray, x: np.ndarray, tol=1e-8):
         res = igamg_result()

@@ -119,3 +119,95 @@ def test_outside_scope_uses_worker_streams():
     b = igamg.Batch(probs)
     assert b.engine() == "streams"      # bilinear (non-rectangle) patches
     b.free()
+
+
+# ---------------------------------------------------------------- several right-hand sides
+
+def _multi_rhs(ctx, count, seed0):
+    n = ctx.num_dofs()
+    return [torch.tensor(workloads.rhs_coefficients(n, seed0 + i), device="cuda") for i in range(count)]
+
+
+@pytest.mark.parametrize("fd_engine", [1, 2])
+def test_solve_multi_matches_single_solves(fd_engine):
+    """igamg_solve_multi on one context (its work arrays copied per extra right-hand side,
+    the constant arrays shared): every answer and iteration count bit-identical to the same
+    right-hand side solved alone, also after a call with more right-hand sides (engines kept
+    per count, copies reused)."""
+    from paper_1804_02539_gb300 import igamg
+    o = igamg.igamg_default_options()
+    o.fd_engine = fd_engine
+    c = igamg.Context(workloads.rect_grid_2d(3, 3, 32), o)
+    for count, seed in ((5, 10), (3, 40), (5, 70)):
+        rhs = _multi_rhs(c, count, seed)
+        if count == 3:
+            rhs[1] = rhs[1] * 1e-3          # a different scale: stops at another iteration
+        xs = [torch.zeros_like(r) for r in rhs]
+        st, res, sts = c.solve_multi(rhs, xs, 1e-9)
+        assert st == 0 and all(s == 0 for s in sts)
+        for i, r in enumerate(rhs):
+            x = torch.zeros_like(r)
+            r1, _ = c.solve(r, x, 1e-9)
+            assert r1.iters == res[i].iters and torch.equal(x, xs[i]), (count, i)
+            assert res[i].relres <= 1e-9
+    c.free()
+
+
+def test_solve_multi_autotuned_and_oracle():
+    """The autotuned default (the lockstep engine may put levels on the tensor cores that a
+    single solve ran on FMA GEMMs): answers equal single solves to rounding and the oracle's
+    direct solve of the same system."""
+    from paper_1804_02539_gb300 import igamg
+    pr = workloads.rect_grid_2d(2, 4, 64)
+    c = igamg.Context(pr)
+    rhs = _multi_rhs(c, 6, 100)
+    xs = [torch.zeros_like(r) for r in rhs]
+    st, res, _ = c.solve_multi(rhs, xs, 1e-10)
+    assert st == 0
+    for i, r in enumerate(rhs):
+        x = torch.zeros_like(r)
+        r1, _ = c.solve(r, x, 1e-10)
+        assert abs(r1.iters - res[i].iters) <= 1
+        assert rel(xs[i].cpu().numpy(), x.cpu().numpy()) < 1e-8, i
+    H = solver.build_hierarchy(pr)
+    sp = H.levels[-1].space
+    perm = permutation(sp, c.dof_map())
+    for i in (0, 5):
+        ref = solver.direct_solve(H.levels[-1].A, rhs[i].cpu().numpy()[perm])
+        assert rel(xs[i].cpu().numpy()[perm], ref) < 1e-8, i
+    c.free()
+
+
+def test_solve_multi_precision_variant_runs_fp64():
+    """A BF16-variant context: the right-hand sides run the FP64 lockstep numerics and meet
+    the tolerance; the answers agree with the context's own mixed-precision solves to the
+    tolerance's level."""
+    from paper_1804_02539_gb300 import igamg
+    o = igamg.igamg_default_options()
+    o.precision = igamg.IGAMG_BF16
+    c = igamg.Context(workloads.rect_grid_2d(3, 4, 32), o)
+    rhs = _multi_rhs(c, 4, 300)
+    xs = [torch.zeros_like(r) for r in rhs]
+    st, res, _ = c.solve_multi(rhs, xs, 1e-8)
+    assert st == 0 and all(r.relres <= 1e-8 for r in res)
+    for i, r in enumerate(rhs):
+        x = torch.zeros_like(r)
+        c.solve(r, x, 1e-8)
+        assert rel(xs[i].cpu().numpy(), x.cpu().numpy()) < 1e-6, i
+    c.free()
+
+
+def test_solve_multi_outside_scope_solves_one_by_one():
+    """A 3D problem (outside the lockstep scope): the right-hand sides are solved one after
+    the other, bit-identical to igamg_solve."""
+    from paper_1804_02539_gb300 import igamg
+    c = igamg.Context(workloads.perturbed_cube_3d(2, 2, 4, 3, 3))
+    rhs = _multi_rhs(c, 3, 500)
+    xs = [torch.zeros_like(r) for r in rhs]
+    st, res, _ = c.solve_multi(rhs, xs, 1e-8)
+    assert st == 0
+    for i, r in enumerate(rhs):
+        x = torch.zeros_like(r)
+        r1, _ = c.solve(r, x, 1e-8)
+        assert r1.iters == res[i].iters and torch.equal(x, xs[i])
+    c.free()

@@ -2,7 +2,10 @@
 sizes) submitted together and answered by concurrent workers.
 
   * each answer is bit-identical to solving that request alone through igamg_solve
-    (the served solve is the single-problem path on a resident hierarchy);
+    (the served solve is the single-problem path on a resident hierarchy), also for the
+    requests of a 2D rectangle-patch model that a worker takes together and solves with
+    igamg_solve_multi (forced FD engine); with the autotuned default such grouped answers
+    equal the single solves to rounding;
   * with a device-memory budget that holds one hierarchy at a time, hierarchies are
     evicted and rebuilt and the answers are unchanged;
   * a model larger than the budget is answered with IGAMG_ERR_OOM, the others are served;
@@ -22,9 +25,16 @@ def models():
             workloads.perturbed_cube_3d(2, 2, 12, 3, 3)]
 
 
-def alone(pr, b):
+def fma_options():
     from paper_1804_02539_gb300 import igamg
-    c = igamg.Context(pr)
+    o = igamg.igamg_default_options()
+    o.fd_engine = 1
+    return o
+
+
+def alone(pr, b, opts=None):
+    from paper_1804_02539_gb300 import igamg
+    c = igamg.Context(pr, opts)
     x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
     res, st = c.solve(torch.tensor(b, device="cuda"), x, 1e-8)
     out = x.cpu().numpy()
@@ -44,10 +54,10 @@ def estimates(mods):
     return est
 
 
-def serve(budget, reqs, workers=3, mods=None):
+def serve(budget, reqs, workers=3, mods=None, opts=None):
     from paper_1804_02539_gb300 import igamg
     mods = mods or models()
-    srv = igamg.Server(workers=workers, hbm_budget_bytes=budget)
+    srv = igamg.Server(opts, workers=workers, hbm_budget_bytes=budget)
     ids = [srv.add_model(pr) for pr in mods]
     sub = []
     for m, seed in reqs:
@@ -64,14 +74,34 @@ REQS = [(i % 5, 100 + i) for i in range(15)]
 
 
 def test_served_answers_match_single_solves():
-    out, stats = serve(8 << 30, REQS)
+    out, stats = serve(8 << 30, REQS, opts=fma_options())
     assert stats["completed"] == len(REQS) and stats["setups"] == 5 and stats["evictions"] == 0
+    assert stats["groups"] > 0 and stats["grouped"] == sum(1 for *_, i in out if i["group"] > 1)
     prs = models()
     for m, b, x, info in out:
-        ref, its = alone(prs[m], b)
+        ref, its = alone(prs[m], b, fma_options())
         assert info["status"] == 0 and info["iters"] == its
         assert np.array_equal(x, ref)
         assert info["t_submit_ms"] <= info["t_start_ms"] <= info["t_done_ms"]
+
+
+def test_grouped_requests_autotuned():
+    """Twelve requests of one 2D rectangle-patch model and four of a 3D model submitted at
+    once to one worker: the 2D ones are answered in groups (at most 16), the 3D ones one at a
+    time; every answer meets the tolerance and equals the request solved alone to rounding."""
+    mods = [workloads.rect_grid_2d(3, 3, 32), workloads.perturbed_cube_3d(2, 2, 4, 3, 3)]
+    reqs = [(0, 700 + i) for i in range(12)] + [(1, 800 + i) for i in range(4)]
+    out, stats = serve(8 << 30, reqs, workers=1, mods=mods)
+    assert stats["completed"] == len(reqs) and stats["groups"] >= 1
+    for m, b, x, info in out:
+        assert info["status"] == 0 and info["relres"] <= 1e-8
+        assert info["t_submit_ms"] <= info["t_start_ms"] <= info["t_done_ms"]
+        if m == 1:
+            assert info["group"] == 1
+        ref, its = alone(mods[m], b)
+        assert abs(info["iters"] - its) <= 1
+        assert np.linalg.norm(x - ref) <= (1e-8 if info["iters"] == its else 1e-6) * np.linalg.norm(ref)
+    assert max(info["group"] for m, *_, info in out if m == 0) > 1
 
 
 def test_eviction_under_a_small_budget():
@@ -79,12 +109,12 @@ def test_eviction_under_a_small_budget():
     less than all five together: every hierarchy is evicted and rebuilt at least once."""
     mods = similar_models()
     est = estimates(mods)
-    out, full = serve(8 << 30, REQS[:5], mods=mods)
+    out, full = serve(8 << 30, REQS[:5], mods=mods, opts=fma_options())
     assert full["device_bytes"] > 1.1 * max(est)   # all five do not fit the budget below
-    out, stats = serve(int(1.05 * max(est)), REQS, workers=2, mods=mods)
+    out, stats = serve(int(1.05 * max(est)), REQS, workers=2, mods=mods, opts=fma_options())
     assert stats["evictions"] > 0 and stats["completed"] == len(REQS)
     for m, b, x, info in out:
-        ref, _ = alone(mods[m], b)
+        ref, _ = alone(mods[m], b, fma_options())
         assert info["status"] == 0 and np.array_equal(x, ref)
 
 
