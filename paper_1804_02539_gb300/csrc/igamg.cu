@@ -117,6 +117,20 @@ struct TcSet {
 
 // Numeric data of one level in one precision: the vectors and the descriptor sets the
 // cycle launches.  FP64 data are built by the setup; lower-precision data are twins of them.
+// Fibre-major stacked tensor-core stage of the 2D interiors (FP64): one descriptor per group
+// of patches sharing the stage's basis and sizes, their fibres stacked along the MMA's M side.
+struct StackSet {
+  std::vector<TcStack<double, double>> h;
+  std::vector<std::vector<const double*>> hX, hE;  // host copies of each descriptor's tables
+  std::vector<std::vector<double*>> hC;
+  TcStack<double, double>* d = nullptr;  // uploaded by bind_stack
+  int batch = 0;
+  int64_t tiles = 0, panels = 0, dig_elems = 0, tau_elems = 0;
+  std::vector<int64_t> dig_off, tau_off;
+  int *tstart_d = nullptr, *pstart_d = nullptr;
+  double flops = 0, exec_flops = 0, dig_bytes = 0;
+};
+
 template <class T>
 struct Num {
   const void* band = nullptr;  // band coefficients of the cycle: T, or __nv_bfloat16 when bf16
@@ -128,6 +142,7 @@ struct Num {
   TcSet<T> tc0F, tc0R, tc1, tc2, tc3;               // interiors on the tensor cores (2D: 4
   TcSet<T> tc4, tc5;                                // stages; 3D: tc0F, tc1..tc5 = 6 stages)
   TcSet<T> tq0, tq1, tq2, tq3;                      // 3D faces on the tensor cores
+  StackSet sk0F, sk0R, sk1, sk2, sk3;               // 2D interiors, stacked (FP64 engine)
   ModeSetT<T> fm[4];                                // 3D faces as mode products (FMA engine)
   FdSmallT<T>* fsmall = nullptr;                    // small 2D interiors, one block each
   SmoothSmallT<T> ssmall{};                         // + edges and vertices in the same launch
@@ -204,6 +219,8 @@ struct WorkCopy {
   double *X = nullptr, *Pv = nullptr, *W = nullptr, *Bt = nullptr, *Rr = nullptr;
   __nv_bfloat16* dig[2] = {nullptr, nullptr};
   int* tau[2] = {nullptr, nullptr};
+  __nv_bfloat16* sdig = nullptr;  // stacked stages' digit scratch
+  int* stau = nullptr;
 };
 }  // namespace igamg
 
@@ -260,6 +277,7 @@ struct igamg_ctx {
   // several right-hand sides solved together (igamg_solve_multi): the FP64 digit scratch
   // sizes, the work-array copies 1.., and the lockstep engines by number of right-hand sides
   int64_t dig64[2] = {0, 0}, tau64[2] = {0, 0};
+  int64_t sdig = 0, stau = 0;  // digit scratch of the stacked 2D stages
   std::deque<igamg::WorkCopy> copies;  // stable addresses: the engines point into it
   std::map<int, igamg::Lockstep*> multi;
 };
@@ -520,6 +538,26 @@ void set_tc(igamg_ctx*, TcSet<T>& ts, const std::vector<TcDesc<T, T>>& v, bool s
   ts.d = nullptr;  // uploaded by bind_tc
 }
 
+void set_stack(StackSet& ss, const std::vector<TcStack<double, double>>& v) {
+  ss.h = v;
+  ss.batch = int(v.size());
+  ss.flops = ss.exec_flops = ss.dig_bytes = 0;
+  ss.dig_elems = ss.tau_elems = 0;
+  ss.dig_off.clear();
+  ss.tau_off.clear();
+  for (auto& d : v) {
+    const double M = double(d.P) * d.F;
+    ss.flops += 2.0 * M * d.N * d.K;
+    ss.exec_flops += tc_stack_exec_flops(d.P, d.F, d.N, d.K);
+    ss.dig_off.push_back(ss.dig_elems);
+    ss.tau_off.push_back(ss.tau_elems);
+    ss.dig_elems += tc_stack_dig_elems(d.P, d.F, d.K);
+    ss.tau_elems += int64_t(d.P) * d.F;
+    ss.dig_bytes += M * d.K * (8.0 + 2.0 * 7) + 4.0 * M;
+  }
+  ss.d = nullptr;  // uploaded by bind_stack
+}
+
 // Every tensor-core set of precision T gets the digit scratch of its stream: the sets
 // launched on the solve's stream run one after another and share one buffer, the interface
 // (face) sets on the side stream share another.  Then the descriptors are uploaded.
@@ -556,6 +594,50 @@ void bind_tc(igamg_ctx* c) {
     p->tstart_d = c->mem.upload(ts, c->stream);
     p->pstart_d = c->mem.upload(ps, c->stream);
   }
+}
+
+// The stacked sets of every level share one digit scratch (they run one after another on
+// the solve's stream).
+void bind_stack(igamg_ctx* c) {
+  std::vector<StackSet*> sets;
+  for (Level& L : c->lv)
+    for (StackSet* p : {&L.n64.sk0F, &L.n64.sk0R, &L.n64.sk1, &L.n64.sk2, &L.n64.sk3})
+      if (p->batch && !p->d) sets.push_back(p);
+  int64_t dig = 0, tau = 0;
+  for (StackSet* p : sets) {
+    dig = std::max(dig, p->dig_elems);
+    tau = std::max(tau, p->tau_elems);
+  }
+  if (sets.empty()) return;
+  c->sdig = dig;
+  c->stau = tau;
+  __nv_bfloat16* dbase = c->mem.alloc<__nv_bfloat16>(size_t(std::max<int64_t>(dig, 1)));
+  int* tbase = c->mem.alloc<int>(size_t(std::max<int64_t>(tau, 1)));
+  for (StackSet* p : sets) {
+    for (int i = 0; i < p->batch; ++i) {
+      p->h[i].Xdig = dbase + p->dig_off[i];
+      p->h[i].Xtau = tbase + p->tau_off[i];
+    }
+    p->d = c->mem.upload(p->h, c->stream);
+    std::vector<int> ts, ps;
+    tc_stack_prefixes(p->h, ts, ps);
+    p->tiles = ts.back();
+    p->panels = ps.back();
+    p->tstart_d = c->mem.upload(ts, c->stream);
+    p->pstart_d = c->mem.upload(ps, c->stream);
+  }
+}
+
+void run_stack(igamg_ctx* c, const StackSet& ss, int epi, double alpha, int cls = CLS_FD) {
+  if (!ss.batch) return;
+  if (!ss.d) throw Fail{IGAMG_ERR_NUMERIC, "stacked tensor-core set without scratch"};
+  {
+    ProfScope ps(c, cls, 0.0, ss.dig_bytes);
+    CK(launch_tc_digits_stack(c->stream, ss.d, ss.batch, ss.pstart_d, ss.panels));
+  }
+  if (c->prof) c->prof_flops[CLS_TENSOR_EXEC] += ss.exec_flops;
+  ProfScope ps(c, cls, ss.flops, 0.0, 1, CLS_TC_KERNEL);
+  CK(launch_gemm_tc_stack(c->stream, ss.d, ss.batch, ss.tstart_d, ss.tiles, epi, alpha, c->tc_err));
 }
 
 template <class T>
@@ -941,6 +1023,23 @@ void build_levels(igamg_ctx* c) {
       }
       return sl[key];
     };
+    // the same bases sliced as the N-side operand of the stacked (fibre-major) stages
+    struct SlN { const __nv_bfloat16* w; const int* e; };
+    std::map<std::pair<const Smoother1D*, int>, SlN> sln;
+    auto slices_n = [&](const Smoother1D* S, int tr) -> SlN {
+      auto key = std::make_pair(S, tr);
+      if (!sln.count(key)) {
+        int n = S->len;
+        std::vector<double> A(size_t(n) * n);
+        for (int i = 0; i < n; ++i)
+          for (int k = 0; k < n; ++k) A[size_t(i) * n + k] = tr ? S->U[size_t(k) * n + i] : S->U[size_t(i) * n + k];
+        std::vector<uint16_t> sv;
+        std::vector<int> ev;
+        slice_constant(A, n, n, 7, sv, ev, 32);
+        sln[key] = SlN{reinterpret_cast<const __nv_bfloat16*>(c->mem.upload(sv, s)), c->mem.upload(ev, s)};
+      }
+      return sln[key];
+    };
     if (d == 2) {
       int64_t fd_total = 0;
       std::vector<GemmDesc> s0F, s0R, s1, s2, s3;
@@ -1048,6 +1147,26 @@ void build_levels(igamg_ctx* c) {
       if (want_tc) {
         // constant-left form: T = U0^T X, Y^T = U1^T T^T (.* Dinv), S = U0 Y, Z^T = U1 S^T
         std::vector<TcDesc<double, double>> t0F, t0R, t1, t2, t3;
+        // fibre-major stacked form (the FP64 engine's): T = U0^T X kept as [n0][n1],
+        // Y = (T U1) .* Dinv kept as Y^T [n1][n0], Q = Y U1^T kept as Q^T [n1][n0] in T's
+        // scratch, Z = U0 Q into the tile; every stage writes fibre-contiguous rows.  Patches
+        // with the same basis and sizes form one descriptor per stage.
+        using SD = TcStack<double, double>;
+        using SKey = std::tuple<const void*, int, int, int, int>;  // W slices, F, K, ldx, ldc
+        struct SGrp {
+          SD proto{};
+          std::vector<const double*> X, E;
+          std::vector<double*> C;
+        };
+        std::map<SKey, SGrp> sgrp[5];
+        auto sadd = [&](int st, const SlN& w, int N, int K, const double* X, int xt, int ldx, int F, double* C, int ldc,
+                        const double* E, int et, int lde) {
+          SGrp& g = sgrp[st][SKey{w.w, F, K, ldx, ldc}];
+          if (g.X.empty()) g.proto = SD{w.w, w.e, nullptr, nullptr, nullptr, ldx, xt, ldc, 0, lde, et, 0, F, N, K};
+          g.X.push_back(X);
+          g.C.push_back(C);
+          g.E.push_back(E);
+        };
         size_t q = 0;
         for (const Interior& in : T.interiors) {
           const PatchDev& P = L.pd_h[in.k];
@@ -1071,7 +1190,31 @@ void build_levels(igamg_ctx* c) {
           t1.push_back(TcDesc<double, double>{a1t.a, a1t.e, a1t.nkb, Tb, n0, 0, Yb, n1, 1, g1.E, n1, n1, n0, n1});
           t2.push_back(TcDesc<double, double>{a0.a, a0.e, a0.nkb, Yb, n1, 0, Tb, n0, 1, nullptr, 0, n0, n1, n0});
           t3.push_back(TcDesc<double, double>{a1.a, a1.e, a1.nkb, Tb, n0, 0, g3.C, P.n[1], 1, nullptr, 0, n1, n0, n1});
+          const SlN w0t = slices_n(S0, 1), w1t = slices_n(S1, 1), w0 = slices_n(S0, 0), w1 = slices_n(S1, 0);
+          sadd(0, w0t, n0, n0, g0.B, 0, P.n[1], n1, Tb, n1, nullptr, 0, 0);
+          sadd(1, w0t, n0, n0, s0R[q].B, 0, P.n[1], n1, Tb, n1, nullptr, 0, 0);
+          sadd(2, w1t, n1, n1, Tb, 1, n1, n0, Yb, n0, g1.E, 1, n1);
+          sadd(3, w1, n1, n1, Yb, 0, n0, n0, Tb, n0, nullptr, 0, 0);
+          sadd(4, w0, n0, n0, Tb, 1, n0, n1, g3.C, P.n[1], nullptr, 0, 0);
           ++q;
+        }
+        StackSet* sout[5] = {&L.n64.sk0F, &L.n64.sk0R, &L.n64.sk1, &L.n64.sk2, &L.n64.sk3};
+        for (int st = 0; st < 5; ++st) {
+          std::vector<SD> v;
+          for (auto& kv : sgrp[st]) {
+            SD dd = kv.second.proto;
+            dd.P = int(kv.second.X.size());
+            dd.X = c->mem.upload(kv.second.X, s);
+            dd.C = c->mem.upload(kv.second.C, s);
+            dd.E = st == 2 ? c->mem.upload(kv.second.E, s) : nullptr;
+            v.push_back(dd);
+          }
+          set_stack(*sout[st], v);
+          for (auto& kv : sgrp[st]) {
+            sout[st]->hX.push_back(kv.second.X);
+            sout[st]->hC.push_back(kv.second.C);
+            sout[st]->hE.push_back(kv.second.E);
+          }
         }
         set_tc(c, L.n64.tc0F, t0F);
         set_tc(c, L.n64.tc0R, t0R);
@@ -1528,6 +1671,7 @@ void build_levels(igamg_ctx* c) {
     }
   }
   bind_tc<double>(c);
+  bind_stack(c);
   // coarse solver: dense A_0 from the level-0 bands, Cholesky, explicit inverse
   Level& L0 = c->lv[0];
   const LevelTopo& T0 = L0.topo;
@@ -1706,10 +1850,22 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
     ProfScope ps(c, CLS_FD, N.fsmall_flops, 0.0);
     CK(launch_fd_small<T>(c->stream, N.fsmall, N.nfsmall, from_F ? 1 : 0, T(tau), add ? 1 : 0));
   } else if (c->pd.dim == 2 && N.use_tc) {
-    run_tc(c, from_F ? N.tc0F : N.tc0R, EPI_STORE, 1.0);
-    run_tc(c, N.tc1, EPI_MUL, 1.0);
-    run_tc(c, N.tc2, EPI_STORE, 1.0);
-    run_tc(c, N.tc3, epi, tau);
+    bool stacked = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (N.sk1.batch) {  // FP64: the fibre-major stacked stages
+        run_stack(c, from_F ? N.sk0F : N.sk0R, EPI_STORE, 1.0);
+        run_stack(c, N.sk1, EPI_MUL, 1.0);
+        run_stack(c, N.sk2, EPI_STORE, 1.0);
+        run_stack(c, N.sk3, epi, tau);
+        stacked = true;
+      }
+    }
+    if (!stacked) {
+      run_tc(c, from_F ? N.tc0F : N.tc0R, EPI_STORE, 1.0);
+      run_tc(c, N.tc1, EPI_MUL, 1.0);
+      run_tc(c, N.tc2, EPI_STORE, 1.0);
+      run_tc(c, N.tc3, epi, tau);
+    }
   } else if (c->pd.dim == 2) {
     run_gemm(c, from_F ? N.st0F : N.st0R, true, false, EPI_STORE, 1.0, CLS_FD);
     run_gemm(c, N.st1, false, false, EPI_MUL, 1.0, CLS_FD);
@@ -2432,6 +2588,13 @@ struct LockTcStage {  // one tensor-core stage over the problems that use the te
   int64_t tiles = 0, panels = 0;
   double exec_flops = 0, flops = 0;
 };
+struct LockStackStage {  // one stacked (fibre-major) tensor-core stage over the problems
+  TcStack<double, double>* d = nullptr;
+  int *tstart = nullptr, *pstart = nullptr;
+  int batch = 0;
+  int64_t tiles = 0, panels = 0;
+  double exec_flops = 0, flops = 0;
+};
 struct LockSmooth {  // the smoother of one depth, one direction (from F, assign / from R, add)
   // one-launch small-level smoothers
   SmoothSmallT<double>* small = nullptr;
@@ -2449,6 +2612,7 @@ struct LockSmooth {  // the smoother of one depth, one direction (from F, assign
   FdSmallT<double>* fsmall = nullptr;
   int nfsmall = 0;
   LockTcStage tc[4];
+  LockStackStage sk[4];
   std::vector<LockGemmGroup> st[4];
   double flops = 0;  // algorithmic FLOPs of the kernels outside the GEMM groups and stages
 };
@@ -2532,6 +2696,43 @@ V* lk_upload(Lockstep* k, const std::vector<V>& h) {
 
 using MemberGemm = std::pair<const GemmSet*, const LockMember*>;
 using MemberTc = std::pair<const TcSet<double>*, const LockMember*>;
+using MemberStack = std::pair<const StackSet*, const LockMember*>;
+
+// The stacked descriptors of every member at one stage (a copy's own tables and scratch).
+void lk_stack_stage(Lockstep* k, const std::vector<MemberStack>& sets, LockStackStage& out) {
+  std::vector<TcStack<double, double>> h;
+  for (const auto& sm : sets) {
+    const StackSet* t = sm.first;
+    const LockMember& m = *sm.second;
+    for (int i = 0; i < t->batch; ++i) {
+      TcStack<double, double> d = t->h[i];
+      if (m.w) {
+        std::vector<const double*> X, E;
+        std::vector<double*> C;
+        for (const double* p : t->hX[i]) X.push_back(m.tr(p));
+        for (double* p : t->hC[i]) C.push_back(m.tr(p));
+        for (const double* p : t->hE[i]) E.push_back(m.tr(p));
+        d.X = lk_upload(k, X);
+        d.C = lk_upload(k, C);
+        d.E = t->h[i].E ? lk_upload(k, E) : nullptr;
+        d.Xdig = m.w->sdig + t->dig_off[i];
+        d.Xtau = m.w->stau + t->tau_off[i];
+      }
+      h.push_back(d);
+    }
+    out.exec_flops += t->exec_flops;
+    out.flops += t->flops;
+  }
+  if (h.empty()) return;
+  std::vector<int> ts, ps;
+  tc_stack_prefixes(h, ts, ps);
+  out.batch = int(h.size());
+  out.tiles = ts.back();
+  out.panels = ps.back();
+  out.d = lk_upload(k, h);
+  out.tstart = lk_upload(k, ts);
+  out.pstart = lk_upload(k, ps);
+}
 
 void lk_gemm_groups(Lockstep* k, const std::vector<MemberGemm>& sets, std::vector<LockGemmGroup>& out) {
   std::map<int, std::vector<GemmDesc>> byR;
@@ -2661,6 +2862,7 @@ Lockstep* lockstep_build(const std::vector<LockMember>& mb, std::string* why, bo
         std::vector<NodeJobT<double>> gather, scatter;
         std::vector<MemberGemm> eA, eB, st[4];
         std::vector<MemberTc> tc[4];
+        std::vector<MemberStack> sk[4];
         std::vector<FdRowsT<double>> rows;
         std::vector<FdSmallT<double>> fsmall;
       } sd[2];
@@ -2734,7 +2936,12 @@ Lockstep* lockstep_build(const std::vector<LockMember>& mb, std::string* why, bo
           // the one-block size: a problem timed alone may lose with few tiles, but the
           // lockstep launches hold the tiles of every problem at this depth.
           const bool tc = N.tc0F.batch && (N.use_tc || (c->opt.fd_engine == 0 && L.tc_ok && !L.fused_ok));
-          if (tc) {
+          if (tc && N.sk1.batch) {  // the stacked stages, as a single solve runs them
+            S.sk[0].push_back({dir == 0 ? &N.sk0F : &N.sk0R, &m});
+            S.sk[1].push_back({&N.sk1, &m});
+            S.sk[2].push_back({&N.sk2, &m});
+            S.sk[3].push_back({&N.sk3, &m});
+          } else if (tc) {
             S.tc[0].push_back({dir == 0 ? &N.tc0F : &N.tc0R, &m});
             S.tc[1].push_back({&N.tc1, &m});
             S.tc[2].push_back({&N.tc2, &m});
@@ -2785,6 +2992,7 @@ Lockstep* lockstep_build(const std::vector<LockMember>& mb, std::string* why, bo
         LS.nfsmall = int(S.fsmall.size());
         for (int st = 0; st < 4; ++st) {
           lk_tc_stage(k, S.tc[st], LS.tc[st]);
+          lk_stack_stage(k, S.sk[st], LS.sk[st]);
           lk_gemm_groups(k, S.st[st], LS.st[st]);
         }
       }
@@ -2882,6 +3090,13 @@ void lk_smooth(Lockstep* k, cudaStream_t s, const LockSmooth& S, bool from_F, bo
     if (!t.batch) continue;
     CK((launch_tc_digits<7, double, double>(s, t.d, t.batch, t.pstart, t.panels)));
     CK((launch_gemm_tc<7, double, double>(s, t.d, t.batch, t.tstart, t.tiles, tepi[st], st == 3 ? tau : 1.0, k->err)));
+    lk_count(k, 2, t.flops, t.exec_flops);
+  }
+  for (int st = 0; st < 4; ++st) {
+    const LockStackStage& t = S.sk[st];
+    if (!t.batch) continue;
+    CK(launch_tc_digits_stack(s, t.d, t.batch, t.pstart, t.panels));
+    CK(launch_gemm_tc_stack(s, t.d, t.batch, t.tstart, t.tiles, tepi[st], st == 3 ? tau : 1.0, k->err));
     lk_count(k, 2, t.flops, t.exec_flops);
   }
   const bool ta[4] = {true, false, false, false}, tb[4] = {false, false, false, true};
@@ -3173,6 +3388,8 @@ void ensure_copies(igamg_ctx* c, int n) {
       if (c->dig64[k]) w.dig[k] = c->mem.alloc<__nv_bfloat16>(size_t(c->dig64[k]));
       if (c->tau64[k]) w.tau[k] = c->mem.alloc<int>(size_t(c->tau64[k]));
     }
+    if (c->sdig) w.sdig = c->mem.alloc<__nv_bfloat16>(size_t(c->sdig));
+    if (c->stau) w.stau = c->mem.alloc<int>(size_t(c->stau));
     c->copies.push_back(std::move(w));
   }
   CK(cudaStreamSynchronize(s));

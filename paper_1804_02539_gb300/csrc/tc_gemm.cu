@@ -361,10 +361,77 @@ __global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>*
   }
 }
 
-template <int S, class TB, class TC>
-__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restrict__ descs, int batch,
+// Digit pass of stacked descriptors: one CTA per 32-fibre panel of the stacked M (fibre
+// m = p F + j of patch p), one warp per 4 fibres as in k_tc_digits; the digit planes go to
+// the M-side layout [M tile][K block][S][128 x 32] and the exponents to Xtau[m].  A panel
+// never straddles an M tile (128 is a multiple of 32).
+__global__ void __launch_bounds__(kDigThreads) k_tc_digits_stack(const TcStack<double, double>* __restrict__ descs,
+                                                                  int batch, const int* __restrict__ pstart) {
+  constexpr int S = 7, ASZ = S * TBM * TBK, RB = kDigRegBlocks;
+  const int total = pstart[batch];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = 4 * warp + (lane >> 3);  // this lane's fibre within the panel
+  const int kq = lane & 7;                // K quad: k = 4 kq .. 4 kq + 3 of a block
+  for (int pnl = blockIdx.x; pnl < total; pnl += gridDim.x) {
+    const int q = tile_desc(pstart, batch, pnl);
+    const TcStack<double, double>& d = descs[q];
+    const int M = d.P * d.F, K = d.K, nkb = (K + TBK - 1) / TBK;
+    const int gm = (pnl - pstart[q]) * 32 + cl;
+    const bool valid = gm < M;
+    const int p = valid ? gm / d.F : 0, j = valid ? gm - p * d.F : 0;
+    const double* X = valid ? d.X[p] : nullptr;
+    __nv_bfloat16* out = d.Xdig + int64_t(gm / TBM) * nkb * ASZ;
+    const int row = gm % TBM;
+    const int nch = (nkb + RB - 1) / RB;
+    double v[RB][4];
+    auto load_chunk = [&](int ch) {
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int gk = (ch * RB + b) * TBK + 4 * kq + kk;
+          v[b][kk] = (valid && gk < K) ? ld_b(X, d.ldx, d.xt, gk, j) : 0.0;
+        }
+    };
+    int emax = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      load_chunk(ch);
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          emax = max(emax, int((uint64_t(__double_as_longlong(v[b][kk])) >> 52) & 0x7FF));
+    }
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+    const int tau = emax ? emax - 1023 + 1 : -1022;
+    if (kq == 0 && valid) d.Xtau[gm] = tau;
+    for (int ch = 0; ch < nch; ++ch) {
+      if (nch > 1) load_chunk(ch);  // one chunk: still in registers from the exponent pass
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int kb = ch * RB + b;
+        if (kb >= nkb) break;
+        __nv_bfloat16* blk = out + int64_t(kb) * ASZ;
+        uint32_t a[7], c[7];
+        digit_pairs7(v[b][0], v[b][1], tau, a);
+        digit_pairs7(v[b][2], v[b][3], tau, c);
+#pragma unroll
+        for (int sq = 0; sq < S; ++sq)
+          *reinterpret_cast<uint2*>(blk + core_off(sq * TBM + row, 4 * kq)) = make_uint2(a[sq], c[sq]);
+      }
+    }
+  }
+}
+
+// D = TcDesc: A (M side) the constant pre-sliced matrix, B (N side) the varying digit planes;
+// D = TcStack (fibre-major): A the stacked fibres' digit planes, B the constant's slices.
+template <int S, class TB, class TC, class D>
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const D* __restrict__ descs, int batch,
                                                  const int* __restrict__ tstart, int epi, TC alpha,
                                                  int* __restrict__ err) {
+  constexpr bool FM = std::is_same<D, TcStack<TB, TC>>::value;
   using CF = TcCfg<S>;
   constexpr int TBN = CF::TBN, NST = CF::NST, ACC = CF::ACC;
   constexpr int ASZ = S * TBM * TBK, BSZ = S * TBN * TBK;  // BF16 elements of one stage
@@ -419,7 +486,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const int q = tile_desc(tstart, batch, t);
-        const TcDesc<TB, TC>& d = descs[q];
+        const D& d = descs[q];
         const int tiles_n = (d.N + TBN - 1) / TBN, r = t - tstart[q], mt = r / tiles_n, nt = r % tiles_n;
         const int nkb = (d.K + TBK - 1) / TBK;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
@@ -430,8 +497,14 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
             break;
           }
           const uint32_t abytes = uint32_t(ASZ) * 2u, bbytes = uint32_t(BSZ) * 2u;
-          const __nv_bfloat16* asrc = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
-          const __nv_bfloat16* bsrc = d.Bdig + (int64_t(nt) * nkb + kb) * BSZ;
+          const __nv_bfloat16 *asrc, *bsrc;
+          if constexpr (FM) {
+            asrc = d.Xdig + (int64_t(mt) * nkb + kb) * ASZ;
+            bsrc = d.Wslices + (int64_t(nt) * nkb + kb) * BSZ;
+          } else {
+            asrc = d.Aslices + (int64_t(mt) * d.nkb + kb) * ASZ;
+            bsrc = d.Bdig + (int64_t(nt) * nkb + kb) * BSZ;
+          }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sptr(full + st)),
                        "r"(abytes + bbytes));
           asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -512,7 +585,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
     int i = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
       const int q = tile_desc(tstart, batch, t);
-      const TcDesc<TB, TC>& d = descs[q];
+      const D& d = descs[q];
       const int tiles_n = (d.N + TBN - 1) / TBN, r = t - tstart[q];
       const int i0 = (r / tiles_n) * TBM, j0 = (r % tiles_n) * TBN;
       const int b = i & 1;
@@ -523,8 +596,22 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int gi = i0 + quarter * 32 + lane;
-      int sig = 0;
-      if (S > 1 && gi < d.M) sig = d.Aexp[gi];
+      int rows, sig = 0;
+      if constexpr (FM) rows = d.P * d.F;
+      else rows = d.M;
+      if constexpr (S > 1) {
+        if (gi < rows) {
+          if constexpr (FM) sig = d.Xtau[gi];
+          else sig = d.Aexp[gi];
+        }
+      }
+      int fp = 0, fj = 0;  // stacked: the lane's patch and fibre
+      if constexpr (FM) {
+        if (gi < rows) {
+          fp = gi / d.F;
+          fj = gi - fp * d.F;
+        }
+      }
       const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * ACC);
       constexpr int CC = S == 1 ? 16 : 8;  // columns per chunk
 #pragma unroll 1
@@ -540,7 +627,11 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
           // column scales of this chunk (loads in flight during the TMEM reads)
           int tj[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) tj[u] = j0 + c0 + u < d.N ? __ldg(d.Btau + j0 + c0 + u) : 0;
+          const int* cexp;
+          if constexpr (FM) cexp = d.Wexp;
+          else cexp = d.Btau;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) tj[u] = j0 + c0 + u < d.N ? __ldg(cexp + j0 + c0 + u) : 0;
           // the 7 diagonals of these 8 columns in one round of TMEM loads, then the exact
           // integer recombination sum_q D_q 2^{7(7-q)} (q = 2..7) plus D_8 / 2^7 in units of
           // 2^-49, and the rounding to FP64 with the power-of-two scale 2^{sigma + tau - 49}
@@ -565,30 +656,66 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const TcDesc<TB, TC>* __restr
           asm volatile("tcgen05.fence::before_thread_sync;");
           mbar_arrive(sptr(acce + b));
         }
-        if (gi < d.M) {
+        if (gi < rows) {
           // epilogue operands first (loads in flight), then the stores
           TA e[CC];
-          const bool needs = epi == EPI_MUL || epi == EPI_ADD;
-#pragma unroll
-          for (int u = 0; u < CC; ++u) {
-            const int gj = j0 + c0 + u;
-            e[u] = TA(0);
-            if (needs && gj < d.N) {
-              if (epi == EPI_MUL) e[u] = TA(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
-              else e[u] = TA(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
+          if constexpr (FM) {
+            // this lane's fibre: C and E addresses of column gj are base + gj * step
+            TC* Cp = d.C[fp];
+            TC* cb = d.ct ? Cp + int64_t(fj) * d.ldc : Cp + fj;
+            const int64_t cst = d.ct ? 1 : d.ldc;
+            const TC* eb = nullptr;
+            int64_t est = 0;
+            if (epi == EPI_MUL) {
+              const TC* Ep = d.E[fp];
+              eb = d.et ? Ep + int64_t(fj) * d.lde : Ep + fj;
+              est = d.et ? 1 : d.lde;
             }
-          }
 #pragma unroll
-          for (int u = 0; u < CC; ++u) {
-            const int gj = j0 + c0 + u;
-            if (gj >= d.N) continue;
-            const TA v = acc[u];
-            TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
-            switch (epi) {
-              case EPI_MUL: *cp = TC(v * e[u]); break;
-              case EPI_ASSIGN: *cp = TC(TA(alpha) * v); break;
-              case EPI_ADD: *cp = TC(fma(TA(alpha), v, e[u])); break;
-              default: *cp = TC(v);
+            for (int u = 0; u < CC; ++u) {
+              const int gj = j0 + c0 + u;
+              e[u] = TA(0);
+              if (gj < d.N) {
+                if (epi == EPI_MUL) e[u] = TA(eb[gj * est]);
+                else if (epi == EPI_ADD) e[u] = TA(cb[gj * cst]);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < CC; ++u) {
+              const int gj = j0 + c0 + u;
+              if (gj >= d.N) continue;
+              const TA v = acc[u];
+              TC* cp = cb + gj * cst;
+              switch (epi) {
+                case EPI_MUL: *cp = TC(v * e[u]); break;
+                case EPI_ASSIGN: *cp = TC(TA(alpha) * v); break;
+                case EPI_ADD: *cp = TC(fma(TA(alpha), v, e[u])); break;
+                default: *cp = TC(v);
+              }
+            }
+          } else {
+            const bool needs = epi == EPI_MUL || epi == EPI_ADD;
+#pragma unroll
+            for (int u = 0; u < CC; ++u) {
+              const int gj = j0 + c0 + u;
+              e[u] = TA(0);
+              if (needs && gj < d.N) {
+                if (epi == EPI_MUL) e[u] = TA(d.E[d.tc ? int64_t(gj) * d.lde + gi : int64_t(gi) * d.lde + gj]);
+                else e[u] = TA(d.C[d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj]);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < CC; ++u) {
+              const int gj = j0 + c0 + u;
+              if (gj >= d.N) continue;
+              const TA v = acc[u];
+              TC* cp = d.C + (d.tc ? int64_t(gj) * d.ldc + gi : int64_t(gi) * d.ldc + gj);
+              switch (epi) {
+                case EPI_MUL: *cp = TC(v * e[u]); break;
+                case EPI_ASSIGN: *cp = TC(TA(alpha) * v); break;
+                case EPI_ADD: *cp = TC(fma(TA(alpha), v, e[u])); break;
+                default: *cp = TC(v);
+              }
             }
           }
         }
@@ -631,16 +758,57 @@ cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int bat
                            int64_t tiles, int epi, TC alpha, int* err) {
   if (batch <= 0 || tiles <= 0) return cudaSuccess;
   const size_t smem = tc_smem_bytes<S>();
-  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC>), smem);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<S, TB, TC, TcDesc<TB, TC>>), smem);
   if (e != cudaSuccess) return e;
   // persistent CTAs, at most one per SM: the fewest that give every CTA the same largest
   // number of tiles as one per SM would, so that SMs left over serve the work running
   // concurrently on the interface stream
   const int64_t nsm = sm_count(), per = (tiles + nsm - 1) / nsm;
   const int grid = int(std::min<int64_t>((tiles + per - 1) / per, nsm));
-  k_gemm_tc<S, TB, TC><<<grid, NT, smem, s>>>(d_desc, batch, tile_start, epi, alpha, err);
+  k_gemm_tc<S, TB, TC, TcDesc<TB, TC>><<<grid, NT, smem, s>>>(d_desc, batch, tile_start, epi, alpha, err);
   return cudaGetLastError();
 }
+
+cudaError_t launch_gemm_tc_stack(cudaStream_t s, const TcStack<double, double>* d_desc, int batch,
+                                 const int* tile_start, int64_t tiles, int epi, double alpha, int* err) {
+  if (batch <= 0 || tiles <= 0) return cudaSuccess;
+  using SD = TcStack<double, double>;
+  const size_t smem = tc_smem_bytes<7>();
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_gemm_tc<7, double, double, SD>), smem);
+  if (e != cudaSuccess) return e;
+  const int64_t nsm = sm_count(), per = (tiles + nsm - 1) / nsm;
+  const int grid = int(std::min<int64_t>((tiles + per - 1) / per, nsm));
+  k_gemm_tc<7, double, double, SD><<<grid, NT, smem, s>>>(d_desc, batch, tile_start, epi, alpha, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_digits_stack(cudaStream_t s, const TcStack<double, double>* d_desc, int batch,
+                                   const int* panel_start, int64_t panels) {
+  if (batch <= 0 || panels <= 0) return cudaSuccess;
+  const int grid = int(std::min<int64_t>(panels, 4 * int64_t(sm_count())));
+  k_tc_digits_stack<<<grid, kDigThreads, 0, s>>>(d_desc, batch, panel_start);
+  return cudaGetLastError();
+}
+
+void tc_stack_prefixes(const std::vector<TcStack<double, double>>& h, std::vector<int>& tile_start,
+                       std::vector<int>& panel_start) {
+  tile_start.assign(h.size() + 1, 0);
+  panel_start.assign(h.size() + 1, 0);
+  for (size_t q = 0; q < h.size(); ++q) {
+    const int64_t M = int64_t(h[q].P) * h[q].F;
+    const bool any = M > 0 && h[q].N > 0 && h[q].K > 0;
+    tile_start[q + 1] = tile_start[q] + (any ? int(tc_tiles(int(M), h[q].N, 7)) : 0);
+    panel_start[q + 1] = panel_start[q] + (any ? int((M + 31) / 32) : 0);
+  }
+}
+
+int64_t tc_stack_dig_elems(int P, int F, int K) {
+  const int64_t M = int64_t(P) * F;
+  if (M <= 0 || K <= 0) return 0;
+  return (M + TBM - 1) / TBM * ((K + TBK - 1) / TBK) * 7 * TBM * TBK;
+}
+
+double tc_stack_exec_flops(int P, int F, int N, int K) { return tc_exec_flops(P * F, N, K, 7); }
 template cudaError_t launch_tc_digits<7, double, double>(cudaStream_t, const TcDesc<double, double>*, int, const int*,
                                                          int64_t);
 template cudaError_t launch_tc_digits<1, float, float>(cudaStream_t, const TcDesc<float, float>*, int, const int*,
@@ -701,9 +869,9 @@ double tc_exec_flops(int M, int N, int K, int S) {
 }
 
 void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
-                    std::vector<int>& exps) {
-  const int mt = (M + TBM - 1) / TBM, nkb = (K + TBK - 1) / TBK;
-  slices.assign(size_t(mt) * nkb * S * TBM * TBK, 0);
+                    std::vector<int>& exps, int tile_rows) {
+  const int R = tile_rows, mt = (M + R - 1) / R, nkb = (K + TBK - 1) / TBK;
+  slices.assign(size_t(mt) * nkb * S * R * TBK, 0);
   exps.assign(M, 0);
   for (int i = 0; i < M; ++i) {
     double mx = 0.0;
@@ -713,8 +881,8 @@ void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vect
     exps[i] = e;
     for (int k = 0; k < K; ++k) {
       double a = A[size_t(i) * K + k];
-      size_t base = ((size_t(i / TBM) * nkb + k / TBK) * S) * TBM * TBK;
-      int r = i % TBM, kk = k % TBK;
+      size_t base = ((size_t(i / R) * nkb + k / TBK) * S) * R * TBK;
+      int r = i % R, kk = k % TBK;
       size_t off = size_t(((r >> 3) * (TBK / 8) + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7));
       if (S == 1) {
         slices[base + off] = bf16_bits_rn(float(a));
@@ -725,7 +893,7 @@ void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vect
       for (int s = 1; s <= S; ++s) {
         float dgt = float((Fi >> (7 * (S - s))) & 127u);
         if (a < 0) dgt = -dgt;
-        slices[base + size_t(s - 1) * TBM * TBK + off] = bf16_bits_rn(dgt);
+        slices[base + size_t(s - 1) * R * TBK + off] = bf16_bits_rn(dgt);
       }
     }
   }

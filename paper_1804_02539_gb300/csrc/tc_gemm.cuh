@@ -29,6 +29,28 @@ struct TcDesc {
   int* Btau = nullptr;
 };
 
+// Fibre-major stacked product (FP64, S = 7): the varying operand on the MMA's M side.  For
+// each of P patches p sharing one constant W (N x K, sliced at setup in 32-row tiles):
+//   C_p(i, j) = sum_k W(i, k) X_p(k, j),   i < N, j < F,
+// X_p(k, j) = xt ? X_p[j * ldx + k] : X_p[k * ldx + j],  C_p(i, j) = ct ? C_p[j * ldc + i]
+// : C_p[i * ldc + j], E_p(i, j) likewise with et and lde (EPI_MUL operand).  The P F fibres
+// are stacked along M, so the 128-row MMA tiles are padded once per set instead of once per
+// patch, and an epilogue lane owns one fibre (ct = 0 stores are coalesced).
+template <class TB, class TC>
+struct TcStack {
+  const __nv_bfloat16* Wslices;  // [N/32 tiles][K blocks][S][32 x 32] in core-matrix layout
+  const int* Wexp;               // [N] row scale exponents of W
+  const TB* const* X;            // [P] varying operands
+  TC* const* C;                  // [P] outputs
+  const TC* const* E;            // [P] EPI_MUL operands (may be NULL when unused)
+  int ldx, xt, ldc, ct, lde, et;
+  int P, F, N, K;
+  // scratch written by the digit pass and read by the GEMM: the stacked fibres' digit planes
+  // [ceil(P F / 128)][K blocks][S][128 x 32] and their exponents [P F]
+  __nv_bfloat16* Xdig = nullptr;
+  int* Xtau = nullptr;
+};
+
 // Scratch sizes of one descriptor (BF16 elements of Bdig, ints of Btau) for S slices.
 int64_t tc_dig_elems(int N, int K, int S);
 inline int64_t tc_tau_elems(int N, int S) { return S > 1 ? N : 0; }
@@ -49,6 +71,18 @@ cudaError_t launch_tc_digits(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int b
 template <int S, class TB, class TC>
 cudaError_t launch_gemm_tc(cudaStream_t s, const TcDesc<TB, TC>* d_desc, int batch, const int* tile_start,
                            int64_t tiles, int epi, TC alpha, int* err);
+// The same two launches for stacked descriptors (S = 7, TB = TC = double): panels are 32-fibre
+// groups of the stacked M, tiles 128 fibres x 32 rows of W.
+cudaError_t launch_tc_digits_stack(cudaStream_t s, const TcStack<double, double>* d_desc, int batch,
+                                   const int* panel_start, int64_t panels);
+cudaError_t launch_gemm_tc_stack(cudaStream_t s, const TcStack<double, double>* d_desc, int batch,
+                                 const int* tile_start, int64_t tiles, int epi, double alpha, int* err);
+void tc_stack_prefixes(const std::vector<TcStack<double, double>>& h, std::vector<int>& tile_start,
+                       std::vector<int>& panel_start);
+// Scratch of one stacked descriptor (BF16 elements of Xdig; ints of Xtau = P F), and the
+// BF16 MMA FLOPs one launch issues for it.
+int64_t tc_stack_dig_elems(int P, int F, int K);
+double tc_stack_exec_flops(int P, int F, int N, int K);
 // Prefix sums over descriptors of their output tiles (GEMM work items) and of their
 // 32-column (S = 7) or 128-column (S = 1) panels of B (digit-pass work items).
 template <class TB, class TC>
@@ -64,7 +98,8 @@ double tc_exec_flops(int M, int N, int K, int S);
 
 // Host: slices of a constant row-major M x K matrix in the layout TcDesc::Aslices expects.
 // S = 7 gives integer digits and the row exponents; S = 1 gives BF16 roundings.
+// tile_rows = 128 gives TcDesc::Aslices (the M side), 32 gives TcStack::Wslices (the N side).
 void slice_constant(const std::vector<double>& A, int M, int K, int S, std::vector<uint16_t>& slices,
-                    std::vector<int>& exps);
+                    std::vector<int>& exps, int tile_rows = 128);
 
 }  // namespace igamg
