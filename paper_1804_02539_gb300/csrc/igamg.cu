@@ -156,6 +156,8 @@ struct Num {
   bool use_tc = false;
   GemmSetT<T> m0f, m1f, m2f, m0b, m1b, m2b;         // 3D interiors
   ModeSetT<T> md[6];                                // the same six products as mode products
+  Fd3SmallT<T>* fd3 = nullptr;                      // small 3D interiors: the six in one launch
+  int nfd3 = 0;
   T* cX = nullptr;                                  // compact 3D interior tensor
   T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
   GemmSetT<T> edgeA, edgeB, face0, face1, face2, face3;
@@ -197,6 +199,8 @@ struct Level {
   // transfer from level l-1 (valid for level >= 1): host descriptors per pass
   std::vector<XferT<double>> rp_h[3], pp_h[3];
   std::vector<Xfer2T<double>> r2_h, p2_h;  // 2D: both passes fused (when the tables allow)
+  std::vector<Fd3SmallT<double>> fd3_h;      // 3D small interiors (kFd3SmallN), host copy
+  int64_t box_vol = 0;                        // 3D interior nodes of the level
   int x2_rout0 = 0, x2_rout1 = 0, x2_pout0 = 0, x2_pout1 = 0, x2_rw1 = 0, x2_pw1 = 0;
   int64_t rmax[3] = {0, 0, 0}, pmax[3] = {0, 0, 0};
   double apply_flops = 0, band_bytes = 0, xfer_flops = 0, xfer_bytes = 0;
@@ -1271,6 +1275,27 @@ void build_levels(igamg_ctx* c) {
       }
       L.nbox = int(boxes.size());
       L.boxes = c->mem.upload(boxes, s);
+      L.box_vol = tot;
+      {  // every interior small enough for the one-launch kernel
+        bool ok = !pend.empty();
+        std::vector<Fd3SmallT<double>> f3;
+        for (size_t i = 0; i < pend.size() && ok; ++i) {
+          const Pend& pe = pend[i];
+          ok = std::max(pe.n0, std::max(pe.n1, pe.n2)) <= kFd3SmallN;
+          Fd3SmallT<double> f{pe.S[0]->dU, pe.S[1]->dU, pe.S[2]->dU, pe.Dinv, boxes[i].tile_off, {}, {}, {}};
+          for (int j = 0; j < 3; ++j) {
+            f.n[j] = boxes[i].n[j];
+            f.lo[j] = boxes[i].lo[j];
+            f.len[j] = boxes[i].len[j];
+          }
+          f3.push_back(f);
+        }
+        if (ok) {
+          L.fd3_h = f3;
+          L.n64.fd3 = c->mem.upload(f3, s);
+          L.n64.nfd3 = int(f3.size());
+        }
+      }
       L.n64.cX = reg_work(c, c->mem.alloc<double>(tot), tot);
       double* cB1 = reg_work(c, c->mem.alloc<double>(tot), tot);
       double* cB2 = reg_work(c, c->mem.alloc<double>(tot), tot);
@@ -1871,6 +1896,10 @@ void smooth(igamg_ctx* c, int l, bool from_F, bool add) {
     run_gemm(c, N.st1, false, false, EPI_MUL, 1.0, CLS_FD);
     run_gemm(c, N.st2, false, false, EPI_STORE, 1.0, CLS_FD);
     run_gemm(c, N.st3, false, true, epi, tau, CLS_FD);
+  } else if (L.nbox && N.fd3 && !N.use_tc) {  // small interiors: one launch, same arithmetic
+    const double fl = N.m0f.flops + N.m1f.flops + N.m2f.flops + N.m0b.flops + N.m1b.flops + N.m2b.flops;
+    ProfScope ps(c, CLS_FD, fl, 2.0 * sizeof(T) * L.box_vol);
+    CK(launch_fd3_small<T>(c->stream, N.fd3, N.nfd3, v, N.U, T(tau), add ? 1 : 0));
   } else if (L.nbox) {
     {
       ProfScope ps(c, CLS_FD, 0.0, 2.0 * sizeof(T) * L.max_box * L.nbox);
@@ -2509,6 +2538,20 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       set_mode(c, b, v);
     };
     for (int j = 0; j < 6; ++j) tr_mode(A.md[j], B.md[j]);
+    if (!L.fd3_h.empty()) {
+      std::vector<Fd3SmallT<float>> f3;
+      for (const auto& f : L.fd3_h) {
+        Fd3SmallT<float> g{tr(f.U0), tr(f.U1), tr(f.U2), tr(f.Dinv), f.tile_off, {}, {}, {}};
+        for (int j = 0; j < 3; ++j) {
+          g.n[j] = f.n[j];
+          g.lo[j] = f.lo[j];
+          g.len[j] = f.len[j];
+        }
+        f3.push_back(g);
+      }
+      B.fd3 = c->mem.upload(f3, s);
+      B.nfd3 = int(f3.size());
+    }
     for (int j = 0; j < 4; ++j) tr_mode(A.fm[j], B.fm[j]);
     tr_set(A.edgeA, B.edgeA); tr_set(A.edgeB, B.edgeB);
     tr_set(A.face0, B.face0); tr_set(A.face1, B.face1); tr_set(A.face2, B.face2); tr_set(A.face3, B.face3);

@@ -1771,6 +1771,78 @@ cudaError_t launch_mode_product(cudaStream_t s, const ModeDescT<T>* d, int batch
 template cudaError_t launch_mode_product<double>(cudaStream_t, const ModeDescT<double>*, int, int64_t, int, int);
 template cudaError_t launch_mode_product<float>(cudaStream_t, const ModeDescT<float>*, int, int64_t, int, int);
 
+// ---------------------------------------------------------------- small 3D interiors in one launch
+
+// One mode product of a box held in shared memory: Y(..., i, ...) = sum_k M(i, k) X(..., k, ...)
+// along mode `mode` of the n0 x n1 x n2 box, M(i, k) = mtr ? Mat[k n + i] : Mat[i n + k]
+// (Mat in shared memory), optionally times E; one FMA chain per output over k in order.
+template <class T>
+__device__ void fd3_mode(const T* X, T* Y, const T* Mat, int mtr, int mode, const int* n, const T* E) {
+  const int n0 = n[0], n1 = n[1], n2 = n[2], total = n0 * n1 * n2, nm = n[mode];
+  const int stride = mode == 0 ? n1 * n2 : (mode == 1 ? n2 : 1);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int q = idx % n2, b = (idx / n2) % n1, a = idx / (n1 * n2);
+    const int i = mode == 0 ? a : (mode == 1 ? b : q);
+    const int base = idx - i * stride;  // element with the contracted index at 0
+    T acc = T(0);
+    for (int k = 0; k < nm; ++k) {
+      const T m = mtr ? Mat[k * nm + i] : Mat[i * nm + k];
+      acc = fma(m, X[base + k * stride], acc);
+    }
+    Y[idx] = E ? acc * E[idx] : acc;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fd3_small(const Fd3SmallT<T>* __restrict__ ds, const T* __restrict__ v,
+                                                   T* __restrict__ u, T tau, int add) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Fd3SmallT<T> d = ds[blockIdx.x];
+  const int n0 = d.len[0], n1 = d.len[1], n2 = d.len[2], total = n0 * n1 * n2;
+  constexpr int NN = kFd3SmallN * kFd3SmallN * kFd3SmallN;
+  T* X = reinterpret_cast<T*>(smraw);
+  T* Y = X + NN;
+  T* M0 = Y + NN;
+  T* M1 = M0 + kFd3SmallN * kFd3SmallN;
+  T* M2 = M1 + kFd3SmallN * kFd3SmallN;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n0 * n0; i += blockDim.x) M0[i] = d.U0[i];
+  for (int i = tid; i < n1 * n1; i += blockDim.x) M1[i] = d.U1[i];
+  for (int i = tid; i < n2 * n2; i += blockDim.x) M2[i] = d.U2[i];
+  auto tile = [&](int idx) {
+    const int q = idx % n2, b = (idx / n2) % n1, a = idx / (n1 * n2);
+    return d.tile_off + ((int64_t(a + d.lo[0]) * d.n[1] + (b + d.lo[1])) * d.n[2] + (q + d.lo[2]));
+  };
+  for (int idx = tid; idx < total; idx += blockDim.x) X[idx] = v[tile(idx)];
+  __syncthreads();
+  const int nn[3] = {n0, n1, n2};
+  fd3_mode(X, Y, M0, 1, 0, nn, static_cast<const T*>(nullptr));
+  fd3_mode(Y, X, M1, 1, 1, nn, static_cast<const T*>(nullptr));
+  fd3_mode(X, Y, M2, 1, 2, nn, d.Dinv);
+  fd3_mode(Y, X, M0, 0, 0, nn, static_cast<const T*>(nullptr));
+  fd3_mode(X, Y, M1, 0, 1, nn, static_cast<const T*>(nullptr));
+  fd3_mode(Y, X, M2, 0, 2, nn, static_cast<const T*>(nullptr));
+  for (int idx = tid; idx < total; idx += blockDim.x) {
+    const int64_t t = tile(idx);
+    u[t] = add ? fma(tau, X[idx], u[t]) : tau * X[idx];
+  }
+}
+
+template <class T>
+cudaError_t launch_fd3_small(cudaStream_t s, const Fd3SmallT<T>* d, int n, const T* v, T* u, T tau, int add) {
+  if (n <= 0) return cudaSuccess;
+  const size_t sm = sizeof(T) * (2 * size_t(kFd3SmallN) * kFd3SmallN * kFd3SmallN + 3 * size_t(kFd3SmallN) * kFd3SmallN);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_fd3_small<T>), sm);
+  if (e != cudaSuccess) return e;
+  k_fd3_small<T><<<n, 256, sm, s>>>(d, v, u, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fd3_small<double>(cudaStream_t, const Fd3SmallT<double>*, int, const double*, double*,
+                                              double, int);
+template cudaError_t launch_fd3_small<float>(cudaStream_t, const Fd3SmallT<float>*, int, const float*, float*, float,
+                                             int);
+
 // ---------------------------------------------------------------- interior box gather/scatter
 
 // Compact copy of every patch-interior box (3D FD works on compact tensors) and the

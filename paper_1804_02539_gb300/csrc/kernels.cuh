@@ -212,6 +212,23 @@ struct ModeDescT {
   int64_t inner, fibres;
 };
 constexpr int kModeMaxN = 80;
+
+// Interior fast diagonalisation of one small 3D patch interior (every length <= kFd3SmallN):
+// the box of the tile (tile_off, tile extents n, first index lo, lengths len) and the FD
+// operands U0, U1, U2 (len x len) and Dinv (len0 x len1 x len2).
+template <class T>
+struct Fd3SmallT {
+  const T *U0, *U1, *U2, *Dinv;
+  int64_t tile_off;
+  int n[3], lo[3], len[3];
+};
+constexpr int kFd3SmallN = 16;
+// u = (add ? u + tau z : tau z) on every interior box, z = L^{-1} v restricted to the box:
+// one block per interior, the six mode products (transposed bases, Dinv, bases) in shared
+// memory with the FMA order of launch_mode_product, so the result equals the box copy +
+// mode products + box copy path bit for bit.
+template <class T>
+cudaError_t launch_fd3_small(cudaStream_t s, const Fd3SmallT<T>* d, int n, const T* v, T* u, T tau, int add);
 template <class T>
 cudaError_t launch_mode_product(cudaStream_t s, const ModeDescT<T>* d, int batch, int64_t max_fibres, int max_n,
                                 int epi);
