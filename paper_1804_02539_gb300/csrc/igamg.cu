@@ -136,6 +136,7 @@ struct Num {
   const void* band = nullptr;  // band coefficients of the cycle: T, or __nv_bfloat16 when bf16
   bool bf16 = false;
   const T* band_op = nullptr;  // band coefficients of the Krylov operator (always type T)
+  PatchDev* pd_pair = nullptr; // 3D BF16 cycle bands in the paired layout: patch offsets into it
   KronDevT<T>* kd = nullptr;   // rectangle patches: Kronecker-sum operator per patch
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
@@ -1787,6 +1788,9 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
       if (c->pd.dim == 2)
         CK((launch_band_apply_2d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p,
                                                          band, u, f, r, L.uniform_p)));
+      else if (N.pd_pair)
+        CK(launch_band_apply_3d_pair<__nv_bfloat16>(c->stream, N.pd_pair, c->pd.K, L.max_n, L.uniform_p, band, u, f,
+                                                    r));
       else
         CK((launch_band_apply_3d<float, __nv_bfloat16>(c->stream, L.pd, c->pd.K, L.max_n, L.max_p, band, u, f, r,
                                                          L.uniform_p)));
@@ -2458,12 +2462,34 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
         kf.push_back(KronDevT<float>{k.off, k.n0, k.n1, k.p0, k.p1, tr(k.K0), tr(k.M0), tr(k.K1), tr(k.M1),
                                      float(k.c0), float(k.c1)});
       B.kd = c->mem.upload(kf, s);
-    } else if (!bf16_bands || finest) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
+    }
+    // 3D BF16 bands of one degree: the paired layout (rows padded to even length, one
+    // bfloat162 load per tap and node pair; FP32 bands stay flat: paired float2 loads
+    // measured slower)
+    const bool pair = bf16_bands && !L.kron && c->pd.dim == 3 && L.uniform_p >= 2 && L.uniform_p <= 4;
+    const int taps = (2 * L.uniform_p + 1) * (2 * L.uniform_p + 1) * (2 * L.uniform_p + 1);
+    int64_t ptot = 0, pmaxe = 0;
+    if (pair) {
+      std::vector<PatchDev> pp = L.pd_h;
+      for (auto& q : pp) {
+        const int64_t ne = int64_t(q.n[0]) * q.n[1] * band_row_even(q.n[2]);
+        q.band_off = ptot;
+        ptot += taps * ne;
+        pmaxe = std::max(pmaxe, ne);
+      }
+      B.pd_pair = c->mem.upload(pp, s);
+    }
+    if (!L.kron && (!bf16_bands || finest)) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
       b32 = c->mem.alloc<float>(nb);
       CK(launch_convert_f64_f32(s, nb, L.band, 1.0, b32));
       B.band_op = b32;
     }
-    if (bf16_bands && !L.kron) {
+    if (bf16_bands && !L.kron && pair) {
+      __nv_bfloat16* bb = c->mem.alloc<__nv_bfloat16>(size_t(std::max<int64_t>(ptot, 1)));
+      CK(launch_band_pair<__nv_bfloat16>(s, L.pd, B.pd_pair, int(L.pd_h.size()), taps, pmaxe, L.band, bb));
+      B.band = bb;
+      B.bf16 = true;
+    } else if (bf16_bands && !L.kron) {
       __nv_bfloat16* bb = c->mem.alloc<__nv_bfloat16>(nb);
       CK(launch_convert_f64_bf16(s, nb, L.band, bb));
       B.band = bb;

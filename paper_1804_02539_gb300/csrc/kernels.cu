@@ -1448,6 +1448,115 @@ __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDe
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
 }
 
+// ---------------------------------------------------------------- paired BF16 3D apply
+
+template <class TB>
+__global__ void k_band_pair(const PatchDev* __restrict__ spd, const PatchDev* __restrict__ dpd, int taps,
+                            const double* __restrict__ src, TB* __restrict__ dst) {
+  const PatchDev a = spd[blockIdx.z], b = dpd[blockIdx.z];
+  const int n2 = a.n[2], n2e = band_row_even(n2), t = blockIdx.y;
+  if (t >= taps) return;
+  const int64_t nn = int64_t(a.n[0]) * a.n[1] * n2, ne = int64_t(a.n[0]) * a.n[1] * n2e;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < ne; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t row = i / n2e;
+    const int i2 = int(i - row * n2e);
+    dst[b.band_off + t * ne + i] = i2 < n2 ? TB(double(src[a.band_off + t * nn + row * n2 + i2]) * 1.0) : TB(0.0f);
+  }
+}
+
+template <class TB>
+cudaError_t launch_band_pair(cudaStream_t s, const PatchDev* src_pd, const PatchDev* dst_pd, int K, int taps,
+                             int64_t max_nodes, const double* src, TB* dst) {
+  if (K <= 0 || taps <= 0 || max_nodes <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((max_nodes + 255) / 256, 1024);
+  k_band_pair<TB><<<dim3(unsigned(g), unsigned(taps), unsigned(K)), 256, 0, s>>>(src_pd, dst_pd, taps, src, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_band_pair<__nv_bfloat16>(cudaStream_t, const PatchDev*, const PatchDev*, int, int, int64_t,
+                                                     const double*, __nv_bfloat16*);
+template cudaError_t launch_band_pair<float>(cudaStream_t, const PatchDev*, const PatchDev*, int, int, int64_t,
+                                             const double*, float*);
+
+__device__ __forceinline__ float2 pair_val(const __nv_bfloat16* p) {
+  return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+}
+__device__ __forceinline__ float2 pair_val(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+// Block: 32 x 4 x 2 threads, 64 x 4 x 2 nodes (two adjacent nodes of a row per thread); the
+// u halo in shared memory as in k_band_apply_3d.  (16 x 8 x 2 threads spanning 32 nodes of
+// a row measured slower on the 67-node rows of the 3D benchmark.)
+constexpr int PBX = 32, PBY = 4, PBZ = 2;
+template <class TB, int P>
+__global__ void __launch_bounds__(PBX * PBY * PBZ) k_band_apply_3d_pair(const PatchDev* __restrict__ pds,
+                                                                        const TB* __restrict__ band,
+                                                                        const float* __restrict__ u,
+                                                                        const float* __restrict__ f,
+                                                                        float* __restrict__ y, int tiles1) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* su = reinterpret_cast<float*>(smraw);
+  constexpr int W = 2 * P + 1, BXN = 2 * PBX;
+  const PatchDev pd = pds[blockIdx.z];
+  const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2], n2e = band_row_even(n2);
+  const int i0b = (blockIdx.y / tiles1) * PBZ, i1b = (blockIdx.y % tiles1) * PBY, i2b = blockIdx.x * BXN;
+  if (i0b >= n0 || i1b >= n1 || i2b >= n2) return;
+  constexpr int H0 = PBZ + 2 * P, H1 = PBY + 2 * P, H2 = BXN + 2 * P;
+  const float* ut = u + pd.off;
+  const int tid = (threadIdx.z * PBY + threadIdx.y) * PBX + threadIdx.x;
+  for (int idx = tid; idx < H0 * H1 * H2; idx += PBX * PBY * PBZ) {
+    const int a = idx / (H1 * H2), rem = idx % (H1 * H2), b = rem / H2, c = rem % H2;
+    const int g0 = i0b - P + a, g1 = i1b - P + b, g2 = i2b - P + c;
+    su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1 && g2 >= 0 && g2 < n2) ? ut[(int64_t(g0) * n1 + g1) * n2 + g2]
+                                                                                : 0.0f;
+  }
+  __syncthreads();
+  const int i0 = i0b + threadIdx.z, i1 = i1b + threadIdx.y, i2 = i2b + 2 * threadIdx.x;
+  if (i0 >= n0 || i1 >= n1 || i2 >= n2) return;
+  const int64_t ne = int64_t(n0) * n1 * n2e, nodep = (int64_t(i0) * n1 + i1) * n2e + i2;
+  const TB* bp = band + pd.band_off + nodep;  // node pair: 2 x sizeof(TB) aligned (nodep, ne even)
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 1
+  for (int t0 = 0; t0 < W; ++t0) {
+#pragma unroll
+    for (int t1 = 0; t1 < W; ++t1) {
+      const float* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + 2 * threadIdx.x;
+      const TB* bq = bp + int64_t((t0 * W + t1) * W) * ne;
+#pragma unroll
+      for (int t2 = 0; t2 < W; ++t2) {
+        const float2 w = pair_val(bq + int64_t(t2) * ne);
+        acc0 = fma(w.x, srow[t2], acc0);
+        acc1 = fma(w.y, srow[t2 + 1], acc1);
+      }
+    }
+  }
+  const int64_t node = pd.off + (int64_t(i0) * n1 + i1) * n2 + i2;
+  y[node] = f ? f[node] - acc0 : acc0;
+  if (i2 + 1 < n2) y[node + 1] = f ? f[node + 1] - acc1 : acc1;
+}
+
+template <class TB>
+cudaError_t launch_band_apply_3d_pair(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int p,
+                                      const TB* band, const float* u, const float* f, float* y) {
+  const int t1 = (max_n[1] + PBY - 1) / PBY, t0 = (max_n[0] + PBZ - 1) / PBZ;
+  const dim3 grid((max_n[2] + 2 * PBX - 1) / (2 * PBX), t0 * t1, K), block(PBX, PBY, PBZ);
+  const size_t sm = sizeof(float) * (PBZ + 2 * p) * (PBY + 2 * p) * (2 * PBX + 2 * p);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, sm, s>>>(pd_dev, band, u, f, y, t1);
+    return cudaGetLastError();
+  };
+  switch (p) {
+    case 2: return go(k_band_apply_3d_pair<TB, 2>);
+    case 3: return go(k_band_apply_3d_pair<TB, 3>);
+    case 4: return go(k_band_apply_3d_pair<TB, 4>);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_band_apply_3d_pair<__nv_bfloat16>(cudaStream_t, const PatchDev*, int, const int*, int,
+                                                              const __nv_bfloat16*, const float*, const float*, float*);
+template cudaError_t launch_band_apply_3d_pair<float>(cudaStream_t, const PatchDev*, int, const int*, int, const float*,
+                                                      const float*, const float*, float*);
+
 template <class TV, class TB, int P>
 static cudaError_t launch_apply_3d_p(cudaStream_t s, dim3 grid, size_t sm, const PatchDev* pd_dev, const TB* band,
                                      const TV* u, const TV* f, TV* y, int t1) {

@@ -213,6 +213,22 @@ struct ModeDescT {
 };
 constexpr int kModeMaxN = 80;
 
+// FP32/BF16 bands of 3D patches in the paired layout: per patch (PatchDev.band_off in band
+// elements) the (2p+1)^3 tap planes of n0 x n1 x n2e nodes, n2e = n2 rounded up to even
+// (padding zero), so that every node pair (2x, 2x+1) of a row is one aligned 2-element load.
+__host__ __device__ inline int band_row_even(int n2) { return (n2 + 1) & ~1; }
+// Copies the FP64 bands (layout of `src_pd`) into the paired layout of `dst_pd` (TB = float
+// or __nv_bfloat16, rounded as the flat conversions round).
+template <class TB>
+cudaError_t launch_band_pair(cudaStream_t s, const PatchDev* src_pd, const PatchDev* dst_pd, int K, int taps,
+                             int64_t max_nodes, const double* src, TB* dst);
+// The 3D apply on paired bands (every patch of degree p = uniform_p in 2..4): each thread
+// computes two adjacent nodes of a row from one 2-element load per tap, FP32 accumulation
+// in the tap order of launch_band_apply_3d (bit-identical results).
+template <class TB>
+cudaError_t launch_band_apply_3d_pair(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int p,
+                                      const TB* band, const float* u, const float* f, float* y);
+
 // Interior fast diagonalisation of one small 3D patch interior (every length <= kFd3SmallN):
 // the box of the tile (tile_off, tile extents n, first index lo, lengths len) and the FD
 // operands U0, U1, U2 (len x len) and Dinv (len0 x len1 x len2).
