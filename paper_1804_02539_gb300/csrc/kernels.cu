@@ -62,10 +62,30 @@ template <class T> __device__ __forceinline__ float to_acc(T v);
 template <> __device__ __forceinline__ float to_acc<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_acc<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// Band coefficients are read once per apply.  The 2D apply loads FP32 and BF16 bands
+// without L1 allocation and with 256-byte L2 prefetch (its tap planes are read along long
+// rows); the 3D apply, whose row blocks span 32 nodes of short rows, keeps plain loads
+// (the prefetch measured slower there).  FP64 bands (FP64-pipe bound) use the read-only path.
+__device__ __forceinline__ float ld_band_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_band_stream(const __nv_bfloat16* p) {
+  unsigned short r;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.b16 %0, [%1];" : "=h"(r) : "l"(p));
+  return __bfloat162float(__ushort_as_bfloat16(r));
+}
+
 template <class TV, class TB>
 __device__ __forceinline__ TV band_val(const TB* p) {
   if constexpr (sizeof(TV) == sizeof(TB) && std::is_same<TV, TB>::value) return __ldg(p);
   else return TV(to_acc<TB>(*p));
+}
+template <class TV, class TB>
+__device__ __forceinline__ TV band_val_stream(const TB* p) {
+  if constexpr (std::is_same<TB, double>::value) return TV(__ldg(p));
+  else return TV(ld_band_stream(p));
 }
 
 // P > 0: every patch has degree P (taps unrolled; one partial sum per tap row, so a thread
@@ -105,7 +125,7 @@ __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __res
       part[t0] = TV(0);
 #pragma unroll
       for (int t1 = 0; t1 < W; ++t1)
-        part[t0] = fma(band_val<TV, TB>(bp + int64_t(t0 * W + t1) * nn), srow[t1], part[t0]);
+        part[t0] = fma(band_val_stream<TV, TB>(bp + int64_t(t0 * W + t1) * nn), srow[t1], part[t0]);
     }
 #pragma unroll
     for (int t0 = 0; t0 < W; ++t0) acc += part[t0];
@@ -114,7 +134,7 @@ __global__ void __launch_bounds__(AX * AY) k_band_apply_2d(const PatchDev* __res
     for (int t0 = 0; t0 <= 2 * p0; ++t0) {
       const TV* srow = su + (threadIdx.y + t0) * H1 + threadIdx.x;
       const TB* brow = bp + int64_t(t0 * w1) * nn;
-      for (int t1 = 0; t1 < w1; ++t1) acc = fma(band_val<TV, TB>(brow + int64_t(t1) * nn), srow[t1], acc);
+      for (int t1 = 0; t1 < w1; ++t1) acc = fma(band_val_stream<TV, TB>(brow + int64_t(t1) * nn), srow[t1], acc);
     }
   }
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
