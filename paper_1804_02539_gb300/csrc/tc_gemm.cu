@@ -362,16 +362,22 @@ __global__ void __launch_bounds__(kDigThreads) k_tc_digits(const TcDesc<TB, TC>*
 }
 
 // Digit pass of stacked descriptors: one CTA per 32-fibre panel of the stacked M (fibre
-// m = p F + j of patch p), one warp per 4 fibres as in k_tc_digits; the digit planes go to
-// the M-side layout [M tile][K block][S][128 x 32] and the exponents to Xtau[m].  A panel
+// m = p F + j of patch p); 16 warps: warp w takes 4 fibres (w & 7) and the K blocks
+// kb = w >> 3, (w >> 3) + 2, ... (two warps per fibre group, so that twice as many warps
+// hide the latency of the integer digit arithmetic), a lane 4 consecutive k of each of its
+// blocks.  The fibre exponent is the maximum over both halves (shared memory); digit planes
+// go to the M-side layout [M tile][K block][S][128 x 32], exponents to Xtau[m].  A panel
 // never straddles an M tile (128 is a multiple of 32).
-__global__ void __launch_bounds__(kDigThreads) k_tc_digits_stack(const TcStack<double, double>* __restrict__ descs,
-                                                                  int batch, const int* __restrict__ pstart) {
-  constexpr int S = 7, ASZ = S * TBM * TBK, RB = kDigRegBlocks;
+constexpr int kDigStackThreads = 512, kDigStackRB = 5;  // K blocks a lane keeps in registers
+__global__ void __launch_bounds__(kDigStackThreads) k_tc_digits_stack(const TcStack<double, double>* __restrict__ descs,
+                                                                       int batch, const int* __restrict__ pstart) {
+  constexpr int S = 7, ASZ = S * TBM * TBK, RB = kDigStackRB;
+  __shared__ int s_emax[2][32];
   const int total = pstart[batch];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cl = 4 * warp + (lane >> 3);  // this lane's fibre within the panel
-  const int kq = lane & 7;                // K quad: k = 4 kq .. 4 kq + 3 of a block
+  const int cl = 4 * (warp & 7) + (lane >> 3);  // this lane's fibre within the panel
+  const int kg = warp >> 3;                      // K blocks kg, kg + 2, ...
+  const int kq = lane & 7;                       // K quad: k = 4 kq .. 4 kq + 3 of a block
   for (int pnl = blockIdx.x; pnl < total; pnl += gridDim.x) {
     const int q = tile_desc(pstart, batch, pnl);
     const TcStack<double, double>& d = descs[q];
@@ -382,37 +388,46 @@ __global__ void __launch_bounds__(kDigThreads) k_tc_digits_stack(const TcStack<d
     const double* X = valid ? d.X[p] : nullptr;
     __nv_bfloat16* out = d.Xdig + int64_t(gm / TBM) * nkb * ASZ;
     const int row = gm % TBM;
-    const int nch = (nkb + RB - 1) / RB;
+    const int mine = nkb > kg ? (nkb - kg + 1) / 2 : 0;  // K blocks of this warp
+    const bool keep = mine <= RB;                        // all of them fit in registers
     double v[RB][4];
-    auto load_chunk = [&](int ch) {
+    auto load_block = [&](int b, int kb) {
 #pragma unroll
-      for (int b = 0; b < RB; ++b)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int gk = (ch * RB + b) * TBK + 4 * kq + kk;
-          v[b][kk] = (valid && gk < K) ? ld_b(X, d.ldx, d.xt, gk, j) : 0.0;
-        }
+      for (int kk = 0; kk < 4; ++kk) {
+        const int gk = kb * TBK + 4 * kq + kk;
+        v[b][kk] = (valid && gk < K) ? ld_b(X, d.ldx, d.xt, gk, j) : 0.0;
+      }
     };
     int emax = 0;
-    for (int ch = 0; ch < nch; ++ch) {
-      load_chunk(ch);
+    for (int c0 = 0; c0 < mine; c0 += RB) {
 #pragma unroll
       for (int b = 0; b < RB; ++b)
+        if (c0 + b < mine) load_block(b, kg + 2 * (c0 + b));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          emax = max(emax, int((uint64_t(__double_as_longlong(v[b][kk])) >> 52) & 0x7FF));
+      for (int b = 0; b < RB; ++b)
+        if (c0 + b < mine)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            emax = max(emax, int((uint64_t(__double_as_longlong(v[b][kk])) >> 52) & 0x7FF));
     }
     emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
     emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 2));
     emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 4));
+    if (kq == 0) s_emax[kg][cl] = emax;
+    __syncthreads();
+    emax = max(s_emax[0][cl], s_emax[1][cl]);
     const int tau = emax ? emax - 1023 + 1 : -1022;
-    if (kq == 0 && valid) d.Xtau[gm] = tau;
-    for (int ch = 0; ch < nch; ++ch) {
-      if (nch > 1) load_chunk(ch);  // one chunk: still in registers from the exponent pass
+    if (kg == 0 && kq == 0 && valid) d.Xtau[gm] = tau;
+    for (int c0 = 0; c0 < mine; c0 += RB) {
+      if (!keep) {  // reload (K beyond the register blocks)
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+          if (c0 + b < mine) load_block(b, kg + 2 * (c0 + b));
+      }
 #pragma unroll
       for (int b = 0; b < RB; ++b) {
-        const int kb = ch * RB + b;
-        if (kb >= nkb) break;
+        if (c0 + b >= mine) break;
+        const int kb = kg + 2 * (c0 + b);
         __nv_bfloat16* blk = out + int64_t(kb) * ASZ;
         uint32_t a[7], c[7];
         digit_pairs7(v[b][0], v[b][1], tau, a);
@@ -422,6 +437,7 @@ __global__ void __launch_bounds__(kDigThreads) k_tc_digits_stack(const TcStack<d
           *reinterpret_cast<uint2*>(blk + core_off(sq * TBM + row, 4 * kq)) = make_uint2(a[sq], c[sq]);
       }
     }
+    __syncthreads();  // s_emax is reused by the next panel
   }
 }
 
@@ -786,7 +802,7 @@ cudaError_t launch_tc_digits_stack(cudaStream_t s, const TcStack<double, double>
                                    const int* panel_start, int64_t panels) {
   if (batch <= 0 || panels <= 0) return cudaSuccess;
   const int grid = int(std::min<int64_t>(panels, 4 * int64_t(sm_count())));
-  k_tc_digits_stack<<<grid, kDigThreads, 0, s>>>(d_desc, batch, panel_start);
+  k_tc_digits_stack<<<grid, kDigStackThreads, 0, s>>>(d_desc, batch, panel_start);
   return cudaGetLastError();
 }
 
