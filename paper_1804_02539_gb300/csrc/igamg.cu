@@ -159,6 +159,8 @@ struct Num {
   ModeSetT<T> md[6];                                // the same six products as mode products
   Fd3SmallT<T>* fd3 = nullptr;                      // small 3D interiors: the six in one launch
   int nfd3 = 0;
+  Iface3SmallT<T> i3s{};                            // small 3D interface pieces: one launch
+  bool i3_ok = false;
   T* cX = nullptr;                                  // compact 3D interior tensor
   T *G = nullptr, *Z = nullptr, *vscale = nullptr;  // interface nodes
   GemmSetT<T> edgeA, edgeB, face0, face1, face2, face3;
@@ -187,6 +189,9 @@ struct Level {
   bool small_ok = false;     // ... and every edge too: the whole smoother is one launch
   std::vector<FdRowsT<double>> fr_h;
   std::vector<EdgeSmallT<double>> es_h;
+  std::vector<FaceSmallT<double>> f3s_h;       // 3D small interface pieces, host copies
+  std::vector<EdgeSmallT<double>> e3s_h;
+  int64_t v3_beg = 0, v3_end = 0;
   std::vector<FdSmallT<double>> fs_h;
   Num<double> n64;
   Num<float> n32;
@@ -1396,6 +1401,8 @@ void build_levels(igamg_ctx* c) {
     bool face_tc = true;
     std::vector<EdgeSmallT<double>> es;
     bool edges_small = d == 2;
+    std::vector<FaceSmallT<double>> fsm;  // 3D: faces for the one-launch interface smoother
+    bool iface3_small = d == 3;
     int64_t vtx_beg = 0, vtx_end = 0;
     int64_t face_tot = 0;
     for (auto& kv : groups) {
@@ -1431,6 +1438,7 @@ void build_levels(igamg_ctx* c) {
         double* dU = reg_const(c, c->mem.upload(U, s), U.size());
         double* ddv = reg_const(c, c->mem.upload(dv, s), dv.size());
         edges_small = edges_small && len0 <= kFdSmallMax;
+        iface3_small = iface3_small && len0 <= kFd3SmallN;
         for (int j = 0; j < np; ++j) es.push_back(EdgeSmallT<double>{dU, ddv, gbase + int64_t(j) * len0, len0});
         eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len0, len0, len0, 0, np, len0, len0});
         eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len0, len0, len0, 0, np, len0, len0});
@@ -1454,8 +1462,10 @@ void build_levels(igamg_ctx* c) {
           a0 = slices(S0, 0);
           a1 = slices(S1, 0);
         }
+        iface3_small = iface3_small && std::max(len0, len1) <= kFd3SmallN;
         for (int f = 0; f < np; ++f) {
           int64_t off = gbase + int64_t(f) * len0 * len1, tb = face_tot + int64_t(f) * len0 * len1;
+          fsm.push_back(FaceSmallT<double>{S0->dU, S1->dU, Dinv, off, len0, len1});
           q0.push_back(GemmDesc{S0->dU, (double*)(intptr_t)off, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
           q1.push_back(GemmDesc{(double*)(intptr_t)tb, S1->dU, (double*)(intptr_t)tb, Dinv, len1, len1, len1, len1, len0, len1, len1});
           q2.push_back(GemmDesc{S0->dU, (double*)(intptr_t)tb, (double*)(intptr_t)tb, nullptr, len0, len1, len1, 0, len0, len1, len0});
@@ -1480,6 +1490,24 @@ void build_levels(igamg_ctx* c) {
     L.if_ptr = c->mem.upload(ptr, s);
     L.if_idx = c->mem.upload(idx, s);
     L.n64.vscale = reg_const(c, c->mem.upload(vsc, s), vsc.size());
+    if (iface3_small && L.n_if > 0) {  // every face and edge small: the one-launch interface smoother
+      L.f3s_h = fsm;
+      L.e3s_h = es;
+      L.v3_beg = vtx_beg;
+      L.v3_end = vtx_end;
+      Iface3SmallT<double>& q = L.n64.i3s;
+      q.faces = fsm.empty() ? nullptr : c->mem.upload(fsm, s);
+      q.nfaces = int(fsm.size());
+      q.edges = es.empty() ? nullptr : c->mem.upload(es, s);
+      q.nedges = int(es.size());
+      q.ptr = L.if_ptr;
+      q.idx = L.if_idx;
+      q.vscale = L.n64.vscale;
+      q.vbeg = vtx_beg;
+      q.vend = vtx_end;
+      q.u = L.n64.U;
+      L.n64.i3_ok = true;
+    }
     L.n64.G = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
     L.n64.Z = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
     double* Yif = reg_work(c, c->mem.alloc<double>(L.n_if), L.n_if);
@@ -1817,6 +1845,13 @@ struct OnStream {
 // gather of the copies before and the scatter after (Sigma of Eq. ops6).
 template <class T>
 void smooth_interface(igamg_ctx* c, Level& L, Num<T>& N, const T* v, double tau, bool add) {
+  if (N.i3_ok) {  // small 3D level: gather, face and edge FD, vertices and scatter in one launch
+    ProfScope ps(c, CLS_IFACE, N.face0.flops + N.face1.flops + N.face2.flops + N.face3.flops + N.edgeA.flops +
+                                   N.edgeB.flops + 2.0 * L.n_if,
+                 4.0 * sizeof(T) * L.n_if);
+    CK(launch_iface3_small<T>(c->stream, N.i3s, v, T(tau), add ? 1 : 0));
+    return;
+  }
   {
     ProfScope ps(c, CLS_IFACE, 0.0, 2.0 * sizeof(T) * L.n_if);
     CK(launch_iface_gather<T>(c->stream, L.n_if, L.if_ptr, L.if_idx, v, N.G));
@@ -2579,6 +2614,24 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       B.nfd3 = int(f3.size());
     }
     for (int j = 0; j < 4; ++j) tr_mode(A.fm[j], B.fm[j]);
+    if (A.i3_ok) {
+      std::vector<FaceSmallT<float>> f3;
+      for (const auto& f : L.f3s_h) f3.push_back(FaceSmallT<float>{tr(f.U0), tr(f.U1), tr(f.Dinv), f.first, f.len0, f.len1});
+      std::vector<EdgeSmallT<float>> e3;
+      for (const auto& e : L.e3s_h) e3.push_back(EdgeSmallT<float>{tr(e.U), tr(e.dinv), e.first, e.len});
+      Iface3SmallT<float>& q = B.i3s;
+      q.faces = f3.empty() ? nullptr : c->mem.upload(f3, s);
+      q.nfaces = int(f3.size());
+      q.edges = e3.empty() ? nullptr : c->mem.upload(e3, s);
+      q.nedges = int(e3.size());
+      q.ptr = L.if_ptr;
+      q.idx = L.if_idx;
+      q.vscale = tr(A.vscale);
+      q.vbeg = L.v3_beg;
+      q.vend = L.v3_end;
+      q.u = tr(A.U);
+      B.i3_ok = true;
+    }
     tr_set(A.edgeA, B.edgeA); tr_set(A.edgeB, B.edgeB);
     tr_set(A.face0, B.face0); tr_set(A.face1, B.face1); tr_set(A.face2, B.face2); tr_set(A.face3, B.face3);
     if (!L.r2_h.empty()) {

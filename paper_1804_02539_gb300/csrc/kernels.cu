@@ -1972,6 +1972,94 @@ template cudaError_t launch_fd3_small<double>(cudaStream_t, const Fd3SmallT<doub
 template cudaError_t launch_fd3_small<float>(cudaStream_t, const Fd3SmallT<float>*, int, const float*, float*, float,
                                              int);
 
+// ---------------------------------------------------------------- small 3D interface pieces in one launch
+
+template <class T>
+__global__ void __launch_bounds__(256) k_iface3_small(const Iface3SmallT<T> p, const T* __restrict__ v, T tau,
+                                                      int add) {
+  constexpr int M = kFd3SmallN;
+  __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
+  const int tid = threadIdx.x, b = blockIdx.x;
+  auto scatter = [&](int64_t g, T val) {
+    for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) {
+      T* up = p.u + p.idx[c];
+      *up = add ? *up + val : val;
+    }
+  };
+  auto gather = [&](int64_t g) {
+    T acc = 0;
+    for (int64_t c = p.ptr[g]; c < p.ptr[g + 1]; ++c) acc += v[p.idx[c]];
+    return acc;
+  };
+  if (b < p.nfaces) {
+    const FaceSmallT<T> f = p.faces[b];
+    const int n0 = f.len0, n1 = f.len1, nn = n0 * n1;
+    for (int i = tid; i < n0 * n0; i += 256) U0[i] = f.U0[i];
+    for (int i = tid; i < n1 * n1; i += 256) U1[i] = f.U1[i];
+    for (int i = tid; i < nn; i += 256) X[i] = gather(f.first + i);
+    __syncthreads();
+    for (int i = tid; i < nn; i += 256) {  // T = U0^T G
+      const int a = i / n1, c = i % n1;
+      T acc = 0;
+      for (int k = 0; k < n0; ++k) acc = fma(U0[k * n0 + a], X[k * n1 + c], acc);
+      Tm[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < nn; i += 256) {  // Y = (T U1) .* Dinv
+      const int r = i / n1, j = i % n1;
+      T acc = 0;
+      for (int k = 0; k < n1; ++k) acc = fma(U1[k * n1 + j], Tm[r * n1 + k], acc);
+      X[i] = acc * f.Dinv[i];
+    }
+    __syncthreads();
+    for (int i = tid; i < nn; i += 256) {  // S = U0 Y
+      const int a = i / n1, c = i % n1;
+      T acc = 0;
+      for (int k = 0; k < n0; ++k) acc = fma(U0[a * n0 + k], X[k * n1 + c], acc);
+      Tm[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < nn; i += 256) {  // Z = S U1^T, scattered
+      const int r = i / n1, j = i % n1;
+      T acc = 0;
+      for (int k = 0; k < n1; ++k) acc = fma(U1[j * n1 + k], Tm[r * n1 + k], acc);
+      scatter(f.first + i, tau * acc);
+    }
+    return;
+  }
+  if (b < p.nfaces + p.nedges) {
+    const EdgeSmallT<T> e = p.edges[b - p.nfaces];
+    const int n = e.len;
+    for (int i = tid; i < n * n; i += 256) U0[i] = e.U[i];
+    for (int i = tid; i < n; i += 256) X[i] = gather(e.first + i);
+    __syncthreads();
+    for (int j = tid; j < n; j += 256) {  // y = (g^T U) .* dinv
+      T acc = 0;
+      for (int i = 0; i < n; ++i) acc = fma(X[i], U0[i * n + j], acc);
+      Tm[j] = acc * e.dinv[j];
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += 256) {  // z = U y, scattered
+      T acc = 0;
+      for (int j = 0; j < n; ++j) acc = fma(Tm[j], U0[i * n + j], acc);
+      scatter(e.first + i, tau * acc);
+    }
+    return;
+  }
+  for (int64_t g = p.vbeg + tid; g < p.vend; g += 256) scatter(g, tau * (p.vscale[g] * gather(g)));
+}
+
+template <class T>
+cudaError_t launch_iface3_small(cudaStream_t s, const Iface3SmallT<T>& p, const T* v, T tau, int add) {
+  const int blocks = p.nfaces + p.nedges + (p.vend > p.vbeg ? 1 : 0);
+  if (blocks <= 0) return cudaSuccess;
+  k_iface3_small<T><<<blocks, 256, 0, s>>>(p, v, tau, add);
+  return cudaGetLastError();
+}
+template cudaError_t launch_iface3_small<double>(cudaStream_t, const Iface3SmallT<double>&, const double*, double,
+                                                 int);
+template cudaError_t launch_iface3_small<float>(cudaStream_t, const Iface3SmallT<float>&, const float*, float, int);
+
 // ---------------------------------------------------------------- interior box gather/scatter
 
 // Compact copy of every patch-interior box (3D FD works on compact tensors) and the

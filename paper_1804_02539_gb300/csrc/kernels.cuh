@@ -239,6 +239,31 @@ struct Fd3SmallT {
   int n[3], lo[3], len[3];
 };
 constexpr int kFd3SmallN = 16;
+
+// The interface pieces of a small 3D level in one launch (faces and edges of length <=
+// kFd3SmallN): block per face (gather of the sum of its nodes' copies, the face's 2D fast
+// diagonalisation Z = U0 ((U0^T G U1) .* Dinv) U1^T, tau-scatter to every copy), block per
+// edge (1D: z = U ((g^T U) .* dinv)), and one block for the vertices (z = vscale g); the FMA
+// order of the gather, face/edge and scatter launches it replaces.
+template <class T>
+struct FaceSmallT {
+  const T *U0, *U1, *Dinv;
+  int64_t first;  // first interface node of the face (row-major len0 x len1)
+  int len0, len1;
+};
+template <class T>
+struct Iface3SmallT {
+  const FaceSmallT<T>* faces;
+  int nfaces;
+  const EdgeSmallT<T>* edges;
+  int nedges;
+  const int64_t *ptr, *idx;  // interface node -> its copies in the level vectors
+  const T* vscale;
+  int64_t vbeg, vend;        // vertex nodes
+  T* u;
+};
+template <class T>
+cudaError_t launch_iface3_small(cudaStream_t s, const Iface3SmallT<T>& p, const T* v, T tau, int add);
 // u = (add ? u + tau z : tau z) on every interior box, z = L^{-1} v restricted to the box:
 // one block per interior, the six mode products (transposed bases, Dinv, bases) in shared
 // memory with the FMA order of launch_mode_product, so the result equals the box copy +
