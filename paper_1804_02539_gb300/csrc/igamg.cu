@@ -1438,7 +1438,7 @@ void build_levels(igamg_ctx* c) {
         double* dU = reg_const(c, c->mem.upload(U, s), U.size());
         double* ddv = reg_const(c, c->mem.upload(dv, s), dv.size());
         edges_small = edges_small && len0 <= kFdSmallMax;
-        iface3_small = iface3_small && len0 <= kFd3SmallN;
+        iface3_small = iface3_small && len0 <= kIface3SmallN;
         for (int j = 0; j < np; ++j) es.push_back(EdgeSmallT<double>{dU, ddv, gbase + int64_t(j) * len0, len0});
         eA.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, ddv, len0, len0, len0, 0, np, len0, len0});
         eB.push_back(GemmDesc{(double*)(intptr_t)gbase, dU, (double*)(intptr_t)gbase, nullptr, len0, len0, len0, 0, np, len0, len0});
@@ -1462,7 +1462,7 @@ void build_levels(igamg_ctx* c) {
           a0 = slices(S0, 0);
           a1 = slices(S1, 0);
         }
-        iface3_small = iface3_small && std::max(len0, len1) <= kFd3SmallN;
+        iface3_small = iface3_small && std::max(len0, len1) <= kIface3SmallN;
         for (int f = 0; f < np; ++f) {
           int64_t off = gbase + int64_t(f) * len0 * len1, tb = face_tot + int64_t(f) * len0 * len1;
           fsm.push_back(FaceSmallT<double>{S0->dU, S1->dU, Dinv, off, len0, len1});

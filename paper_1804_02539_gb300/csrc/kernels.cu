@@ -1977,7 +1977,7 @@ template cudaError_t launch_fd3_small<float>(cudaStream_t, const Fd3SmallT<float
 template <class T>
 __global__ void __launch_bounds__(256) k_iface3_small(const Iface3SmallT<T> p, const T* __restrict__ v, T tau,
                                                       int add) {
-  constexpr int M = kFd3SmallN;
+  constexpr int M = kIface3SmallN;
   __shared__ T U0[M * M], U1[M * M], X[M * M], Tm[M * M];
   const int tid = threadIdx.x, b = blockIdx.x;
   auto scatter = [&](int64_t g, T val) {

@@ -241,10 +241,12 @@ struct Fd3SmallT {
 constexpr int kFd3SmallN = 16;
 
 // The interface pieces of a small 3D level in one launch (faces and edges of length <=
-// kFd3SmallN): block per face (gather of the sum of its nodes' copies, the face's 2D fast
+// kIface3SmallN; a face costs one block 4 n^3 FMAs, less than the eight launches it replaces
+// at these sizes): block per face (gather of the sum of its nodes' copies, the face's 2D fast
 // diagonalisation Z = U0 ((U0^T G U1) .* Dinv) U1^T, tau-scatter to every copy), block per
 // edge (1D: z = U ((g^T U) .* dinv)), and one block for the vertices (z = vscale g); the FMA
 // order of the gather, face/edge and scatter launches it replaces.
+constexpr int kIface3SmallN = 24;
 template <class T>
 struct FaceSmallT {
   const T *U0, *U1, *Dinv;
