@@ -137,6 +137,7 @@ struct Num {
   bool bf16 = false;
   const T* band_op = nullptr;  // band coefficients of the Krylov operator (always type T)
   PatchDev* pd_pair = nullptr; // 3D BF16 cycle bands in the paired layout: patch offsets into it
+  PatchDev* pd_blk = nullptr;  // 3D FP32 bands in the tap-blocked layout: patch offsets into it
   KronDevT<T>* kd = nullptr;   // rectangle patches: Kronecker-sum operator per patch
   T *F = nullptr, *U = nullptr, *R = nullptr;
   GemmSetT<T> st0F, st0R, st1, st2, st3;            // 2D interiors
@@ -1826,6 +1827,12 @@ void residual(igamg_ctx* c, int l, const T* f, const T* u, T* r, bool krylov = f
     return;
   }
   const T* band = krylov ? N.band_op : static_cast<const T*>(N.band);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->pd.dim == 3 && N.pd_blk) {  // FP32 bands in the tap-blocked layout
+      CK(launch_band_apply_3d_blk(c->stream, N.pd_blk, c->pd.K, L.max_n, L.uniform_p, band, u, f, r));
+      return;
+    }
+  }
   if (c->pd.dim == 2)
     CK((launch_band_apply_2d<T, T>(c->stream, L.pd, c->pd.K, L.max_n[0], L.max_n[1], L.max_p, band, u, f, r,
                                    L.uniform_p)));
@@ -2515,8 +2522,24 @@ void build_low(igamg_ctx* c, bool bf16_bands) {
       B.pd_pair = c->mem.upload(pp, s);
     }
     if (!L.kron && (!bf16_bands || finest)) {  // FP32 bands: the cycle's (FP32 mode) and the Krylov operator's
-      b32 = c->mem.alloc<float>(nb);
-      CK(launch_convert_f64_f32(s, nb, L.band, 1.0, b32));
+      if (c->pd.dim == 3 && L.uniform_p >= 2 && L.uniform_p <= 4) {
+        // tap-blocked layout: all taps of 32 consecutive nodes contiguous
+        const int tp = (2 * L.uniform_p + 1) * (2 * L.uniform_p + 1) * (2 * L.uniform_p + 1);
+        std::vector<PatchDev> pb = L.pd_h;
+        int64_t tot = 0, maxn = 0;
+        for (auto& q : pb) {
+          const int64_t nn = int64_t(q.n[0]) * q.n[1] * q.n[2];
+          q.band_off = tot;
+          tot += (nn + 31) / 32 * 32 * tp;
+          maxn = std::max(maxn, nn);
+        }
+        b32 = c->mem.alloc<float>(size_t(std::max<int64_t>(tot, 1)));
+        B.pd_blk = c->mem.upload(pb, s);
+        CK(launch_band_blk_f32(s, L.pd, B.pd_blk, int(pb.size()), tp, maxn, L.band, b32));
+      } else {
+        b32 = c->mem.alloc<float>(nb);
+        CK(launch_convert_f64_f32(s, nb, L.band, 1.0, b32));
+      }
       B.band_op = b32;
     }
     if (bf16_bands && !L.kron && pair) {

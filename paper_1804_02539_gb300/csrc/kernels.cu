@@ -1468,6 +1468,87 @@ __global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d(const PatchDe
   y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
 }
 
+// ---------------------------------------------------------------- tap-blocked FP32 3D apply
+
+__global__ void k_band_blk_f32(const PatchDev* __restrict__ spd, const PatchDev* __restrict__ dpd, int taps,
+                               const double* __restrict__ src, float* __restrict__ dst) {
+  const PatchDev a = spd[blockIdx.z], b = dpd[blockIdx.z];
+  const int t = blockIdx.y;
+  if (t >= taps) return;
+  const int64_t nn = int64_t(a.n[0]) * a.n[1] * a.n[2], nr = (nn + 31) / 32 * 32;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nr; i += int64_t(gridDim.x) * blockDim.x)
+    dst[b.band_off + ((i >> 5) * taps + t) * 32 + (i & 31)] = i < nn ? float(double(src[a.band_off + t * nn + i]) * 1.0)
+                                                                     : 0.0f;
+}
+
+cudaError_t launch_band_blk_f32(cudaStream_t s, const PatchDev* src_pd, const PatchDev* dst_pd, int K, int taps,
+                                int64_t max_nodes, const double* src, float* dst) {
+  if (K <= 0 || taps <= 0 || max_nodes <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((max_nodes + 31 + 255) / 256, 1024);
+  k_band_blk_f32<<<dim3(unsigned(g), unsigned(taps), unsigned(K)), 256, 0, s>>>(src_pd, dst_pd, taps, src, dst);
+  return cudaGetLastError();
+}
+
+template <int P>
+__global__ void __launch_bounds__(BX3 * BY3 * BZ3) k_band_apply_3d_blk(const PatchDev* __restrict__ pds,
+                                                                       const float* __restrict__ band,
+                                                                       const float* __restrict__ u,
+                                                                       const float* __restrict__ f,
+                                                                       float* __restrict__ y, int tiles1) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* su = reinterpret_cast<float*>(smraw);
+  constexpr int W = 2 * P + 1, TAPS = W * W * W;
+  const PatchDev pd = pds[blockIdx.z];
+  const int n0 = pd.n[0], n1 = pd.n[1], n2 = pd.n[2];
+  const int i0b = (blockIdx.y / tiles1) * BZ3, i1b = (blockIdx.y % tiles1) * BY3, i2b = blockIdx.x * BX3;
+  if (i0b >= n0 || i1b >= n1 || i2b >= n2) return;
+  constexpr int H0 = BZ3 + 2 * P, H1 = BY3 + 2 * P, H2 = BX3 + 2 * P;
+  const float* ut = u + pd.off;
+  const int tid = (threadIdx.z * BY3 + threadIdx.y) * BX3 + threadIdx.x;
+  for (int idx = tid; idx < H0 * H1 * H2; idx += BX3 * BY3 * BZ3) {
+    const int a = idx / (H1 * H2), rem = idx % (H1 * H2), b = rem / H2, c = rem % H2;
+    const int g0 = i0b - P + a, g1 = i1b - P + b, g2 = i2b - P + c;
+    su[idx] = (g0 >= 0 && g0 < n0 && g1 >= 0 && g1 < n1 && g2 >= 0 && g2 < n2) ? ut[(int64_t(g0) * n1 + g1) * n2 + g2]
+                                                                                : 0.0f;
+  }
+  __syncthreads();
+  const int i0 = i0b + threadIdx.z, i1 = i1b + threadIdx.y, i2 = i2b + threadIdx.x;
+  if (i0 >= n0 || i1 >= n1 || i2 >= n2) return;
+  const int64_t node = (int64_t(i0) * n1 + i1) * n2 + i2;
+  const float* bp = band + pd.band_off + (node >> 5) * (int64_t(TAPS) * 32) + (node & 31);
+  float acc = 0.f;
+#pragma unroll 1
+  for (int t0 = 0; t0 < W; ++t0) {
+#pragma unroll
+    for (int t1 = 0; t1 < W; ++t1) {
+      const float* srow = su + ((threadIdx.z + t0) * H1 + threadIdx.y + t1) * H2 + threadIdx.x;
+      const float* bq = bp + (t0 * W + t1) * W * 32;
+#pragma unroll
+      for (int t2 = 0; t2 < W; ++t2) acc = fma(__ldg(bq + t2 * 32), srow[t2], acc);
+    }
+  }
+  y[pd.off + node] = f ? f[pd.off + node] - acc : acc;
+}
+
+cudaError_t launch_band_apply_3d_blk(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int p,
+                                     const float* band, const float* u, const float* f, float* y) {
+  const int t1 = (max_n[1] + BY3 - 1) / BY3, t0 = (max_n[0] + BZ3 - 1) / BZ3;
+  const dim3 grid((max_n[2] + BX3 - 1) / BX3, t0 * t1, K), block(BX3, BY3, BZ3);
+  const size_t sm = sizeof(float) * (BZ3 + 2 * p) * (BY3 + 2 * p) * (BX3 + 2 * p);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, sm, s>>>(pd_dev, band, u, f, y, t1);
+    return cudaGetLastError();
+  };
+  switch (p) {
+    case 2: return go(k_band_apply_3d_blk<2>);
+    case 3: return go(k_band_apply_3d_blk<3>);
+    case 4: return go(k_band_apply_3d_blk<4>);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // ---------------------------------------------------------------- paired BF16 3D apply
 
 template <class TB>

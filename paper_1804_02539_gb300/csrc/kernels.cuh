@@ -222,6 +222,16 @@ __host__ __device__ inline int band_row_even(int n2) { return (n2 + 1) & ~1; }
 template <class TB>
 cudaError_t launch_band_pair(cudaStream_t s, const PatchDev* src_pd, const PatchDev* dst_pd, int K, int taps,
                              int64_t max_nodes, const double* src, TB* dst);
+// FP32 bands of 3D patches in the tap-blocked layout: per patch (PatchDev.band_off in floats)
+// blocks of 32 consecutive nodes (flat order), each holding its (2p+1)^3 taps x 32 nodes, so
+// that a warp's loads of all taps of a row segment stream through contiguous memory:
+// element (t, node) at band_off + ((node / 32) taps + t) 32 + node % 32 (padding zero).
+cudaError_t launch_band_blk_f32(cudaStream_t s, const PatchDev* src_pd, const PatchDev* dst_pd, int K, int taps,
+                                int64_t max_nodes, const double* src, float* dst);
+// The 3D apply on tap-blocked FP32 bands (uniform degree 2..4), same tap order and FMA chain
+// as launch_band_apply_3d (bit-identical results).
+cudaError_t launch_band_apply_3d_blk(cudaStream_t s, const PatchDev* pd_dev, int K, const int* max_n, int p,
+                                     const float* band, const float* u, const float* f, float* y);
 // The 3D apply on paired bands (every patch of degree p = uniform_p in 2..4): each thread
 // computes two adjacent nodes of a row from one 2-element load per tap, FP32 accumulation
 // in the tap order of launch_band_apply_3d (bit-identical results).
