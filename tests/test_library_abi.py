@@ -51,6 +51,20 @@ def test_setup_rejects_bad_problems_without_gpu(built_lib):
     assert lib.igamg_free(None) == 0
 
 
+def test_multi_and_server_reject_bad_arguments_without_gpu(built_lib):
+    """igamg_solve_multi without a context and a server without workers are refused
+    before any device work."""
+    from paper_1804_02539_gb300 import igamg
+    lib = igamg.load_library()
+    b = (ctypes.c_void_p * 2)()
+    x = (ctypes.c_void_p * 2)()
+    assert lib.igamg_solve_multi(None, 2, b, x, 1e-8, None, None) == 1
+    srv = ctypes.c_void_p()
+    assert lib.igamg_server_create(None, 0, 1 << 30, ctypes.byref(srv)) == 1
+    assert srv.value is None and b"workers" in lib.igamg_last_error(None)
+    assert lib.igamg_server_free(None) == 0
+
+
 STRUCTS = ("igamg_problem", "igamg_options", "igamg_result", "igamg_request_info", "igamg_server_counters")
 
 
