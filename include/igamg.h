@@ -185,7 +185,8 @@ igamg_status igamg_solve(igamg_ctx* ctx, const double* rhs_dev, double* x_dev, d
  * context's device bytes).  This path runs the FP64 numerics whatever the precision option
  * (each answer meets the same tolerance); with a forced FD engine (fd_engine 1..4) and FP64
  * each answer is bit-identical to igamg_solve of that right-hand side alone.  Otherwise the
- * right-hand sides are solved one after the other by igamg_solve.  `res` and `status` (may
+ * right-hand sides are solved one after the other by igamg_solve (also when the lockstep
+ * engine cannot be built, e.g. without device memory for the copies).  `res` and `status` (may
  * be NULL) receive nrhs entries.  Returns the worst status (IGAMG_ERR_NOT_CONVERGED only if
  * nothing worse); IGAMG_ERR_ARG for nrhs < 1, null arrays or vectors, tol < 0.
  * Synchronises the stream. */

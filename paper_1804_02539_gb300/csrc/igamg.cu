@@ -3930,12 +3930,15 @@ igamg_status igamg_solve_multi(igamg_ctx* c, int nrhs, const double* const* b, d
       return IGAMG_ERR_ARG;
     }
   igamg::Lockstep* k = nullptr;
-  if (nrhs > 1) {
-    igamg_status st = guarded(c, [&]() {
-      k = igamg::multi_engine(c, nrhs);
-      return IGAMG_OK;
-    });
-    if (st != IGAMG_OK) return st;
+  if (nrhs > 1) {  // an engine that cannot be built (e.g. no memory for the copies): one at a time
+    if (guarded(c, [&]() {
+          k = igamg::multi_engine(c, nrhs);
+          return IGAMG_OK;
+        }) != IGAMG_OK) {
+      k = nullptr;
+      c->multi[nrhs] = nullptr;  // not retried for this count
+      cudaGetLastError();        // a failed allocation leaves no error for the next launch check
+    }
   }
   if (!k) {  // one at a time
     igamg_status worst = IGAMG_OK;

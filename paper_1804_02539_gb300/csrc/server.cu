@@ -182,6 +182,10 @@ void run_group(Worker& w, Model& m, const std::vector<Request*>& rs) {
   const int64_t n = m.ndofs;
   const int g = int(rs.size());
   ensure_staging(w, n * g);
+  if (g > 1 && w.cap < n * g) {  // no staging for the whole group: one request at a time
+    for (Request* r : rs) run_group(w, m, std::vector<Request*>{r});
+    return;
+  }
   std::vector<igamg_result> res(static_cast<size_t>(g), igamg_result{});
   std::vector<igamg_status> sts(static_cast<size_t>(g), IGAMG_ERR_OOM);
   if (w.cap >= n * g) {
